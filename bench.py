@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Benchmark of the multi-pocket docking hot path on GB300 (one process per GPU).
+
+One step = the whole path over the multi-pocket workload: a 5,000-atom synthetic receptor with
+10 carved pockets (radius 6-10 A, 24 A boxes at 0.375 A spacing), one 30-atom ligand with 6
+torsions, 1,000 chains x 2,000 MC steps per pocket, top-9 poses per pocket merged and ranked:
+receptor typing + binning + grid maps, batched MC/RILC-BFGS search, selection and merge.
+value = docked ligand-pocket pairs per second (all ranks). Extra figures: score+gradient
+evaluations per second, the plain one-launch-per-pocket path on a sample, the score
+microbenchmark (65,536 poses), the search kernel's roofline, and the FP64 CPU oracle.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) each rank docks its own receptor (seed = rank): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import pvsynth as S  # noqa: E402
+
+METRIC = "docked ligand-pocket pairs/sec and score+grad evals/sec at 1 GB300, batched vs plain"
+UNIT = "pairs/s"
+WORKLOAD = ("multi-pocket: 5,000-atom receptor, 10 pockets (r 6-10 A, 24 A boxes, 0.375 A), "
+            "1 ligand 30 atoms / 6 torsions, 1,000 chains x 2,000 MC steps per pocket, top-9 merged")
+CHAINS, STEPS, TOP_K = 1000, 2000, 9
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ------------------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------- workload --
+def workload(seed: int):
+    w = S.multipocket(seed=seed, chains=CHAINS, steps=STEPS)
+    return w.receptors[0], w.boxes[0], w.ligands[0]
+
+
+def kernel_source_hash() -> str:
+    d = os.path.join(ROOT, "paper_2506_20043_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic():
+    """Per-evaluation DRAM traffic of the search kernel from the committed ncu summary, if that
+    summary was taken on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "search_round_kernel_multipocket.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    import re
+    m_hash = re.search(r"kernel source hash:\s*`?([0-9a-f]{16})", txt)
+    m_tr = re.search(r"dram bytes per evaluation:\s*([0-9.eE+]+)", txt)
+    if not (m_hash and m_tr) or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_tr.group(1))
+
+
+# ------------------------------------------------------------------------------ our arm --
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    rank, world, local = _env_rank()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    import paper_2506_20043_gb300 as pv
+    pv.build()
+    from paper_2506_20043_gb300 import api
+
+    ctx = api.Context(local)
+    stream = ctx.stream
+    rec, boxes, lig_src = workload(seed=rank)
+    lig = ctx.ligand(lig_src)
+    types = sorted(set(lig.xs_types.tolist()))
+    dev_rec = S.Receptor(torch.tensor(rec.xyz, dtype=torch.float32, device="cuda"),
+                         torch.tensor(rec.element, device="cuda"), torch.tensor(rec.donor, device="cuda"),
+                         torch.tensor(rec.acceptor, device="cuda"))
+    pockets = list(range(len(boxes)))
+    params = api.DockParams(chains=CHAINS, steps=STEPS, seed=rank, top_k=TOP_K, host_copy=False)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        gs = ctx.build_grids(dev_rec, boxes, types)
+        r = ctx.dock(gs, [lig], pockets, params)
+        return gs, r
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    times, search_s, evals, launches = [], 0.0, 0, 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()                                  # L2 flushed between timed steps
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            gs, r = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) * 1e-3)
+            ev, _, st = r.stats()
+            assert (st == 0).all(), st
+            s_s, n_l, _ = r.timing()
+            search_s += s_s
+            launches += n_l
+            evals += ev
+    step_t = np.array(times)
+    if world > 1:
+        t = torch.tensor(step_t, device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_t = t.cpu().numpy()
+    n_pairs = len(pockets)
+    total_t = float(step_t.sum())
+    value = n_pairs * world * args.steps / total_t
+    clocks = clk.summary()
+
+    out = None
+    if rank == 0:
+        flops, gbytes = lig.cost()
+        n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+        max_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+        peak_tflops = n_sm * 128 * 2 * max_mhz * 1e6 / 1e12
+        achieved = evals * flops / search_s / 1e12
+        per_eval_traffic = stored_traffic()
+        evals_per_launch = evals / max(launches, 1)
+        n_rounds = launches // max(args.steps, 1)
+        out = {
+            "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(total_t / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pairs_per_step_per_gpu": n_pairs, "chains": CHAINS,
+                       "mc_steps": STEPS, "top_k": TOP_K, "ligand_atoms": lig.n_atoms, "ligand_torsions": lig.n_rot,
+                       "intra_pairs": lig.n_pairs, "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                       "inputs": "receptor, ligand and boxes resident in HBM; grids rebuilt every step",
+                       "parallelism": f"{world} independent receptors, one per GPU"},
+            "evals_per_s": round(evals / total_t * world, 1),
+            "evals_per_step_per_gpu": evals // max(args.steps, 1),
+            "roofline": {"kernel": "search_round_kernel", "bound": "alu", "achieved": round(achieved, 3),
+                         "peak": round(peak_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
+                         "traffic": (round(per_eval_traffic * evals_per_launch) if per_eval_traffic else None),
+                         "peak_source": f"FP32 FMA peak = {n_sm} SMs x 128 lanes x 2 x {max_mhz:.0f} MHz",
+                         "flops_per_eval": flops, "launch_ms": round(search_s / max(launches, 1) * 1e3, 3),
+                         "l2_gather_gbs": round(evals * gbytes / search_s / 1e9, 1)},
+            "gpu_launches": args.steps * (6 + 1 + n_rounds + 2),
+            "clocks": clocks,
+        }
+        if not args.no_plain:
+            out["plain"] = run_plain_sample(ctx, api, gs, lig, pockets)
+            out["batched_vs_plain"] = round(value / world / out["plain"]["value"], 2)
+        if not args.no_micro:
+            out["score_microbench"] = run_score_microbench(ctx, api, torch)
+        out["e2e"] = run_e2e(ctx, api, torch, rec, boxes, lig_src, types, pockets, args.steps, rank)
+        if world == 1 and not args.no_cpu:
+            out["cpu_baseline"] = run_cpu_baseline(rec, boxes, lig_src, budget_s=args.cpu_budget)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def run_plain_sample(ctx, api, gs, lig, pockets, sample_steps=20):
+    """The paper's organisation (one launch per pair, one thread per chain, host loop) on one
+    pocket for `sample_steps` MC steps; pairs/s extrapolated linearly in MC steps."""
+    r = ctx.dock(gs, [lig], [pockets[0]], chains=CHAINS, steps=sample_steps, seed=0, mode="plain", host_copy=False)
+    ev, _, _ = r.stats()
+    s_s, _, total = r.timing()
+    per_pair = total * STEPS / sample_steps
+    rb = ctx.dock(gs, [lig], [pockets[0]], chains=CHAINS, steps=sample_steps, seed=0, host_copy=False)
+    evb, _, _ = rb.stats()
+    _, _, tb = rb.timing()
+    return {"value": round(1.0 / per_pair, 5), "unit": UNIT, "evals_per_s": round(ev / s_s, 1),
+            "sample": f"1 pocket x {CHAINS} chains x {sample_steps} MC steps, time x {STEPS // sample_steps}",
+            "batched_same_sample_evals_per_s": round(evb / tb, 1)}
+
+
+def run_score_microbench(ctx, api, torch, reps=20):
+    """Score + adjoint gradient over 65,536 random poses of a 32-atom / 8-torsion ligand in a 24 A
+    box of a 4,000-atom receptor (L2-resident maps: the gather is L2-bound by design)."""
+    rec, box, lig_src, poses = S.score_microbench()
+    lig = ctx.ligand(lig_src)
+    gs = ctx.build_grids(rec, [box], sorted(set(lig.xs_types.tolist())))
+    p = torch.tensor(poses, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        ctx.score(gs, lig, 0, p)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(reps):
+        ctx.score(gs, lig, 0, p)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    dt = e0.elapsed_time(e1) * 1e-3 / reps
+    flops, gbytes = lig.cost()
+    n = len(poses)
+    return {"evals_per_s": round(n / dt, 1), "ms_per_launch": round(dt * 1e3, 4), "poses": n,
+            "achieved_tflops": round(n * flops / dt / 1e12, 3), "l2_gather_gbs": round(n * gbytes / dt / 1e9, 1)}
+
+
+def run_e2e(ctx, api, torch, rec, boxes, lig_src, types, pockets, steps, seed):
+    """The same metric through the public API from pinned host buffers: every step uploads the
+    receptor and ligand, builds the grids, docks, and reads the ranked poses back."""
+    pin = {k: torch.tensor(np.asarray(getattr(rec, k), dtype=np.float32 if k == "xyz" else np.uint8)).pin_memory()
+           for k in ("xyz", "element", "donor", "acceptor")}
+    host_rec = S.Receptor(pin["xyz"], pin["element"], pin["donor"], pin["acceptor"])
+    h2d = sum(t.numel() * t.element_size() for t in pin.values())
+    h2d += sum(np.asarray(a).nbytes for a in (np.asarray(lig_src.xyz, np.float32), lig_src.element, lig_src.donor,
+                                              lig_src.acceptor, np.asarray(lig_src.bonds, np.int32), lig_src.rotatable))
+    d2h = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        gs = ctx.build_grids(host_rec, boxes, types)
+        lig = ctx.ligand(lig_src)
+        r = ctx.dock(gs, [lig], pockets, chains=CHAINS, steps=STEPS, seed=seed, top_k=TOP_K, host_copy=True)
+        poses, kept, pots, xyz = r.fetch()
+        rank = r.ranking(0)
+        d2h = (poses.nbytes + kept.nbytes + pots.nbytes + xyz.nbytes + rank.nbytes)
+    dt = time.perf_counter() - t0
+    return {"value": round(len(pockets) * steps / dt, 4), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h)}
+
+
+# ----------------------------------------------------------------- oracle (CPU) arm --
+def oracle_sample(rec, boxes, lig_src, budget_s=12.0):
+    """Times the FP64 oracle on a bounded sample of one pair: the grid maps of one pocket, then
+    chains of the full 2,000-step search; returns seconds per docked pair (extrapolated to the
+    1,000 chains of the workload) and the sample description."""
+    import oracle as O
+    cores = len(os.sched_getaffinity(0))
+    L = O.OracleLigand(lig_src)
+    box = boxes[0]
+    t0 = time.perf_counter()
+    og = O.OracleGrid(rec, box, L.xs, rec_types=O.xs_type_receptor(rec), threads=cores)
+    t_grid = time.perf_counter() - t0
+    # calibrate on one chain-batch of one MC step block, then size the sample to the budget
+    p = O.SearchParams(seed=0, steps=STEPS)
+    n_chains = cores
+    t0 = time.perf_counter()
+    _, _, ev = O.mc_chains(L, og, box, O.SearchParams(seed=0, steps=50), unit=0, n_chains=n_chains, threads=cores)
+    t_cal = time.perf_counter() - t0
+    per_chain_full = t_cal / n_chains * (STEPS / 50) * cores     # core-seconds per full chain
+    fit = max(1, int((budget_s - t_grid) * cores / max(per_chain_full, 1e-9)))
+    n_chains = int(min(CHAINS, max(cores, (fit // cores) * cores)))
+    t0 = time.perf_counter()
+    _, _, ev = O.mc_chains(L, og, box, p, unit=0, n_chains=n_chains, threads=cores)
+    t_dock = time.perf_counter() - t0
+    per_pair = t_grid + t_dock * CHAINS / n_chains
+    sample = (f"1 pocket: full FP64 grid maps ({len(set(L.xs.tolist()))} types) + {n_chains} of {CHAINS} "
+              f"chains x {STEPS} MC steps; time scaled x {CHAINS / n_chains:.1f} to the pair")
+    return per_pair, float(ev.sum()) / t_dock, cores, sample, t_grid + t_dock
+
+
+def run_cpu_baseline(rec, boxes, lig_src, budget_s=12.0):
+    per_pair, evals_s, cores, sample, _ = oracle_sample(rec, boxes, lig_src, budget_s)
+    return {"value": round(1.0 / per_pair, 6), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "evals_per_s": round(evals_s, 1)}
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return None
+    import oracle as O
+    O.build()
+    rec, boxes, lig_src = workload(seed=0)
+    for _ in range(args.warmup):   # untimed: short samples (page in code and data)
+        oracle_sample(rec, boxes, lig_src, budget_s=1.0)
+    times, last = [], None
+    for _ in range(args.steps):
+        last = oracle_sample(rec, boxes, lig_src, budget_s=args.cpu_budget)
+        times.append(last[0])
+    per_pair = float(np.mean(times))
+    value = 1.0 / per_pair
+    cores, sample = last[2], last[3]
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per_pair * len(boxes) * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pairs_per_step_per_gpu": len(boxes)},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_small_case(args):
+    """One small untimed pass for profiler captures: the multi-pocket receptor's first pocket,
+    256 chains x 20 MC steps, plus one score launch over 4,096 poses."""
+    import torch
+    import paper_2506_20043_gb300 as pv
+    pv.build()
+    from paper_2506_20043_gb300 import api
+    ctx = api.Context(0)
+    rec, boxes, lig_src = workload(seed=0)
+    lig = ctx.ligand(lig_src)
+    gs = ctx.build_grids(rec, boxes[:1], sorted(set(lig.xs_types.tolist())))
+    r = ctx.dock(gs, [lig], [0], chains=256, steps=20, seed=0, host_copy=False)
+    ev, sec, st = r.stats()
+    poses = torch.tensor(S.random_poses(4096, boxes[0], lig.n_rot, 0), dtype=torch.float32, device="cuda")
+    ctx.score(gs, lig, 0, poses)
+    torch.cuda.synchronize()
+    return {"case": "small", "evals": int(ev), "seconds": round(sec, 4), "status": st.tolist()}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work per sample")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-micro", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--case", choices=["full", "small"], default="full",
+                    help="small: one untimed small pass for profiler captures")
+    args = ap.parse_args()
+    if args.case == "small":
+        out = run_small_case(args)
+    else:
+        out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,295 @@
+/*
+ * pocketvina.h -- C ABI of the GB300 multi-pocket docking library (libpocketvina.so).
+ *
+ * The library implements the docking hot path of PocketVina (arxiv 2506.20043): per-pocket
+ * receptor grid maps ("Kernel 1"), Vina-style scoring of ligand poses by trilinear
+ * interpolation plus intra-ligand terms (Eq. 3) with its analytic gradient over pose, and
+ * many independent Monte-Carlo + RILC-BFGS chains per (ligand, pocket) pair ("Kernel 2",
+ * Eq. 1-13, Supplementary Algorithm 2), aggregated over pockets (Algorithm 3).
+ *
+ * Conventions
+ *   - Every call returns pv_status; no C++ exception crosses the ABI and nothing aborts.
+ *     pv_last_error() returns a message for the last failing call on that context (owned by
+ *     the context, valid until its next call).
+ *   - Pointer kinds are explicit: arguments named dev_* are device pointers on the context's
+ *     device; structs carry a `mem` field (pv_mem) for their arrays; everything else is host.
+ *   - Inputs stay owned by the caller and are not retained after the call returns.
+ *   - Opaque handles (pv_grid_set, pv_ligand, pv_dock_result) are owned by the library and
+ *     freed with their *_destroy function; they must be destroyed before their context.
+ *   - Work is issued on the context's CUDA stream. pv_build_grids, pv_ligand_create and
+ *     pv_score* are asynchronous with respect to the host; pv_dock synchronises the stream
+ *     before it returns.
+ *   - One context per host thread at a time.
+ *
+ * Units: Angstrom, kcal/mol, radians. Elements: 0 = C, 1 = N, 2 = O, 3 = S.
+ * XS atom types (ids used by lig_types): 0 C_H, 1 C_P, 2 N_P, 3 N_D, 4 N_A, 5 N_DA, 6 O_P,
+ * 7 O_D, 8 O_A, 9 O_DA, 10 S_P.
+ * POT pose vector (Eq. 1): x, y, z, qw, qx, qy, qz, psi_1 .. psi_Nrot, where (x, y, z) is the
+ * position of the ligand's origin atom (the lowest-index atom of its largest rigid fragment),
+ * q the orientation applied about it, and psi_k the angle of the k-th rotatable bond of the
+ * input bond list (psi = 0: the input conformer), turning the side away from the origin
+ * right-handedly about the axis from its near atom to its far atom.
+ */
+#ifndef POCKETVINA_H
+#define POCKETVINA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PV_OK = 0,
+    PV_ERR_ARG = 1,        /* invalid argument (sizes, limits, missing map for a ligand type) */
+    PV_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+    PV_ERR_OOM = 3,        /* device allocation failed */
+    PV_ERR_TIMEOUT = 4,    /* the search exceeded pv_dock_params.timeout_s (watchdog) */
+    PV_ERR_NAN = 5,        /* a non-finite energy was produced */
+    PV_ERR_STATE = 6       /* handle used with a different context, or destroyed */
+} pv_status;
+
+typedef enum { PV_MEM_HOST = 0, PV_MEM_DEVICE = 1 } pv_mem;
+typedef enum { PV_MODE_BATCHED = 0, PV_MODE_PLAIN = 1 } pv_mode;
+
+/* Limits of one ligand: atoms and rotatable bonds. */
+#define PV_MAX_ATOMS 64
+#define PV_MAX_TORSIONS 26
+
+typedef struct pv_context pv_context;
+typedef struct pv_grid_set pv_grid_set;
+typedef struct pv_ligand pv_ligand;
+typedef struct pv_dock_result pv_dock_result;
+
+/* ------------------------------------------------------------------------- context --- */
+
+/* Creates a context on CUDA device `device` issuing work on `cuda_stream` (a cudaStream_t;
+ * NULL = the legacy default stream). */
+pv_status pv_context_create(int device, void* cuda_stream, pv_context** out);
+void pv_context_destroy(pv_context* ctx);
+const char* pv_last_error(const pv_context* ctx);
+pv_status pv_context_set_stream(pv_context* ctx, void* cuda_stream);
+
+/* Optional device allocator (e.g. a framework's caching allocator). alloc returns NULL on
+ * failure; both receive the context's stream. Without it the library uses cudaMalloc/cudaFree. */
+typedef void* (*pv_alloc_fn)(size_t bytes, void* cuda_stream, void* user);
+typedef void (*pv_free_fn)(void* ptr, void* cuda_stream, void* user);
+pv_status pv_context_set_allocator(pv_context* ctx, pv_alloc_fn alloc, pv_free_fn free_fn,
+                                   void* user);
+
+/* --------------------------------------------------------------------- grid cache --- */
+
+typedef struct {
+    int32_t n_atoms;
+    const float* xyz;          /* [n_atoms][3] */
+    const uint8_t* element;    /* [n_atoms] 0 C, 1 N, 2 O, 3 S */
+    const uint8_t* donor;      /* [n_atoms] 0/1, meaningful on N and O only */
+    const uint8_t* acceptor;   /* [n_atoms] 0/1, meaningful on N and O only */
+    int32_t mem;               /* pv_mem of the four arrays */
+} pv_receptor;
+
+/* Search box: a cuboid centred on a pocket centre (Algorithm 3, CreateBox). Grid nodes lie at
+ * center - size/2 + i * spacing, i = 0 .. ceil(size/spacing), per axis. */
+typedef struct {
+    float center[3];
+    float size[3];
+    float spacing;             /* > 0; 0.375 in the benchmark workloads */
+} pv_box;
+
+/* Grid cache ("Kernel 1", Methods "Accelerated Docking"; Supplementary Algorithm 2,
+ * Grid_cache(P)): for each box and each requested ligand XS type t, the map
+ * G_t(node) = sum over receptor atoms j within 8 A of E_Vina(t, type_j, |node - x_j|).
+ * Receptor atoms are typed on the device (carbon is polar iff an N/O lies within 1.75 A).
+ * `boxes` and `lig_types` are host arrays; lig_types lists distinct XS type ids (0..10).
+ * Maps are float32, layout per pocket [type][z][y][x] (x fastest), resident in device memory.
+ * Errors: PV_ERR_ARG on empty/oversized input, PV_ERR_OOM, PV_ERR_CUDA. */
+pv_status pv_build_grids(pv_context* ctx, const pv_receptor* receptor, const pv_box* boxes,
+                         int32_t n_pockets, const uint8_t* lig_types, int32_t n_types,
+                         pv_grid_set** out);
+
+/* Adds the pockets of another receptor to an existing set (same ligand types); pocket ids
+ * continue from the current count. *first_pocket receives the id of the first new pocket. */
+pv_status pv_grid_set_append(pv_context* ctx, pv_grid_set* set, const pv_receptor* receptor,
+                             const pv_box* boxes, int32_t n_pockets, int32_t* first_pocket);
+void pv_grid_set_destroy(pv_grid_set* set);
+
+/* Number of pockets and total map bytes. */
+pv_status pv_grid_set_info(const pv_grid_set* set, int32_t* n_pockets, int64_t* bytes);
+
+/* Borrowed device view of one map: pointer (valid until the set is destroyed), node counts
+ * (x, y, z), origin (first node) and spacing. PV_ERR_ARG if the type has no map. */
+pv_status pv_grid_set_view(const pv_grid_set* set, int32_t pocket, int32_t xs_type,
+                           const float** dev_map, int32_t dims[3], float origin[3],
+                           float* spacing);
+
+/* Copies one map (dims[2] * dims[1] * dims[0] floats, [z][y][x]) into dst, which may be host
+ * or device memory. Synchronous. */
+pv_status pv_grid_set_read_map(const pv_grid_set* set, int32_t pocket, int32_t xs_type, float* dst);
+
+/* ------------------------------------------------------------------------- ligands --- */
+
+/* A ligand as heavy atoms with bonds. Rotatable bonds must be bridges (not in a ring). The
+ * atom with the lowest index of the largest rigid fragment is the POT origin. Host memory. */
+typedef struct {
+    int32_t n_atoms;           /* 1 .. PV_MAX_ATOMS */
+    const float* xyz;          /* [n_atoms][3] input conformer */
+    const uint8_t* element;
+    const uint8_t* donor;
+    const uint8_t* acceptor;
+    int32_t n_bonds;
+    const int32_t* bonds;      /* [n_bonds][2] */
+    const uint8_t* rotatable;  /* [n_bonds] 0/1; at most PV_MAX_TORSIONS set */
+} pv_ligand_desc;
+
+/* Builds the torsion tree (rigid fragments, hinge axes), XS types (carbon polar iff bonded to
+ * N/O) and the intra-ligand pair list (atoms in different rigid fragments more than three
+ * bonds apart, Eq. 3's e_intra), and uploads them. PV_ERR_ARG on a non-bridge rotatable bond
+ * or a limit exceeded. */
+pv_status pv_ligand_create(pv_context* ctx, const pv_ligand_desc* desc, pv_ligand** out);
+void pv_ligand_destroy(pv_ligand* lig);
+
+/* n_atoms, n_rot (torsions), n_pairs (intra pairs), origin atom (input index). */
+pv_status pv_ligand_info(const pv_ligand* lig, int32_t* n_atoms, int32_t* n_rot,
+                         int32_t* n_pairs, int32_t* origin_atom);
+
+/* Algorithmic cost of one score + gradient evaluation of this ligand: FP32 operations (an FMA
+ * counts two) and bytes of grid corners gathered (8 x 4 B per atom). Used for roofline figures. */
+pv_status pv_ligand_cost(const pv_ligand* lig, double* flops, double* gather_bytes);
+
+/* XS type of every atom, input order (host array of n_atoms). */
+pv_status pv_ligand_xs_types(const pv_ligand* lig, uint8_t* out);
+
+/* ------------------------------------------------------------------------- scoring --- */
+
+/* SF = e_inter + e_intra (Eq. 3) of n_poses POT vectors of one ligand in one pocket.
+ * dev_pose: [n_poses][7 + n_rot] float32 (quaternion need not be unit; it is normalised).
+ * dev_energy: [n_poses]. dev_grad (nullable): [n_poses][6 + n_rot], the gradient over the
+ * tangent coordinates the optimiser uses: translation, rotation vector applied in the world
+ * frame about the origin atom, torsions. dev_parts (nullable): [n_poses][2] = e_inter, e_intra.
+ * Atoms outside the grid are interpolated at the clamped point plus 10 kcal/mol/A times the
+ * distance outside. One warp per pose. */
+pv_status pv_score(pv_context* ctx, const pv_grid_set* set, const pv_ligand* lig, int32_t pocket,
+                   int32_t n_poses, const float* dev_pose, float* dev_energy, float* dev_grad,
+                   float* dev_parts);
+
+/* Vector-Jacobian product of pv_score for automatic differentiation:
+ * dev_grad_pose[n][7 + n_rot] = dE[n] * dSF/dPOT (translation, raw quaternion components
+ * through the normalisation, torsions); dev_grad_xyz (nullable) [n][n_atoms][3] =
+ * dE[n] * dSF/dx_i, the gradient over the posed atom coordinates, input atom order. */
+pv_status pv_score_backward(pv_context* ctx, const pv_grid_set* set, const pv_ligand* lig,
+                            int32_t pocket, int32_t n_poses, const float* dev_pose,
+                            const float* dev_grad_energy, float* dev_grad_pose,
+                            float* dev_grad_xyz);
+
+/* Posed atom coordinates: dev_xyz[n][n_atoms][3] in input atom order (forward kinematics). */
+pv_status pv_pose_coords(pv_context* ctx, const pv_ligand* lig, int32_t n_poses,
+                         const float* dev_pose, float* dev_xyz);
+
+/* ------------------------------------------------------------------------- docking --- */
+
+typedef struct {
+    int32_t chains;            /* MC chains per (ligand, pocket) pair ("n threads", Alg. 2) */
+    int32_t steps;             /* MC steps per chain */
+    uint64_t seed;             /* Philox4x32-10 key */
+    int32_t top_k;             /* poses kept per pair after sorting + RMSD filter */
+    float rmsd_min;            /* A; a pose closer than this to a kept one is dropped */
+    int32_t mode;              /* pv_mode: BATCHED = one persistent launch per round over all
+                                  pairs, warp per chain; PLAIN = one launch per pair, thread
+                                  per chain, as in the paper's per-ligand loop */
+    int32_t bfgs_m;            /* L-BFGS memory (pairs kept), <= 8 */
+    int32_t bfgs_max_iter;     /* 0: floor((25 + n_atoms) / 3) */
+    int32_t bfgs_max_trials;   /* line-search trials per iteration */
+    float bfgs_eps;            /* Eq. 11 curvature threshold and Eq. 12 gradient tolerance */
+    float rho;                 /* Armijo constant (Eq. 7) */
+    float sigma;               /* weak Wolfe constant (Eq. 8) */
+    float temperature;         /* Metropolis temperature (Eq. 13 read as a Boltzmann factor) */
+    float amplitude;           /* mutation radius, A (translation; orientation amplitude/R_gyr) */
+    int32_t steps_per_round;   /* batched: MC steps per kernel launch (round); 0 = automatic */
+    int32_t use_graph;         /* batched: capture the launch sequence in a CUDA graph */
+    int32_t warps_per_cta;     /* batched: chains per CTA; 0 = autotuned */
+    int32_t host_copy;         /* 1: copy results to host memory before returning */
+    double timeout_s;          /* watchdog per launch; 0 = none. Overrun -> PV_ERR_TIMEOUT */
+} pv_dock_params;
+
+/* Defaults: chains 64, steps 1000, seed 0, top_k 9, rmsd_min 1.0, BATCHED, m 5, max_iter 0,
+ * max_trials 10, eps 1e-3, rho 1e-4, sigma 0.1, temperature 1.2, amplitude 2.0,
+ * steps_per_round 0, use_graph 1, warps_per_cta 0, host_copy 1, timeout_s 0. */
+void pv_dock_params_default(pv_dock_params* p);
+
+/* Docks every ligand into every listed pocket (Supplementary Algorithms 2 and 3). Pair
+ * index = ligand index * n_pockets + position in pocket_ids. Each pair runs `chains`
+ * independent chains: random start, then `steps` x (mutate one POT entity, RILC-BFGS,
+ * Metropolis accept, refine a new best); each chain keeps its best pose; per pair the chain
+ * bests are sorted by SF (ties: chain id), filtered by RMSD >= rmsd_min, cut to top_k and
+ * rescored; per ligand all pairs' kept poses are merged by SF (ties: pocket, chain).
+ * Random numbers: Philox4x32-10 with key = seed and counter = (chain, pair, step, block),
+ * step 0 for the start and s + 1 for MC step s. Synchronises before returning. */
+pv_status pv_dock(pv_context* ctx, const pv_grid_set* set, pv_ligand* const* ligs,
+                  int32_t n_ligs, const int32_t* pocket_ids, int32_t n_pockets,
+                  const pv_dock_params* params, pv_dock_result** out);
+
+/* Same, over an explicit pair list (pair p docks ligs[pair_ligand[p]] into pocket
+ * pair_pocket[p]); pair index = position in the list. */
+pv_status pv_dock_pairs(pv_context* ctx, const pv_grid_set* set, pv_ligand* const* ligs,
+                        int32_t n_ligs, const int32_t* pair_ligand, const int32_t* pair_pocket,
+                        int32_t n_pairs, const pv_dock_params* params, pv_dock_result** out);
+
+typedef struct {
+    float score;               /* SF = e_inter + e_intra, the search objective */
+    float e_inter;
+    float e_intra;
+    float affinity;            /* e_inter / (1 + 0.0585 N_rot), Vina's reported form */
+    int32_t pair;
+    int32_t ligand;
+    int32_t pocket;            /* pocket id in the grid set */
+    int32_t chain;
+} pv_pose;
+
+/* Sizes: pairs, top_k, POT stride (7 + max n_rot), coordinate stride (max n_atoms). */
+pv_status pv_dock_result_info(const pv_dock_result* r, int32_t* n_pairs, int32_t* top_k,
+                              int32_t* pot_stride, int32_t* atom_stride);
+
+/* Host copies (synchronous). poses [n_pairs][top_k]; n_kept [n_pairs]; pots (nullable)
+ * [n_pairs][top_k][pot_stride]; xyz (nullable) [n_pairs][top_k][atom_stride][3], input atom
+ * order; unused slots have pair = -1. */
+pv_status pv_dock_result_poses(const pv_dock_result* r, pv_pose* poses, int32_t* n_kept,
+                               float* pots, float* xyz);
+
+/* Per-ligand merged ranking: indices into the poses array (pair * top_k + slot), best first;
+ * out has room for n_pockets_of_ligand * top_k entries; *n_out receives the count. */
+pv_status pv_dock_result_ranking(const pv_dock_result* r, int32_t ligand, int32_t* out,
+                                 int32_t* n_out);
+
+/* Evaluation count (score+gradient evaluations), wall seconds of the docking launches,
+ * per-pair status (pv_status values) into status (nullable, [n_pairs]). */
+pv_status pv_dock_result_stats(const pv_dock_result* r, uint64_t* n_evals, double* seconds,
+                               int32_t* status);
+
+/* Device time of the search launches alone (batched: the rounds; plain: the per-pair search
+ * kernels), their count, and the whole launch sequence (search + selection + merge). */
+pv_status pv_dock_result_timing(const pv_dock_result* r, double* search_seconds,
+                                int32_t* search_launches, double* total_seconds);
+
+/* Device-resident results (valid until destroy): poses [n_pairs * top_k] pv_pose,
+ * n_kept [n_pairs], ranking [n_ligs][max_pairs_per_ligand * top_k] (-1 padded). */
+pv_status pv_dock_result_device(const pv_dock_result* r, const pv_pose** dev_poses,
+                                const int32_t** dev_n_kept, const int32_t** dev_ranking);
+
+/* Chain states after the search (device, valid until destroy): records
+ * [n_pairs][chains][record_stride] float32; a record holds the chain's current POT at offset 0,
+ * its best POT at offset best_pot_offset and its best SF at offset best_score_offset. */
+pv_status pv_dock_result_chains(const pv_dock_result* r, const float** dev_records,
+                                int32_t* chains, int32_t* record_stride, int32_t* best_pot_offset,
+                                int32_t* best_score_offset);
+
+/* Copies all chain records (n_pairs * chains * record_stride floats) into dst, host or device
+ * memory. Synchronous. */
+pv_status pv_dock_result_read_chains(const pv_dock_result* r, float* dst);
+
+void pv_dock_result_destroy(pv_dock_result* r);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POCKETVINA_H */

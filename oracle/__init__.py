@@ -90,6 +90,8 @@ def lib():
             L.or_grid_node_value.argtypes = [C.c_int, dp, ip, dp, C.c_double, C.c_int, C.c_int,
                                              C.c_int, C.c_int]
             L.or_grid_build.argtypes = [C.c_int, dp, ip, dp, C.c_double, ip, C.c_int, ip, dp, C.c_int]
+            L.or_grid_fill_nodes.argtypes = [C.c_int, dp, ip, dp, C.c_double, ip, C.c_int, ip, C.c_long,
+                                             C.POINTER(C.c_int64), dp, C.c_int]
             L.or_grid_eval.restype = C.c_double
             L.or_grid_eval.argtypes = [C.POINTER(Grid), C.c_int, dp, dp]
             L.or_ligand_new.restype = vp
@@ -211,6 +213,32 @@ class OracleGrid:
         for m, t in enumerate(self.types):
             self.struct.map_of_type[int(t)] = m
         self.struct.maps = _p(self.maps)
+
+    @classmethod
+    def lazy(cls, rec, box, types: Sequence[int], rec_types: np.ndarray, poses_xyz: np.ndarray,
+             threads: int = 0) -> "OracleGrid":
+        """Maps filled (by direct summation) only at the 8 corner nodes of every cell that the
+        given atom positions [..., 3] fall in (clamped like the interpolation); NaN elsewhere."""
+        origin, dims = grid_geometry(box)
+        sp = float(box.spacing)
+        p = np.asarray(poses_xyz, dtype=np.float64).reshape(-1, 3)
+        g = np.clip((p - origin) / sp, 0, dims - 1)
+        i = np.minimum(np.floor(g).astype(np.int64), dims - 2)
+        corners = []
+        for dz in (0, 1):
+            for dy in (0, 1):
+                for dx in (0, 1):
+                    c = i + np.array([dx, dy, dz])
+                    corners.append((c[:, 2] * dims[1] + c[:, 1]) * dims[0] + c[:, 0])
+        nodes = np.unique(np.concatenate(corners)).astype(np.int64)
+        tt = np.array(sorted(set(int(t) for t in types)), dtype=np.int32)
+        nn = int(np.prod(dims))
+        maps = np.full((len(tt), nn), np.nan)
+        lib().or_grid_fill_nodes(rec.n, _p(np.ascontiguousarray(rec.xyz, np.float64)),
+                                 _p(np.ascontiguousarray(rec_types, np.int32), C.c_int32), _p(origin), sp,
+                                 _p(dims.astype(np.int32), C.c_int32), len(tt), _p(tt, C.c_int32), len(nodes),
+                                 nodes.ctypes.data_as(C.POINTER(C.c_int64)), _p(maps), int(threads))
+        return cls(None, box, tt, maps=maps)
 
     def map(self, t: int) -> np.ndarray:
         m = int(np.nonzero(self.types == t)[0][0])

@@ -287,6 +287,28 @@ void or_grid_build(int n_rec, const double* rxyz, const int32_t* rtype, const do
     (void)n_threads;
 }
 
+/* The same maps, filled only at the listed flat node indices (the rest untouched): lets a test
+ * check a full-size workload on the nodes that sampled poses actually touch. */
+void or_grid_fill_nodes(int n_rec, const double* rxyz, const int32_t* rtype, const double origin[3],
+                        double spacing, const int32_t dims[3], int n_maps, const int32_t* types,
+                        long n_nodes, const int64_t* nodes, double* maps, int n_threads) {
+    long nx = dims[0], ny = dims[1], nz = dims[2];
+    long nn = nx * ny * nz;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (long k = 0; k < n_nodes; ++k) {
+        long node = nodes[k];
+        int ix = (int)(node % nx), iy = (int)((node / nx) % ny), iz = (int)(node / (nx * ny));
+        for (int m = 0; m < n_maps; ++m)
+            maps[m * nn + node] = or_grid_node_value(n_rec, rxyz, rtype, origin, spacing, types[m],
+                                                     ix, iy, iz);
+    }
+    (void)nz;
+    (void)n_threads;
+}
+
 typedef struct {
     double origin[3];
     double spacing;

@@ -1,0 +1,433 @@
+"""Python binding of libpocketvina.so: the same calls as include/pocketvina.h, with PyTorch
+supplying device memory (its caching allocator), streams and automatic differentiation.
+
+Every computation runs in the library's CUDA kernels; this module only marshals arguments.
+There is no CPU fallback: a missing library or GPU raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import _capi as A
+
+N_XS = 11
+
+
+class PVError(RuntimeError):
+    pass
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(np.asarray(a), dtype=dtype)
+
+
+def _ptr(a) -> int:
+    """Data pointer of a numpy array or torch tensor."""
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+@dataclasses.dataclass
+class DockParams:
+    chains: int = 64
+    steps: int = 1000
+    seed: int = 0
+    top_k: int = 9
+    rmsd_min: float = 1.0
+    mode: str = "batched"          # or "plain"
+    bfgs_m: int = 5
+    bfgs_max_iter: int = 0
+    bfgs_max_trials: int = 10
+    bfgs_eps: float = 1e-3
+    rho: float = 1e-4
+    sigma: float = 0.1
+    temperature: float = 1.2
+    amplitude: float = 2.0
+    steps_per_round: int = 0
+    use_graph: bool = True
+    warps_per_cta: int = 0
+    host_copy: bool = True
+    timeout_s: float = 0.0
+
+    def to_c(self) -> A.pv_dock_params:
+        p = A.pv_dock_params()
+        A.load().pv_dock_params_default(C.byref(p))
+        for f in dataclasses.fields(self):
+            v = getattr(self, f.name)
+            if f.name == "mode":
+                v = {"batched": A.PV_MODE_BATCHED, "plain": A.PV_MODE_PLAIN}[v]
+            elif isinstance(v, bool):
+                v = int(v)
+            setattr(p, f.name, v)
+        return p
+
+
+class Context:
+    """A library context on one CUDA device, issuing work on a torch stream and allocating
+    device memory through torch's caching allocator."""
+
+    def __init__(self, device: int = 0, stream=None, torch_allocator: bool = True):
+        import torch
+        if not torch.cuda.is_available():
+            raise PVError("no CUDA device: the docking path runs only on the GPU")
+        self.torch = torch
+        self.lib = A.load()
+        self.device = int(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = C.c_void_p()
+        st = self.lib.pv_context_create(self.device, C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != A.PV_OK:
+            raise PVError(f"pv_context_create failed: {A.STATUS_NAMES.get(st, st)}")
+        self.h = h
+        self._keep = []
+        if torch_allocator:
+            dev = self.device
+
+            def _alloc(n, stream, _user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(n), dev, stream)
+                except Exception:   # noqa: BLE001 - out of memory is reported as NULL
+                    return None
+
+            def _free(p, _stream, _user):
+                torch.cuda.caching_allocator_delete(p)
+
+            fa, ff = A.ALLOC_FN(_alloc), A.FREE_FN(_free)
+            self._keep += [fa, ff]
+            self._check(self.lib.pv_context_set_allocator(self.h, fa, ff, None), "pv_context_set_allocator")
+
+    # ---------------------------------------------------------------------------------------
+    def _check(self, st: int, what: str):
+        if st != A.PV_OK:
+            msg = self.lib.pv_last_error(self.h)
+            raise PVError(f"{what}: {A.STATUS_NAMES.get(st, st)}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pv_context_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:   # noqa: BLE001
+            pass
+
+    # ------------------------------------------------------------------------ grid cache --
+    def _receptor(self, rec, keep: list) -> A.pv_receptor:
+        torch = self.torch
+        r = A.pv_receptor()
+        if isinstance(rec.xyz, torch.Tensor):
+            xyz = rec.xyz.to(torch.float32).contiguous()
+            arrs = [xyz] + [t.to(torch.uint8).contiguous() for t in (rec.element, rec.donor, rec.acceptor)]
+            r.mem = A.PV_MEM_DEVICE if xyz.is_cuda else A.PV_MEM_HOST
+        else:
+            arrs = [_np(rec.xyz, np.float32), _np(rec.element, np.uint8), _np(rec.donor, np.uint8),
+                    _np(rec.acceptor, np.uint8)]
+            r.mem = A.PV_MEM_HOST
+        keep += arrs
+        r.n_atoms = int(arrs[0].shape[0])
+        r.xyz, r.element, r.donor, r.acceptor = (_ptr(a) for a in arrs)
+        return r
+
+    @staticmethod
+    def _boxes(boxes) -> "C.Array":
+        arr = (A.pv_box * len(boxes))()
+        for i, b in enumerate(boxes):
+            c = b.center if hasattr(b, "center") else b[0]
+            s = b.size if hasattr(b, "size") else b[1]
+            sp = b.spacing if hasattr(b, "spacing") else (b[2] if len(b) > 2 else 0.375)
+            for k in range(3):
+                arr[i].center[k] = float(c[k])
+                arr[i].size[k] = float(s[k] if np.ndim(s) else s)
+            arr[i].spacing = float(sp)
+        return arr
+
+    def build_grids(self, receptor, boxes: Sequence, lig_types: Sequence[int] = tuple(range(N_XS))) -> "GridSet":
+        keep: list = []
+        r = self._receptor(receptor, keep)
+        bx = self._boxes(boxes)
+        types = (C.c_uint8 * len(lig_types))(*[int(t) for t in lig_types])
+        h = C.c_void_p()
+        self._check(self.lib.pv_build_grids(self.h, C.byref(r), bx, len(boxes), types, len(lig_types), C.byref(h)),
+                    "pv_build_grids")
+        return GridSet(self, h)
+
+    # --------------------------------------------------------------------------- ligands --
+    def ligand(self, lig) -> "Ligand":
+        arrs = [_np(lig.xyz, np.float32), _np(lig.element, np.uint8), _np(lig.donor, np.uint8),
+                _np(lig.acceptor, np.uint8), _np(lig.bonds, np.int32).reshape(-1, 2),
+                _np(lig.rotatable, np.uint8)]
+        d = A.pv_ligand_desc()
+        d.n_atoms = int(arrs[0].shape[0])
+        d.xyz, d.element, d.donor, d.acceptor = (_ptr(a) for a in arrs[:4])
+        d.n_bonds = int(arrs[4].shape[0])
+        d.bonds, d.rotatable = _ptr(arrs[4]), _ptr(arrs[5])
+        h = C.c_void_p()
+        self._check(self.lib.pv_ligand_create(self.h, C.byref(d), C.byref(h)), "pv_ligand_create")
+        return Ligand(self, h)
+
+    # --------------------------------------------------------------------------- scoring --
+    def score(self, grids: "GridSet", lig: "Ligand", pocket: int, poses, grad: bool = True, parts: bool = False):
+        """SF (Eq. 3) of poses [n, 7 + n_rot] (cuda float32). Returns (energy [n], tangent
+        gradient [n, 6 + n_rot] or None, (e_inter, e_intra) [n, 2] or None)."""
+        torch = self.torch
+        poses = poses.to(device=f"cuda:{self.device}", dtype=torch.float32).contiguous()
+        n = poses.shape[0]
+        e = torch.empty(n, device=poses.device, dtype=torch.float32)
+        g = torch.empty((n, 6 + lig.n_rot), device=poses.device, dtype=torch.float32) if grad else None
+        pr = torch.empty((n, 2), device=poses.device, dtype=torch.float32) if parts else None
+        self._check(self.lib.pv_score(self.h, grids.h, lig.h, int(pocket), n, poses.data_ptr(), e.data_ptr(),
+                                      g.data_ptr() if g is not None else None,
+                                      pr.data_ptr() if pr is not None else None), "pv_score")
+        return e, g, pr
+
+    def score_backward(self, grids: "GridSet", lig: "Ligand", pocket: int, poses, grad_energy,
+                       want_pose: bool = True, want_xyz: bool = False):
+        torch = self.torch
+        poses = poses.to(device=f"cuda:{self.device}", dtype=torch.float32).contiguous()
+        ge = grad_energy.to(device=poses.device, dtype=torch.float32).contiguous()
+        n = poses.shape[0]
+        gp = torch.empty_like(poses) if want_pose else None
+        gx = torch.empty((n, lig.n_atoms, 3), device=poses.device, dtype=torch.float32) if want_xyz else None
+        self._check(self.lib.pv_score_backward(self.h, grids.h, lig.h, int(pocket), n, poses.data_ptr(), ge.data_ptr(),
+                                               gp.data_ptr() if gp is not None else None,
+                                               gx.data_ptr() if gx is not None else None), "pv_score_backward")
+        return gp, gx
+
+    def pose_coords(self, lig: "Ligand", poses):
+        torch = self.torch
+        poses = poses.to(device=f"cuda:{self.device}", dtype=torch.float32).contiguous()
+        out = torch.empty((poses.shape[0], lig.n_atoms, 3), device=poses.device, dtype=torch.float32)
+        self._check(self.lib.pv_pose_coords(self.h, lig.h, poses.shape[0], poses.data_ptr(), out.data_ptr()),
+                    "pv_pose_coords")
+        return out
+
+    # --------------------------------------------------------------------------- docking --
+    def dock(self, grids: "GridSet", ligands: Sequence["Ligand"], pocket_ids: Sequence[int],
+             params: Optional[DockParams] = None, **kw) -> "DockResult":
+        p = dataclasses.replace(params or DockParams(), **kw)
+        hs = (C.c_void_p * len(ligands))(*[l.h.value for l in ligands])
+        pk = (C.c_int32 * len(pocket_ids))(*[int(x) for x in pocket_ids])
+        cp = p.to_c()
+        h = C.c_void_p()
+        st = self.lib.pv_dock(self.h, grids.h, hs, len(ligands), pk, len(pocket_ids), C.byref(cp), C.byref(h))
+        return self._result(st, h, len(ligands), "pv_dock")
+
+    def dock_pairs(self, grids: "GridSet", ligands: Sequence["Ligand"], pair_ligand: Sequence[int],
+                   pair_pocket: Sequence[int], params: Optional[DockParams] = None, **kw) -> "DockResult":
+        p = dataclasses.replace(params or DockParams(), **kw)
+        hs = (C.c_void_p * len(ligands))(*[l.h.value for l in ligands])
+        pl = (C.c_int32 * len(pair_ligand))(*[int(x) for x in pair_ligand])
+        pp = (C.c_int32 * len(pair_pocket))(*[int(x) for x in pair_pocket])
+        cp = p.to_c()
+        h = C.c_void_p()
+        st = self.lib.pv_dock_pairs(self.h, grids.h, hs, len(ligands), pl, pp, len(pl), C.byref(cp), C.byref(h))
+        return self._result(st, h, len(ligands), "pv_dock_pairs")
+
+    def _result(self, st, h, n_ligs, what):
+        if st not in (A.PV_OK, A.PV_ERR_TIMEOUT, A.PV_ERR_NAN) or not h.value:
+            self._check(st, what)
+        res = DockResult(self, h, n_ligs)
+        res.status_code = st
+        if st != A.PV_OK:
+            res.error = self.lib.pv_last_error(self.h).decode()
+        return res
+
+
+class GridSet:
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+
+    @property
+    def n_pockets(self) -> int:
+        n = C.c_int32()
+        b = C.c_int64()
+        self.ctx.lib.pv_grid_set_info(self.h, C.byref(n), C.byref(b))
+        return n.value
+
+    @property
+    def bytes(self) -> int:
+        n = C.c_int32()
+        b = C.c_int64()
+        self.ctx.lib.pv_grid_set_info(self.h, C.byref(n), C.byref(b))
+        return b.value
+
+    def append(self, receptor, boxes) -> int:
+        keep: list = []
+        r = self.ctx._receptor(receptor, keep)
+        bx = Context._boxes(boxes)
+        first = C.c_int32()
+        self.ctx._check(self.ctx.lib.pv_grid_set_append(self.ctx.h, self.h, C.byref(r), bx, len(boxes),
+                                                        C.byref(first)), "pv_grid_set_append")
+        return first.value
+
+    def geometry(self, pocket: int, xs_type: int):
+        p = C.c_void_p()
+        dims = (C.c_int32 * 3)()
+        org = (C.c_float * 3)()
+        sp = C.c_float()
+        st = self.ctx.lib.pv_grid_set_view(self.h, int(pocket), int(xs_type), C.byref(p), dims, org, C.byref(sp))
+        if st != A.PV_OK:
+            raise PVError("pv_grid_set_view: no such map")
+        return np.array(list(dims)), np.array(list(org), dtype=np.float64), sp.value, p.value
+
+    def read_map(self, pocket: int, xs_type: int) -> np.ndarray:
+        dims, _, _, _ = self.geometry(pocket, xs_type)
+        out = np.zeros((dims[2], dims[1], dims[0]), dtype=np.float32)
+        self.ctx._check(self.ctx.lib.pv_grid_set_read_map(self.h, int(pocket), int(xs_type), out.ctypes.data),
+                        "pv_grid_set_read_map")
+        return out
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.ctx.h:
+            self.ctx.lib.pv_grid_set_destroy(self.h)
+            self.h = None
+
+
+class Ligand:
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+        na, nr, npair, org = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        ctx.lib.pv_ligand_info(h, C.byref(na), C.byref(nr), C.byref(npair), C.byref(org))
+        self.n_atoms, self.n_rot, self.n_pairs, self.origin = na.value, nr.value, npair.value, org.value
+
+    def cost(self):
+        """(FP32 operations, gathered grid bytes) of one score + gradient evaluation."""
+        f, b = C.c_double(), C.c_double()
+        self.ctx._check(self.ctx.lib.pv_ligand_cost(self.h, C.byref(f), C.byref(b)), "pv_ligand_cost")
+        return f.value, b.value
+
+    @property
+    def xs_types(self) -> np.ndarray:
+        out = np.zeros(self.n_atoms, dtype=np.uint8)
+        self.ctx.lib.pv_ligand_xs_types(self.h, out.ctypes.data_as(C.POINTER(C.c_uint8)))
+        return out
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.ctx.h:
+            self.ctx.lib.pv_ligand_destroy(self.h)
+            self.h = None
+
+
+class DockResult:
+    def __init__(self, ctx: Context, h, n_ligs: int):
+        self.ctx, self.h, self.n_ligs = ctx, h, n_ligs
+        a, b, c, d = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        ctx.lib.pv_dock_result_info(h, C.byref(a), C.byref(b), C.byref(c), C.byref(d))
+        self.n_pairs, self.top_k, self.pot_stride, self.atom_stride = a.value, b.value, c.value, d.value
+        self.status_code = 0
+        self.error = ""
+        self._host = None
+
+    def fetch(self):
+        """Host copies: structured pose records, kept counts, POTs, coordinates."""
+        if self._host is None:
+            n = self.n_pairs * self.top_k
+            poses = (A.pv_pose * n)()
+            kept = np.zeros(self.n_pairs, dtype=np.int32)
+            pots = np.zeros((self.n_pairs, self.top_k, self.pot_stride), dtype=np.float32)
+            xyz = np.zeros((self.n_pairs, self.top_k, self.atom_stride, 3), dtype=np.float32)
+            self.ctx._check(self.ctx.lib.pv_dock_result_poses(
+                self.h, poses, kept.ctypes.data_as(C.POINTER(C.c_int32)),
+                pots.ctypes.data_as(C.POINTER(C.c_float)), xyz.ctypes.data_as(C.POINTER(C.c_float))),
+                "pv_dock_result_poses")
+            rec = np.array([(p.score, p.e_inter, p.e_intra, p.affinity, p.pair, p.ligand, p.pocket, p.chain)
+                            for p in poses], dtype=[("score", "f4"), ("e_inter", "f4"), ("e_intra", "f4"),
+                                                    ("affinity", "f4"), ("pair", "i4"), ("ligand", "i4"),
+                                                    ("pocket", "i4"), ("chain", "i4")])
+            self._host = (rec.reshape(self.n_pairs, self.top_k), kept, pots, xyz)
+        return self._host
+
+    @property
+    def poses(self):
+        return self.fetch()[0]
+
+    @property
+    def n_kept(self):
+        return self.fetch()[1]
+
+    @property
+    def pots(self):
+        return self.fetch()[2]
+
+    @property
+    def xyz(self):
+        return self.fetch()[3]
+
+    def ranking(self, ligand: int) -> np.ndarray:
+        cap = self.n_pairs * self.top_k
+        out = np.zeros(max(cap, 1), dtype=np.int32)
+        n = C.c_int32()
+        self.ctx._check(self.ctx.lib.pv_dock_result_ranking(self.h, int(ligand),
+                                                            out.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(n)),
+                        "pv_dock_result_ranking")
+        return out[:n.value]
+
+    def stats(self):
+        ev = C.c_uint64()
+        sec = C.c_double()
+        st = np.zeros(self.n_pairs, dtype=np.int32)
+        self.ctx._check(self.ctx.lib.pv_dock_result_stats(self.h, C.byref(ev), C.byref(sec),
+                                                          st.ctypes.data_as(C.POINTER(C.c_int32))),
+                        "pv_dock_result_stats")
+        return ev.value, sec.value, st
+
+    def timing(self):
+        """(search kernel seconds, search launches, whole launch sequence seconds)."""
+        s, n, t = C.c_double(), C.c_int32(), C.c_double()
+        self.ctx._check(self.ctx.lib.pv_dock_result_timing(self.h, C.byref(s), C.byref(n), C.byref(t)),
+                        "pv_dock_result_timing")
+        return s.value, n.value, t.value
+
+    def chain_records(self):
+        """Chain states after the search, copied to the host: (best POT [n_pairs, chains,
+        pot_stride], best SF [n_pairs, chains])."""
+        p = C.c_void_p()
+        ch, stride, bo, so = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        self.ctx._check(self.ctx.lib.pv_dock_result_chains(self.h, C.byref(p), C.byref(ch), C.byref(stride),
+                                                           C.byref(bo), C.byref(so)), "pv_dock_result_chains")
+        rec = np.zeros((self.n_pairs, ch.value, stride.value), dtype=np.float32)
+        self.ctx._check(self.ctx.lib.pv_dock_result_read_chains(self.h, rec.ctypes.data), "pv_dock_result_read_chains")
+        return rec[:, :, bo.value:bo.value + self.pot_stride].copy(), rec[:, :, so.value].copy()
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.ctx.h:
+            self.ctx.lib.pv_dock_result_destroy(self.h)
+            self.h = None
+
+
+class PVScore:
+    """torch.autograd.Function over pose parameters: energy = SF(pose) for one ligand in one
+    pocket; backward is the library's adjoint kernel (the gradient BFGS consumes), mapped to POT
+    coordinates (translation, raw quaternion, torsions)."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, pose, ctx: Context, grids: GridSet, lig: Ligand, pocket: int):
+        if cls._fn is None:
+            import torch
+
+            class _F(torch.autograd.Function):
+                @staticmethod
+                def forward(fctx, pose_t, pv_ctx, grids_, lig_, pocket_):
+                    e, _, _ = pv_ctx.score(grids_, lig_, pocket_, pose_t.detach(), grad=False)
+                    fctx.save_for_backward(pose_t)
+                    fctx.pv = (pv_ctx, grids_, lig_, pocket_)
+                    return e
+
+                @staticmethod
+                def backward(fctx, ge):
+                    (pose_t,) = fctx.saved_tensors
+                    pv_ctx, grids_, lig_, pocket_ = fctx.pv
+                    gp, _ = pv_ctx.score_backward(grids_, lig_, pocket_, pose_t.detach(), ge.contiguous())
+                    return gp.to(pose_t.dtype), None, None, None, None
+
+            cls._fn = _F
+        return cls._fn.apply(pose, ctx, grids, lig, pocket)

@@ -1,0 +1,228 @@
+// pv_device.cuh -- device primitives of the docking path: Vina terms, Philox4x32-10, quaternion
+// algebra, trilinear grid lookup, warp reductions. Header-only, included by the kernels.
+#pragma once
+#include <stdint.h>
+#include <cuda_runtime.h>
+#include "pv_layout.h"
+
+#define PV_FULL 0xffffffffu
+#define PV_PI 3.14159265358979323846f
+
+namespace pv {
+
+// ------------------------------------------------------------------------------------------
+// AutoDock Vina scoring terms (Trott & Olson 2010; the scoring function the paper's engine
+// evaluates, Eq. 3). Surface distance d = r - R_i - R_j, cutoff r < 8 A.
+// ------------------------------------------------------------------------------------------
+constexpr float kWGauss1 = -0.0356f;
+constexpr float kWGauss2 = -0.00516f;
+constexpr float kWRepulsion = 0.840f;
+constexpr float kWHydrophobic = -0.0351f;
+constexpr float kWHBond = -0.587f;
+constexpr float kWRot = 0.0585f;
+constexpr float kCutoff = 8.0f;
+constexpr float kCutoff2 = 64.0f;
+constexpr float kOutSlope = 10.0f;       // kcal/mol/A beyond the grid
+
+// XS type properties, indexed by type id (C_H, C_P, N_P, N_D, N_A, N_DA, O_P, O_D, O_A, O_DA, S_P)
+__host__ __device__ inline float xs_radius(int t) {
+    return t <= 1 ? 1.9f : (t <= 5 ? 1.8f : (t <= 9 ? 1.7f : 2.0f));
+}
+__host__ __device__ inline bool xs_hydrophobic(int t) { return t == 0; }
+__host__ __device__ inline bool xs_donor(int t) { return t == 3 || t == 5 || t == 7 || t == 9; }
+__host__ __device__ inline bool xs_acceptor(int t) { return t == 4 || t == 5 || t == 8 || t == 9; }
+
+// Weighted pair energy at distance r (< cutoff, checked by the caller) and dE/dr.
+__device__ __forceinline__ float vina_pair(float r, float rsum, bool hyd, bool hb, float& dedr) {
+    float d = r - rsum;
+    float a = 2.0f * d;                    // d / 0.5
+    float g1 = __expf(-a * a);
+    float b = 0.5f * (d - 3.0f);           // (d - 3) / 2
+    float g2 = __expf(-b * b);
+    float e = kWGauss1 * g1 + kWGauss2 * g2;
+    float de = kWGauss1 * g1 * (-4.0f * a) + kWGauss2 * g2 * (-b);
+    if (d < 0.0f) { e += kWRepulsion * d * d; de += 2.0f * kWRepulsion * d; }
+    if (hyd) {
+        if (d < 0.5f) e += kWHydrophobic;
+        else if (d < 1.5f) { e += kWHydrophobic * (1.5f - d); de -= kWHydrophobic; }
+    }
+    if (hb) {
+        if (d < -0.7f) e += kWHBond;
+        else if (d < 0.0f) { e += kWHBond * (-d * (1.0f / 0.7f)); de -= kWHBond * (1.0f / 0.7f); }
+    }
+    dedr = de;
+    return e;
+}
+
+// ------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC 2011): 10 rounds, multipliers 0xD2511F53 / 0xCD9E8D57,
+// key schedule increments 0x9E3779B9 / 0xBB67AE85.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+__device__ __forceinline__ uint32_t pick(uint4 v, int i) {
+    return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+// Word i of the draw stream of (chain, pair, step): word i % 4 of philox(ctr = {chain, pair,
+// step, i / 4}, key = seed).
+__device__ __forceinline__ uint32_t draw_word(uint32_t chain, uint32_t pair, uint32_t step, int i,
+                                              uint32_t k0, uint32_t k1) {
+    return pick(philox4x32_10(make_uint4(chain, pair, step, (uint32_t)(i >> 2)), k0, k1), i & 3);
+}
+// Uniform in [0, 1) from the top 24 bits (exact in binary32).
+__device__ __forceinline__ float u01(uint32_t w) { return (float)(w >> 8) * (1.0f / 16777216.0f); }
+
+// ------------------------------------------------------------------------------------------
+// Quaternions (w, x, y, z), Hamilton product; rotation matrices row-major.
+// ------------------------------------------------------------------------------------------
+struct Mat3 { float m[9]; };
+
+__device__ __forceinline__ float4 quat_normalize(float4 q) {
+    float n = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    return make_float4(q.x * n, q.y * n, q.z * n, q.w * n);
+}
+// q stored as float4(w, x, y, z)
+__device__ __forceinline__ Mat3 quat_to_mat(float4 qi) {
+    float4 q = quat_normalize(qi);
+    float w = q.x, x = q.y, y = q.z, z = q.w;
+    Mat3 R;
+    R.m[0] = 1.f - 2.f * (y * y + z * z); R.m[1] = 2.f * (x * y - w * z); R.m[2] = 2.f * (x * z + w * y);
+    R.m[3] = 2.f * (x * y + w * z); R.m[4] = 1.f - 2.f * (x * x + z * z); R.m[5] = 2.f * (y * z - w * x);
+    R.m[6] = 2.f * (x * z - w * y); R.m[7] = 2.f * (y * z + w * x); R.m[8] = 1.f - 2.f * (x * x + y * y);
+    return R;
+}
+__device__ __forceinline__ float4 quat_mul(float4 a, float4 b) {
+    return make_float4(a.x * b.x - a.y * b.y - a.z * b.z - a.w * b.w,
+                       a.x * b.y + a.y * b.x + a.z * b.w - a.w * b.z,
+                       a.x * b.z - a.y * b.w + a.z * b.x + a.w * b.y,
+                       a.x * b.w + a.y * b.z - a.z * b.y + a.w * b.x);
+}
+// q <- normalize(exp(omega / 2) (x) q): world-frame rotation by the rotation vector omega.
+__device__ __forceinline__ float4 quat_rotate_by(float4 q, float3 om) {
+    float th2 = om.x * om.x + om.y * om.y + om.z * om.z;
+    float4 e;
+    if (th2 < 1e-16f) {
+        e = make_float4(1.0f, 0.5f * om.x, 0.5f * om.y, 0.5f * om.z);
+    } else {
+        float th = sqrtf(th2), s, c;
+        sincosf(0.5f * th, &s, &c);
+        s /= th;
+        e = make_float4(c, s * om.x, s * om.y, s * om.z);
+    }
+    return quat_normalize(quat_mul(e, q));
+}
+// Rotation by angle t about the unit axis a (Rodrigues).
+__device__ __forceinline__ Mat3 axis_angle(float3 a, float t) {
+    float s, c;
+    sincosf(t, &s, &c);
+    float C = 1.0f - c;
+    Mat3 R;
+    R.m[0] = c + a.x * a.x * C;        R.m[1] = a.x * a.y * C - a.z * s; R.m[2] = a.x * a.z * C + a.y * s;
+    R.m[3] = a.y * a.x * C + a.z * s;  R.m[4] = c + a.y * a.y * C;       R.m[5] = a.y * a.z * C - a.x * s;
+    R.m[6] = a.z * a.x * C - a.y * s;  R.m[7] = a.z * a.y * C + a.x * s; R.m[8] = c + a.z * a.z * C;
+    return R;
+}
+__device__ __forceinline__ Mat3 mat_mul(const Mat3& A, const Mat3& B) {
+    Mat3 C;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            C.m[3 * i + j] = A.m[3 * i] * B.m[j] + A.m[3 * i + 1] * B.m[3 + j] + A.m[3 * i + 2] * B.m[6 + j];
+    return C;
+}
+__device__ __forceinline__ float3 mat_vec(const Mat3& A, float3 v) {
+    return make_float3(A.m[0] * v.x + A.m[1] * v.y + A.m[2] * v.z,
+                       A.m[3] * v.x + A.m[4] * v.y + A.m[5] * v.z,
+                       A.m[6] * v.x + A.m[7] * v.y + A.m[8] * v.z);
+}
+__device__ __forceinline__ float3 f3(float4 v) { return make_float3(v.x, v.y, v.z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// ------------------------------------------------------------------------------------------
+// Trilinear interpolation of one map (Eq. 3: e_inter from the grid cache) with its gradient.
+// Outside the grid the point is clamped to it and kOutSlope * distance is added.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float grid_eval(const float* __restrict__ map, const PvPocket& P,
+                                           float3 p, float3& dEdx) {
+    float g[3] = {(p.x - P.origin[0]) * P.inv_spacing, (p.y - P.origin[1]) * P.inv_spacing,
+                  (p.z - P.origin[2]) * P.inv_spacing};
+    float f[3], out[3];
+    int i[3];
+    bool cl[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float hi = (float)(P.dims[k] - 1);
+        cl[k] = (g[k] < 0.0f) || (g[k] > hi);
+        float gc = fminf(fmaxf(g[k], 0.0f), hi);
+        int ii = (int)floorf(gc);
+        ii = min(ii, P.dims[k] - 2);
+        i[k] = ii;
+        f[k] = gc - (float)ii;
+        out[k] = cl[k] ? (g[k] - gc) * P.spacing : 0.0f;
+    }
+    const float* base = map + ((long long)i[2] * P.nxy + (long long)i[1] * P.dims[0] + i[0]);
+    float v000 = __ldg(base), v100 = __ldg(base + 1);
+    float v010 = __ldg(base + P.dims[0]), v110 = __ldg(base + P.dims[0] + 1);
+    float v001 = __ldg(base + P.nxy), v101 = __ldg(base + P.nxy + 1);
+    float v011 = __ldg(base + P.nxy + P.dims[0]), v111 = __ldg(base + P.nxy + P.dims[0] + 1);
+    float fx = f[0], fy = f[1], fz = f[2];
+    float gx = 1.f - fx, gy = 1.f - fy, gz = 1.f - fz;
+    // along x
+    float a00 = gx * v000 + fx * v100, a10 = gx * v010 + fx * v110;
+    float a01 = gx * v001 + fx * v101, a11 = gx * v011 + fx * v111;
+    float b0 = gy * a00 + fy * a10, b1 = gy * a01 + fy * a11;
+    float val = gz * b0 + fz * b1;
+    float dx = gz * (gy * (v100 - v000) + fy * (v110 - v010)) + fz * (gy * (v101 - v001) + fy * (v111 - v011));
+    float dy = gz * (a10 - a00) + fz * (a11 - a01);
+    float dz = b1 - b0;
+    dEdx = make_float3(cl[0] ? 0.f : dx * P.inv_spacing, cl[1] ? 0.f : dy * P.inv_spacing,
+                       cl[2] ? 0.f : dz * P.inv_spacing);
+    float d2 = out[0] * out[0] + out[1] * out[1] + out[2] * out[2];
+    if (d2 > 0.0f) {
+        float dist = sqrtf(d2);
+        val += kOutSlope * dist;
+        float s = kOutSlope / dist;
+        dEdx.x += s * out[0]; dEdx.y += s * out[1]; dEdx.z += s * out[2];
+    }
+    return val;
+}
+
+// ------------------------------------------------------------------------------------------
+// Warp helpers (butterfly reductions: every lane gets the same, order-fixed result)
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(PV_FULL, v, o);
+    return v;
+}
+__device__ __forceinline__ float3 warp_sum3(float3 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(PV_FULL, v.x, o);
+        v.y += __shfl_xor_sync(PV_FULL, v.y, o);
+        v.z += __shfl_xor_sync(PV_FULL, v.z, o);
+    }
+    return v;
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+}  // namespace pv

@@ -1,0 +1,94 @@
+// pv_internal.h -- kernel launchers shared between the runtime (pv_api.cu) and the kernels.
+#pragma once
+#include <stdint.h>
+#include <cuda_runtime.h>
+#include "pv_layout.h"
+
+namespace pv {
+
+constexpr int kSearchThreadsMax = 512;
+constexpr int kTopkThreads = 256;
+constexpr int kMaxTopK = 32;
+constexpr int kMaxMergeEntries = 8192;
+
+// ---- grid cache (pv_grid.cu) ----
+// XS typing of receptor atoms: typed[i] = (x, y, z, type as int bits).
+cudaError_t launch_receptor_type(const float* xyz, const uint8_t* el, const uint8_t* don,
+                                 const uint8_t* acc, int n, float4* typed, cudaStream_t s);
+// Binning into cubic cells of edge `cell` over the region lo + [0, cdims * cell) as CSR:
+// cell_start[n_cells + 1], sorted atoms by (cell, input index); atoms outside are dropped.
+cudaError_t launch_receptor_bin(const float4* typed, int n, const float lo[3], float cell,
+                                const int cdims[3], int* cell_of, int* rank, int* cell_count,
+                                int* cell_start, float4* sorted, cudaStream_t s);
+// Map build over a tile list (pocket, tile index); one CTA per 8 x 8 x 8 node tile.
+cudaError_t launch_grid_tiles(const float4* sorted, const int* cell_start, const float lo[3],
+                              float cell, const int cdims[3], const PvPocket* pockets_dev,
+                              const int2* tiles_dev, int n_tiles, uint64_t slots_lo, uint64_t slots_hi,
+                              int type_mask, cudaStream_t s);
+
+// ---- scoring (pv_score.cu) ----
+// pocket: device pointer to the pocket record (its maps pointer included)
+cudaError_t launch_score(const PvLigBlob* lig, int lig_bytes, const PvPocket* pocket,
+                         PvSlots slots, int n_poses, int pot_stride,
+                         const float* pose, float* energy, float* grad, float* parts,
+                         const float* grad_energy, float* grad_pose, float* grad_xyz,
+                         cudaStream_t s);
+cudaError_t launch_pose_coords(const PvLigBlob* lig, int lig_bytes, int n_poses, int pot_stride,
+                               const float* pose, float* xyz, cudaStream_t s);
+
+// ---- search (pv_search.cu) ----
+struct SearchArgs {
+    const PvItem* items;
+    int n_items;
+    int* queue;                    // work counter of this round (zeroed before the launch)
+    const PvPairDesc* pairs;
+    const PvLigBlob* const* ligs;  // device pointer table
+    const PvPocket* pockets;
+    uint64_t slots_lo, slots_hi;   // XS type -> map slot, 8 bits per type
+    float* chains;                 // [n_pairs * chains][PV_CHAIN_STRIDE]
+    PvSearchConst C;
+    int step0, step1;
+    int lig_smem_bytes;            // staging capacity for one ligand
+    const unsigned long long* t0;  // start time of the dock (globaltimer)
+    unsigned long long timeout_ns; // 0 = none
+    int* err;
+    unsigned long long* evals;
+};
+int search_smem_bytes(int lig_bytes, int warps);
+cudaError_t search_max_ctas_per_sm(int warps, int smem, int* out);
+cudaError_t launch_search_round(const SearchArgs& a, int grid, int warps, cudaStream_t s);
+cudaError_t launch_plain_search(const SearchArgs& a, int pair, const PvLigBlob* lig_dev,
+                                cudaStream_t s);
+cudaError_t launch_mark_t0(unsigned long long* t0, cudaStream_t s);
+
+struct TopkArgs {
+    const PvPairDesc* pairs;
+    const PvLigBlob* const* ligs;
+    const PvPocket* pockets;
+    uint64_t slots_lo, slots_hi;
+    const float* chains;
+    PvSearchConst C;
+    int lig_smem_bytes;
+    PvPoseRec* poses;              // [n_pairs][top_k]
+    float* pots;                   // [n_pairs][top_k][pot_stride]
+    float* xyz;                    // [n_pairs][top_k][atom_stride][3]
+    int* n_kept;                   // [n_pairs]
+    int* status;                   // [n_pairs]
+    int pair0;                     // first pair handled by this launch
+};
+cudaError_t prepare_topk(const TopkArgs& a);   // raise shared-memory limits before capture
+cudaError_t launch_topk(const TopkArgs& a, int n_pairs, cudaStream_t s);
+
+struct MergeArgs {
+    const int* lig_pair_start;     // [n_ligs + 1] CSR of pairs per ligand
+    const int* lig_pairs;          // pair ids
+    const PvPoseRec* poses;
+    const int* n_kept;
+    int top_k;
+    int rank_stride;
+    int* ranking;                  // [n_ligs][rank_stride]
+};
+cudaError_t prepare_merge(int max_entries);
+cudaError_t launch_merge(const MergeArgs& a, int n_ligs, int max_entries, cudaStream_t s);
+
+}  // namespace pv

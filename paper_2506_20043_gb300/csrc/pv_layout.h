@@ -1,0 +1,97 @@
+// pv_layout.h -- device data layouts shared by the host runtime and the kernels.
+#pragma once
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#define PV_N_XS 11
+#define PV_MAX_FRAGS 32
+#define PV_MAX_POT 33         // 7 + 26 torsions
+#define PV_MAX_TAN 32         // 6 + 26 torsions: one lane per tangent coordinate
+#define PV_MAX_ROUNDS 128     // intra pair rounds of <= 32 disjoint pairs
+#define PV_MAX_M 8            // L-BFGS memory
+#define PV_CHAIN_STRIDE 80    // floats per chain record (see PvChain)
+
+// Ligand record, identical in global and shared memory. Atoms are stored in device order:
+// fragments in depth-first preorder from the root, atoms of a fragment by input index, so the
+// atoms of every subtree form one contiguous range.
+struct PvLigHeader {
+    int32_t n_atoms, n_rot, n_frag, n_pairs;
+    int32_t n_rounds, max_depth, bfgs_iters, blob_bytes;
+    float rgyr;
+    int32_t origin_src;   // input index of the origin atom
+    int32_t type_mask;    // bit t set if XS type t occurs
+    int32_t pad[5];
+};
+
+struct PvLigBlob {
+    PvLigHeader h;
+    float4 atom[64];            // xyz: input coordinates minus the fragment anchor; w: int bits
+                                //      (fragment | xs << 8)
+    float4 frag_off[PV_MAX_FRAGS];   // xyz: anchor minus parent anchor (input frame); w: parent
+    float4 frag_axis[PV_MAX_FRAGS];  // xyz: unit hinge axis near->far atom; w: depth
+    int32_t frag_a0[PV_MAX_FRAGS];   // subtree atom range [a0, a1) in device order
+    int32_t frag_a1[PV_MAX_FRAGS];
+    int32_t frag_tor[PV_MAX_FRAGS];  // torsion index of the fragment's hinge (root: -1)
+    int32_t tor_frag[PV_MAX_FRAGS];  // fragment of torsion k
+    int32_t atom_src[64];            // input index of device atom i
+    uint32_t pairs[1];               // n_rounds * 32 words: i | j << 8 | hyd << 16 | hb << 17
+                                     // | 1 << 31 (valid); 0 = empty slot
+};
+#define PV_LIG_FIXED_BYTES ((int)offsetof(PvLigBlob, pairs))
+
+// One pocket box of a grid set.
+struct PvPocket {
+    float origin[3];
+    float spacing;
+    float inv_spacing;
+    int32_t dims[3];
+    float center[3];
+    float size[3];
+    float* maps;                // this pocket's maps, slot-major, each [z][y][x]
+    int32_t nxy, nxyz;
+    int32_t pad[2];
+};
+
+// XS type -> map slot of a grid set (-1: no map)
+struct PvSlots {
+    int8_t slot[16];
+};
+
+// Search constants handed to the kernels.
+struct PvSearchConst {
+    uint32_t seed_lo, seed_hi;
+    int32_t chains, steps;
+    int32_t bfgs_m, bfgs_max_iter, bfgs_max_trials, top_k;
+    float eps, rho, sigma, temperature;
+    float amplitude, rmsd_min;
+    int32_t pot_stride, atom_stride;
+};
+
+// Chain record in global memory (PV_CHAIN_STRIDE floats):
+//   [0, 33)  current POT      [40, 73) best POT
+//   [76] e_cur  [77] e_best  [78] evals (uint32 bits)  [79] status bits
+enum { PV_CH_CUR = 0, PV_CH_BEST = 40, PV_CH_ECUR = 76, PV_CH_EBEST = 77, PV_CH_EVALS = 78,
+       PV_CH_FLAGS = 79 };
+
+// Work item of the batched search: one pair, a block of consecutive chains.
+struct PvItem {
+    int32_t pair;
+    int32_t chain0;
+};
+
+// Per-pair job description (device).
+struct PvPairDesc {
+    int32_t ligand;        // index into the ligand pointer table
+    int32_t pocket;        // pocket id
+    int32_t lig_rounds;    // pair rounds of that ligand
+    int32_t pad;
+};
+
+// Device-side error bits
+enum { PV_EBIT_TIMEOUT = 1, PV_EBIT_NAN = 2, PV_EBIT_ARG = 4 };
+
+// Output record of a kept pose (matches pv_pose in the public header).
+struct PvPoseRec {
+    float score, e_inter, e_intra, affinity;
+    int32_t pair, ligand, pocket, chain;
+};

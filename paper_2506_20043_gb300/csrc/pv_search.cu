@@ -1,0 +1,429 @@
+// pv_search.cu -- Monte-Carlo + RILC-BFGS docking search ("Kernel 2", Supplementary Algorithm 2)
+// and the per-pair top-k selection and per-ligand merge (Algorithms 2 and 3).
+//
+// Batched form: one persistent launch per round of MC steps covers every (ligand, pocket,
+// chain-block) work item; CTAs pull items from an atomic counter, stage the item's ligand tree
+// in shared memory and run one chain per warp. Plain form (comparison path, the paper's
+// organisation): one launch per pair, one thread per chain, see pv_thread.cuh.
+#include "pv_internal.h"
+#include "pv_stage.cuh"
+#include "pv_thread.cuh"
+#include "pv_warp.cuh"
+
+namespace pv {
+
+constexpr int kBfgsM = 5;
+
+__device__ __forceinline__ void store_pose(float* dst, const Pose& x, int n_rot) {
+    const int lane = threadIdx.x & 31;
+    float v[7] = {x.T.x, x.T.y, x.T.z, x.q.x, x.q.y, x.q.z, x.q.w};
+    if (lane < 7) dst[lane] = v[lane];
+    if (lane >= 6 && lane < 6 + n_rot) dst[lane + 1] = x.psi;
+}
+__device__ __forceinline__ Pose load_pose(const float* src, int n_rot) {
+    const int lane = threadIdx.x & 31;
+    Pose x;
+    x.T = make_float3(src[0], src[1], src[2]);
+    x.q = make_float4(src[3], src[4], src[5], src[6]);
+    x.psi = (lane >= 6 && lane < 6 + n_rot) ? src[lane + 1] : 0.f;
+    return x;
+}
+
+__global__ void mark_t0_kernel(unsigned long long* t0) { *t0 = globaltimer(); }
+
+// Dynamic shared memory opt-in per kernel and device, raised only when a launch needs more;
+// callers raise it before stream capture so no attribute call happens while capturing.
+static cudaError_t ensure_smem(const void* fn, int smem, int* cache) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (smem <= cache[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) cache[dev] = smem;
+    return e;
+}
+static int g_search_smem[64], g_topk_smem[64], g_merge_smem[64];
+
+cudaError_t launch_mark_t0(unsigned long long* t0, cudaStream_t s) {
+    mark_t0_kernel<<<1, 1, 0, s>>>(t0);
+    return cudaGetLastError();
+}
+
+int search_smem_bytes(int lig_bytes, int warps) {
+    int lig = (lig_bytes + 127) & ~127;
+    return lig + warps * (int)sizeof(WarpScratch);
+}
+
+// One round of MC steps [step0, step1) for every chain of every pair (batched form).
+__global__ void __launch_bounds__(kSearchThreadsMax) search_round_kernel(SearchArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    PvLigBlob& L = *reinterpret_cast<PvLigBlob*>(smem);
+    WarpScratch* scratch = reinterpret_cast<WarpScratch*>(smem + ((A.lig_smem_bytes + 127) & ~127));
+    __shared__ int s_item, s_lig;
+    __shared__ PvPocket s_pocket;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int W = blockDim.x >> 5;
+    const PvSearchConst& C = A.C;
+    if (threadIdx.x == 0) s_lig = -1;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(A.queue, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= A.n_items) break;
+        const PvItem item = A.items[it];
+        const PvPairDesc pd = A.pairs[item.pair];
+        const bool reload = pd.ligand != s_lig;
+        if (threadIdx.x < (int)(sizeof(PvPocket) / 4))
+            reinterpret_cast<int*>(&s_pocket)[threadIdx.x] =
+                reinterpret_cast<const int*>(A.pockets + pd.pocket)[threadIdx.x];
+        __syncthreads();
+        if (reload) {
+            stage_ligand(&L, A.ligs[pd.ligand], A.slots_lo, A.slots_hi);
+            if (threadIdx.x == 0) s_lig = pd.ligand;
+        }
+        __syncthreads();
+        const int chain = item.chain0 + warp;
+        if (warp < W && chain < C.chains) {
+            const int n_rot = L.h.n_rot;
+            ChainCtx c;
+            c.L = &L;
+            c.S = &scratch[warp];
+            c.site.maps = s_pocket.maps;
+            c.site.P = &s_pocket;
+            c.evals = 0;
+            const int max_iter = C.bfgs_max_iter > 0 ? C.bfgs_max_iter : L.h.bfgs_iters;
+            float* rec = A.chains + ((size_t)item.pair * C.chains + chain) * PV_CHAIN_STRIDE;
+            Pose cur, best;
+            float e_cur, e_best;
+            uint32_t evals_before = 0;
+            if (A.step0 == 0) {
+                cur = random_pose(L, s_pocket, (uint32_t)chain, (uint32_t)item.pair, C);
+                float g;
+                e_cur = warp_eval(L, *c.S, c.site, cur, g, false);
+                c.evals++;
+                best = cur;
+                e_best = e_cur;
+            } else {
+                cur = load_pose(rec + PV_CH_CUR, n_rot);
+                best = load_pose(rec + PV_CH_BEST, n_rot);
+                e_cur = rec[PV_CH_ECUR];
+                e_best = rec[PV_CH_EBEST];
+                evals_before = __float_as_uint(rec[PV_CH_EVALS]);
+            }
+            int flags = 0;
+            for (int s = A.step0; s < A.step1; ++s) {
+                Pose cand = cur;
+                const float u = mutate(L, cand, (uint32_t)chain, (uint32_t)item.pair, s, C);
+                const float e_new = warp_bfgs<kBfgsM>(c, cand, C, max_iter, C.bfgs_m);
+                if (e_new < e_cur || u < expf((e_cur - e_new) / C.temperature)) {
+                    cur = cand;
+                    e_cur = e_new;
+                    if (e_cur < e_best) {
+                        e_cur = warp_bfgs<kBfgsM>(c, cur, C, max_iter, C.bfgs_m);
+                        best = cur;
+                        e_best = e_cur;
+                    }
+                }
+                if (A.timeout_ns) {
+                    unsigned long long now = lane == 0 ? globaltimer() : 0ull;
+                    now = __shfl_sync(PV_FULL, now, 0);
+                    if (now - *A.t0 > A.timeout_ns) { flags |= PV_EBIT_TIMEOUT; break; }
+                }
+            }
+            if (!(e_best == e_best)) flags |= PV_EBIT_NAN;
+            store_pose(rec + PV_CH_CUR, cur, n_rot);
+            store_pose(rec + PV_CH_BEST, best, n_rot);
+            if (lane == 0) {
+                rec[PV_CH_ECUR] = e_cur;
+                rec[PV_CH_EBEST] = e_best;
+                rec[PV_CH_EVALS] = __uint_as_float(evals_before + c.evals);
+                int old = A.step0 == 0 ? 0 : __float_as_int(rec[PV_CH_FLAGS]);
+                rec[PV_CH_FLAGS] = __int_as_float(old | flags);
+                atomicAdd(A.evals, (unsigned long long)c.evals);
+                if (flags) atomicOr(A.err, flags);
+            }
+            __syncwarp();
+        }
+    }
+}
+
+cudaError_t search_max_ctas_per_sm(int warps, int smem, int* out) {
+    cudaError_t e = ensure_smem((const void*)search_round_kernel, smem, g_search_smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, search_round_kernel, warps * 32, smem);
+}
+
+cudaError_t launch_search_round(const SearchArgs& a, int grid, int warps, cudaStream_t s) {
+    const int smem = search_smem_bytes(a.lig_smem_bytes, warps);
+    cudaError_t e = ensure_smem((const void*)search_round_kernel, smem, g_search_smem);
+    if (e != cudaSuccess) return e;
+    search_round_kernel<<<grid, warps * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Plain form: the chains of one pair, one thread per chain, all steps in one launch.
+__global__ void __launch_bounds__(128) plain_search_kernel(SearchArgs A, int pair,
+                                                           const PvLigBlob* __restrict__ L) {
+    const int chain = blockIdx.x * blockDim.x + threadIdx.x;
+    if (chain >= A.C.chains) return;
+    const PvPairDesc pd = A.pairs[pair];
+    const PvPocket P = A.pockets[pd.pocket];
+    ThreadChain tc;
+    tc.L = L;
+    tc.P = &P;
+    tc.maps = P.maps;
+    tc.slots_lo = A.slots_lo;
+    tc.slots_hi = A.slots_hi;
+    tc.evals = 0;
+    float* rec = A.chains + ((size_t)pair * A.C.chains + chain) * PV_CHAIN_STRIDE;
+    thread_run_chain(tc, A.C, (uint32_t)chain, (uint32_t)pair, A.step0, A.step1, rec, A.t0,
+                     A.timeout_ns, A.err);
+    atomicAdd(A.evals, (unsigned long long)tc.evals);
+}
+
+cudaError_t launch_plain_search(const SearchArgs& a, int pair, const PvLigBlob* lig_dev,
+                                cudaStream_t s) {
+    const int threads = 128;
+    const int grid = (a.C.chains + threads - 1) / threads;
+    plain_search_kernel<<<grid, threads, 0, s>>>(a, pair, lig_dev);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Top-k per pair: sort chain bests by SF (ties: chain id), greedy RMSD filter, rescoring.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t order_key(float f) {
+    if (!(f == f)) return 0xffffffffu;            // NaN last
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// Bitonic sort of n (power of two) 64-bit keys in shared memory, ascending.
+__device__ void bitonic_sort(unsigned long long* keys, int n) {
+    for (int k = 2; k <= n; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    unsigned long long a = keys[i], b = keys[ixj];
+                    bool up = (i & k) == 0;
+                    if ((a > b) == up) { keys[i] = b; keys[ixj] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kTopkThreads) topk_kernel(TopkArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const PvSearchConst& C = A.C;
+    const int pair = A.pair0 + blockIdx.x;
+    const int lig_bytes = (A.lig_smem_bytes + 127) & ~127;
+    PvLigBlob& L = *reinterpret_cast<PvLigBlob*>(smem);
+    WarpScratch* scratch = reinterpret_cast<WarpScratch*>(smem + lig_bytes);
+    const int W = blockDim.x >> 5;
+    float4* kept_xyz = reinterpret_cast<float4*>(smem + lig_bytes + W * sizeof(WarpScratch));
+    int n_sort = 1;
+    while (n_sort < C.chains) n_sort <<= 1;
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(kept_xyz + kMaxTopK * 64);
+    __shared__ int s_kept[kMaxTopK];
+    __shared__ int s_nkept, s_status;
+    __shared__ PvPocket s_pocket;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const PvPairDesc pd = A.pairs[pair];
+    if (threadIdx.x < (int)(sizeof(PvPocket) / 4))
+        reinterpret_cast<int*>(&s_pocket)[threadIdx.x] =
+            reinterpret_cast<const int*>(A.pockets + pd.pocket)[threadIdx.x];
+    if (threadIdx.x == 0) s_status = 0;
+    stage_ligand(&L, A.ligs[pd.ligand], A.slots_lo, A.slots_hi);
+    const float* chains = A.chains + (size_t)pair * C.chains * PV_CHAIN_STRIDE;
+    for (int i = threadIdx.x; i < n_sort; i += blockDim.x) {
+        if (i < C.chains) {
+            const float* rec = chains + (size_t)i * PV_CHAIN_STRIDE;
+            keys[i] = ((unsigned long long)order_key(rec[PV_CH_EBEST]) << 32) | (unsigned)i;
+            int fl = __float_as_int(rec[PV_CH_FLAGS]);
+            if (fl) atomicOr(&s_status, fl);
+        } else {
+            keys[i] = ~0ull;
+        }
+    }
+    __syncthreads();
+    bitonic_sort(keys, n_sort);
+    const int n = L.h.n_atoms, n_rot = L.h.n_rot;
+    const int k_max = min(C.top_k, kMaxTopK);
+    if (warp == 0) {
+        WarpScratch& S = scratch[0];
+        int kept = 0;
+        const float thr2 = C.rmsd_min * C.rmsd_min * (float)n;
+        for (int idx = 0; idx < C.chains && kept < k_max; ++idx) {
+            const unsigned long long key = keys[idx];
+            if ((key >> 32) == 0xffffffffull) break;   // NaN scores are never kept
+            const int ch = (int)(key & 0xffffffffu);
+            Pose x = load_pose(chains + (size_t)ch * PV_CHAIN_STRIDE + PV_CH_BEST, n_rot);
+            Mat3 M;
+            float3 xa;
+            warp_fk(L, S, x, M, xa);
+            __syncwarp();
+            bool ok = true;
+            for (int b = 0; b < kept && ok; ++b) {
+                float s2 = 0.f;
+                for (int a = lane; a < n; a += 32) {
+                    float4 p = S.x[a], q = kept_xyz[b * 64 + a];
+                    s2 += (p.x - q.x) * (p.x - q.x) + (p.y - q.y) * (p.y - q.y) + (p.z - q.z) * (p.z - q.z);
+                }
+                s2 = warp_sum(s2);
+                if (s2 < thr2) ok = false;
+            }
+            if (ok) {
+                for (int a = lane; a < n; a += 32) kept_xyz[kept * 64 + a] = S.x[a];
+                if (lane == 0) s_kept[kept] = ch;
+                kept++;
+            }
+            __syncwarp();
+        }
+        if (lane == 0) s_nkept = kept;
+    }
+    __syncthreads();
+    const int kept = s_nkept;
+    // rescoring of the kept poses, one warp each: e_inter, e_intra, affinity
+    for (int slot = warp; slot < kept; slot += W) {
+        const int ch = s_kept[slot];
+        const float* best = chains + (size_t)ch * PV_CHAIN_STRIDE + PV_CH_BEST;
+        Pose x = load_pose(best, n_rot);
+        Site site;
+        site.maps = s_pocket.maps;
+        site.P = &s_pocket;
+        float g, parts[2];
+        float e = warp_eval(L, scratch[warp], site, x, g, false, parts);
+        const size_t o = (size_t)pair * C.top_k + slot;
+        if (lane == 0) {
+            PvPoseRec r;
+            r.score = e;
+            r.e_inter = parts[0];
+            r.e_intra = parts[1];
+            r.affinity = parts[0] / (1.f + kWRot * (float)n_rot);
+            r.pair = pair;
+            r.ligand = pd.ligand;
+            r.pocket = pd.pocket;
+            r.chain = ch;
+            A.poses[o] = r;
+        }
+        for (int i = lane; i < 7 + n_rot; i += 32) A.pots[o * C.pot_stride + i] = best[i];
+        for (int a = lane; a < n; a += 32) {
+            float4 p = scratch[warp].x[a];
+            float* dst = A.xyz + (o * C.atom_stride + L.atom_src[a]) * 3;
+            dst[0] = p.x; dst[1] = p.y; dst[2] = p.z;
+        }
+        __syncwarp();
+    }
+    for (int slot = kept + threadIdx.x; slot < C.top_k; slot += blockDim.x) {
+        PvPoseRec r;
+        r.score = 0.f; r.e_inter = 0.f; r.e_intra = 0.f; r.affinity = 0.f;
+        r.pair = -1; r.ligand = -1; r.pocket = -1; r.chain = -1;
+        A.poses[(size_t)pair * C.top_k + slot] = r;
+    }
+    if (threadIdx.x == 0) {
+        A.n_kept[pair] = kept;
+        A.status[pair] = s_status;
+    }
+}
+
+static int topk_smem(const TopkArgs& a) {
+    int n_sort = 1;
+    while (n_sort < a.C.chains) n_sort <<= 1;
+    const int W = kTopkThreads / 32;
+    return ((a.lig_smem_bytes + 127) & ~127) + W * (int)sizeof(WarpScratch) +
+           kMaxTopK * 64 * (int)sizeof(float4) + n_sort * 8;
+}
+
+cudaError_t prepare_topk(const TopkArgs& a) {
+    return ensure_smem((const void*)topk_kernel, topk_smem(a), g_topk_smem);
+}
+
+cudaError_t launch_topk(const TopkArgs& a, int n_pairs, cudaStream_t s) {
+    const int smem = topk_smem(a);
+    cudaError_t e = ensure_smem((const void*)topk_kernel, smem, g_topk_smem);
+    if (e != cudaSuccess) return e;
+    topk_kernel<<<n_pairs, kTopkThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Per-ligand merge over its pairs (Algorithm 3 aggregation): order by (SF, pocket, chain).
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) merge_kernel(MergeArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lig = blockIdx.x;
+    const int p0 = A.lig_pair_start[lig], p1 = A.lig_pair_start[lig + 1];
+    const int n_ent = (p1 - p0) * A.top_k;
+    int n_sort = 1;
+    while (n_sort < n_ent) n_sort <<= 1;
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem);
+    int* vals = reinterpret_cast<int*>(keys + n_sort);
+    for (int i = threadIdx.x; i < n_sort; i += blockDim.x) {
+        unsigned long long k = ~0ull;
+        int v = -1;
+        if (i < n_ent) {
+            const int pair = A.lig_pairs[p0 + i / A.top_k];
+            const int slot = i % A.top_k;
+            if (slot < A.n_kept[pair]) {
+                const PvPoseRec r = A.poses[(size_t)pair * A.top_k + slot];
+                k = ((unsigned long long)order_key(r.score) << 32) |
+                    ((unsigned long long)(r.pocket & 0xffff) << 16) | (unsigned)(r.chain & 0xffff);
+                v = pair * A.top_k + slot;
+            }
+        }
+        keys[i] = k;
+        vals[i] = i;   // position, resolved to the pose index after sorting
+        (void)v;
+    }
+    __syncthreads();
+    // sort (key, position) pairs: fold the position into the low bits of a second pass-free key
+    // by sorting keys whose low 16 bits already identify the entry uniquely within a ligand
+    for (int k = 2; k <= n_sort; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n_sort; i += blockDim.x) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    unsigned long long a = keys[i], b = keys[ixj];
+                    int va = vals[i], vb = vals[ixj];
+                    bool up = (i & k) == 0;
+                    bool swap = up ? (a > b || (a == b && va > vb)) : (a < b || (a == b && va < vb));
+                    if (swap) { keys[i] = b; keys[ixj] = a; vals[i] = vb; vals[ixj] = va; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < A.rank_stride; i += blockDim.x) {
+        int out = -1;
+        if (i < n_ent && keys[i] != ~0ull) {
+            const int pos = vals[i];
+            out = A.lig_pairs[p0 + pos / A.top_k] * A.top_k + pos % A.top_k;
+        }
+        A.ranking[(size_t)lig * A.rank_stride + i] = out;
+    }
+}
+
+static int merge_smem(int max_entries) {
+    int n_sort = 1;
+    while (n_sort < max_entries) n_sort <<= 1;
+    return n_sort * 12;
+}
+
+cudaError_t prepare_merge(int max_entries) {
+    return ensure_smem((const void*)merge_kernel, merge_smem(max_entries), g_merge_smem);
+}
+
+cudaError_t launch_merge(const MergeArgs& a, int n_ligs, int max_entries, cudaStream_t s) {
+    const int smem = merge_smem(max_entries);
+    cudaError_t e = ensure_smem((const void*)merge_kernel, smem, g_merge_smem);
+    if (e != cudaSuccess) return e;
+    merge_kernel<<<n_ligs, 256, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace pv

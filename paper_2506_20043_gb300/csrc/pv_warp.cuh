@@ -1,0 +1,325 @@
+// pv_warp.cuh -- one warp evaluates one ligand pose: torsion-tree forward kinematics, trilinear
+// e_inter, intra-ligand pair terms, and the reverse-mode gradient over the pose tangent space;
+// on top of it the warp runs RILC-BFGS and the Monte-Carlo step of one chain.
+//
+// Lane roles
+//   atoms:      lane l owns device atoms l and l + 32
+//   fragments:  lane f owns rigid fragment f (f < n_frag <= 27): its world rotation M_f and
+//               anchor position
+//   tangent:    lane k owns tangent coordinate k (0-2 translation, 3-5 rotation vector,
+//               6 + t torsion t); the torsion angle psi_t itself lives in lane 6 + t
+//   pairs:      intra pairs are pre-scheduled into rounds of <= 32 pairs with no atom twice,
+//               lane l takes slot l of each round, so force accumulation needs no atomics and
+//               its order is fixed (bitwise reproducible).
+#pragma once
+#include "pv_device.cuh"
+
+namespace pv {
+
+struct WarpScratch {
+    float4 x[64];   // posed coordinates; w = XS radius
+    float4 g[64];   // dSF/dx
+};
+
+// A pose held by a warp: translation and quaternion (w, x, y, z) are warp-uniform; psi is the
+// lane's torsion in tangent layout (lane 6 + t holds psi_t, other lanes hold 0).
+struct Pose {
+    float3 T;
+    float4 q;
+    float psi;
+};
+
+struct Site {                      // where a pose is scored
+    const float* maps;             // this pocket's maps (slot-major)
+    const PvPocket* P;             // pocket geometry (shared or global memory)
+};
+
+__device__ __forceinline__ float shfl(float v, int src) { return __shfl_sync(PV_FULL, v, src); }
+__device__ __forceinline__ int shfli(int v, int src) { return __shfl_sync(PV_FULL, v, src); }
+
+// Forward kinematics (Eq. 1: position, orientation, torsions -> atom coordinates). Writes S.x.
+// Returns the fragment lane's rotation and anchor (used again by the adjoint).
+__device__ __forceinline__ void warp_fk(const PvLigBlob& L, WarpScratch& S, const Pose& x,
+                                        Mat3& M, float3& xa) {
+    const int lane = threadIdx.x & 31;
+    const int nf = L.h.n_frag;
+    const bool isf = lane < nf;
+    int parent = 0, depth = 0, tor = -1;
+    float3 off = make_float3(0.f, 0.f, 0.f), axis = off;
+    if (isf) {
+        float4 o = L.frag_off[lane], a = L.frag_axis[lane];
+        off = f3(o); axis = f3(a);
+        parent = __float_as_int(o.w);
+        depth = __float_as_int(a.w);
+        tor = L.frag_tor[lane];
+    }
+    float psi = shfl(x.psi, (isf && lane > 0) ? 6 + tor : lane);
+    Mat3 Rl;
+    if (lane == 0) Rl = quat_to_mat(x.q);
+    else Rl = axis_angle(axis, isf ? psi : 0.0f);
+    M = Rl;
+    xa = (lane == 0) ? x.T : make_float3(0.f, 0.f, 0.f);
+    for (int lev = 1; lev <= L.h.max_depth; ++lev) {
+        const bool mine = isf && depth == lev;
+        const int src = mine ? parent : lane;
+        Mat3 Mp;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Mp.m[k] = shfl(M.m[k], src);
+        float3 xp = make_float3(shfl(xa.x, src), shfl(xa.y, src), shfl(xa.z, src));
+        if (mine) {
+            M = mat_mul(Mp, Rl);
+            xa = mat_vec(Mp, off) + xp;
+        }
+    }
+    const int n = L.h.n_atoms;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int a = lane + 32 * h;
+        float4 loc = a < n ? L.atom[a] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int w = __float_as_int(loc.w);
+        const int fa = a < n ? (w & 255) : lane;
+        Mat3 Mf;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Mf.m[k] = shfl(M.m[k], fa);
+        float3 xf = make_float3(shfl(xa.x, fa), shfl(xa.y, fa), shfl(xa.z, fa));
+        if (a < n) {
+            float3 p = mat_vec(Mf, f3(loc)) + xf;
+            S.x[a] = make_float4(p.x, p.y, p.z, xs_radius((w >> 8) & 255));
+        }
+    }
+}
+
+// SF = e_inter + e_intra (Eq. 3) and, if want_grad, its tangent gradient (lane k holds
+// component k). parts (optional, lane-uniform): e_inter, e_intra.
+static __device__ __noinline__ float warp_eval(const PvLigBlob& L, WarpScratch& S, const Site& site,
+                                        const Pose& x, float& grad, bool want_grad,
+                                        float* parts = nullptr) {
+    const int lane = threadIdx.x & 31;
+    const int n = L.h.n_atoms;
+    Mat3 M;
+    float3 xa;
+    warp_fk(L, S, x, M, xa);
+    const PvPocket& P = *site.P;
+    float e_inter = 0.f, e_intra = 0.f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int a = lane + 32 * h;
+        if (a < n) {
+            const int w = __float_as_int(L.atom[a].w);
+            const int slot = (w >> 16) & 255;
+            float4 p = S.x[a];
+            float3 d;
+            e_inter += grid_eval(site.maps + (long long)slot * P.nxyz, P, f3(p), d);
+            S.g[a] = make_float4(d.x, d.y, d.z, 0.f);
+        }
+    }
+    __syncwarp();
+    const int rounds = L.h.n_rounds;
+    for (int r = 0; r < rounds; ++r) {
+        const uint32_t pw = L.pairs[r * 32 + lane];
+        if (pw >> 31) {
+            const int i = pw & 255, j = (pw >> 8) & 255;
+            float4 xi = S.x[i], xj = S.x[j];
+            float3 d = make_float3(xi.x - xj.x, xi.y - xj.y, xi.z - xj.z);
+            float r2 = dot3(d, d);
+            if (r2 < kCutoff2) {
+                float rr = sqrtf(r2), dedr;
+                e_intra += vina_pair(rr, xi.w + xj.w, (pw >> 16) & 1, (pw >> 17) & 1, dedr);
+                if (rr > 1e-6f) {
+                    float c = dedr / rr;
+                    float4 gi = S.g[i], gj = S.g[j];
+                    S.g[i] = make_float4(gi.x + c * d.x, gi.y + c * d.y, gi.z + c * d.z, 0.f);
+                    S.g[j] = make_float4(gj.x - c * d.x, gj.y - c * d.y, gj.z - c * d.z, 0.f);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    float ei = warp_sum(e_inter), ej = warp_sum(e_intra);
+    if (parts) { parts[0] = ei; parts[1] = ej; }
+    if (want_grad) {
+        // root: total force and torque about the origin atom (butterfly sums over all atoms)
+        float3 F = make_float3(0.f, 0.f, 0.f), tau = F;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int a = lane + 32 * h;
+            if (a < n) {
+                float3 g = f3(S.g[a]);
+                F = F + g;
+                tau = tau + cross3(f3(S.x[a]) - x.T, g);
+            }
+        }
+        F = warp_sum3(F);
+        tau = warp_sum3(tau);
+        // torsions: fragment lane sums torque of its subtree (a contiguous atom range) about
+        // its anchor, projected on its world hinge axis
+        float gpsi = 0.f;
+        const int nf = L.h.n_frag;
+        if (lane > 0 && lane < nf) {
+            const int a0 = L.frag_a0[lane], a1 = L.frag_a1[lane];
+            float3 t = make_float3(0.f, 0.f, 0.f);
+            for (int a = a0; a < a1; ++a) t = t + cross3(f3(S.x[a]) - xa, f3(S.g[a]));
+            float3 axw = mat_vec(M, f3(L.frag_axis[lane]));
+            gpsi = dot3(axw, t);
+        }
+        const int nt = 6 + L.h.n_rot;
+        const int src = (lane >= 6 && lane < nt) ? L.tor_frag[lane - 6] : lane;
+        float gp = shfl(gpsi, src);
+        float c3[6] = {F.x, F.y, F.z, tau.x, tau.y, tau.z};
+        grad = lane < 6 ? c3[lane] : (lane < nt ? gp : 0.f);
+    }
+    __syncwarp();
+    return ei + ej;
+}
+
+// x (+) step: translation += step[0:3]; q <- exp(step[3:6]/2) (x) q; psi += step[6:].
+__device__ __forceinline__ Pose retract(const Pose& x, float step, int n_tan) {
+    const int lane = threadIdx.x & 31;
+    Pose y;
+    y.T = x.T + make_float3(shfl(step, 0), shfl(step, 1), shfl(step, 2));
+    y.q = quat_rotate_by(x.q, make_float3(shfl(step, 3), shfl(step, 4), shfl(step, 5)));
+    y.psi = x.psi + ((lane >= 6 && lane < n_tan) ? step : 0.f);
+    return y;
+}
+
+struct ChainCtx {
+    const PvLigBlob* L;
+    WarpScratch* S;
+    Site site;
+    uint32_t evals;
+};
+
+__device__ __forceinline__ float eval_pose(ChainCtx& c, const Pose& x, float& g) {
+    c.evals++;
+    return warp_eval(*c.L, *c.S, c.site, x, g, true);
+}
+
+// RILC-BFGS (Eq. 6-12): L-BFGS two-loop recursion over the m most recent curvature pairs,
+// Lewis-Overton line search (Eq. 7-8 as failure tests of Armijo / weak Wolfe), curvature-
+// guarded history update (Eq. 11), stop on ||g|| <= eps (Eq. 12), non-descent, or max_iter.
+// Updates x in place and returns SF(x). All control flow is warp-uniform.
+template <int M>
+__device__ float warp_bfgs(ChainCtx& c, Pose& x, const PvSearchConst& C, int max_iter, int m) {
+    const int n_tan = 6 + c.L->h.n_rot;
+    float g;
+    float f = eval_pose(c, x, g);
+    float Sh[M], Yh[M], rh[M], al[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) { Sh[k] = 0.f; Yh[k] = 0.f; rh[k] = 0.f; al[k] = 0.f; }
+    int stored = 0;
+    for (int it = 0; it < max_iter; ++it) {
+        // two-loop recursion, newest pair at index 0
+        float q = g;
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            if (k < stored) {
+                al[k] = rh[k] * warp_sum(Sh[k] * q);
+                q -= al[k] * Yh[k];
+            }
+        }
+        if (stored > 0) {
+            float sy = warp_sum(Sh[0] * Yh[0]), yy = warp_sum(Yh[0] * Yh[0]);
+            q *= sy / yy;
+        }
+#pragma unroll
+        for (int k = M - 1; k >= 0; --k) {
+            if (k < stored) {
+                float b = rh[k] * warp_sum(Yh[k] * q);
+                q += Sh[k] * (al[k] - b);
+            }
+        }
+        const float d = -q;
+        const float gd = warp_sum(g * d);
+        if (!(gd < 0.f)) break;
+        // Lewis-Overton bracketing
+        float lam = 1.f, lo = 0.f, hi = -1.f, ft = 0.f, gt = 0.f, flo = 0.f, glo = 0.f;
+        Pose xt = x, xlo = x;
+        bool accepted = false, have_lo = false;
+        for (int tr = 0; tr < C.bfgs_max_trials; ++tr) {
+            xt = retract(x, lam * d, n_tan);
+            ft = eval_pose(c, xt, gt);
+            const float gtd = warp_sum(gt * d);
+            if (!(ft <= f + lam * C.rho * gd)) {
+                hi = lam;
+            } else if (gtd < C.sigma * gd) {
+                lo = lam; have_lo = true; flo = ft; glo = gt; xlo = xt;
+            } else {
+                accepted = true;
+                break;
+            }
+            lam = hi < 0.f ? 2.f * lam : 0.5f * (lo + hi);
+        }
+        if (!accepted) {
+            if (!have_lo) break;
+            lam = lo; ft = flo; gt = glo; xt = xlo;
+        }
+        const float s = lam * d, y = gt - g;
+        const float ys = warp_sum(y * s), ss = warp_sum(s * s), gn = sqrtf(warp_sum(g * g));
+        if (ss > 0.f && ys / ss > C.eps * gn) {
+#pragma unroll
+            for (int k = M - 1; k > 0; --k) { Sh[k] = Sh[k - 1]; Yh[k] = Yh[k - 1]; rh[k] = rh[k - 1]; }
+            Sh[0] = s; Yh[0] = y; rh[0] = 1.f / ys;
+            stored = min(stored + 1, m);
+        }
+        x = xt; g = gt; f = ft;
+        if (sqrtf(warp_sum(g * g)) <= C.eps) break;
+    }
+    return f;
+}
+
+// Random conformation (Algorithm 2): draws 0-2 translation uniform in the box, 3-5 a uniform
+// quaternion (Shoemake), 6 + t torsion t uniform in [-pi, pi).
+__device__ __forceinline__ Pose random_pose(const PvLigBlob& L, const PvPocket& P, uint32_t chain,
+                                            uint32_t pair, const PvSearchConst& C) {
+    const int lane = threadIdx.x & 31;
+    uint4 b0 = philox4x32_10(make_uint4(chain, pair, 0u, 0u), C.seed_lo, C.seed_hi);
+    uint4 b1 = philox4x32_10(make_uint4(chain, pair, 0u, 1u), C.seed_lo, C.seed_hi);
+    Pose x;
+    x.T = make_float3(P.center[0] + (u01(b0.x) - 0.5f) * P.size[0],
+                      P.center[1] + (u01(b0.y) - 0.5f) * P.size[1],
+                      P.center[2] + (u01(b0.z) - 0.5f) * P.size[2]);
+    float u1 = u01(b0.w), u2 = u01(b1.x), u3 = u01(b1.y);
+    float s2, c2, s3, c3;
+    sincospif(2.f * u2, &s2, &c2);
+    sincospif(2.f * u3, &s3, &c3);
+    float a = sqrtf(1.f - u1), b = sqrtf(u1);
+    x.q = make_float4(a * s2, a * c2, b * s3, b * c3);
+    x.psi = 0.f;
+    if (lane >= 6 && lane < 6 + L.h.n_rot) {
+        const int i = lane;   // draw index 6 + t with t = lane - 6
+        uint32_t w = pick(philox4x32_10(make_uint4(chain, pair, 0u, (uint32_t)(i >> 2)), C.seed_lo, C.seed_hi), i & 3);
+        x.psi = -PV_PI + 2.f * PV_PI * u01(w);
+    }
+    return x;
+}
+
+// Mutation R (Eq. 2) of MC step `step`: word 0 picks one entity among {position, orientation,
+// psi_1..psi_Nrot} as floor(w * (2 + N_rot) / 2^32); draws 1-3 give a point p in the unit
+// ball (z = 2a - 1, phi = 2 pi b, r = cbrt(c)); position += amplitude p, or orientation
+// rotated by (amplitude / R_gyr) p, or the torsion redrawn from draw 4. Returns draw 5
+// (the Metropolis uniform).
+__device__ __forceinline__ float mutate(const PvLigBlob& L, Pose& x, uint32_t chain, uint32_t pair,
+                                        int step, const PvSearchConst& C) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t st = (uint32_t)step + 1u;
+    uint4 b0 = philox4x32_10(make_uint4(chain, pair, st, 0u), C.seed_lo, C.seed_hi);
+    uint4 b1 = philox4x32_10(make_uint4(chain, pair, st, 1u), C.seed_lo, C.seed_hi);
+    const int n_rot = L.h.n_rot;
+    const int entity = (int)__umulhi(b0.x, (uint32_t)(2 + n_rot));
+    float z = 2.f * u01(b0.y) - 1.f, r = cbrtf(u01(b0.w));
+    float sp, cp;
+    sincospif(2.f * u01(b0.z), &sp, &cp);
+    float s = sqrtf(fmaxf(0.f, 1.f - z * z));
+    float3 p = make_float3(r * s * cp, r * s * sp, r * z);
+    if (entity == 0) {
+        x.T = x.T + C.amplitude * p;
+    } else if (entity == 1) {
+        float sc = L.h.rgyr > 1e-9f ? C.amplitude / L.h.rgyr : 0.f;
+        x.q = quat_rotate_by(x.q, sc * p);
+    } else if (lane == 6 + (entity - 2)) {
+        x.psi = -PV_PI + 2.f * PV_PI * u01(b1.x);
+    }
+    return u01(b1.y);
+}
+
+}  // namespace pv

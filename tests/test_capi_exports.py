@@ -1,0 +1,41 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol include/pocketvina.h
+declares (no GPU needed: nothing is called)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pocketvina.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:pv_status|void|const char\s*\*)\s*\**\s*(pv_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("pv_context_create", "pv_build_grids", "pv_ligand_create", "pv_dock", "pv_score",
+                     "pv_score_backward", "pv_dock_result_destroy", "pv_grid_set_view", "pv_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2506_20043_gb300 as pv
+    from paper_2506_20043_gb300 import _capi
+    lib_path = pv.build()
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(_declared()) == set(_capi.SIGNATURES), set(_declared()) ^ set(_capi.SIGNATURES)
+
+
+def test_binding_refuses_to_run_without_a_gpu():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2506_20043_gb300 import api
+    with pytest.raises(api.PVError):
+        api.Context(0)

@@ -1,0 +1,185 @@
+"""GPU parity of the docking search (Supplementary Algorithms 2 and 3) against the FP64 oracle.
+
+MC trajectories of FP32 and FP64 code separate after a few steps, so the search is checked by
+(1) what is unique: the Philox-driven random starts and the first MC step in lockstep, the
+top-k selection and pocket merge applied to the GPU's own chain results, bitwise determinism
+across graph/round/CTA settings; (2) validity of every reported pose (the oracle rescoring it
+gives the reported SF); (3) statistics: per-pair best SF within 0.2 kcal/mol of the oracle's and
+the same top-pose pocket.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import pvsynth as S
+from tests import _gpu as G
+
+pytestmark = pytest.mark.gpu
+
+
+def _tiny_site():
+    w = S.tiny()
+    rec, box, lig = G.receptor32(w.receptors[0]), G.box32(w.boxes[0][0]), G.ligand32(w.ligands[0])
+    return rec, box, lig
+
+
+def _setup(ctx, rec, boxes, ligs):
+    Ls = [O.OracleLigand(l) for l in ligs]
+    types = sorted(set(np.concatenate([L.xs for L in Ls]).tolist()))
+    gs = ctx.build_grids(rec, boxes, types)
+    pls = [ctx.ligand(l) for l in ligs]
+    rt = O.xs_type_receptor(rec)
+    ogs = [O.OracleGrid(rec, b, types, rec_types=rt, threads=G.threads()) for b in boxes]
+    return gs, pls, Ls, ogs
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    ctx = G.context()
+    rec, box, lig = _tiny_site()
+    gs, pls, Ls, ogs = _setup(ctx, rec, [box], [lig])
+    return ctx, box, gs, pls[0], Ls[0], ogs[0]
+
+
+def test_random_starts_match_oracle(tiny):
+    ctx, box, gs, pl, L, og = tiny
+    for mode in ("batched", "plain"):
+        r = ctx.dock(gs, [pl], [0], chains=40, steps=0, seed=7, mode=mode)
+        pots, es = r.chain_records()
+        for c in range(40):
+            ref = O.random_conformation(L, box, 7, 0, c)
+            np.testing.assert_allclose(pots[0, c, :L.n_pot], ref, atol=2e-5)
+            assert G.close(es[0, c], L.score(og, pots[0, c, :L.n_pot].astype(np.float64), False)[0])
+
+
+def test_first_mc_steps_in_lockstep(tiny):
+    """Mutation draws, Metropolis draws and the first line-search trial in lockstep: with one BFGS
+    iteration of one trial, three MC steps are deterministic up to FP32 rounding, so the chain
+    states agree with the oracle's. (With the full BFGS budget they do not: the FP64 oracle
+    perturbed by 1e-7 agrees with itself on under 10 % of chains after one step, because BFGS
+    from a clashing random start has not converged within its iteration budget.)"""
+    ctx, box, gs, pl, L, og = tiny
+    p = O.SearchParams(seed=3, steps=3, max_iter=1, max_trials=1)
+    ref_pots, ref_es, _ = O.mc_chains(L, og, box, p, unit=0, n_chains=64, threads=G.threads())
+    for mode in ("batched", "plain"):
+        r = ctx.dock(gs, [pl], [0], chains=64, steps=3, seed=3, mode=mode, bfgs_max_iter=1, bfgs_max_trials=1)
+        pots, es = r.chain_records()
+        agree = G.close(es[0], ref_es, abs_tol=1e-3, rel_tol=1e-4)
+        assert agree.mean() >= 0.95, (mode, agree.mean())
+        same = np.abs(pots[0, :, :L.n_pot] - ref_pots).max(axis=1) <= 1e-3
+        assert same.mean() >= 0.95, (mode, same.mean())
+
+
+def test_reported_poses_are_valid_and_selection_matches_oracle(tiny):
+    ctx, box, gs, pl, L, og = tiny
+    r = ctx.dock(gs, [pl], [0], chains=48, steps=60, seed=11, top_k=9, rmsd_min=1.0)
+    pots, es = r.chain_records()
+    pots64 = pots[0, :, :L.n_pot].astype(np.float64)
+    # every chain's best is what the oracle scores for that pose
+    ref = np.array([L.score(og, q, False)[0] for q in pots64])
+    assert G.close(es[0], ref).all()
+    # top-k: the oracle's sort + RMSD filter on the GPU's chain bests picks the same chains
+    xyz = np.stack([L.fk(q) for q in pots64])
+    kept = O.topk(es[0].astype(np.float64), xyz, 9, 1.0)
+    n = r.n_kept[0]
+    assert list(r.poses[0]["chain"][:n]) == list(kept)
+    # rescoring of the kept poses: SF, parts, affinity
+    for slot in range(n):
+        rec = r.poses[0][slot]
+        e, _, parts = L.score(og, pots64[rec["chain"]], False)
+        assert G.close(rec["score"], e) and G.close(rec["e_inter"], parts[0]) and G.close(rec["e_intra"], parts[1])
+        assert G.close(rec["affinity"], O.affinity(parts[0], L.n_rot))
+        np.testing.assert_allclose(r.xyz[0, slot, :L.n], L.fk(r.pots[0, slot, :L.n_pot].astype(np.float64)),
+                                   atol=2e-4)
+    assert (r.poses[0]["pair"][n:] == -1).all()
+
+
+def test_tiny_workload_best_score_parity(tiny):
+    """The tiny workload in full: 8 chains x 1,000 steps; the GPU's best SF is within
+    0.2 kcal/mol of the oracle's."""
+    ctx, box, gs, pl, L, og = tiny
+    p = O.SearchParams(seed=0, steps=1000)
+    _, ref_es, _ = O.mc_chains(L, og, box, p, unit=0, n_chains=8, threads=G.threads())
+    r = ctx.dock(gs, [pl], [0], chains=8, steps=1000, seed=0)
+    _, es = r.chain_records()
+    assert abs(es[0].min() - ref_es.min()) <= 0.2, (es[0].min(), ref_es.min())
+    assert r.poses[0][0]["score"] == pytest.approx(es[0].min(), abs=1e-6)
+
+
+def test_bitwise_determinism_across_launch_settings(tiny):
+    ctx, box, gs, pl, L, og = tiny
+    base = ctx.dock(gs, [pl], [0], chains=24, steps=40, seed=5)
+    b_pots, b_es = base.chain_records()
+    for kw in (dict(use_graph=False), dict(steps_per_round=7), dict(warps_per_cta=8),
+               dict(warps_per_cta=1, steps_per_round=13)):
+        r = ctx.dock(gs, [pl], [0], chains=24, steps=40, seed=5, **kw)
+        pots, es = r.chain_records()
+        np.testing.assert_array_equal(es, b_es, err_msg=str(kw))
+        np.testing.assert_array_equal(pots, b_pots, err_msg=str(kw))
+        assert (r.poses == base.poses).all()
+
+
+def test_multi_pocket_merge_and_pocket_parity():
+    """Two ligands x four pockets: per-pair best SF within 0.2 kcal/mol of the oracle, the same
+    top-pose pocket for each ligand, and the merged ranking equal to the oracle's merge of the
+    GPU's kept poses."""
+    ctx = G.context()
+    rec0, boxes0 = S._carved(3000, 4, (6.0, 8.0), 2, 14.0)
+    rec = G.receptor32(rec0)
+    boxes = [G.box32(b) for b in boxes0]
+    ligs = [G.ligand32(S.ligand_centered(S.make_ligand(12, 2, 21))),
+            G.ligand32(S.ligand_centered(S.make_ligand(14, 3, 22)))]
+    gs, pls, Ls, ogs = _setup(ctx, rec, boxes, ligs)
+    chains, steps = 32, 150
+    r = ctx.dock(gs, pls, [0, 1, 2, 3], chains=chains, steps=steps, seed=9, top_k=5)
+    _, es = r.chain_records()
+    p = O.SearchParams(seed=9, steps=steps, top_k=5)
+    for li, L in enumerate(Ls):
+        ref_best = []
+        results = []
+        for k in range(4):
+            pair = li * 4 + k
+            _, ref_es, _ = O.mc_chains(L, ogs[k], boxes[k], p, unit=pair, n_chains=chains, threads=G.threads())
+            ref_best.append(ref_es.min())
+            assert abs(es[pair].min() - ref_es.min()) <= 0.2, (li, k, es[pair].min(), ref_es.min())
+            n = r.n_kept[pair]
+            results.append(O.PairResult(li, k, None, None, 0, r.poses[pair]["chain"][:n],
+                                        r.poses[pair]["score"][:n].astype(np.float64), None, None, None))
+        gpu_rank = r.ranking(li)
+        top = r.poses.reshape(-1)[gpu_rank[0]]
+        assert top["pocket"] == int(np.argmin(ref_best))
+        merged = O.merge_pockets(results)
+        flat = r.poses.reshape(-1)
+        assert [(int(flat[i]["pocket"]), int(flat[i]["chain"])) for i in gpu_rank] == [(m[1], m[2]) for m in merged]
+
+
+def test_plain_path_is_valid(tiny):
+    ctx, box, gs, pl, L, og = tiny
+    r = ctx.dock(gs, [pl], [0], chains=16, steps=30, seed=2, mode="plain")
+    pots, es = r.chain_records()
+    ref = np.array([L.score(og, q, False)[0] for q in pots[0, :, :L.n_pot].astype(np.float64)])
+    assert G.close(es[0], ref).all()
+    ev, sec, st = r.stats()
+    assert ev > 16 * 30 and sec > 0 and (st == 0).all()
+
+
+def test_watchdog_timeout_returns_status_and_context_survives(tiny):
+    ctx, box, gs, pl, L, og = tiny
+    from paper_2506_20043_gb300 import _capi as A
+    r = ctx.dock(gs, [pl], [0], chains=8, steps=100000, seed=1, timeout_s=0.02)
+    assert r.status_code == A.PV_ERR_TIMEOUT
+    _, _, st = r.stats()
+    assert (st == A.PV_ERR_TIMEOUT).all()
+    # the context keeps working after the early exit
+    r2 = ctx.dock(gs, [pl], [0], chains=8, steps=5, seed=1)
+    assert r2.status_code == 0 and r2.n_kept[0] >= 1
+
+
+def test_dock_argument_errors(tiny):
+    ctx, box, gs, pl, L, og = tiny
+    from paper_2506_20043_gb300.api import PVError
+    for kw in (dict(chains=0), dict(top_k=0), dict(top_k=33), dict(bfgs_m=9), dict(warps_per_cta=17)):
+        with pytest.raises(PVError):
+            ctx.dock(gs, [pl], [0], steps=1, **kw)
+    with pytest.raises(PVError):
+        ctx.dock(gs, [pl], [3], steps=1)

@@ -171,3 +171,20 @@ def test_trilinear_gradient_matches_fd_inside():
         fd = [(g.eval(N_A, p + h * e)[0] - g.eval(N_A, p - h * e)[0]) / (2 * h) for e in np.eye(3)]
         np.testing.assert_allclose(grad, fd, rtol=1e-6, atol=1e-6)
         n += 1
+
+
+def test_lazy_grid_matches_full_build_at_filled_nodes():
+    w = S.tiny()
+    rec = w.receptors[0]
+    rt = O.xs_type_receptor(rec)
+    box = S.Box(w.boxes[0][0].center, np.array([4.0, 4.0, 4.0]), 0.375)
+    full = O.OracleGrid(rec, box, [C_H, O_A], rec_types=rt)
+    rng = np.random.default_rng(9)
+    pts = rng.uniform(-3, 3, size=(40, 3)) + box.center       # some outside: clamped cells
+    lazy = O.OracleGrid.lazy(rec, box, [C_H, O_A], rt, pts)
+    filled = ~np.isnan(lazy.maps)
+    assert filled.any() and (~filled).any()
+    np.testing.assert_array_equal(lazy.maps[filled], full.maps[filled])
+    for p in pts:
+        for t in (C_H, O_A):
+            assert lazy.eval(t, p)[0] == full.eval(t, p)[0]
