@@ -289,6 +289,34 @@ pv_status pv_dock_result_read_chains(const pv_dock_result* r, float* dst);
 
 void pv_dock_result_destroy(pv_dock_result* r);
 
+/* -------------------------------------------------------- allocation-free grid build --- */
+
+/* Sizes of the fixed device scratch used by pv_build_grid_noalloc. */
+#define PV_NOALLOC_MAX_ATOMS 16384
+#define PV_NOALLOC_MAX_CELLS 65536
+#define PV_NOALLOC_MAX_TILES 4096
+#define PV_NOALLOC_SCRATCH_BYTES 1458688
+
+/* The maps of one pocket box, like pv_build_grids, for callers that cannot allocate device
+ * memory when they need a grid (a framework that has reserved the whole device for its own
+ * pool, or a callback/plugin that is handed buffers but may not call cudaMalloc or a caching
+ * allocator). The paper has no counterpart of this call; it is a service of this library.
+ *   - Allocates no device memory: every intermediate array lives in one fixed array of
+ *     PV_NOALLOC_SCRATCH_BYTES (about 1.4 MiB) that every GPU loading the library keeps until the
+ *     process exits. The first call on a device looks up that array's address on the device
+ *     (set-up, once per device); make that first call before any stream capture.
+ *   - The receptor may be host or device memory (mem field); at most PV_NOALLOC_MAX_ATOMS atoms.
+ *     The box may span at most PV_NOALLOC_MAX_CELLS 3 A binning cells (box plus 9 A on each
+ *     side) and PV_NOALLOC_MAX_TILES tiles of 8 x 8 x 8 nodes; beyond that PV_ERR_ARG.
+ *   - dev_maps (caller-owned device memory) receives one float32 map per distinct type in
+ *     lig_types, in increasing XS type order, each [z][y][x] with the node counts of
+ *     pv_build_grids (ceil(size / spacing) + 1 per axis).
+ *   - Work is issued on ctx's stream and is asynchronous. All calls share the one scratch
+ *     array, so calls that overlap on the GPU (different streams, threads or contexts on the
+ *     same device) race and corrupt each other's maps; serialise them. */
+pv_status pv_build_grid_noalloc(pv_context* ctx, const pv_receptor* receptor, const pv_box* box,
+                                const uint8_t* lig_types, int32_t n_types, float* dev_maps);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,7 @@ SIGNATURES = {
     "pv_dock_result_chains": (i32, [vp, C.POINTER(vp), pi32, pi32, pi32, pi32]),
     "pv_dock_result_read_chains": (i32, [vp, vp]),
     "pv_dock_result_destroy": (None, [vp]),
+    "pv_build_grid_noalloc": (i32, [vp, C.POINTER(pv_receptor), C.POINTER(pv_box), C.POINTER(C.c_uint8), i32, vp]),
 }
 
 _lib = None

@@ -138,6 +138,17 @@ static uint64_t pack_slots(const int8_t* s, int hi) {
 
 // ---------------------------------------------------------------------------- context ---
 
+bool pv::context_device_stream(pv_context* ctx, int* device, cudaStream_t* stream) {
+    if (!ctx || ctx->magic != kCtxMagic) return false;
+    *device = ctx->device;
+    *stream = ctx->stream;
+    return true;
+}
+
+void pv::context_set_error(pv_context* ctx, const char* msg) {
+    if (ctx && ctx->magic == kCtxMagic) ctx->err = msg;
+}
+
 extern "C" pv_status pv_context_create(int device, void* cuda_stream, pv_context** out) {
     if (!out) return PV_ERR_ARG;
     *out = nullptr;

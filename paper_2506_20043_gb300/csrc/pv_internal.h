@@ -4,7 +4,13 @@
 #include <cuda_runtime.h>
 #include "pv_layout.h"
 
+struct pv_context;
+
 namespace pv {
+
+// Context access for entry points defined outside pv_api.cu (false on a bad handle).
+bool context_device_stream(pv_context* ctx, int* device, cudaStream_t* stream);
+void context_set_error(pv_context* ctx, const char* msg);
 
 constexpr int kSearchThreadsMax = 512;
 constexpr int kTopkThreads = 256;
