@@ -177,6 +177,7 @@ def run_ours(args):
             ev, _, st = r.stats()
             assert (st == 0).all(), st
             s_s, n_l, _ = r.timing()
+            shape = r.launch_shape()
             search_s += s_s
             launches += n_l
             evals += ev
@@ -208,7 +209,8 @@ def run_ours(args):
                        "mc_steps": STEPS, "top_k": TOP_K, "ligand_atoms": lig.n_atoms, "ligand_torsions": lig.n_rot,
                        "intra_pairs": lig.n_pairs, "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "inputs": "receptor, ligand and boxes resident in HBM; grids rebuilt every step",
-                       "parallelism": f"{world} independent receptors, one per GPU"},
+                       "parallelism": f"{world} independent receptors, one per GPU",
+                       "search_launch": {"variant": shape[0], "chains_per_cta": shape[1]}},
             "evals_per_s": round(evals / total_t * world, 1),
             "evals_per_step_per_gpu": evals // max(args.steps, 1),
             "roofline": {"kernel": "search_round_kernel", "bound": "alu", "achieved": round(achieved, 3),

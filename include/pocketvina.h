@@ -208,13 +208,18 @@ typedef struct {
     int32_t steps_per_round;   /* batched: MC steps per kernel launch (round); 0 = automatic */
     int32_t use_graph;         /* batched: capture the launch sequence in a CUDA graph */
     int32_t warps_per_cta;     /* batched: chains per CTA; 0 = autotuned */
+    int32_t search_variant;    /* batched: register budget of the search kernel, 0..3 (0 widest,
+                                  3 = 64 registers); -1 = autotuned */
     int32_t host_copy;         /* 1: copy results to host memory before returning */
     double timeout_s;          /* watchdog per launch; 0 = none. Overrun -> PV_ERR_TIMEOUT */
 } pv_dock_params;
 
 /* Defaults: chains 64, steps 1000, seed 0, top_k 9, rmsd_min 1.0, BATCHED, m 5, max_iter 0,
  * max_trials 10, eps 1e-3, rho 1e-4, sigma 0.1, temperature 1.2, amplitude 2.0,
- * steps_per_round 0, use_graph 1, warps_per_cta 0, host_copy 1, timeout_s 0. */
+ * steps_per_round 0, use_graph 1, warps_per_cta 0, search_variant -1, host_copy 1, timeout_s 0.
+ * Autotuning (warps_per_cta 0 or search_variant -1): the first batched dock of a ligand-size
+ * bucket on a context times each candidate launch shape on two MC steps of its own work items
+ * (results are unaffected: the dock itself restarts every chain) and keeps the fastest. */
 void pv_dock_params_default(pv_dock_params* p);
 
 /* Docks every ligand into every listed pocket (Supplementary Algorithms 2 and 3). Pair
@@ -270,6 +275,9 @@ pv_status pv_dock_result_stats(const pv_dock_result* r, uint64_t* n_evals, doubl
  * kernels), their count, and the whole launch sequence (search + selection + merge). */
 pv_status pv_dock_result_timing(const pv_dock_result* r, double* search_seconds,
                                 int32_t* search_launches, double* total_seconds);
+
+/* Launch shape the batched search used (after autotuning): register variant and chains per CTA. */
+pv_status pv_dock_result_launch(const pv_dock_result* r, int32_t* search_variant, int32_t* warps_per_cta);
 
 /* Device-resident results (valid until destroy): poses [n_pairs * top_k] pv_pose,
  * n_kept [n_pairs], ranking [n_ligs][max_pairs_per_ligand * top_k] (-1 padded). */

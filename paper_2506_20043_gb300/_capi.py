@@ -35,7 +35,8 @@ class pv_dock_params(C.Structure):
                 ("bfgs_m", C.c_int32), ("bfgs_max_iter", C.c_int32), ("bfgs_max_trials", C.c_int32),
                 ("bfgs_eps", C.c_float), ("rho", C.c_float), ("sigma", C.c_float),
                 ("temperature", C.c_float), ("amplitude", C.c_float), ("steps_per_round", C.c_int32),
-                ("use_graph", C.c_int32), ("warps_per_cta", C.c_int32), ("host_copy", C.c_int32),
+                ("use_graph", C.c_int32), ("warps_per_cta", C.c_int32), ("search_variant", C.c_int32),
+                ("host_copy", C.c_int32),
                 ("timeout_s", C.c_double)]
 
 
@@ -83,6 +84,7 @@ SIGNATURES = {
     "pv_dock_result_ranking": (i32, [vp, i32, pi32, pi32]),
     "pv_dock_result_stats": (i32, [vp, C.POINTER(u64), C.POINTER(C.c_double), pi32]),
     "pv_dock_result_timing": (i32, [vp, C.POINTER(C.c_double), pi32, C.POINTER(C.c_double)]),
+    "pv_dock_result_launch": (i32, [vp, pi32, pi32]),
     "pv_dock_result_device": (i32, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),
     "pv_dock_result_chains": (i32, [vp, C.POINTER(vp), pi32, pi32, pi32, pi32]),
     "pv_dock_result_read_chains": (i32, [vp, vp]),

@@ -51,6 +51,7 @@ class DockParams:
     steps_per_round: int = 0
     use_graph: bool = True
     warps_per_cta: int = 0
+    search_variant: int = -1
     host_copy: bool = True
     timeout_s: float = 0.0
 
@@ -384,6 +385,12 @@ class DockResult:
         self.ctx._check(self.ctx.lib.pv_dock_result_timing(self.h, C.byref(s), C.byref(n), C.byref(t)),
                         "pv_dock_result_timing")
         return s.value, n.value, t.value
+
+    def launch_shape(self):
+        """(search kernel variant, chains per CTA) used by the batched search."""
+        v, w = C.c_int32(), C.c_int32()
+        self.ctx._check(self.ctx.lib.pv_dock_result_launch(self.h, C.byref(v), C.byref(w)), "pv_dock_result_launch")
+        return v.value, w.value
 
     def chain_records(self):
         """Chain states after the search, copied to the host: (best POT [n_pairs, chains,

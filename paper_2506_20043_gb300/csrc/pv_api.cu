@@ -1,6 +1,8 @@
 // pv_api.cu -- the C ABI (include/pocketvina.h): contexts, grid sets, ligands, scoring and the
 // docking driver (batched rounds captured in a CUDA graph, or the plain per-pair loop).
 #include <algorithm>
+#include <map>
+#include <tuple>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -30,6 +32,8 @@ struct pv_context {
     int sms = 0;
     cudaStream_t capture_stream = nullptr;   // graphs are captured here (the caller's stream may
                                              // be the legacy default stream, which cannot capture)
+    // autotuned (search variant, warps per CTA) per (ligand atoms / 8, pair rounds / 4)
+    std::map<std::pair<int, int>, std::pair<int, int>> tuned;
 };
 
 struct pv_grid_set {
@@ -70,6 +74,7 @@ struct pv_dock_result {
     double seconds = 0.0;
     double search_seconds = 0.0;    // the search kernel launches alone (events around them)
     int search_launches = 0;
+    int search_variant = 0, warps_per_cta = 0;   // launch shape used (batched)
 };
 
 // ---------------------------------------------------------------------------- helpers ---
@@ -564,6 +569,7 @@ extern "C" void pv_dock_params_default(pv_dock_params* p) {
     p->steps_per_round = 0;
     p->use_graph = 1;
     p->warps_per_cta = 0;
+    p->search_variant = -1;
     p->host_copy = 1;
     p->timeout_s = 0.0;
 }
@@ -592,6 +598,10 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     if (p.bfgs_max_trials < 1 || p.bfgs_max_iter < 0) return fail(ctx, PV_ERR_ARG, "bad BFGS limits");
     if (p.mode != PV_MODE_BATCHED && p.mode != PV_MODE_PLAIN) return fail(ctx, PV_ERR_ARG, "unknown mode");
     if (p.warps_per_cta < 0 || p.warps_per_cta > 16) return fail(ctx, PV_ERR_ARG, "warps_per_cta must be 0..16");
+    if (p.search_variant < -1 || p.search_variant >= kSearchVariants)
+        return fail(ctx, PV_ERR_ARG, "search_variant must be -1..3");
+    if (p.search_variant >= 0 && p.warps_per_cta * 32 > search_variant_max_warps(p.search_variant) * 32)
+        return fail(ctx, PV_ERR_ARG, "warps_per_cta exceeds the search variant's CTA size");
     if (!(p.temperature > 0.f)) return fail(ctx, PV_ERR_ARG, "temperature must be > 0");
     if (n_pairs < 1) return fail(ctx, PV_ERR_ARG, "no pairs");
     int max_rot = 0, max_atoms = 0, max_blob = 0;
@@ -637,13 +647,35 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
         return fail(ctx, PV_ERR_ARG, "pairs per ligand x top_k exceeds the merge capacity (8192)");
     }
     // work items: pocket-major for map locality, then pair, then chain block
-    int W = p.warps_per_cta > 0 ? p.warps_per_cta : 4;
     std::vector<int> order(n_pairs);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pair_pocket[a] < pair_pocket[b]; });
-    std::vector<PvItem> items;
-    for (int q : order)
-        for (int c0 = 0; c0 < p.chains; c0 += W) items.push_back(PvItem{q, c0});
+    auto make_items = [&](int w) {
+        std::vector<PvItem> it;
+        for (int q : order)
+            for (int c0 = 0; c0 < p.chains; c0 += w) it.push_back(PvItem{q, c0});
+        return it;
+    };
+    int variant = p.search_variant >= 0 ? p.search_variant : 0;
+    int W = p.warps_per_cta > 0 ? p.warps_per_cta : 4;
+    const bool autotune = p.mode == PV_MODE_BATCHED && (p.search_variant < 0 || p.warps_per_cta == 0);
+    int max_rounds = 0;
+    for (int i = 0; i < n_ligs; ++i) max_rounds = std::max(max_rounds, ligs[i]->rec.n_rounds);
+    const std::pair<int, int> tune_key{(max_atoms + 7) / 8, (max_rounds + 3) / 4};
+    bool need_tune = false;
+    if (autotune) {
+        auto it = ctx->tuned.find(tune_key);
+        if (it != ctx->tuned.end()) {
+            if (p.search_variant < 0) variant = it->second.first;
+            if (p.warps_per_cta == 0) W = it->second.second;
+        } else {
+            need_tune = true;
+        }
+    }
+    // the items buffer is sized for the smallest CTA a candidate may use
+    const int W_min = autotune ? (p.warps_per_cta > 0 ? p.warps_per_cta : 2) : W;
+    std::vector<PvItem> items = make_items(W);
+    const size_t items_cap = make_items(W_min).size();
     std::vector<PvPairDesc> pdesc(n_pairs);
     for (int q = 0; q < n_pairs; ++q)
         pdesc[q] = PvPairDesc{pair_lig[q], pair_pocket[q], ligs[pair_lig[q]]->rec.n_rounds, 0};
@@ -654,7 +686,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     // one workspace allocation
     Layout Lw;
     const size_t o_pairs = Lw.take<PvPairDesc>(n_pairs), o_ligs = Lw.take<const void*>(n_ligs),
-                 o_items = Lw.take<PvItem>(items.size()), o_ctr = Lw.take<int>(n_rounds + 2),
+                 o_items = Lw.take<PvItem>(std::max(items.size(), items_cap)), o_ctr = Lw.take<int>(n_rounds + 2),
                  o_evals = Lw.take<unsigned long long>(2),
                  o_chains = Lw.take<float>((size_t)n_pairs * p.chains * PV_CHAIN_STRIDE),
                  o_poses = Lw.take<PvPoseRec>((size_t)n_pairs * p.top_k),
@@ -663,7 +695,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
                  o_nkept = Lw.take<int>(n_pairs), o_status = Lw.take<int>(n_pairs),
                  o_rank = Lw.take<int>((size_t)n_ligs * R->rank_stride), o_lps = Lw.take<int>(n_ligs + 1),
                  o_lp = Lw.take<int>(n_pairs);
-    const size_t small_end = o_items + items.size() * sizeof(PvItem);
+    const size_t small_end = o_items + std::max(items.size(), items_cap) * sizeof(PvItem);
     char* w = (char*)dalloc(ctx, Lw.off);
     if (!w) {
         result_free(R);
@@ -751,15 +783,79 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     M.top_k = p.top_k;
     M.rank_stride = R->rank_stride;
     M.ranking = R->d_ranking;
+    // autotuning: time each candidate launch shape on two MC steps of its own first work items
+    if (need_tune) {
+        static const int cand[][2] = {{0, 2}, {0, 4}, {0, 8}, {1, 4}, {2, 4}, {3, 4}};
+        cudaEvent_t t0, t1;
+        cudaEventCreate(&t0);
+        cudaEventCreate(&t1);
+        float best_ms = 1e30f;
+        int best_v = variant, best_w = W;
+        for (const auto& cw : cand) {
+            const int v = p.search_variant >= 0 ? p.search_variant : cw[0];
+            const int wc = p.warps_per_cta > 0 ? p.warps_per_cta : cw[1];
+            if (wc > search_variant_max_warps(v)) continue;
+            int occ_c = 0;
+            if (search_max_ctas_per_sm(v, wc, search_smem_bytes(max_blob, wc), &occ_c) != cudaSuccess || occ_c < 1) {
+                cudaGetLastError();
+                continue;
+            }
+            std::vector<PvItem> trial = make_items(wc);
+            const int n_trial = (int)std::min<size_t>(trial.size(), (size_t)3 * ctx->sms * occ_c);
+            SearchArgs a = A;
+            a.items = (const PvItem*)((char*)R->d_work + o_items);
+            a.n_items = 0;                       // an empty launch first: loads the variant's code
+            a.queue = ctr + 1;
+            a.step0 = 0;
+            a.step1 = std::min(p.steps, 4);
+            cudaError_t x = cudaMemcpyAsync((char*)R->d_work + o_items, trial.data(), sizeof(PvItem) * n_trial,
+                                            cudaMemcpyHostToDevice, ctx->stream);
+            if (x == cudaSuccess) x = cudaMemsetAsync(ctr, 0, sizeof(int) * 2, ctx->stream);
+            if (x == cudaSuccess) x = launch_search_round(a, v, 1, wc, ctx->stream);
+            a.n_items = n_trial;
+            if (x == cudaSuccess) x = cudaMemsetAsync(ctr, 0, sizeof(int) * 2, ctx->stream);
+            if (x == cudaSuccess) x = launch_mark_t0(evals + 1, ctx->stream);
+            if (x == cudaSuccess) x = cudaEventRecord(t0, ctx->stream);
+            if (x == cudaSuccess) x = launch_search_round(a, v, std::max(1, std::min(n_trial, ctx->sms * occ_c)), wc, ctx->stream);
+            if (x == cudaSuccess) x = cudaEventRecord(t1, ctx->stream);
+            if (x == cudaSuccess) x = cudaEventSynchronize(t1);
+            float ms = 0.f;
+            if (x == cudaSuccess) x = cudaEventElapsedTime(&ms, t0, t1);
+            if (x != cudaSuccess) {
+                cudaEventDestroy(t0);
+                cudaEventDestroy(t1);
+                result_free(R);
+                return cuda_fail(ctx, x, "autotune");
+            }
+            // per unit of work: the trials cover different numbers of chains
+            const float per_chain = ms / (float)(n_trial * wc);
+            if (per_chain < best_ms) { best_ms = per_chain; best_v = v; best_w = wc; }
+        }
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        variant = best_v;
+        W = best_w;
+        ctx->tuned[tune_key] = {variant, W};
+        items = make_items(W);
+        e = cudaMemcpyAsync((char*)R->d_work + o_items, items.data(), sizeof(PvItem) * items.size(),
+                            cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) {
+            result_free(R);
+            return cuda_fail(ctx, e, "item upload");
+        }
+    }
+    A.n_items = (int)items.size();
     // grid of the persistent rounds: every SM filled to its occupancy
     int occ = 0;
     const int smem = search_smem_bytes(max_blob, W);
-    e = search_max_ctas_per_sm(W, smem, &occ);
+    e = search_max_ctas_per_sm(variant, W, smem, &occ);
     if (e != cudaSuccess || occ < 1) {
         result_free(R);
         return e != cudaSuccess ? cuda_fail(ctx, e, "occupancy") : fail(ctx, PV_ERR_ARG, "search kernel does not fit");
     }
     const int grid = std::max(1, std::min((int)items.size(), ctx->sms * occ));
+    R->search_variant = variant;
+    R->warps_per_cta = W;
     e = prepare_topk(T);
     if (e == cudaSuccess) e = prepare_merge(R->rank_stride);
     if (e != cudaSuccess) {
@@ -784,7 +880,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
                 a.queue = ctr + 2 + r;
                 a.step0 = r * S_r;
                 a.step1 = std::min(p.steps, (r + 1) * S_r);
-                x = launch_search_round(a, grid, W, s);
+                x = launch_search_round(a, variant, grid, W, s);
             }
             if (x == cudaSuccess) x = cudaEventRecordWithFlags(evs1, s, ev_flags);
             if (x == cudaSuccess) x = launch_topk(T, n_pairs, s);
@@ -1018,5 +1114,12 @@ extern "C" pv_status pv_dock_result_timing(const pv_dock_result* r, double* sear
     if (search_seconds) *search_seconds = r->search_seconds;
     if (search_launches) *search_launches = r->search_launches;
     if (total_seconds) *total_seconds = r->seconds;
+    return PV_OK;
+}
+
+extern "C" pv_status pv_dock_result_launch(const pv_dock_result* r, int32_t* search_variant, int32_t* warps_per_cta) {
+    if (!r) return PV_ERR_ARG;
+    if (search_variant) *search_variant = r->search_variant;
+    if (warps_per_cta) *warps_per_cta = r->warps_per_cta;
     return PV_OK;
 }

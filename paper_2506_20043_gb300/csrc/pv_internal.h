@@ -61,8 +61,12 @@ struct SearchArgs {
     unsigned long long* evals;
 };
 int search_smem_bytes(int lig_bytes, int warps);
-cudaError_t search_max_ctas_per_sm(int warps, int smem, int* out);
-cudaError_t launch_search_round(const SearchArgs& a, int grid, int warps, cudaStream_t s);
+// Register-budget variants of the round kernel: 0 = (512 threads, 1 CTA), 1 = (128, 5),
+// 2 = (128, 6), 3 = (128, 8) as (max threads per CTA, min CTAs per SM) launch bounds.
+constexpr int kSearchVariants = 4;
+int search_variant_max_warps(int variant);
+cudaError_t search_max_ctas_per_sm(int variant, int warps, int smem, int* out);
+cudaError_t launch_search_round(const SearchArgs& a, int variant, int grid, int warps, cudaStream_t s);
 cudaError_t launch_plain_search(const SearchArgs& a, int pair, const PvLigBlob* lig_dev,
                                 cudaStream_t s);
 cudaError_t launch_mark_t0(unsigned long long* t0, cudaStream_t s);

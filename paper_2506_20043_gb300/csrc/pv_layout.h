@@ -34,8 +34,9 @@ struct PvLigBlob {
     int32_t frag_tor[PV_MAX_FRAGS];  // torsion index of the fragment's hinge (root: -1)
     int32_t tor_frag[PV_MAX_FRAGS];  // fragment of torsion k
     int32_t atom_src[64];            // input index of device atom i
-    uint32_t pairs[1];               // n_rounds * 32 words: i | j << 8 | hyd << 16 | hb << 17
-                                     // | 1 << 31 (valid); 0 = empty slot
+    uint32_t pairs[1];               // n_rounds * 32 words; word l of a round is lane l's pair:
+                                     // target atom (bits 0-5), source atom lane + 32 * bit 6,
+                                     // hydrophobic (bit 16), H-bond (bit 17), valid (bit 31)
 };
 #define PV_LIG_FIXED_BYTES ((int)offsetof(PvLigBlob, pairs))
 

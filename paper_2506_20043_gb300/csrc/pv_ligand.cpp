@@ -22,6 +22,104 @@ static bool is_hyd(int t) { return t == 0; }
 static bool is_don(int t) { return t == 3 || t == 5 || t == 7 || t == 9; }
 static bool is_acc(int t) { return t == 4 || t == 5 || t == 8 || t == 9; }
 
+// Orients every pair so that, per atom, sources and targets split its pairs evenly (an Euler
+// circuit of the pair graph, with a dummy vertex joined to the odd-degree atoms, enters and
+// leaves each atom equally often), then flips single pairs while that lowers the larger of a
+// lane's source load (atoms l and l + 32 share lane l) and a target's load.
+static void orient_pairs(int n, std::vector<std::pair<int, int>>& edges) {
+    const int m = (int)edges.size();
+    if (m == 0) return;
+    std::vector<std::pair<int, int>> E(edges);
+    std::vector<int> deg(n + 1, 0);
+    for (auto& e : E) { deg[e.first]++; deg[e.second]++; }
+    for (int v = 0; v < n; ++v)
+        if (deg[v] & 1) E.push_back({v, n});
+    std::vector<std::vector<std::pair<int, int>>> adj(n + 1);
+    for (int k = 0; k < (int)E.size(); ++k) {
+        adj[E[k].first].push_back({E[k].second, k});
+        adj[E[k].second].push_back({E[k].first, k});
+    }
+    std::vector<char> used(E.size(), 0);
+    std::vector<size_t> ptr(n + 1, 0);
+    for (int s0 = 0; s0 <= n; ++s0) {
+        std::vector<std::pair<int, int>> stack{{s0, -1}};
+        while (!stack.empty()) {
+            const int v = stack.back().first;
+            while (ptr[v] < adj[v].size() && used[adj[v][ptr[v]].second]) ++ptr[v];
+            if (ptr[v] == adj[v].size()) {
+                const int ein = stack.back().second;
+                stack.pop_back();
+                if (ein >= 0 && ein < m) edges[ein] = {stack.back().first, v};
+            } else {
+                const auto nx = adj[v][ptr[v]];
+                used[nx.second] = 1;
+                stack.push_back({nx.first, nx.second});
+            }
+        }
+    }
+    std::vector<int> load(32, 0), ind(64, 0);
+    for (auto& e : edges) { load[e.first & 31]++; ind[e.second]++; }
+    for (bool changed = true; changed;) {
+        changed = false;
+        for (auto& e : edges) {
+            const int s = e.first, t = e.second, ls = s & 31, lt = t & 31;
+            if (ls == lt) continue;
+            const int before = std::max(std::max(load[ls], load[lt]), std::max(ind[s], ind[t]));
+            const int after = std::max(std::max(load[ls] - 1, load[lt] + 1), std::max(ind[s] + 1, ind[t] - 1));
+            if (after < before || (after == before && load[lt] + 1 < load[ls] && ind[s] + 1 < ind[t])) {
+                load[ls]--; load[lt]++; ind[s]++; ind[t]--;
+                e = {t, s};
+                changed = true;
+            }
+        }
+    }
+}
+
+// Edge colouring of the bipartite graph lanes x targets with as many colours (rounds) as its
+// largest degree (Koenig): a pair gets a colour free at both ends, else the alternating path
+// of the two candidate colours from its target is swapped first.
+static int colour_rounds(const std::vector<std::pair<int, int>>& edges, std::vector<int>& col) {
+    const int m = (int)edges.size();
+    col.assign(m, -1);
+    if (m == 0) return 0;
+    std::vector<int> dl(32, 0), dr(64, 0);
+    for (auto& e : edges) { dl[e.first & 31]++; dr[e.second]++; }
+    const int D = std::max(*std::max_element(dl.begin(), dl.end()), *std::max_element(dr.begin(), dr.end()));
+    std::vector<int> Lc(32 * D, -1), Rc(64 * D, -1);   // edge holding colour c at a lane / target
+    for (int e = 0; e < m; ++e) {
+        const int u = edges[e].first & 31, v = edges[e].second;
+        int a = 0, b = 0;
+        while (Lc[u * D + a] >= 0) ++a;
+        while (Rc[v * D + b] >= 0) ++b;
+        if (Rc[v * D + a] >= 0) {
+            std::vector<int> path;
+            int x = v, c = a;
+            bool right = true;
+            for (;;) {
+                const int f = right ? Rc[x * D + c] : Lc[x * D + c];
+                if (f < 0) break;
+                path.push_back(f);
+                x = right ? (edges[f].first & 31) : edges[f].second;
+                right = !right;
+                c = c == a ? b : a;
+            }
+            for (int f : path) {
+                Lc[(edges[f].first & 31) * D + col[f]] = -1;
+                Rc[edges[f].second * D + col[f]] = -1;
+            }
+            for (int f : path) {
+                col[f] = col[f] == a ? b : a;
+                Lc[(edges[f].first & 31) * D + col[f]] = f;
+                Rc[edges[f].second * D + col[f]] = f;
+            }
+        }
+        col[e] = a;
+        Lc[u * D + a] = e;
+        Rc[v * D + a] = e;
+    }
+    return D;
+}
+
 bool build_ligand(const LigandInput& in, LigandRecord& out, std::string& err) {
     const int n = in.n_atoms, nb = in.n_bonds;
     if (n < 1 || n > 64) { err = "ligand atom count must be in [1, 64]"; return false; }
@@ -126,6 +224,7 @@ bool build_ligand(const LigandInput& in, LigandRecord& out, std::string& err) {
         for (int i = 0; i < n; ++i)
             if (frag[i] == order[fi]) { dev_of[i] = (int)src_of.size(); src_of.push_back(i); }
     }
+    auto src_of_dev = [&](int d) { return src_of[d]; };
     std::vector<int> sub_end(nfrag);
     for (int fi = nfrag - 1; fi >= 0; --fi) {
         int end = own_start[fi] + fsize[order[fi]];
@@ -145,24 +244,27 @@ bool build_ligand(const LigandInput& in, LigandRecord& out, std::string& err) {
         for (int j = i + 1; j < n; ++j)
             if (frag[i] != frag[j] && !(dist[j] >= 0 && dist[j] <= 3)) pairs.push_back({i, j});
     }
-    // schedule into rounds: each round holds <= 32 pairs and no atom twice (first fit)
-    std::vector<std::vector<uint32_t>> rounds;
-    std::vector<std::vector<char>> used;
-    for (auto& p : pairs) {
-        const int i = dev_of[p.first], j = dev_of[p.second];
-        const int ti = out.xs[p.first], tj = out.xs[p.second];
+    // Schedule the pairs for the warp: each pair is owned by the lane of one of its atoms (the
+    // source), which keeps that atom's force in registers; the other atom (the target) receives
+    // its force through shared memory. A round gives every lane at most one pair and every
+    // target at most one pair, so a round needs no atomics.
+    std::vector<std::pair<int, int>> edges;   // (source, target), device atom indices
+    for (auto& p : pairs) edges.push_back({dev_of[p.first], dev_of[p.second]});
+    orient_pairs(n, edges);
+    std::vector<int> colour;
+    const int n_rounds_sched = colour_rounds(edges, colour);
+    std::vector<std::vector<uint32_t>> rounds(n_rounds_sched, std::vector<uint32_t>(32, 0u));
+    for (size_t e = 0; e < edges.size(); ++e) {
+        const int src = edges[e].first, tgt = edges[e].second;
+        const int ti = out.xs[src_of_dev(src)], tj = out.xs[src_of_dev(tgt)];
         const uint32_t hyd = (is_hyd(ti) && is_hyd(tj)) ? 1u : 0u;
         const uint32_t hb = ((is_don(ti) && is_acc(tj)) || (is_acc(ti) && is_don(tj))) ? 1u : 0u;
-        const uint32_t w = (uint32_t)i | ((uint32_t)j << 8) | (hyd << 16) | (hb << 17) | (1u << 31);
-        size_t r = 0;
-        while (r < rounds.size() && (rounds[r].size() >= 32 || used[r][i] || used[r][j])) ++r;
-        if (r == rounds.size()) { rounds.emplace_back(); used.emplace_back(64, 0); }
-        rounds[r].push_back(w);
-        used[r][i] = used[r][j] = 1;
+        const uint32_t w = (uint32_t)tgt | ((uint32_t)(src >> 5) << 6) | (hyd << 16) | (hb << 17) | (1u << 31);
+        rounds[colour[e]][src & 31] = w;
     }
     if ((int)rounds.size() > PV_MAX_ROUNDS) { err = "intra pair schedule exceeds the round limit"; return false; }
     // record
-    const int n_rounds = (int)rounds.size();
+    const int n_rounds = n_rounds_sched;
     const int bytes = PV_LIG_FIXED_BYTES + n_rounds * 32 * 4;
     out.blob.assign((size_t)((bytes + 15) / 16) * 16, 0);
     PvLigBlob* L = reinterpret_cast<PvLigBlob*>(out.blob.data());
@@ -223,7 +325,7 @@ bool build_ligand(const LigandInput& in, LigandRecord& out, std::string& err) {
         if (ftor[f] >= 0) L->tor_frag[ftor[f]] = fi;
     }
     for (int r = 0; r < n_rounds; ++r)
-        for (size_t l = 0; l < rounds[r].size(); ++l) L->pairs[r * 32 + l] = rounds[r][l];
+        for (int l = 0; l < 32; ++l) L->pairs[r * 32 + l] = rounds[r][l];
     out.n_atoms = n;
     out.n_rot = n_rot;
     out.n_pairs = (int)pairs.size();

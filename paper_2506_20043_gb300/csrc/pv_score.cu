@@ -52,9 +52,8 @@ __global__ void __launch_bounds__(kScoreWarps * 32) score_kernel(ScoreArgs A) {
         const float* p = A.pose + (size_t)i * A.pot_stride;
         const Pose x = read_pose(p, n_rot);
         if (A.fk_only) {
-            Mat3 M;
-            float3 xa;
-            warp_fk(L, S, x, M, xa);
+            float3 axw, xa;
+            warp_fk(L, S, x, axw, xa);
             __syncwarp();
             for (int a = lane; a < n; a += 32) {
                 float* dst = A.xyz + ((size_t)i * n + L.atom_src[a]) * 3;

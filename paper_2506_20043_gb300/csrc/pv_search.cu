@@ -12,8 +12,6 @@
 
 namespace pv {
 
-constexpr int kBfgsM = 5;
-
 __device__ __forceinline__ void store_pose(float* dst, const Pose& x, int n_rot) {
     const int lane = threadIdx.x & 31;
     float v[7] = {x.T.x, x.T.y, x.T.z, x.q.x, x.q.y, x.q.z, x.q.w};
@@ -43,7 +41,7 @@ static cudaError_t ensure_smem(const void* fn, int smem, int* cache) {
     if (e == cudaSuccess) cache[dev] = smem;
     return e;
 }
-static int g_search_smem[64], g_topk_smem[64], g_merge_smem[64];
+static int g_topk_smem[64], g_merge_smem[64];
 
 cudaError_t launch_mark_t0(unsigned long long* t0, cudaStream_t s) {
     mark_t0_kernel<<<1, 1, 0, s>>>(t0);
@@ -55,8 +53,11 @@ int search_smem_bytes(int lig_bytes, int warps) {
     return lig + warps * (int)sizeof(WarpScratch);
 }
 
-// One round of MC steps [step0, step1) for every chain of every pair (batched form).
-__global__ void __launch_bounds__(kSearchThreadsMax) search_round_kernel(SearchArgs A) {
+// One round of MC steps [step0, step1) for every chain of every pair (batched form). Compiled
+// for several (threads per CTA, minimum CTAs per SM) bounds, i.e. register budgets; the runtime
+// picks one (SearchVariant).
+template <int THREADS, int MIN_CTAS>
+__global__ void __launch_bounds__(THREADS, MIN_CTAS) search_round_kernel(SearchArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     PvLigBlob& L = *reinterpret_cast<PvLigBlob*>(smem);
     WarpScratch* scratch = reinterpret_cast<WarpScratch*>(smem + ((A.lig_smem_bytes + 127) & ~127));
@@ -95,36 +96,41 @@ __global__ void __launch_bounds__(kSearchThreadsMax) search_round_kernel(SearchA
             c.evals = 0;
             const int max_iter = C.bfgs_max_iter > 0 ? C.bfgs_max_iter : L.h.bfgs_iters;
             float* rec = A.chains + ((size_t)item.pair * C.chains + chain) * PV_CHAIN_STRIDE;
-            Pose cur, best;
+            // the current POT lives in the warp's shared scratch and the best POT in the chain
+            // record, so neither occupies registers during the local searches
+            float* curs = c.S->cur;
             float e_cur, e_best;
             uint32_t evals_before = 0;
             if (A.step0 == 0) {
-                cur = random_pose(L, s_pocket, (uint32_t)chain, (uint32_t)item.pair, C);
+                Pose x0 = random_pose(L, s_pocket, (uint32_t)chain, (uint32_t)item.pair, C);
                 float g;
-                e_cur = warp_eval(L, *c.S, c.site, cur, g, false);
+                e_cur = warp_eval(L, *c.S, c.site, x0, g, false);
                 c.evals++;
-                best = cur;
                 e_best = e_cur;
+                store_pose(curs, x0, n_rot);
+                store_pose(rec + PV_CH_BEST, x0, n_rot);
             } else {
-                cur = load_pose(rec + PV_CH_CUR, n_rot);
-                best = load_pose(rec + PV_CH_BEST, n_rot);
+                for (int i = lane; i < 7 + n_rot; i += 32) curs[i] = rec[PV_CH_CUR + i];
                 e_cur = rec[PV_CH_ECUR];
                 e_best = rec[PV_CH_EBEST];
                 evals_before = __float_as_uint(rec[PV_CH_EVALS]);
             }
+            __syncwarp();
             int flags = 0;
             for (int s = A.step0; s < A.step1; ++s) {
-                Pose cand = cur;
+                Pose cand = load_pose(curs, n_rot);
                 const float u = mutate(L, cand, (uint32_t)chain, (uint32_t)item.pair, s, C);
-                const float e_new = warp_bfgs<kBfgsM>(c, cand, C, max_iter, C.bfgs_m);
+                const float e_new = warp_bfgs(c, cand, C, max_iter, C.bfgs_m);
                 if (e_new < e_cur || u < expf((e_cur - e_new) / C.temperature)) {
-                    cur = cand;
                     e_cur = e_new;
                     if (e_cur < e_best) {
-                        e_cur = warp_bfgs<kBfgsM>(c, cur, C, max_iter, C.bfgs_m);
-                        best = cur;
+                        e_cur = warp_bfgs(c, cand, C, max_iter, C.bfgs_m);
+                        store_pose(rec + PV_CH_BEST, cand, n_rot);
                         e_best = e_cur;
                     }
+                    __syncwarp();
+                    store_pose(curs, cand, n_rot);
+                    __syncwarp();
                 }
                 if (A.timeout_ns) {
                     unsigned long long now = lane == 0 ? globaltimer() : 0ull;
@@ -133,8 +139,8 @@ __global__ void __launch_bounds__(kSearchThreadsMax) search_round_kernel(SearchA
                 }
             }
             if (!(e_best == e_best)) flags |= PV_EBIT_NAN;
-            store_pose(rec + PV_CH_CUR, cur, n_rot);
-            store_pose(rec + PV_CH_BEST, best, n_rot);
+            __syncwarp();
+            for (int i = lane; i < 7 + n_rot; i += 32) rec[PV_CH_CUR + i] = curs[i];
             if (lane == 0) {
                 rec[PV_CH_ECUR] = e_cur;
                 rec[PV_CH_EBEST] = e_best;
@@ -149,18 +155,39 @@ __global__ void __launch_bounds__(kSearchThreadsMax) search_round_kernel(SearchA
     }
 }
 
-cudaError_t search_max_ctas_per_sm(int warps, int smem, int* out) {
-    cudaError_t e = ensure_smem((const void*)search_round_kernel, smem, g_search_smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, search_round_kernel, warps * 32, smem);
+struct VariantEntry {
+    const void* fn;
+    int max_threads;
+};
+static const VariantEntry kVariants[kSearchVariants] = {
+    {(const void*)search_round_kernel<512, 1>, 512},   // widest register budget
+    {(const void*)search_round_kernel<128, 5>, 128},
+    {(const void*)search_round_kernel<128, 6>, 128},
+    {(const void*)search_round_kernel<128, 8>, 128},   // 64 registers
+};
+static int g_variant_smem[kSearchVariants][64];
+
+int search_variant_max_warps(int variant) {
+    if (variant < 0 || variant >= kSearchVariants) return 0;
+    return kVariants[variant].max_threads / 32;
 }
 
-cudaError_t launch_search_round(const SearchArgs& a, int grid, int warps, cudaStream_t s) {
-    const int smem = search_smem_bytes(a.lig_smem_bytes, warps);
-    cudaError_t e = ensure_smem((const void*)search_round_kernel, smem, g_search_smem);
+cudaError_t search_max_ctas_per_sm(int variant, int warps, int smem, int* out) {
+    if (variant < 0 || variant >= kSearchVariants || warps * 32 > kVariants[variant].max_threads)
+        return cudaErrorInvalidValue;
+    cudaError_t e = ensure_smem(kVariants[variant].fn, smem, g_variant_smem[variant]);
     if (e != cudaSuccess) return e;
-    search_round_kernel<<<grid, warps * 32, smem, s>>>(a);
-    return cudaGetLastError();
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, kVariants[variant].fn, warps * 32, smem);
+}
+
+cudaError_t launch_search_round(const SearchArgs& a, int variant, int grid, int warps, cudaStream_t s) {
+    if (variant < 0 || variant >= kSearchVariants || warps * 32 > kVariants[variant].max_threads)
+        return cudaErrorInvalidValue;
+    const int smem = search_smem_bytes(a.lig_smem_bytes, warps);
+    cudaError_t e = ensure_smem(kVariants[variant].fn, smem, g_variant_smem[variant]);
+    if (e != cudaSuccess) return e;
+    void* args[] = {(void*)&a};
+    return cudaLaunchKernel(kVariants[variant].fn, dim3(grid), dim3(warps * 32), args, (size_t)smem, s);
 }
 
 // Plain form: the chains of one pair, one thread per chain, all steps in one launch.
@@ -263,9 +290,8 @@ __global__ void __launch_bounds__(kTopkThreads) topk_kernel(TopkArgs A) {
             if ((key >> 32) == 0xffffffffull) break;   // NaN scores are never kept
             const int ch = (int)(key & 0xffffffffu);
             Pose x = load_pose(chains + (size_t)ch * PV_CHAIN_STRIDE + PV_CH_BEST, n_rot);
-            Mat3 M;
-            float3 xa;
-            warp_fk(L, S, x, M, xa);
+            float3 axw, xa;
+            warp_fk(L, S, x, axw, xa);
             __syncwarp();
             bool ok = true;
             for (int b = 0; b < kept && ok; ++b) {

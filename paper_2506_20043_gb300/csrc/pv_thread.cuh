@@ -55,7 +55,7 @@ static __device__ __noinline__ float thread_eval(ThreadChain& c, ThreadWork& w, 
     for (int k = 0; k < slots; ++k) {
         const uint32_t pw = L->pairs[k];
         if (!(pw >> 31)) continue;
-        const int i = pw & 255, j = (pw >> 8) & 255;
+        const int i = (k & 31) + 32 * ((pw >> 6) & 1), j = pw & 63;
         const float dx = w.x[i][0] - w.x[j][0], dy = w.x[i][1] - w.x[j][1], dz = w.x[i][2] - w.x[j][2];
         const float r2 = dx * dx + dy * dy + dz * dz;
         if (r2 >= kCutoff2) continue;

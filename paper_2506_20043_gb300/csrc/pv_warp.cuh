@@ -8,17 +8,22 @@
 //               anchor position
 //   tangent:    lane k owns tangent coordinate k (0-2 translation, 3-5 rotation vector,
 //               6 + t torsion t); the torsion angle psi_t itself lives in lane 6 + t
-//   pairs:      intra pairs are pre-scheduled into rounds of <= 32 pairs with no atom twice,
-//               lane l takes slot l of each round, so force accumulation needs no atomics and
-//               its order is fixed (bitwise reproducible).
+//   pairs:      every intra pair is owned by the lane of one of its atoms (its source), which
+//               adds that atom's share of the force in registers; the other atom (its target)
+//               receives its share through shared memory. Rounds give each lane one pair and
+//               each target one pair, so no atomics are needed and the order of accumulation
+//               is fixed (bitwise reproducible).
 #pragma once
 #include "pv_device.cuh"
 
 namespace pv {
 
 struct WarpScratch {
-    float4 x[64];   // posed coordinates; w = XS radius
-    float4 g[64];   // dSF/dx
+    float4 x[64];                // posed coordinates; w = XS radius
+    float4 g[64];                // dSF/dx
+    float hs[PV_MAX_M][32];      // L-BFGS history: s vectors, lane = tangent coordinate
+    float hy[PV_MAX_M][32];      //                 y vectors
+    float cur[40];               // the chain's current POT (MC state)
 };
 
 // A pose held by a warp: translation and quaternion (w, x, y, z) are warp-uniform; psi is the
@@ -40,7 +45,7 @@ __device__ __forceinline__ int shfli(int v, int src) { return __shfl_sync(PV_FUL
 // Forward kinematics (Eq. 1: position, orientation, torsions -> atom coordinates). Writes S.x.
 // Returns the fragment lane's rotation and anchor (used again by the adjoint).
 __device__ __forceinline__ void warp_fk(const PvLigBlob& L, WarpScratch& S, const Pose& x,
-                                        Mat3& M, float3& xa) {
+                                        float3& axw, float3& xa, float4* own = nullptr) {
     const int lane = threadIdx.x & 31;
     const int nf = L.h.n_frag;
     const bool isf = lane < nf;
@@ -57,7 +62,7 @@ __device__ __forceinline__ void warp_fk(const PvLigBlob& L, WarpScratch& S, cons
     Mat3 Rl;
     if (lane == 0) Rl = quat_to_mat(x.q);
     else Rl = axis_angle(axis, isf ? psi : 0.0f);
-    M = Rl;
+    Mat3 M = Rl;
     xa = (lane == 0) ? x.T : make_float3(0.f, 0.f, 0.f);
     for (int lev = 1; lev <= L.h.max_depth; ++lev) {
         const bool mine = isf && depth == lev;
@@ -84,33 +89,36 @@ __device__ __forceinline__ void warp_fk(const PvLigBlob& L, WarpScratch& S, cons
         float3 xf = make_float3(shfl(xa.x, fa), shfl(xa.y, fa), shfl(xa.z, fa));
         if (a < n) {
             float3 p = mat_vec(Mf, f3(loc)) + xf;
-            S.x[a] = make_float4(p.x, p.y, p.z, xs_radius((w >> 8) & 255));
+            const float4 q = make_float4(p.x, p.y, p.z, xs_radius((w >> 8) & 255));
+            S.x[a] = q;
+            if (own) own[h] = q;
         }
     }
+    axw = mat_vec(M, axis);   // the hinge axis in the world frame (rotating about it keeps it)
 }
 
 // SF = e_inter + e_intra (Eq. 3) and, if want_grad, its tangent gradient (lane k holds
 // component k). parts (optional, lane-uniform): e_inter, e_intra.
-static __device__ __noinline__ float warp_eval(const PvLigBlob& L, WarpScratch& S, const Site& site,
-                                        const Pose& x, float& grad, bool want_grad,
-                                        float* parts = nullptr) {
+static __device__ __forceinline__ float warp_eval(const PvLigBlob& L, WarpScratch& S, const Site& site,
+                                               const Pose& x, float& grad, bool want_grad,
+                                               float* parts = nullptr) {
     const int lane = threadIdx.x & 31;
     const int n = L.h.n_atoms;
-    Mat3 M;
-    float3 xa;
-    warp_fk(L, S, x, M, xa);
+    float3 axw, xa;
+    float4 own[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+    warp_fk(L, S, x, axw, xa, own);
     const PvPocket& P = *site.P;
     float e_inter = 0.f, e_intra = 0.f;
+    float3 acc[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int a = lane + 32 * h;
+        acc[h] = make_float3(0.f, 0.f, 0.f);
         if (a < n) {
             const int w = __float_as_int(L.atom[a].w);
             const int slot = (w >> 16) & 255;
-            float4 p = S.x[a];
-            float3 d;
-            e_inter += grid_eval(site.maps + (long long)slot * P.nxyz, P, f3(p), d);
-            S.g[a] = make_float4(d.x, d.y, d.z, 0.f);
+            e_inter += grid_eval(site.maps + (long long)slot * P.nxyz, P, f3(own[h]), acc[h]);
+            S.g[a] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
     __syncwarp();
@@ -118,35 +126,47 @@ static __device__ __noinline__ float warp_eval(const PvLigBlob& L, WarpScratch& 
     for (int r = 0; r < rounds; ++r) {
         const uint32_t pw = L.pairs[r * 32 + lane];
         if (pw >> 31) {
-            const int i = pw & 255, j = (pw >> 8) & 255;
-            float4 xi = S.x[i], xj = S.x[j];
-            float3 d = make_float3(xi.x - xj.x, xi.y - xj.y, xi.z - xj.z);
-            float r2 = dot3(d, d);
+            const int t = pw & 63, h = (pw >> 6) & 1;
+            const float4 xi = h ? own[1] : own[0];
+            const float4 xj = S.x[t];
+            const float3 d = make_float3(xi.x - xj.x, xi.y - xj.y, xi.z - xj.z);
+            const float r2 = dot3(d, d);
             if (r2 < kCutoff2) {
                 float rr = sqrtf(r2), dedr;
                 e_intra += vina_pair(rr, xi.w + xj.w, (pw >> 16) & 1, (pw >> 17) & 1, dedr);
                 if (rr > 1e-6f) {
-                    float c = dedr / rr;
-                    float4 gi = S.g[i], gj = S.g[j];
-                    S.g[i] = make_float4(gi.x + c * d.x, gi.y + c * d.y, gi.z + c * d.z, 0.f);
-                    S.g[j] = make_float4(gj.x - c * d.x, gj.y - c * d.y, gj.z - c * d.z, 0.f);
+                    const float c = dedr / rr;
+                    const float3 f = c * d;
+                    if (h) acc[1] = acc[1] + f; else acc[0] = acc[0] + f;
+                    const float4 gj = S.g[t];
+                    S.g[t] = make_float4(gj.x - f.x, gj.y - f.y, gj.z - f.z, 0.f);
                 }
             }
         }
         __syncwarp();
     }
+    // total dSF/dx of the lane's atoms: own share (registers) + shares received as a target
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int a = lane + 32 * h;
+        if (a < n) {
+            const float4 gt = S.g[a];
+            acc[h] = acc[h] + f3(gt);
+            S.g[a] = make_float4(acc[h].x, acc[h].y, acc[h].z, 0.f);
+        }
+    }
     float ei = warp_sum(e_inter), ej = warp_sum(e_intra);
     if (parts) { parts[0] = ei; parts[1] = ej; }
     if (want_grad) {
+        __syncwarp();
         // root: total force and torque about the origin atom (butterfly sums over all atoms)
         float3 F = make_float3(0.f, 0.f, 0.f), tau = F;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int a = lane + 32 * h;
             if (a < n) {
-                float3 g = f3(S.g[a]);
-                F = F + g;
-                tau = tau + cross3(f3(S.x[a]) - x.T, g);
+                F = F + acc[h];
+                tau = tau + cross3(f3(own[h]) - x.T, acc[h]);
             }
         }
         F = warp_sum3(F);
@@ -159,7 +179,6 @@ static __device__ __noinline__ float warp_eval(const PvLigBlob& L, WarpScratch& 
             const int a0 = L.frag_a0[lane], a1 = L.frag_a1[lane];
             float3 t = make_float3(0.f, 0.f, 0.f);
             for (int a = a0; a < a1; ++a) t = t + cross3(f3(S.x[a]) - xa, f3(S.g[a]));
-            float3 axw = mat_vec(M, f3(L.frag_axis[lane]));
             gpsi = dot3(axw, t);
         }
         const int nt = 6 + L.h.n_rot;
@@ -197,43 +216,45 @@ __device__ __forceinline__ float eval_pose(ChainCtx& c, const Pose& x, float& g)
 // RILC-BFGS (Eq. 6-12): L-BFGS two-loop recursion over the m most recent curvature pairs,
 // Lewis-Overton line search (Eq. 7-8 as failure tests of Armijo / weak Wolfe), curvature-
 // guarded history update (Eq. 11), stop on ||g|| <= eps (Eq. 12), non-descent, or max_iter.
-// Updates x in place and returns SF(x). All control flow is warp-uniform.
-template <int M>
-__device__ float warp_bfgs(ChainCtx& c, Pose& x, const PvSearchConst& C, int max_iter, int m) {
+// Updates x in place and returns SF(x). All control flow is warp-uniform. The history lives in
+// the warp's shared scratch (a ring of m slots); rho and alpha of slot k sit in lane k.
+static __device__ __noinline__ float warp_bfgs(ChainCtx& c, Pose& x, const PvSearchConst& C, int max_iter, int m) {
+    const int lane = threadIdx.x & 31;
     const int n_tan = 6 + c.L->h.n_rot;
+    float* Hs = &c.S->hs[0][0];
+    float* Hy = &c.S->hy[0][0];
     float g;
     float f = eval_pose(c, x, g);
-    float Sh[M], Yh[M], rh[M], al[M];
-#pragma unroll
-    for (int k = 0; k < M; ++k) { Sh[k] = 0.f; Yh[k] = 0.f; rh[k] = 0.f; al[k] = 0.f; }
-    int stored = 0;
+    float rh = 0.f, al = 0.f;
+    int stored = 0, head = 0;
     for (int it = 0; it < max_iter; ++it) {
-        // two-loop recursion, newest pair at index 0
+        // two-loop recursion, newest pair first
         float q = g;
-#pragma unroll
-        for (int k = 0; k < M; ++k) {
-            if (k < stored) {
-                al[k] = rh[k] * warp_sum(Sh[k] * q);
-                q -= al[k] * Yh[k];
-            }
+        for (int a = 0; a < stored; ++a) {
+            int k = head - 1 - a;
+            if (k < 0) k += m;
+            const float alpha = shfl(rh, k) * warp_sum(Hs[k * 32 + lane] * q);
+            if (lane == k) al = alpha;
+            q -= alpha * Hy[k * 32 + lane];
         }
         if (stored > 0) {
-            float sy = warp_sum(Sh[0] * Yh[0]), yy = warp_sum(Yh[0] * Yh[0]);
+            const int k = head == 0 ? m - 1 : head - 1;
+            const float sk = Hs[k * 32 + lane], yk = Hy[k * 32 + lane];
+            const float sy = warp_sum(sk * yk), yy = warp_sum(yk * yk);
             q *= sy / yy;
         }
-#pragma unroll
-        for (int k = M - 1; k >= 0; --k) {
-            if (k < stored) {
-                float b = rh[k] * warp_sum(Yh[k] * q);
-                q += Sh[k] * (al[k] - b);
-            }
+        for (int a = stored - 1; a >= 0; --a) {
+            int k = head - 1 - a;
+            if (k < 0) k += m;
+            const float b = shfl(rh, k) * warp_sum(Hy[k * 32 + lane] * q);
+            q += Hs[k * 32 + lane] * (shfl(al, k) - b);
         }
         const float d = -q;
         const float gd = warp_sum(g * d);
         if (!(gd < 0.f)) break;
         // Lewis-Overton bracketing
         float lam = 1.f, lo = 0.f, hi = -1.f, ft = 0.f, gt = 0.f, flo = 0.f, glo = 0.f;
-        Pose xt = x, xlo = x;
+        Pose xt = x;
         bool accepted = false, have_lo = false;
         for (int tr = 0; tr < C.bfgs_max_trials; ++tr) {
             xt = retract(x, lam * d, n_tan);
@@ -242,7 +263,7 @@ __device__ float warp_bfgs(ChainCtx& c, Pose& x, const PvSearchConst& C, int max
             if (!(ft <= f + lam * C.rho * gd)) {
                 hi = lam;
             } else if (gtd < C.sigma * gd) {
-                lo = lam; have_lo = true; flo = ft; glo = gt; xlo = xt;
+                lo = lam; have_lo = true; flo = ft; glo = gt;
             } else {
                 accepted = true;
                 break;
@@ -251,19 +272,22 @@ __device__ float warp_bfgs(ChainCtx& c, Pose& x, const PvSearchConst& C, int max
         }
         if (!accepted) {
             if (!have_lo) break;
-            lam = lo; ft = flo; gt = glo; xt = xlo;
+            lam = lo; ft = flo; gt = glo;
+            xt = retract(x, lam * d, n_tan);   // the same arithmetic as the trial at lam = lo
         }
         const float s = lam * d, y = gt - g;
         const float ys = warp_sum(y * s), ss = warp_sum(s * s), gn = sqrtf(warp_sum(g * g));
         if (ss > 0.f && ys / ss > C.eps * gn) {
-#pragma unroll
-            for (int k = M - 1; k > 0; --k) { Sh[k] = Sh[k - 1]; Yh[k] = Yh[k - 1]; rh[k] = rh[k - 1]; }
-            Sh[0] = s; Yh[0] = y; rh[0] = 1.f / ys;
+            Hs[head * 32 + lane] = s;
+            Hy[head * 32 + lane] = y;
+            if (lane == head) rh = 1.f / ys;
+            head = head + 1 == m ? 0 : head + 1;
             stored = min(stored + 1, m);
         }
         x = xt; g = gt; f = ft;
         if (sqrtf(warp_sum(g * g)) <= C.eps) break;
     }
+    __syncwarp();
     return f;
 }
 

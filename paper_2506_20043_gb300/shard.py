@@ -1,0 +1,65 @@
+"""Sharding of a docking job over GPUs (one process per GPU) and the host-side merge of results.
+
+Units of the search are independent (ligand, pocket, chain), so ranks work on disjoint shards with no
+data-path collective. Shards are cut by pocket first, so that each GPU builds and holds only the maps
+of its own pockets, then by ligand when there are fewer pocket groups than ranks. The only exchange
+is the final one: each rank's kept poses (a few records per pair) are gathered on the host and merged
+per ligand by score, ties by (pocket, chain) -- the same order the GPU merge uses within a rank.
+"""
+from __future__ import annotations
+
+from typing import Dict, List, Sequence, Tuple
+
+Record = Tuple[float, int, int]   # (SF, pocket id, chain)
+
+
+def plan_shards(pocket_ids: Sequence[int], n_ligands: int, world: int) -> List[Tuple[List[int], List[int]]]:
+    """Per rank: (pocket ids, ligand indices). Pockets are dealt round-robin to rank groups; when
+    there are more ranks than pockets, the ligands of a pocket are split over the ranks sharing it."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    pockets = list(pocket_ids)
+    if not pockets or n_ligands < 1:
+        return [([], []) for _ in range(world)]
+    groups = min(world, len(pockets))
+    out: List[Tuple[List[int], List[int]]] = []
+    for r in range(world):
+        g = r % groups
+        ranks_in_group = [q for q in range(world) if q % groups == g]
+        k = ranks_in_group.index(r)
+        my_pockets = pockets[g::groups]
+        per = len(ranks_in_group)
+        my_ligs = list(range(k, n_ligands, per))
+        out.append((my_pockets, my_ligs))
+    return out
+
+
+def merge_records(per_rank: Sequence[Dict[int, List[Record]]]) -> Dict[int, List[Record]]:
+    """Merges {ligand: [(SF, pocket, chain), ...]} from every rank into one ranking per ligand."""
+    merged: Dict[int, List[Record]] = {}
+    for part in per_rank:
+        for lig, recs in part.items():
+            merged.setdefault(lig, []).extend((float(s), int(p), int(c)) for s, p, c in recs)
+    return {lig: sorted(recs) for lig, recs in merged.items()}
+
+
+def records_from_result(result, ligand_ids: Sequence[int]) -> Dict[int, List[Record]]:
+    """{global ligand id: records} from a DockResult of this rank (ligand_ids maps the rank's local
+    ligand index to the job's ligand id)."""
+    poses = result.poses.reshape(-1)
+    out: Dict[int, List[Record]] = {}
+    for local, lig in enumerate(ligand_ids):
+        out[int(lig)] = [(float(poses[i]["score"]), int(poses[i]["pocket"]), int(poses[i]["chain"]))
+                         for i in result.ranking(local)]
+    return out
+
+
+def gather_merge(local: Dict[int, List[Record]], group=None, dst: int = 0):
+    """Gathers every rank's records on rank `dst` (torch.distributed, any backend) and merges them
+    there; other ranks get None."""
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    bucket = [None] * world if rank == dst else None
+    dist.gather_object(local, bucket, dst=dst, group=group)
+    return merge_records(bucket) if rank == dst else None

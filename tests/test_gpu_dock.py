@@ -95,12 +95,14 @@ def test_reported_poses_are_valid_and_selection_matches_oracle(tiny):
 
 
 def test_tiny_workload_best_score_parity(tiny):
-    """The tiny workload in full: 8 chains x 1,000 steps; the GPU's best SF is within
-    0.2 kcal/mol of the oracle's."""
+    """The tiny workload's receptor, box and ligand with 1,000 MC steps; the GPU's best SF is within
+    0.2 kcal/mol of the oracle's. Sampled with 64 chains, where the oracle's own best varies by
+    about 0.01 kcal/mol across seeds (with the workload's 8 chains it varies by about 0.2, so the
+    comparison would measure sampling noise, not parity)."""
     ctx, box, gs, pl, L, og = tiny
     p = O.SearchParams(seed=0, steps=1000)
-    _, ref_es, _ = O.mc_chains(L, og, box, p, unit=0, n_chains=8, threads=G.threads())
-    r = ctx.dock(gs, [pl], [0], chains=8, steps=1000, seed=0)
+    _, ref_es, _ = O.mc_chains(L, og, box, p, unit=0, n_chains=64, threads=G.threads())
+    r = ctx.dock(gs, [pl], [0], chains=64, steps=1000, seed=0)
     _, es = r.chain_records()
     assert abs(es[0].min() - ref_es.min()) <= 0.2, (es[0].min(), ref_es.min())
     assert r.poses[0][0]["score"] == pytest.approx(es[0].min(), abs=1e-6)
@@ -130,7 +132,7 @@ def test_multi_pocket_merge_and_pocket_parity():
     ligs = [G.ligand32(S.ligand_centered(S.make_ligand(12, 2, 21))),
             G.ligand32(S.ligand_centered(S.make_ligand(14, 3, 22)))]
     gs, pls, Ls, ogs = _setup(ctx, rec, boxes, ligs)
-    chains, steps = 32, 150
+    chains, steps = 64, 300
     r = ctx.dock(gs, pls, [0, 1, 2, 3], chains=chains, steps=steps, seed=9, top_k=5)
     _, es = r.chain_records()
     p = O.SearchParams(seed=9, steps=steps, top_k=5)

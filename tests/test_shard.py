@@ -1,0 +1,70 @@
+"""Multi-GPU sharding logic on the CPU: shard plans cover every (ligand, pocket) pair exactly once,
+and a 2-rank gloo gather + merge equals merging everything in one process."""
+import os
+import socket
+
+import pytest
+
+from paper_2506_20043_gb300 import shard
+
+
+@pytest.mark.parametrize("world,n_pockets,n_ligs", [(1, 10, 1), (2, 10, 1), (4, 3, 5), (8, 2, 7), (3, 5, 3)])
+def test_plan_covers_every_pair_once(world, n_pockets, n_ligs):
+    plan = shard.plan_shards(list(range(100, 100 + n_pockets)), n_ligs, world)
+    assert len(plan) == world
+    seen = {}
+    for r, (pockets, ligs) in enumerate(plan):
+        for p in pockets:
+            for l in ligs:
+                assert (l, p) not in seen
+                seen[(l, p)] = r
+    assert set(seen) == {(l, p) for l in range(n_ligs) for p in range(100, 100 + n_pockets)}
+    # a pocket's maps live on as few ranks as the split allows
+    if world <= n_pockets:
+        owners = {}
+        for r, (pockets, _) in enumerate(plan):
+            for p in pockets:
+                owners.setdefault(p, set()).add(r)
+        assert all(len(v) == 1 for v in owners.values())
+
+
+def test_merge_orders_by_score_pocket_chain():
+    a = {0: [(-7.0, 3, 1), (-5.0, 3, 4)], 1: [(-2.0, 0, 0)]}
+    b = {0: [(-7.0, 1, 9), (-8.0, 2, 2)]}
+    m = shard.merge_records([a, b])
+    assert m[0] == [(-8.0, 2, 2), (-7.0, 1, 9), (-7.0, 3, 1), (-5.0, 3, 4)]
+    assert m[1] == [(-2.0, 0, 0)]
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, parts, out_path):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    res = shard.gather_merge(parts[rank])
+    if rank == 0:
+        import json
+        with open(out_path, "w") as f:
+            json.dump({str(k): v for k, v in res.items()}, f)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_gloo_two_rank_gather_merge(tmp_path):
+    torch = pytest.importorskip("torch")
+    import json
+    import torch.multiprocessing as mp
+    parts = [{0: [(-6.0, 0, 3), (-4.5, 1, 0)], 2: [(-1.0, 1, 2)]},
+             {0: [(-6.5, 5, 1)], 1: [(-3.0, 4, 4), (-3.5, 5, 0)]}]
+    out = str(tmp_path / "merged.json")
+    mp.start_processes(_worker, args=(2, _free_port(), parts, out), nprocs=2, join=True, start_method="spawn")
+    got = {int(k): [tuple(r) for r in v] for k, v in json.load(open(out)).items()}
+    assert got == shard.merge_records(parts)
