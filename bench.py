@@ -359,8 +359,9 @@ def run_reference(args):
 
 
 def run_small_case(args):
-    """One small untimed pass for profiler captures: the multi-pocket receptor's first pocket,
-    256 chains x 20 MC steps, plus one score launch over 4,096 poses."""
+    """One short untimed pass for profiler captures: the multi-pocket workload (10 pockets x 1,000
+    chains) for 5 MC steps with a fixed launch shape (--variant, --warps; no autotuning), plus one
+    score launch over the 65,536 microbenchmark poses."""
     import torch
     import paper_2506_20043_gb300 as pv
     pv.build()
@@ -368,13 +369,17 @@ def run_small_case(args):
     ctx = api.Context(0)
     rec, boxes, lig_src = workload(seed=0)
     lig = ctx.ligand(lig_src)
-    gs = ctx.build_grids(rec, boxes[:1], sorted(set(lig.xs_types.tolist())))
-    r = ctx.dock(gs, [lig], [0], chains=256, steps=20, seed=0, host_copy=False)
+    gs = ctx.build_grids(rec, boxes, sorted(set(lig.xs_types.tolist())))
+    r = ctx.dock(gs, [lig], list(range(len(boxes))), chains=CHAINS, steps=5, seed=0, host_copy=False,
+                 search_variant=args.variant, warps_per_cta=args.warps, steps_per_round=5)
     ev, sec, st = r.stats()
-    poses = torch.tensor(S.random_poses(4096, boxes[0], lig.n_rot, 0), dtype=torch.float32, device="cuda")
-    ctx.score(gs, lig, 0, poses)
+    mrec, mbox, mlig_src, mposes = S.score_microbench()
+    mlig = ctx.ligand(mlig_src)
+    mgs = ctx.build_grids(mrec, [mbox], sorted(set(mlig.xs_types.tolist())))
+    ctx.score(mgs, mlig, 0, torch.tensor(mposes, dtype=torch.float32, device="cuda"))
     torch.cuda.synchronize()
-    return {"case": "small", "evals": int(ev), "seconds": round(sec, 4), "status": st.tolist()}
+    return {"case": "small", "evals": int(ev), "seconds": round(sec, 4), "launch": r.launch_shape(),
+            "status_ok": bool((st == 0).all())}
 
 
 def main():
@@ -389,6 +394,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--case", choices=["full", "small"], default="full",
                     help="small: one untimed small pass for profiler captures")
+    ap.add_argument("--variant", type=int, default=2, help="search kernel variant of --case small")
+    ap.add_argument("--warps", type=int, default=4, help="chains per CTA of --case small")
     args = ap.parse_args()
     if args.case == "small":
         out = run_small_case(args)

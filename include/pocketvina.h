@@ -218,7 +218,7 @@ typedef struct {
  * max_trials 10, eps 1e-3, rho 1e-4, sigma 0.1, temperature 1.2, amplitude 2.0,
  * steps_per_round 0, use_graph 1, warps_per_cta 0, search_variant -1, host_copy 1, timeout_s 0.
  * Autotuning (warps_per_cta 0 or search_variant -1): the first batched dock of a ligand-size
- * bucket on a context times each candidate launch shape on two MC steps of its own work items
+ * bucket on a context times each candidate launch shape on eight MC steps of its own work items
  * (results are unaffected: the dock itself restarts every chain) and keeps the fastest. */
 void pv_dock_params_default(pv_dock_params* p);
 

@@ -783,7 +783,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     M.top_k = p.top_k;
     M.rank_stride = R->rank_stride;
     M.ranking = R->d_ranking;
-    // autotuning: time each candidate launch shape on two MC steps of its own first work items
+    // autotuning: time each candidate launch shape on eight MC steps of its own first work items
     if (need_tune) {
         static const int cand[][2] = {{0, 2}, {0, 4}, {0, 8}, {1, 4}, {2, 4}, {3, 4}};
         cudaEvent_t t0, t1;
@@ -801,26 +801,31 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
                 continue;
             }
             std::vector<PvItem> trial = make_items(wc);
-            const int n_trial = (int)std::min<size_t>(trial.size(), (size_t)3 * ctx->sms * occ_c);
+            const int n_trial = (int)std::min<size_t>(trial.size(), (size_t)4 * ctx->sms * occ_c);
             SearchArgs a = A;
             a.items = (const PvItem*)((char*)R->d_work + o_items);
             a.n_items = 0;                       // an empty launch first: loads the variant's code
             a.queue = ctr + 1;
             a.step0 = 0;
-            a.step1 = std::min(p.steps, 4);
+            a.step1 = std::min(p.steps, 8);
             cudaError_t x = cudaMemcpyAsync((char*)R->d_work + o_items, trial.data(), sizeof(PvItem) * n_trial,
                                             cudaMemcpyHostToDevice, ctx->stream);
             if (x == cudaSuccess) x = cudaMemsetAsync(ctr, 0, sizeof(int) * 2, ctx->stream);
             if (x == cudaSuccess) x = launch_search_round(a, v, 1, wc, ctx->stream);
             a.n_items = n_trial;
-            if (x == cudaSuccess) x = cudaMemsetAsync(ctr, 0, sizeof(int) * 2, ctx->stream);
-            if (x == cudaSuccess) x = launch_mark_t0(evals + 1, ctx->stream);
-            if (x == cudaSuccess) x = cudaEventRecord(t0, ctx->stream);
-            if (x == cudaSuccess) x = launch_search_round(a, v, std::max(1, std::min(n_trial, ctx->sms * occ_c)), wc, ctx->stream);
-            if (x == cudaSuccess) x = cudaEventRecord(t1, ctx->stream);
-            if (x == cudaSuccess) x = cudaEventSynchronize(t1);
-            float ms = 0.f;
-            if (x == cudaSuccess) x = cudaEventElapsedTime(&ms, t0, t1);
+            float ms = 1e30f;
+            for (int rep = 0; rep < 2 && x == cudaSuccess; ++rep) {   // the faster of two runs
+                x = cudaMemsetAsync(ctr, 0, sizeof(int) * 2, ctx->stream);
+                if (x == cudaSuccess) x = launch_mark_t0(evals + 1, ctx->stream);
+                if (x == cudaSuccess) x = cudaEventRecord(t0, ctx->stream);
+                if (x == cudaSuccess)
+                    x = launch_search_round(a, v, std::max(1, std::min(n_trial, ctx->sms * occ_c)), wc, ctx->stream);
+                if (x == cudaSuccess) x = cudaEventRecord(t1, ctx->stream);
+                if (x == cudaSuccess) x = cudaEventSynchronize(t1);
+                float t = 0.f;
+                if (x == cudaSuccess) x = cudaEventElapsedTime(&t, t0, t1);
+                if (x == cudaSuccess) ms = std::min(ms, t);
+            }
             if (x != cudaSuccess) {
                 cudaEventDestroy(t0);
                 cudaEventDestroy(t1);

@@ -32,6 +32,30 @@ __host__ __device__ inline bool xs_hydrophobic(int t) { return t == 0; }
 __host__ __device__ inline bool xs_donor(int t) { return t == 3 || t == 5 || t == 7 || t == 9; }
 __host__ __device__ inline bool xs_acceptor(int t) { return t == 4 || t == 5 || t == 8 || t == 9; }
 
+// Weighted pair energy at distance r and (dE/dr) / r, from r^2 (< cutoff^2, checked by the caller):
+// one reciprocal square root gives both r and the force scale; the piecewise terms are written as
+// clamps with matching one-sided derivatives (the same values as vina_pair below).
+__device__ __forceinline__ float vina_pair_r2(float r2, float rsum, float hyd, float hb, float& dedr_over_r) {
+    const float rinv = rsqrtf(fmaxf(r2, 1e-12f));
+    const float r = r2 * rinv;
+    const float d = r - rsum;
+    const float a = 2.0f * d;                    // d / 0.5
+    const float g1 = __expf(-a * a);
+    const float b = 0.5f * (d - 3.0f);           // (d - 3) / 2
+    const float g2 = __expf(-b * b);
+    const float rep = fminf(d, 0.0f);
+    const float hydv = fminf(fmaxf(1.5f - d, 0.0f), 1.0f);
+    const float hbv = fminf(fmaxf(d * (-1.0f / 0.7f), 0.0f), 1.0f);
+    const float dhyd = (d >= 0.5f && d < 1.5f) ? -1.0f : 0.0f;
+    const float dhb = (d >= -0.7f && d < 0.0f) ? (-1.0f / 0.7f) : 0.0f;
+    const float e = kWGauss1 * g1 + kWGauss2 * g2 + kWRepulsion * rep * rep +
+                    hyd * (kWHydrophobic * hydv) + hb * (kWHBond * hbv);
+    const float de = kWGauss1 * g1 * (-4.0f * a) + kWGauss2 * g2 * (-b) + (2.0f * kWRepulsion) * rep +
+                     hyd * (kWHydrophobic * dhyd) + hb * (kWHBond * dhb);
+    dedr_over_r = r2 > 1e-12f ? de * rinv : 0.0f;
+    return e;
+}
+
 // Weighted pair energy at distance r (< cutoff, checked by the caller) and dE/dr.
 __device__ __forceinline__ float vina_pair(float r, float rsum, bool hyd, bool hb, float& dedr) {
     float d = r - rsum;
@@ -119,6 +143,15 @@ __device__ __forceinline__ float4 quat_rotate_by(float4 q, float3 om) {
     }
     return quat_normalize(quat_mul(e, q));
 }
+// Rotation matrix of the unit quaternion (w, x, y, z) given already normalised.
+__device__ __forceinline__ Mat3 unit_quat_to_mat(float w, float x, float y, float z) {
+    Mat3 R;
+    R.m[0] = 1.f - 2.f * (y * y + z * z); R.m[1] = 2.f * (x * y - w * z); R.m[2] = 2.f * (x * z + w * y);
+    R.m[3] = 2.f * (x * y + w * z); R.m[4] = 1.f - 2.f * (x * x + z * z); R.m[5] = 2.f * (y * z - w * x);
+    R.m[6] = 2.f * (x * z - w * y); R.m[7] = 2.f * (y * z + w * x); R.m[8] = 1.f - 2.f * (x * x + y * y);
+    return R;
+}
+
 // Rotation by angle t about the unit axis a (Rodrigues).
 __device__ __forceinline__ Mat3 axis_angle(float3 a, float t) {
     float s, c;

@@ -59,9 +59,12 @@ __device__ __forceinline__ void warp_fk(const PvLigBlob& L, WarpScratch& S, cons
         tor = L.frag_tor[lane];
     }
     float psi = shfl(x.psi, (isf && lane > 0) ? 6 + tor : lane);
-    Mat3 Rl;
-    if (lane == 0) Rl = quat_to_mat(x.q);
-    else Rl = axis_angle(axis, isf ? psi : 0.0f);
+    // one rotation path for all lanes: the root's orientation quaternion, or a torsion's
+    // half-angle quaternion (cos psi/2, sin psi/2 * axis) about its hinge axis
+    float s2, c2;
+    sincosf(0.5f * (isf ? psi : 0.0f), &s2, &c2);
+    float4 qr = lane == 0 ? quat_normalize(x.q) : make_float4(c2, s2 * axis.x, s2 * axis.y, s2 * axis.z);
+    const Mat3 Rl = unit_quat_to_mat(qr.x, qr.y, qr.z, qr.w);
     Mat3 M = Rl;
     xa = (lane == 0) ? x.T : make_float3(0.f, 0.f, 0.f);
     for (int lev = 1; lev <= L.h.max_depth; ++lev) {
@@ -132,15 +135,12 @@ static __device__ __forceinline__ float warp_eval(const PvLigBlob& L, WarpScratc
             const float3 d = make_float3(xi.x - xj.x, xi.y - xj.y, xi.z - xj.z);
             const float r2 = dot3(d, d);
             if (r2 < kCutoff2) {
-                float rr = sqrtf(r2), dedr;
-                e_intra += vina_pair(rr, xi.w + xj.w, (pw >> 16) & 1, (pw >> 17) & 1, dedr);
-                if (rr > 1e-6f) {
-                    const float c = dedr / rr;
-                    const float3 f = c * d;
-                    if (h) acc[1] = acc[1] + f; else acc[0] = acc[0] + f;
-                    const float4 gj = S.g[t];
-                    S.g[t] = make_float4(gj.x - f.x, gj.y - f.y, gj.z - f.z, 0.f);
-                }
+                float c;
+                e_intra += vina_pair_r2(r2, xi.w + xj.w, (float)((pw >> 16) & 1), (float)((pw >> 17) & 1), c);
+                const float3 f = c * d;
+                if (h) acc[1] = acc[1] + f; else acc[0] = acc[0] + f;
+                const float4 gj = S.g[t];
+                S.g[t] = make_float4(gj.x - f.x, gj.y - f.y, gj.z - f.z, 0.f);
             }
         }
         __syncwarp();
@@ -213,79 +213,107 @@ __device__ __forceinline__ float eval_pose(ChainCtx& c, const Pose& x, float& g)
     return warp_eval(*c.L, *c.S, c.site, x, g, true);
 }
 
+// L-BFGS two-loop recursion (Eq. 10-11 history, newest pair first) for the direction d = -H g.
+__device__ __forceinline__ float lbfgs_direction(const float* Hs, const float* Hy, float rh, float& al,
+                                                 float g, int stored, int head, int m) {
+    const int lane = threadIdx.x & 31;
+    float q = g;
+    for (int a = 0; a < stored; ++a) {
+        int k = head - 1 - a;
+        if (k < 0) k += m;
+        const float alpha = shfl(rh, k) * warp_sum(Hs[k * 32 + lane] * q);
+        if (lane == k) al = alpha;
+        q -= alpha * Hy[k * 32 + lane];
+    }
+    if (stored > 0) {
+        const int k = head == 0 ? m - 1 : head - 1;
+        const float sk = Hs[k * 32 + lane], yk = Hy[k * 32 + lane];
+        const float sy = warp_sum(sk * yk), yy = warp_sum(yk * yk);
+        q *= sy / yy;
+    }
+    for (int a = stored - 1; a >= 0; --a) {
+        int k = head - 1 - a;
+        if (k < 0) k += m;
+        const float b = shfl(rh, k) * warp_sum(Hy[k * 32 + lane] * q);
+        q += Hs[k * 32 + lane] * (shfl(al, k) - b);
+    }
+    return -q;
+}
+
 // RILC-BFGS (Eq. 6-12): L-BFGS two-loop recursion over the m most recent curvature pairs,
 // Lewis-Overton line search (Eq. 7-8 as failure tests of Armijo / weak Wolfe), curvature-
 // guarded history update (Eq. 11), stop on ||g|| <= eps (Eq. 12), non-descent, or max_iter.
 // Updates x in place and returns SF(x). All control flow is warp-uniform. The history lives in
 // the warp's shared scratch (a ring of m slots); rho and alpha of slot k sit in lane k.
+// Written as one loop with a single evaluation site (the start point, then every line-search
+// trial), so the evaluator's code appears once.
 static __device__ __noinline__ float warp_bfgs(ChainCtx& c, Pose& x, const PvSearchConst& C, int max_iter, int m) {
     const int lane = threadIdx.x & 31;
     const int n_tan = 6 + c.L->h.n_rot;
     float* Hs = &c.S->hs[0][0];
     float* Hy = &c.S->hy[0][0];
-    float g;
-    float f = eval_pose(c, x, g);
     float rh = 0.f, al = 0.f;
-    int stored = 0, head = 0;
-    for (int it = 0; it < max_iter; ++it) {
-        // two-loop recursion, newest pair first
-        float q = g;
-        for (int a = 0; a < stored; ++a) {
-            int k = head - 1 - a;
-            if (k < 0) k += m;
-            const float alpha = shfl(rh, k) * warp_sum(Hs[k * 32 + lane] * q);
-            if (lane == k) al = alpha;
-            q -= alpha * Hy[k * 32 + lane];
-        }
-        if (stored > 0) {
-            const int k = head == 0 ? m - 1 : head - 1;
-            const float sk = Hs[k * 32 + lane], yk = Hy[k * 32 + lane];
-            const float sy = warp_sum(sk * yk), yy = warp_sum(yk * yk);
-            q *= sy / yy;
-        }
-        for (int a = stored - 1; a >= 0; --a) {
-            int k = head - 1 - a;
-            if (k < 0) k += m;
-            const float b = shfl(rh, k) * warp_sum(Hy[k * 32 + lane] * q);
-            q += Hs[k * 32 + lane] * (shfl(al, k) - b);
-        }
-        const float d = -q;
-        const float gd = warp_sum(g * d);
-        if (!(gd < 0.f)) break;
-        // Lewis-Overton bracketing
-        float lam = 1.f, lo = 0.f, hi = -1.f, ft = 0.f, gt = 0.f, flo = 0.f, glo = 0.f;
-        Pose xt = x;
-        bool accepted = false, have_lo = false;
-        for (int tr = 0; tr < C.bfgs_max_trials; ++tr) {
-            xt = retract(x, lam * d, n_tan);
-            ft = eval_pose(c, xt, gt);
-            const float gtd = warp_sum(gt * d);
-            if (!(ft <= f + lam * C.rho * gd)) {
-                hi = lam;
+    int stored = 0, head = 0, it = 0, tr = 0;
+    float f = 0.f, g = 0.f, d = 0.f, gd = 0.f;
+    float lam = 1.f, lo = 0.f, hi = -1.f, flo = 0.f, glo = 0.f;
+    bool have_lo = false, start = true;
+    Pose xt = x;
+    for (;;) {
+        float ge;
+        const float fe = eval_pose(c, xt, ge);
+        bool next_iter = false, done = false;
+        if (start) {                        // the start point: f, g at x
+            start = false;
+            f = fe;
+            g = ge;
+            next_iter = true;
+        } else {                            // a line-search trial at x + lam d
+            const float gtd = warp_sum(ge * d);
+            bool take = false;
+            float ft = fe, gt = ge;
+            if (!(fe <= f + lam * C.rho * gd)) {
+                hi = lam;                                   // Eq. 7 holds: Armijo fails
             } else if (gtd < C.sigma * gd) {
-                lo = lam; have_lo = true; flo = ft; glo = gt;
+                lo = lam; have_lo = true; flo = fe; glo = ge;   // Eq. 8 holds: Wolfe fails
             } else {
-                accepted = true;
-                break;
+                take = true;
             }
-            lam = hi < 0.f ? 2.f * lam : 0.5f * (lo + hi);
+            if (!take) {
+                ++tr;
+                if (tr < C.bfgs_max_trials) {
+                    lam = hi < 0.f ? 2.f * lam : 0.5f * (lo + hi);
+                    xt = retract(x, lam * d, n_tan);
+                    continue;
+                }
+                if (!have_lo) break;                        // no acceptable step: stop here
+                lam = lo; ft = flo; gt = glo;
+                xt = retract(x, lam * d, n_tan);            // the same arithmetic as that trial
+                take = true;
+            }
+            // accepted step: curvature-guarded history update, move, convergence test
+            const float s = lam * d, y = gt - g;
+            const float ys = warp_sum(y * s), ss = warp_sum(s * s), gn = sqrtf(warp_sum(g * g));
+            if (ss > 0.f && ys / ss > C.eps * gn) {
+                Hs[head * 32 + lane] = s;
+                Hy[head * 32 + lane] = y;
+                if (lane == head) rh = 1.f / ys;
+                head = head + 1 == m ? 0 : head + 1;
+                stored = min(stored + 1, m);
+            }
+            x = xt; g = gt; f = ft;
+            ++it;
+            if (sqrtf(warp_sum(g * g)) <= C.eps) done = true;
+            next_iter = !done;
         }
-        if (!accepted) {
-            if (!have_lo) break;
-            lam = lo; ft = flo; gt = glo;
-            xt = retract(x, lam * d, n_tan);   // the same arithmetic as the trial at lam = lo
+        if (done) break;
+        if (next_iter) {
+            if (it >= max_iter) break;
+            d = lbfgs_direction(Hs, Hy, rh, al, g, stored, head, m);
+            gd = warp_sum(g * d);
+            if (!(gd < 0.f)) break;
+            lam = 1.f; lo = 0.f; hi = -1.f; have_lo = false; tr = 0;
+            xt = retract(x, lam * d, n_tan);
         }
-        const float s = lam * d, y = gt - g;
-        const float ys = warp_sum(y * s), ss = warp_sum(s * s), gn = sqrtf(warp_sum(g * g));
-        if (ss > 0.f && ys / ss > C.eps * gn) {
-            Hs[head * 32 + lane] = s;
-            Hy[head * 32 + lane] = y;
-            if (lane == head) rh = 1.f / ys;
-            head = head + 1 == m ? 0 : head + 1;
-            stored = min(stored + 1, m);
-        }
-        x = xt; g = gt; f = ft;
-        if (sqrtf(warp_sum(g * g)) <= C.eps) break;
     }
     __syncwarp();
     return f;
