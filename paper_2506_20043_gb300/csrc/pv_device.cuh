@@ -44,8 +44,8 @@ __device__ __forceinline__ float vina_pair_r2(float r2, float rsum, float hyd, f
     const float b = 0.5f * (d - 3.0f);           // (d - 3) / 2
     const float g2 = __expf(-b * b);
     const float rep = fminf(d, 0.0f);
-    const float hydv = fminf(fmaxf(1.5f - d, 0.0f), 1.0f);
-    const float hbv = fminf(fmaxf(d * (-1.0f / 0.7f), 0.0f), 1.0f);
+    const float hydv = __saturatef(1.5f - d);
+    const float hbv = __saturatef(d * (-1.0f / 0.7f));
     const float dhyd = (d >= 0.5f && d < 1.5f) ? -1.0f : 0.0f;
     const float dhb = (d >= -0.7f && d < 0.0f) ? (-1.0f / 0.7f) : 0.0f;
     const float e = kWGauss1 * g1 + kWGauss2 * g2 + kWRepulsion * rep * rep +

@@ -101,36 +101,58 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) search_round_kernel(SearchA
             float* curs = c.S->cur;
             float e_cur, e_best;
             uint32_t evals_before = 0;
-            if (A.step0 == 0) {
-                Pose x0 = random_pose(L, s_pocket, (uint32_t)chain, (uint32_t)item.pair, C);
-                float g;
-                e_cur = warp_eval(L, *c.S, c.site, x0, g, false);
-                c.evals++;
-                e_best = e_cur;
-                store_pose(curs, x0, n_rot);
-                store_pose(rec + PV_CH_BEST, x0, n_rot);
-            } else {
+            if (A.step0 != 0) {
                 for (int i = lane; i < 7 + n_rot; i += 32) curs[i] = rec[PV_CH_CUR + i];
                 e_cur = rec[PV_CH_ECUR];
                 e_best = rec[PV_CH_EBEST];
                 evals_before = __float_as_uint(rec[PV_CH_EVALS]);
             }
             __syncwarp();
+            // One local-search call site for the whole chain (so the optimiser and the evaluator are
+            // inlined once): stage 0 evaluates the random start (a zero-iteration search), stage 1
+            // optimises a mutation of the current pose, stage 2 refines a new best.
             int flags = 0;
-            for (int s = A.step0; s < A.step1; ++s) {
-                Pose cand = load_pose(curs, n_rot);
-                const float u = mutate(L, cand, (uint32_t)chain, (uint32_t)item.pair, s, C);
-                const float e_new = warp_bfgs(c, cand, C, max_iter, C.bfgs_m);
-                if (e_new < e_cur || u < expf((e_cur - e_new) / C.temperature)) {
+            int s = A.step0, stage = A.step0 == 0 ? 0 : 1;
+            float u = 0.f;
+            Pose cand;
+            if (stage == 0) cand = random_pose(L, s_pocket, (uint32_t)chain, (uint32_t)item.pair, C);
+            while (stage == 0 || s < A.step1) {
+                if (stage == 1) {
+                    cand = load_pose(curs, n_rot);
+                    u = mutate(L, cand, (uint32_t)chain, (uint32_t)item.pair, s, C);
+                }
+                const float e_new = warp_bfgs(c, cand, C, stage == 0 ? 0 : max_iter, C.bfgs_m);
+                if (stage == 0) {
                     e_cur = e_new;
-                    if (e_cur < e_best) {
-                        e_cur = warp_bfgs(c, cand, C, max_iter, C.bfgs_m);
-                        store_pose(rec + PV_CH_BEST, cand, n_rot);
-                        e_best = e_cur;
+                    e_best = e_new;
+                    store_pose(curs, cand, n_rot);
+                    store_pose(rec + PV_CH_BEST, cand, n_rot);
+                    __syncwarp();
+                    stage = 1;
+                    continue;
+                }
+                if (stage == 1) {
+                    if (!(e_new < e_cur || u < expf((e_cur - e_new) / C.temperature))) {
+                        ++s;                 // rejected
+                    } else if (e_new < e_best) {
+                        stage = 2;           // accepted and a new best: refine it first
+                        continue;
+                    } else {
+                        e_cur = e_new;       // accepted
+                        __syncwarp();
+                        store_pose(curs, cand, n_rot);
+                        __syncwarp();
+                        ++s;
                     }
+                } else {                     // stage 2: the refined new best
+                    e_cur = e_new;
+                    e_best = e_new;
+                    store_pose(rec + PV_CH_BEST, cand, n_rot);
                     __syncwarp();
                     store_pose(curs, cand, n_rot);
                     __syncwarp();
+                    stage = 1;
+                    ++s;
                 }
                 if (A.timeout_ns) {
                     unsigned long long now = lane == 0 ? globaltimer() : 0ull;

@@ -59,26 +59,29 @@ __device__ __forceinline__ void warp_fk(const PvLigBlob& L, WarpScratch& S, cons
         tor = L.frag_tor[lane];
     }
     float psi = shfl(x.psi, (isf && lane > 0) ? 6 + tor : lane);
-    // one rotation path for all lanes: the root's orientation quaternion, or a torsion's
-    // half-angle quaternion (cos psi/2, sin psi/2 * axis) about its hinge axis
+    // local rotation of every fragment as a unit quaternion: the root's orientation, or a
+    // torsion's half-angle quaternion (cos psi/2, sin psi/2 * axis) about its hinge axis; world
+    // rotations compose down the tree level by level (Q_f = Q_parent (x) q_f)
     float s2, c2;
     sincosf(0.5f * (isf ? psi : 0.0f), &s2, &c2);
-    float4 qr = lane == 0 ? quat_normalize(x.q) : make_float4(c2, s2 * axis.x, s2 * axis.y, s2 * axis.z);
-    const Mat3 Rl = unit_quat_to_mat(qr.x, qr.y, qr.z, qr.w);
-    Mat3 M = Rl;
+    float4 Q = lane == 0 ? quat_normalize(x.q) : make_float4(c2, s2 * axis.x, s2 * axis.y, s2 * axis.z);
+    const float4 ql = Q;
     xa = (lane == 0) ? x.T : make_float3(0.f, 0.f, 0.f);
     for (int lev = 1; lev <= L.h.max_depth; ++lev) {
         const bool mine = isf && depth == lev;
         const int src = mine ? parent : lane;
-        Mat3 Mp;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Mp.m[k] = shfl(M.m[k], src);
-        float3 xp = make_float3(shfl(xa.x, src), shfl(xa.y, src), shfl(xa.z, src));
+        const float4 Qp = make_float4(shfl(Q.x, src), shfl(Q.y, src), shfl(Q.z, src), shfl(Q.w, src));
+        const float3 xp = make_float3(shfl(xa.x, src), shfl(xa.y, src), shfl(xa.z, src));
         if (mine) {
-            M = mat_mul(Mp, Rl);
-            xa = mat_vec(Mp, off) + xp;
+            Q = quat_mul(Qp, ql);
+            // anchor: parent's anchor + parent rotation applied to the offset, v + 2w(u x v) + 2u x (u x v)
+            const float3 u = make_float3(Qp.y, Qp.z, Qp.w);
+            const float3 t1 = cross3(u, off);
+            const float3 t2 = cross3(u, t1);
+            xa = xp + off + (2.f * Qp.x) * t1 + 2.f * t2;
         }
     }
+    const Mat3 M = unit_quat_to_mat(Q.x, Q.y, Q.z, Q.w);
     const int n = L.h.n_atoms;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -125,25 +128,58 @@ static __device__ __forceinline__ float warp_eval(const PvLigBlob& L, WarpScratc
         }
     }
     __syncwarp();
+    // Pair rounds. Positions and pair words are read-only here, so the next round's word and
+    // partner position are loaded before the current round's force update and its __syncwarp
+    // (which orders only the force scatter).
     const int rounds = L.h.n_rounds;
-    for (int r = 0; r < rounds; ++r) {
-        const uint32_t pw = L.pairs[r * 32 + lane];
-        if (pw >> 31) {
-            const int t = pw & 63, h = (pw >> 6) & 1;
-            const float4 xi = h ? own[1] : own[0];
-            const float4 xj = S.x[t];
-            const float3 d = make_float3(xi.x - xj.x, xi.y - xj.y, xi.z - xj.z);
-            const float r2 = dot3(d, d);
-            if (r2 < kCutoff2) {
+    if (rounds > 0) {
+        uint32_t pw = L.pairs[lane];
+        float4 xj = S.x[pw & 63];
+        if (n <= 32) {                        // every source is the lane's first atom
+            for (int r = 0; r < rounds; ++r) {
+                const uint32_t pw_n = r + 1 < rounds ? L.pairs[(r + 1) * 32 + lane] : 0u;
+                const float4 xj_n = S.x[pw_n & 63];
+                const float3 d = make_float3(own[0].x - xj.x, own[0].y - xj.y, own[0].z - xj.z);
+                const float r2 = dot3(d, d);
+                const bool live = (pw >> 31) && r2 < kCutoff2;
                 float c;
-                e_intra += vina_pair_r2(r2, xi.w + xj.w, (float)((pw >> 16) & 1), (float)((pw >> 17) & 1), c);
-                const float3 f = c * d;
-                if (h) acc[1] = acc[1] + f; else acc[0] = acc[0] + f;
-                const float4 gj = S.g[t];
-                S.g[t] = make_float4(gj.x - f.x, gj.y - f.y, gj.z - f.z, 0.f);
+                const float e = vina_pair_r2(r2, own[0].w + xj.w, (float)((pw >> 16) & 1), (float)((pw >> 17) & 1), c);
+                if (live) {
+                    e_intra += e;
+                    const float3 f = c * d;
+                    acc[0] = acc[0] + f;
+                    const int t = pw & 63;
+                    const float4 gj = S.g[t];
+                    S.g[t] = make_float4(gj.x - f.x, gj.y - f.y, gj.z - f.z, 0.f);
+                }
+                __syncwarp();
+                pw = pw_n;
+                xj = xj_n;
+            }
+        } else {
+            for (int r = 0; r < rounds; ++r) {
+                const uint32_t pw_n = r + 1 < rounds ? L.pairs[(r + 1) * 32 + lane] : 0u;
+                const float4 xj_n = S.x[pw_n & 63];
+                const int h = (pw >> 6) & 1;
+                const float4 xi = h ? own[1] : own[0];
+                const float3 d = make_float3(xi.x - xj.x, xi.y - xj.y, xi.z - xj.z);
+                const float r2 = dot3(d, d);
+                const bool live = (pw >> 31) && r2 < kCutoff2;
+                float c;
+                const float e = vina_pair_r2(r2, xi.w + xj.w, (float)((pw >> 16) & 1), (float)((pw >> 17) & 1), c);
+                if (live) {
+                    e_intra += e;
+                    const float3 f = c * d;
+                    if (h) acc[1] = acc[1] + f; else acc[0] = acc[0] + f;
+                    const int t = pw & 63;
+                    const float4 gj = S.g[t];
+                    S.g[t] = make_float4(gj.x - f.x, gj.y - f.y, gj.z - f.z, 0.f);
+                }
+                __syncwarp();
+                pw = pw_n;
+                xj = xj_n;
             }
         }
-        __syncwarp();
     }
     // total dSF/dx of the lane's atoms: own share (registers) + shares received as a target
 #pragma unroll
@@ -247,7 +283,7 @@ __device__ __forceinline__ float lbfgs_direction(const float* Hs, const float* H
 // the warp's shared scratch (a ring of m slots); rho and alpha of slot k sit in lane k.
 // Written as one loop with a single evaluation site (the start point, then every line-search
 // trial), so the evaluator's code appears once.
-static __device__ __noinline__ float warp_bfgs(ChainCtx& c, Pose& x, const PvSearchConst& C, int max_iter, int m) {
+__device__ __forceinline__ float warp_bfgs(ChainCtx& c, Pose& x, const PvSearchConst& C, int max_iter, int m) {
     const int lane = threadIdx.x & 31;
     const int n_tan = 6 + c.L->h.n_rot;
     float* Hs = &c.S->hs[0][0];
