@@ -153,16 +153,18 @@ def run_ours(args):
     params = api.DockParams(chains=CHAINS, steps=STEPS, seed=rank, top_k=TOP_K, host_copy=False)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    def step():
+    def step(mid=None):
         gs = ctx.build_grids(dev_rec, boxes, types)
+        if mid is not None:
+            mid.record(stream)
         r = ctx.dock(gs, [lig], pockets, params)
         return gs, r
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    times, search_s, evals, launches = [], 0.0, 0, 0
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times, grid_t, search_s, evals, launches = [], [], 0.0, 0, 0
+    e0, em, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.zero_()                                  # L2 flushed between timed steps
@@ -170,10 +172,11 @@ def run_ours(args):
                 dist.barrier()
             torch.cuda.synchronize()
             e0.record(stream)
-            gs, r = step()
+            gs, r = step(em)
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1) * 1e-3)
+            grid_t.append(e0.elapsed_time(em) * 1e-3)
             ev, _, st = r.stats()
             assert (st == 0).all(), st
             s_s, n_l, _ = r.timing()
@@ -201,6 +204,8 @@ def run_ours(args):
         per_eval_traffic = stored_traffic()
         evals_per_launch = evals / max(launches, 1)
         n_rounds = launches // max(args.steps, 1)
+        _, _, gather_gbs = ctx.measure_gather(gs, 0, n_points=1 << 24, reps=10)
+        search_gather_gbs = evals * gbytes / search_s / 1e9
         out = {
             "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_t / args.steps * 1e3, 3), "higher_is_better": True,
@@ -210,15 +215,20 @@ def run_ours(args):
                        "intra_pairs": lig.n_pairs, "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "inputs": "receptor, ligand and boxes resident in HBM; grids rebuilt every step",
                        "parallelism": f"{world} independent receptors, one per GPU",
-                       "search_launch": {"variant": shape[0], "chains_per_cta": shape[1]}},
+                       "search_launch": {"variant": shape[0], "warps_per_cta": shape[1], "chains_per_warp": 2 if shape[0] >= 4 else 1}},
             "evals_per_s": round(evals / total_t * world, 1),
+            "breakdown": {"grid_maps_ms": round(float(np.mean(grid_t)) * 1e3, 3),
+                          "dock_ms": round((total_t / args.steps - float(np.mean(grid_t))) * 1e3, 3),
+                          "dock_only_pairs_per_s": round(n_pairs * world / (total_t / args.steps - float(np.mean(grid_t))), 4)},
             "evals_per_step_per_gpu": evals // max(args.steps, 1),
             "roofline": {"kernel": "search_round_kernel", "bound": "alu", "achieved": round(achieved, 3),
                          "peak": round(peak_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
                          "traffic": (round(per_eval_traffic * evals_per_launch) if per_eval_traffic else None),
                          "peak_source": f"FP32 FMA peak = {n_sm} SMs x 128 lanes x 2 x {max_mhz:.0f} MHz",
                          "flops_per_eval": flops, "launch_ms": round(search_s / max(launches, 1) * 1e3, 3),
-                         "l2_gather_gbs": round(evals * gbytes / search_s / 1e9, 1)},
+                         "l2_gather_gbs": round(search_gather_gbs, 1),
+                         "gather_ceiling_gbs": round(gather_gbs, 1),
+                         "gather_frac": round(search_gather_gbs / gather_gbs, 4)},
             "gpu_launches": args.steps * (6 + 1 + n_rounds + 2),
             "clocks": clocks,
         }
@@ -270,8 +280,14 @@ def run_score_microbench(ctx, api, torch, reps=20):
     dt = e0.elapsed_time(e1) * 1e-3 / reps
     flops, gbytes = lig.cost()
     n = len(poses)
+    # the gather step alone on the same maps: its rate bounds the score kernel's gather
+    _, g_pts, g_gbs = ctx.measure_gather(gs, 0, n_points=1 << 24, reps=10)
+    l2 = n * gbytes / dt / 1e9
     return {"evals_per_s": round(n / dt, 1), "ms_per_launch": round(dt * 1e3, 4), "poses": n,
-            "achieved_tflops": round(n * flops / dt / 1e12, 3), "l2_gather_gbs": round(n * gbytes / dt / 1e9, 1)}
+            "achieved_tflops": round(n * flops / dt / 1e12, 3), "l2_gather_gbs": round(l2, 1),
+            "gather_probe": {"gbs": round(g_gbs, 1), "interpolations_per_s": round(g_pts, 1),
+                             "note": "trilinear value + gradient alone, hashed positions in the box, 32 B per point"},
+            "gather_frac": round(l2 / g_gbs, 4)}
 
 
 def run_e2e(ctx, api, torch, rec, boxes, lig_src, types, pockets, steps, seed):
@@ -322,15 +338,19 @@ def oracle_sample(rec, boxes, lig_src, budget_s=12.0):
     _, _, ev = O.mc_chains(L, og, box, p, unit=0, n_chains=n_chains, threads=cores)
     t_dock = time.perf_counter() - t0
     per_pair = t_grid + t_dock * CHAINS / n_chains
+    # one core: two chains of 100 MC steps
+    t0 = time.perf_counter()
+    _, _, ev1 = O.mc_chains(L, og, box, O.SearchParams(seed=1, steps=100), unit=0, n_chains=2, threads=1)
+    single_core_evals_s = float(ev1.sum()) / (time.perf_counter() - t0)
     sample = (f"1 pocket: full FP64 grid maps ({len(set(L.xs.tolist()))} types) + {n_chains} of {CHAINS} "
               f"chains x {STEPS} MC steps; time scaled x {CHAINS / n_chains:.1f} to the pair")
-    return per_pair, float(ev.sum()) / t_dock, cores, sample, t_grid + t_dock
+    return per_pair, float(ev.sum()) / t_dock, cores, sample, t_grid + t_dock, single_core_evals_s
 
 
 def run_cpu_baseline(rec, boxes, lig_src, budget_s=12.0):
-    per_pair, evals_s, cores, sample, _ = oracle_sample(rec, boxes, lig_src, budget_s)
+    per_pair, evals_s, cores, sample, _, single = oracle_sample(rec, boxes, lig_src, budget_s)
     return {"value": round(1.0 / per_pair, 6), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-            "evals_per_s": round(evals_s, 1)}
+            "evals_per_s": round(evals_s, 1), "single_core_evals_per_s": round(single, 1)}
 
 
 def run_reference(args):
@@ -356,6 +376,100 @@ def run_reference(args):
             "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_batch_workload(args):
+    """The uneven-batch and screening shapes (one GPU), each step building every grid map and
+    docking every pair in one batched call; its own JSON line (pairs/s, evals/s, the search
+    kernel's roofline). uneven: a 6,000-atom receptor with 5 pockets x 512 ligands of 10-60 atoms and
+    0-15 torsions, 64 chains x 1,000 MC steps per pair. screening: 256 receptors of 1,500-8,000
+    atoms with 3 pockets each (768 pockets of maps resident in HBM), --ligands-per-receptor
+    30-atom / 6-torsion ligands docked into their receptor's 3 pockets, 32 chains x 1,000 steps."""
+    import torch
+    import paper_2506_20043_gb300 as pv
+    pv.build()
+    from paper_2506_20043_gb300 import api
+    ctx = api.Context(0)
+    t_gen = time.perf_counter()
+    if args.workload == "uneven":
+        w = S.uneven(seed=0)
+        recs, boxes = w.receptors, w.boxes
+        pair_lig = [li for li in range(len(w.ligands)) for _ in range(len(boxes[0]))]
+        pair_pocket = [p for _ in range(len(w.ligands)) for p in range(len(boxes[0]))]
+        desc = ("uneven batch: 6,000-atom receptor, 5 pockets (24 A boxes), 512 ligands of 10-60 atoms and "
+                "0-15 torsions, 64 chains x 1,000 MC steps per pair, top-9")
+    else:
+        w = S.screening(seed=0, ligands_per_receptor=args.ligands_per_receptor)
+        recs, boxes = w.receptors, w.boxes
+        pair_lig, pair_pocket = [], []
+        for r, ids in enumerate(w.ligands_per_receptor):
+            for li in ids:
+                for p in range(len(boxes[r])):
+                    pair_lig.append(li)
+                    pair_pocket.append(3 * r + p)
+        desc = (f"screening: 256 receptors of 1,500-8,000 atoms, 3 pockets each (768 x 24 A boxes), "
+                f"{args.ligands_per_receptor} ligands of 30 atoms / 6 torsions per receptor into its 3 pockets, "
+                f"32 chains x 1,000 MC steps, top-9")
+    t_gen = time.perf_counter() - t_gen
+    ligs = [ctx.ligand(l) for l in w.ligands]
+    types = sorted(set(int(t) for l in ligs for t in l.xs_types.tolist()))
+    dev_recs = [S.Receptor(torch.tensor(r.xyz, dtype=torch.float32, device="cuda"), torch.tensor(r.element, device="cuda"),
+                           torch.tensor(r.donor, device="cuda"), torch.tensor(r.acceptor, device="cuda")) for r in recs]
+    params = api.DockParams(chains=w.chains, steps=w.steps, seed=0, top_k=w.top_k, host_copy=False)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = ctx.stream
+
+    def step():
+        gs = ctx.build_grids(dev_recs[0], boxes[0], types)
+        for r in range(1, len(recs)):
+            gs.append(dev_recs[r], boxes[r])
+        return gs, ctx.dock_pairs(gs, ligs, pair_lig, pair_pocket, params)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times, evals, search_s, map_bytes = [], 0, 0.0, 0
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            gs, r = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) * 1e-3)
+            ev, _, st = r.stats()
+            assert (st == 0).all(), st
+            s_s, _, _ = r.timing()
+            evals += ev
+            search_s += s_s
+            shape = r.launch_shape()
+            map_bytes = gs.bytes
+    total_t = float(np.sum(times))
+    n_pairs = len(pair_lig)
+    # roofline of the search kernel: the pair-weighted mean cost of the batch's ligands
+    costs = [l.cost() for l in ligs]
+    w_flops = float(np.mean([costs[li][0] for li in pair_lig]))
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    clocks = clk.summary()
+    max_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = n_sm * 128 * 2 * max_mhz * 1e6 / 1e12
+    achieved = evals * w_flops / search_s / 1e12
+    return {"metric": METRIC, "value": round(n_pairs * args.steps / total_t, 3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_t / args.steps * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "pairs_per_step": n_pairs, "ligands": len(ligs), "pockets": gs.n_pockets,
+                       "map_bytes": int(map_bytes), "chains": w.chains, "mc_steps": w.steps,
+                       "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                       "inputs": "receptors and ligands resident in HBM; grids rebuilt every step",
+                       "search_launch": {"variant": shape[0], "warps_per_cta": shape[1]},
+                       "host_generation_s": round(t_gen, 1)},
+            "evals_per_s": round(evals / total_t, 1), "search_s_per_step": round(search_s / args.steps, 3),
+            "roofline": {"kernel": "search_round_kernel", "bound": "alu", "achieved": round(achieved, 3),
+                         "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                         "flops_per_eval": round(w_flops, 1)},
+            "clocks": clocks}
 
 
 def run_small_case(args):
@@ -392,6 +506,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-micro", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", choices=["multipocket", "uneven", "screening"], default="multipocket",
+                    help="multipocket: the headline line; uneven / screening: the batch shapes, their own line")
+    ap.add_argument("--ligands-per-receptor", type=int, default=10, help="screening: ligands docked per receptor")
     ap.add_argument("--case", choices=["full", "small"], default="full",
                     help="small: one untimed small pass for profiler captures")
     ap.add_argument("--variant", type=int, default=0, help="search kernel variant of --case small")
@@ -399,6 +516,8 @@ def main():
     args = ap.parse_args()
     if args.case == "small":
         out = run_small_case(args)
+    elif args.workload != "multipocket" and args.impl == "ours":
+        out = run_batch_workload(args)
     else:
         out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:

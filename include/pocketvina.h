@@ -186,6 +186,15 @@ pv_status pv_score_backward(pv_context* ctx, const pv_grid_set* set, const pv_li
 pv_status pv_pose_coords(pv_context* ctx, const pv_ligand* lig, int32_t n_poses,
                          const float* dev_pose, float* dev_xyz);
 
+/* Microbenchmark of the trilinear gather alone (Eq. 3's e_inter from the grid cache, with its
+ * gradient), the ceiling of that step inside pv_score and the search: each launch interpolates
+ * n_points hashed positions in the pocket's box on hashed map slots of the set. One untimed
+ * launch, then `reps` launches timed with events on the context stream; *ms_per_launch = their
+ * mean device time. Algorithmic bytes: 32 per point (8 corner values of 4 bytes).
+ * PV_ERR_ARG for a bad pocket, n_points < 1, reps < 1 or a null output. Synchronous. */
+pv_status pv_measure_gather(pv_context* ctx, const pv_grid_set* set, int32_t pocket, int64_t n_points,
+                            int32_t reps, float* ms_per_launch);
+
 /* ------------------------------------------------------------------------- docking --- */
 
 typedef struct {
@@ -208,8 +217,13 @@ typedef struct {
     int32_t steps_per_round;   /* batched: MC steps per kernel launch (round); 0 = automatic */
     int32_t use_graph;         /* batched: capture the launch sequence in a CUDA graph */
     int32_t warps_per_cta;     /* batched: chains per CTA; 0 = autotuned */
-    int32_t search_variant;    /* batched: register budget of the search kernel, 0..3 (0 widest,
-                                  3 = 64 registers); -1 = autotuned */
+    int32_t search_variant;    /* batched: search kernel variant; 0..3 one chain per warp, 4..7
+                                  one chain per half warp (ligands of <= 32 atoms and <= 10
+                                  torsions); within each group decreasing register budgets and
+                                  bitwise identical results (the team width fixes the order of
+                                  the floating-point sums). -1 = autotuned within the half-warp
+                                  group when every ligand has at most 16 atoms (and fits it),
+                                  else within the whole-warp group */
     int32_t host_copy;         /* 1: copy results to host memory before returning */
     double timeout_s;          /* watchdog per launch; 0 = none. Overrun -> PV_ERR_TIMEOUT */
 } pv_dock_params;

@@ -209,6 +209,15 @@ class Context:
                     "pv_pose_coords")
         return out
 
+    def measure_gather(self, grids: "GridSet", pocket: int = 0, n_points: int = 1 << 24, reps: int = 10):
+        """The trilinear gather alone (value + gradient at hashed positions in the pocket's box):
+        returns (milliseconds per launch, points per second, algorithmic GB/s at 32 B per point)."""
+        ms = C.c_float()
+        self._check(self.lib.pv_measure_gather(self.h, grids.h, int(pocket), int(n_points), int(reps), C.byref(ms)),
+                    "pv_measure_gather")
+        t = ms.value * 1e-3
+        return ms.value, n_points / t, 32.0 * n_points / t / 1e9
+
     # --------------------------------------------------------------------------- docking --
     def dock(self, grids: "GridSet", ligands: Sequence["Ligand"], pocket_ids: Sequence[int],
              params: Optional[DockParams] = None, **kw) -> "DockResult":
@@ -387,7 +396,7 @@ class DockResult:
         return s.value, n.value, t.value
 
     def launch_shape(self):
-        """(search kernel variant, chains per CTA) used by the batched search."""
+        """(search kernel variant, warps per CTA) used by the batched search."""
         v, w = C.c_int32(), C.c_int32()
         self.ctx._check(self.ctx.lib.pv_dock_result_launch(self.h, C.byref(v), C.byref(w)), "pv_dock_result_launch")
         return v.value, w.value

@@ -32,7 +32,7 @@ struct pv_context {
     int sms = 0;
     cudaStream_t capture_stream = nullptr;   // graphs are captured here (the caller's stream may
                                              // be the legacy default stream, which cannot capture)
-    // autotuned (search variant, warps per CTA) per (ligand atoms / 8, pair rounds / 4)
+    // autotuned (search variant, warps per CTA) per (ligand atoms / 8 and team width, pair rounds / 4)
     std::map<std::pair<int, int>, std::pair<int, int>> tuned;
 };
 
@@ -547,6 +547,37 @@ extern "C" pv_status pv_pose_coords(pv_context* ctx, const pv_ligand* lig, int32
     return PV_OK;
 }
 
+extern "C" pv_status pv_measure_gather(pv_context* ctx, const pv_grid_set* set, int32_t pocket, int64_t n_points,
+                                       int32_t reps, float* ms_per_launch) {
+    if (!ctx || ctx->magic != kCtxMagic) return PV_ERR_STATE;
+    if (!set || set->ctx != ctx) return fail(ctx, PV_ERR_STATE, "grid set of another context");
+    if (pocket < 0 || pocket >= (int)set->pockets.size() || n_points < 1 || reps < 1 || !ms_per_launch)
+        return fail(ctx, PV_ERR_ARG, "bad arguments");
+    DeviceGuard g(ctx->device);
+    const PvPocket& P = set->pockets[pocket];
+    float* sink = nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    sink = (float*)dalloc(ctx, sizeof(float));
+    if (!sink) return fail(ctx, PV_ERR_OOM, "device allocation failed");
+    cudaError_t e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    if (e == cudaSuccess) e = launch_gather_probe(P, set->n_maps, n_points, 1u, sink, ctx->sms, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(t0, ctx->stream);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r)
+        e = launch_gather_probe(P, set->n_maps, n_points, 2u + (uint32_t)r * 977u, sink, ctx->sms, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(t1, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, sink);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gather probe");
+    *ms_per_launch = ms / (float)reps;
+    return PV_OK;
+}
+
 // ----------------------------------------------------------------------------- docking ---
 
 extern "C" void pv_dock_params_default(pv_dock_params* p) {
@@ -599,7 +630,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     if (p.mode != PV_MODE_BATCHED && p.mode != PV_MODE_PLAIN) return fail(ctx, PV_ERR_ARG, "unknown mode");
     if (p.warps_per_cta < 0 || p.warps_per_cta > 16) return fail(ctx, PV_ERR_ARG, "warps_per_cta must be 0..16");
     if (p.search_variant < -1 || p.search_variant >= kSearchVariants)
-        return fail(ctx, PV_ERR_ARG, "search_variant must be -1..3");
+        return fail(ctx, PV_ERR_ARG, "search_variant must be -1..7");
     if (p.search_variant >= 0 && p.warps_per_cta * 32 > search_variant_max_warps(p.search_variant) * 32)
         return fail(ctx, PV_ERR_ARG, "warps_per_cta exceeds the search variant's CTA size");
     if (!(p.temperature > 0.f)) return fail(ctx, PV_ERR_ARG, "temperature must be > 0");
@@ -650,18 +681,29 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     std::vector<int> order(n_pairs);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pair_pocket[a] < pair_pocket[b]; });
-    auto make_items = [&](int w) {
+    // a work item is one CTA's chains of one pair: warps x chains per warp
+    auto make_items = [&](int chains_per_cta) {
         std::vector<PvItem> it;
         for (int q : order)
-            for (int c0 = 0; c0 < p.chains; c0 += w) it.push_back(PvItem{q, c0});
+            for (int c0 = 0; c0 < p.chains; c0 += chains_per_cta) it.push_back(PvItem{q, c0});
         return it;
     };
-    int variant = p.search_variant >= 0 ? p.search_variant : 0;
+    bool all_team16 = true;
+    for (int i = 0; i < n_ligs; ++i) all_team16 = all_team16 && ligs[i]->rec.team16;
+    if (p.search_variant >= 0 && search_variant_lanes(p.search_variant) == 16 && !all_team16)
+        return fail(ctx, PV_ERR_ARG, "half-warp search variants need ligands of <= 32 atoms and <= 10 torsions");
+    // The team width fixes the order of the floating-point sums, so the autotuner chooses only
+    // among variants of one width: results are then the same bits whatever register budget, CTA
+    // size, round length or graph setting is used. Half-warp teams pay off for ligands of at most
+    // 16 atoms (one atom per lane; measured +25-35 % evaluations/s), not above (two atoms per lane
+    // and twice the pair rounds per chain).
+    const int auto_lanes = (all_team16 && max_atoms <= 16) ? 16 : 32;
+    int variant = p.search_variant >= 0 ? p.search_variant : (auto_lanes == 16 ? 4 : 0);
     int W = p.warps_per_cta > 0 ? p.warps_per_cta : 4;
     const bool autotune = p.mode == PV_MODE_BATCHED && (p.search_variant < 0 || p.warps_per_cta == 0);
     int max_rounds = 0;
     for (int i = 0; i < n_ligs; ++i) max_rounds = std::max(max_rounds, ligs[i]->rec.n_rounds);
-    const std::pair<int, int> tune_key{(max_atoms + 7) / 8, (max_rounds + 3) / 4};
+    const std::pair<int, int> tune_key{2 * ((max_atoms + 7) / 8) + (auto_lanes == 16 ? 1 : 0), (max_rounds + 3) / 4};
     bool need_tune = false;
     if (autotune) {
         auto it = ctx->tuned.find(tune_key);
@@ -674,7 +716,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     }
     // the items buffer is sized for the smallest CTA a candidate may use
     const int W_min = autotune ? (p.warps_per_cta > 0 ? p.warps_per_cta : 2) : W;
-    std::vector<PvItem> items = make_items(W);
+    std::vector<PvItem> items = make_items(W * (32 / search_variant_lanes(variant)));
     const size_t items_cap = make_items(W_min).size();
     std::vector<PvPairDesc> pdesc(n_pairs);
     for (int q = 0; q < n_pairs; ++q)
@@ -785,7 +827,8 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     M.ranking = R->d_ranking;
     // autotuning: time each candidate launch shape on eight MC steps of its own first work items
     if (need_tune) {
-        static const int cand[][2] = {{0, 2}, {0, 4}, {0, 8}, {1, 4}, {2, 4}, {3, 4}};
+        static const int cand[][2] = {{0, 2}, {0, 4}, {0, 8}, {1, 4}, {2, 4}, {3, 4},
+                                      {4, 2}, {4, 4}, {5, 4}, {6, 4}, {7, 4}};
         cudaEvent_t t0, t1;
         cudaEventCreate(&t0);
         cudaEventCreate(&t1);
@@ -795,12 +838,16 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
             const int v = p.search_variant >= 0 ? p.search_variant : cw[0];
             const int wc = p.warps_per_cta > 0 ? p.warps_per_cta : cw[1];
             if (wc > search_variant_max_warps(v)) continue;
+            const int lanes_c = search_variant_lanes(v);
+            if (lanes_c == 16 && !all_team16) continue;
+            if (p.search_variant < 0 && lanes_c != auto_lanes) continue;
             int occ_c = 0;
-            if (search_max_ctas_per_sm(v, wc, search_smem_bytes(max_blob, wc), &occ_c) != cudaSuccess || occ_c < 1) {
+            if (search_max_ctas_per_sm(v, wc, search_smem_bytes(max_blob, wc, lanes_c), &occ_c) != cudaSuccess ||
+                occ_c < 1) {
                 cudaGetLastError();
                 continue;
             }
-            std::vector<PvItem> trial = make_items(wc);
+            std::vector<PvItem> trial = make_items(wc * (32 / lanes_c));
             const int n_trial = (int)std::min<size_t>(trial.size(), (size_t)4 * ctx->sms * occ_c);
             SearchArgs a = A;
             a.items = (const PvItem*)((char*)R->d_work + o_items);
@@ -833,7 +880,8 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
                 return cuda_fail(ctx, x, "autotune");
             }
             // per unit of work: the trials cover different numbers of chains
-            const float per_chain = ms / (float)(n_trial * wc);
+            const float per_chain = ms / (float)std::min<long long>((long long)n_trial * wc * (32 / lanes_c),
+                                                                     (long long)n_pairs * p.chains);
             if (per_chain < best_ms) { best_ms = per_chain; best_v = v; best_w = wc; }
         }
         cudaEventDestroy(t0);
@@ -841,7 +889,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
         variant = best_v;
         W = best_w;
         ctx->tuned[tune_key] = {variant, W};
-        items = make_items(W);
+        items = make_items(W * (32 / search_variant_lanes(variant)));
         e = cudaMemcpyAsync((char*)R->d_work + o_items, items.data(), sizeof(PvItem) * items.size(),
                             cudaMemcpyHostToDevice, ctx->stream);
         if (e != cudaSuccess) {
@@ -852,7 +900,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     A.n_items = (int)items.size();
     // grid of the persistent rounds: every SM filled to its occupancy
     int occ = 0;
-    const int smem = search_smem_bytes(max_blob, W);
+    const int smem = search_smem_bytes(max_blob, W, search_variant_lanes(variant));
     e = search_max_ctas_per_sm(variant, W, smem, &occ);
     if (e != cudaSuccess || occ < 1) {
         result_free(R);
@@ -876,6 +924,9 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     auto issue = [&](cudaStream_t s) -> cudaError_t {
         cudaError_t x = cudaMemsetAsync(ctr, 0, sizeof(int) * (n_rounds + 2), s);
         if (x == cudaSuccess) x = cudaMemsetAsync(evals, 0, sizeof(unsigned long long), s);
+        // chain records zeroed: the POT entries past a ligand's 7 + n_rot read as 0, not stale data
+        if (x == cudaSuccess)
+            x = cudaMemsetAsync(R->d_chains, 0, sizeof(float) * (size_t)n_pairs * p.chains * PV_CHAIN_STRIDE, s);
         if (x == cudaSuccess) x = launch_mark_t0(evals + 1, s);
         const unsigned ev_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
         if (x == cudaSuccess) x = cudaEventRecordWithFlags(evs0, s, ev_flags);

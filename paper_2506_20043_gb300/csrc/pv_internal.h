@@ -42,6 +42,12 @@ cudaError_t launch_score(const PvLigBlob* lig, int lig_bytes, const PvPocket* po
 cudaError_t launch_pose_coords(const PvLigBlob* lig, int lig_bytes, int n_poses, int pot_stride,
                                const float* pose, float* xyz, cudaStream_t s);
 
+// ---- gather microbenchmark (pv_probe.cu) ----
+// n_points trilinear interpolations (value + gradient) at hashed positions in the pocket's box,
+// on hashed map slots in [0, n_slots); sink is written only in a case that does not occur.
+cudaError_t launch_gather_probe(const PvPocket& P, int n_slots, long long n_points, uint32_t seed,
+                                float* sink, int n_sm, cudaStream_t s);
+
 // ---- search (pv_search.cu) ----
 struct SearchArgs {
     const PvItem* items;
@@ -60,11 +66,13 @@ struct SearchArgs {
     int* err;
     unsigned long long* evals;
 };
-int search_smem_bytes(int lig_bytes, int warps);
-// Register-budget variants of the round kernel: 0 = (512 threads, 1 CTA), 1 = (128, 5),
-// 2 = (128, 6), 3 = (128, 8) as (max threads per CTA, min CTAs per SM) launch bounds.
-constexpr int kSearchVariants = 4;
+int search_smem_bytes(int lig_bytes, int warps, int lanes);
+// Variants of the round kernel: 0-3 run a chain per warp, 4-7 a chain per half warp (ligands of
+// at most 32 atoms and 10 torsions); within each group the launch bounds (max threads per CTA,
+// min CTAs per SM) are (512, 1), (128, 5), (128, 6), (128, 8), i.e. decreasing register budgets.
+constexpr int kSearchVariants = 8;
 int search_variant_max_warps(int variant);
+int search_variant_lanes(int variant);
 cudaError_t search_max_ctas_per_sm(int variant, int warps, int smem, int* out);
 cudaError_t launch_search_round(const SearchArgs& a, int variant, int grid, int warps, cudaStream_t s);
 cudaError_t launch_plain_search(const SearchArgs& a, int pair, const PvLigBlob* lig_dev,

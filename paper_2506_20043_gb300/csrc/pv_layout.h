@@ -20,7 +20,9 @@ struct PvLigHeader {
     float rgyr;
     int32_t origin_src;   // input index of the origin atom
     int32_t type_mask;    // bit t set if XS type t occurs
-    int32_t pad[5];
+    int32_t n_rounds16;   // pair rounds of the half-warp schedule (stored after the warp schedule)
+    int32_t team16;       // 1 if the ligand fits a half-warp team (<= 32 atoms, <= 10 torsions)
+    int32_t pad[3];
 };
 
 struct PvLigBlob {
@@ -34,8 +36,9 @@ struct PvLigBlob {
     int32_t frag_tor[PV_MAX_FRAGS];  // torsion index of the fragment's hinge (root: -1)
     int32_t tor_frag[PV_MAX_FRAGS];  // fragment of torsion k
     int32_t atom_src[64];            // input index of device atom i
-    uint32_t pairs[1];               // n_rounds * 32 words; word l of a round is lane l's pair:
-                                     // target atom (bits 0-5), source atom lane + 32 * bit 6,
+    uint32_t pairs[1];               // n_rounds * 32 words (warp schedule), then n_rounds16 * 16
+                                     // words (half-warp schedule); word l of a round is lane l's
+                                     // pair: target atom (bits 0-5), source atom l + LANES * bit 6,
                                      // hydrophobic (bit 16), H-bond (bit 17), valid (bit 31)
 };
 #define PV_LIG_FIXED_BYTES ((int)offsetof(PvLigBlob, pairs))

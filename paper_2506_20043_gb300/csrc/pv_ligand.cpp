@@ -26,7 +26,7 @@ static bool is_acc(int t) { return t == 4 || t == 5 || t == 8 || t == 9; }
 // circuit of the pair graph, with a dummy vertex joined to the odd-degree atoms, enters and
 // leaves each atom equally often), then flips single pairs while that lowers the larger of a
 // lane's source load (atoms l and l + 32 share lane l) and a target's load.
-static void orient_pairs(int n, std::vector<std::pair<int, int>>& edges) {
+static void orient_pairs(int n, std::vector<std::pair<int, int>>& edges, int lanes) {
     const int m = (int)edges.size();
     if (m == 0) return;
     std::vector<std::pair<int, int>> E(edges);
@@ -57,12 +57,13 @@ static void orient_pairs(int n, std::vector<std::pair<int, int>>& edges) {
             }
         }
     }
-    std::vector<int> load(32, 0), ind(64, 0);
-    for (auto& e : edges) { load[e.first & 31]++; ind[e.second]++; }
+    const int lm = lanes - 1;
+    std::vector<int> load(lanes, 0), ind(64, 0);
+    for (auto& e : edges) { load[e.first & lm]++; ind[e.second]++; }
     for (bool changed = true; changed;) {
         changed = false;
         for (auto& e : edges) {
-            const int s = e.first, t = e.second, ls = s & 31, lt = t & 31;
+            const int s = e.first, t = e.second, ls = s & lm, lt = t & lm;
             if (ls == lt) continue;
             const int before = std::max(std::max(load[ls], load[lt]), std::max(ind[s], ind[t]));
             const int after = std::max(std::max(load[ls] - 1, load[lt] + 1), std::max(ind[s] + 1, ind[t] - 1));
@@ -78,16 +79,17 @@ static void orient_pairs(int n, std::vector<std::pair<int, int>>& edges) {
 // Edge colouring of the bipartite graph lanes x targets with as many colours (rounds) as its
 // largest degree (Koenig): a pair gets a colour free at both ends, else the alternating path
 // of the two candidate colours from its target is swapped first.
-static int colour_rounds(const std::vector<std::pair<int, int>>& edges, std::vector<int>& col) {
+static int colour_rounds(const std::vector<std::pair<int, int>>& edges, std::vector<int>& col, int lanes) {
     const int m = (int)edges.size();
+    const int lm = lanes - 1;
     col.assign(m, -1);
     if (m == 0) return 0;
-    std::vector<int> dl(32, 0), dr(64, 0);
-    for (auto& e : edges) { dl[e.first & 31]++; dr[e.second]++; }
+    std::vector<int> dl(lanes, 0), dr(64, 0);
+    for (auto& e : edges) { dl[e.first & lm]++; dr[e.second]++; }
     const int D = std::max(*std::max_element(dl.begin(), dl.end()), *std::max_element(dr.begin(), dr.end()));
-    std::vector<int> Lc(32 * D, -1), Rc(64 * D, -1);   // edge holding colour c at a lane / target
+    std::vector<int> Lc(lanes * D, -1), Rc(64 * D, -1);   // edge holding colour c at a lane / target
     for (int e = 0; e < m; ++e) {
-        const int u = edges[e].first & 31, v = edges[e].second;
+        const int u = edges[e].first & lm, v = edges[e].second;
         int a = 0, b = 0;
         while (Lc[u * D + a] >= 0) ++a;
         while (Rc[v * D + b] >= 0) ++b;
@@ -99,17 +101,17 @@ static int colour_rounds(const std::vector<std::pair<int, int>>& edges, std::vec
                 const int f = right ? Rc[x * D + c] : Lc[x * D + c];
                 if (f < 0) break;
                 path.push_back(f);
-                x = right ? (edges[f].first & 31) : edges[f].second;
+                x = right ? (edges[f].first & lm) : edges[f].second;
                 right = !right;
                 c = c == a ? b : a;
             }
             for (int f : path) {
-                Lc[(edges[f].first & 31) * D + col[f]] = -1;
+                Lc[(edges[f].first & lm) * D + col[f]] = -1;
                 Rc[edges[f].second * D + col[f]] = -1;
             }
             for (int f : path) {
                 col[f] = col[f] == a ? b : a;
-                Lc[(edges[f].first & 31) * D + col[f]] = f;
+                Lc[(edges[f].first & lm) * D + col[f]] = f;
                 Rc[edges[f].second * D + col[f]] = f;
             }
         }
@@ -248,24 +250,37 @@ bool build_ligand(const LigandInput& in, LigandRecord& out, std::string& err) {
     // source), which keeps that atom's force in registers; the other atom (the target) receives
     // its force through shared memory. A round gives every lane at most one pair and every
     // target at most one pair, so a round needs no atomics.
-    std::vector<std::pair<int, int>> edges;   // (source, target), device atom indices
-    for (auto& p : pairs) edges.push_back({dev_of[p.first], dev_of[p.second]});
-    orient_pairs(n, edges);
-    std::vector<int> colour;
-    const int n_rounds_sched = colour_rounds(edges, colour);
-    std::vector<std::vector<uint32_t>> rounds(n_rounds_sched, std::vector<uint32_t>(32, 0u));
-    for (size_t e = 0; e < edges.size(); ++e) {
-        const int src = edges[e].first, tgt = edges[e].second;
-        const int ti = out.xs[src_of_dev(src)], tj = out.xs[src_of_dev(tgt)];
-        const uint32_t hyd = (is_hyd(ti) && is_hyd(tj)) ? 1u : 0u;
-        const uint32_t hb = ((is_don(ti) && is_acc(tj)) || (is_acc(ti) && is_don(tj))) ? 1u : 0u;
-        const uint32_t w = (uint32_t)tgt | ((uint32_t)(src >> 5) << 6) | (hyd << 16) | (hb << 17) | (1u << 31);
-        rounds[colour[e]][src & 31] = w;
+    // A warp schedule (32 lanes) always; a half-warp schedule (16 lanes) when the ligand fits a
+    // half-warp team (at most 32 atoms, 16 fragments, 6 + n_rot <= 16 tangent coordinates).
+    auto schedule = [&](int lanes, std::vector<std::vector<uint32_t>>& rounds) {
+        std::vector<std::pair<int, int>> edges;   // (source, target), device atom indices
+        for (auto& p : pairs) edges.push_back({dev_of[p.first], dev_of[p.second]});
+        orient_pairs(n, edges, lanes);
+        std::vector<int> colour;
+        const int nr = colour_rounds(edges, colour, lanes);
+        rounds.assign(nr, std::vector<uint32_t>(lanes, 0u));
+        for (size_t e = 0; e < edges.size(); ++e) {
+            const int src = edges[e].first, tgt = edges[e].second;
+            const int ti = out.xs[src_of_dev(src)], tj = out.xs[src_of_dev(tgt)];
+            const uint32_t hyd = (is_hyd(ti) && is_hyd(tj)) ? 1u : 0u;
+            const uint32_t hb = ((is_don(ti) && is_acc(tj)) || (is_acc(ti) && is_don(tj))) ? 1u : 0u;
+            const uint32_t half = (uint32_t)(src / lanes);
+            const uint32_t w = (uint32_t)tgt | (half << 6) | (hyd << 16) | (hb << 17) | (1u << 31);
+            rounds[colour[e]][src % lanes] = w;
+        }
+        return nr;
+    };
+    std::vector<std::vector<uint32_t>> rounds, rounds16;
+    const int n_rounds_sched = schedule(32, rounds);
+    const bool team16 = n <= 32 && nfrag <= 16 && 6 + n_rot <= 16;
+    const int n_rounds16 = team16 ? schedule(16, rounds16) : 0;
+    if ((int)rounds.size() > PV_MAX_ROUNDS || n_rounds16 > 2 * PV_MAX_ROUNDS) {
+        err = "intra pair schedule exceeds the round limit";
+        return false;
     }
-    if ((int)rounds.size() > PV_MAX_ROUNDS) { err = "intra pair schedule exceeds the round limit"; return false; }
     // record
     const int n_rounds = n_rounds_sched;
-    const int bytes = PV_LIG_FIXED_BYTES + n_rounds * 32 * 4;
+    const int bytes = PV_LIG_FIXED_BYTES + (n_rounds * 32 + n_rounds16 * 16) * 4;
     out.blob.assign((size_t)((bytes + 15) / 16) * 16, 0);
     PvLigBlob* L = reinterpret_cast<PvLigBlob*>(out.blob.data());
     L->h.n_atoms = n;
@@ -278,6 +293,8 @@ bool build_ligand(const LigandInput& in, LigandRecord& out, std::string& err) {
     L->h.blob_bytes = (int)out.blob.size();
     L->h.origin_src = origin;
     L->h.type_mask = type_mask;
+    L->h.n_rounds16 = n_rounds16;
+    L->h.team16 = team16 ? 1 : 0;
     double g2 = 0.0;
     for (int i = 0; i < n; ++i)
         for (int k = 0; k < 3; ++k) {
@@ -326,12 +343,15 @@ bool build_ligand(const LigandInput& in, LigandRecord& out, std::string& err) {
     }
     for (int r = 0; r < n_rounds; ++r)
         for (int l = 0; l < 32; ++l) L->pairs[r * 32 + l] = rounds[r][l];
+    for (int r = 0; r < n_rounds16; ++r)
+        for (int l = 0; l < 16; ++l) L->pairs[n_rounds * 32 + r * 16 + l] = rounds16[r][l];
     out.n_atoms = n;
     out.n_rot = n_rot;
     out.n_pairs = (int)pairs.size();
     out.n_rounds = n_rounds;
     out.origin = origin;
     out.type_mask = type_mask;
+    out.team16 = team16;
     out.subtree_atoms = 0;
     for (int fi = 1; fi < nfrag; ++fi) out.subtree_atoms += sub_end[fi] - own_start[fi];
     return true;

@@ -24,6 +24,7 @@ struct LigandRecord {
     std::vector<uint8_t> xs;     // XS type per input atom
     int n_atoms = 0, n_rot = 0, n_pairs = 0, n_rounds = 0, origin = 0, type_mask = 0;
     int subtree_atoms = 0;       // sum over torsions of the atoms each one moves
+    bool team16 = false;         // fits a half-warp team
 };
 
 bool build_ligand(const LigandInput& in, LigandRecord& out, std::string& err);

@@ -1,11 +1,11 @@
-// pv_warp.cuh -- one warp evaluates one ligand pose: torsion-tree forward kinematics, trilinear
-// e_inter, intra-ligand pair terms, and the reverse-mode gradient over the pose tangent space;
-// on top of it the warp runs RILC-BFGS and the Monte-Carlo step of one chain.
+// pv_warp.cuh -- one team of lanes (a whole warp, or half a warp) evaluates one ligand pose:
+// torsion-tree forward kinematics, trilinear e_inter, intra-ligand pair terms and the reverse-mode
+// gradient over the pose tangent space; it also holds the team's pose arithmetic (retraction,
+// L-BFGS direction, random start, mutation) used by the chain runner in pv_search.cu.
 //
-// Lane roles
-//   atoms:      lane l owns device atoms l and l + 32
-//   fragments:  lane f owns rigid fragment f (f < n_frag <= 27): its world rotation M_f and
-//               anchor position
+// Lane roles inside a team of LANES lanes (tl = lane within the team)
+//   atoms:      lane tl owns atoms tl and tl + LANES (device order)
+//   fragments:  lane tl owns rigid fragment tl (n_frag <= LANES): its world rotation and anchor
 //   tangent:    lane k owns tangent coordinate k (0-2 translation, 3-5 rotation vector,
 //               6 + t torsion t); the torsion angle psi_t itself lives in lane 6 + t
 //   pairs:      every intra pair is owned by the lane of one of its atoms (its source), which
@@ -13,20 +13,47 @@
 //               receives its share through shared memory. Rounds give each lane one pair and
 //               each target one pair, so no atomics are needed and the order of accumulation
 //               is fixed (bitwise reproducible).
+// Half-warp teams (LANES = 16) serve ligands of at most 32 atoms and 10 torsions: two chains share
+// a warp and stay converged at the evaluator (one evaluation per loop iteration).
 #pragma once
 #include "pv_device.cuh"
 
 namespace pv {
 
-struct WarpScratch {
-    float4 x[64];                // posed coordinates; w = XS radius
-    float4 g[64];                // dSF/dx
-    float hs[PV_MAX_M][32];      // L-BFGS history: s vectors, lane = tangent coordinate
-    float hy[PV_MAX_M][32];      //                 y vectors
-    float cur[40];               // the chain's current POT (MC state)
+struct WarpScratch {            // one per team
+    float4 x[64];               // posed coordinates; w = XS radius
+    float4 g[64];               // dSF/dx
+    float hs[PV_MAX_M][32];     // L-BFGS history: s vectors, lane = tangent coordinate
+    float hy[PV_MAX_M][32];     //                 y vectors
+    float cur[40];              // the chain's current POT (MC state)
 };
 
-// A pose held by a warp: translation and quaternion (w, x, y, z) are warp-uniform; psi is the
+template <int LANES>
+struct Team {
+    static __device__ __forceinline__ int lane() { return threadIdx.x & (LANES - 1); }
+    static __device__ __forceinline__ int index() { return (threadIdx.x & 31) / LANES; }
+    static __device__ __forceinline__ unsigned mask() {
+        return LANES == 32 ? PV_FULL : (0xffffu << (16 * ((threadIdx.x & 31) >> 4)));
+    }
+    static __device__ __forceinline__ float shfl(float v, int src) { return __shfl_sync(mask(), v, src, LANES); }
+    static __device__ __forceinline__ float sum(float v) {
+#pragma unroll
+        for (int o = LANES / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask(), v, o, LANES);
+        return v;
+    }
+    static __device__ __forceinline__ float3 sum3(float3 v) {
+#pragma unroll
+        for (int o = LANES / 2; o > 0; o >>= 1) {
+            v.x += __shfl_xor_sync(mask(), v.x, o, LANES);
+            v.y += __shfl_xor_sync(mask(), v.y, o, LANES);
+            v.z += __shfl_xor_sync(mask(), v.z, o, LANES);
+        }
+        return v;
+    }
+    static __device__ __forceinline__ void sync() { __syncwarp(mask()); }
+};
+
+// A pose held by a team: translation and quaternion (w, x, y, z) are team-uniform; psi is the
 // lane's torsion in tangent layout (lane 6 + t holds psi_t, other lanes hold 0).
 struct Pose {
     float3 T;
@@ -39,39 +66,50 @@ struct Site {                      // where a pose is scored
     const PvPocket* P;             // pocket geometry (shared or global memory)
 };
 
-__device__ __forceinline__ float shfl(float v, int src) { return __shfl_sync(PV_FULL, v, src); }
-__device__ __forceinline__ int shfli(int v, int src) { return __shfl_sync(PV_FULL, v, src); }
+// Pair words of the team width's schedule.
+template <int LANES>
+__device__ __forceinline__ const uint32_t* pair_rounds(const PvLigBlob& L, int& rounds) {
+    if (LANES == 32) {
+        rounds = L.h.n_rounds;
+        return L.pairs;
+    }
+    rounds = L.h.n_rounds16;
+    return L.pairs + L.h.n_rounds * 32;
+}
 
 // Forward kinematics (Eq. 1: position, orientation, torsions -> atom coordinates). Writes S.x.
-// Returns the fragment lane's rotation and anchor (used again by the adjoint).
-__device__ __forceinline__ void warp_fk(const PvLigBlob& L, WarpScratch& S, const Pose& x,
+// Returns the fragment lane's world hinge axis and anchor (used again by the adjoint) and the
+// lane's own atoms' positions.
+template <int LANES>
+__device__ __forceinline__ void team_fk(const PvLigBlob& L, WarpScratch& S, const Pose& x,
                                         float3& axw, float3& xa, float4* own = nullptr) {
-    const int lane = threadIdx.x & 31;
+    using Tm = Team<LANES>;
+    const int tl = Tm::lane();
     const int nf = L.h.n_frag;
-    const bool isf = lane < nf;
+    const bool isf = tl < nf;
     int parent = 0, depth = 0, tor = -1;
     float3 off = make_float3(0.f, 0.f, 0.f), axis = off;
     if (isf) {
-        float4 o = L.frag_off[lane], a = L.frag_axis[lane];
+        float4 o = L.frag_off[tl], a = L.frag_axis[tl];
         off = f3(o); axis = f3(a);
         parent = __float_as_int(o.w);
         depth = __float_as_int(a.w);
-        tor = L.frag_tor[lane];
+        tor = L.frag_tor[tl];
     }
-    float psi = shfl(x.psi, (isf && lane > 0) ? 6 + tor : lane);
+    float psi = Tm::shfl(x.psi, (isf && tl > 0) ? 6 + tor : tl);
     // local rotation of every fragment as a unit quaternion: the root's orientation, or a
     // torsion's half-angle quaternion (cos psi/2, sin psi/2 * axis) about its hinge axis; world
     // rotations compose down the tree level by level (Q_f = Q_parent (x) q_f)
     float s2, c2;
     sincosf(0.5f * (isf ? psi : 0.0f), &s2, &c2);
-    float4 Q = lane == 0 ? quat_normalize(x.q) : make_float4(c2, s2 * axis.x, s2 * axis.y, s2 * axis.z);
+    float4 Q = tl == 0 ? quat_normalize(x.q) : make_float4(c2, s2 * axis.x, s2 * axis.y, s2 * axis.z);
     const float4 ql = Q;
-    xa = (lane == 0) ? x.T : make_float3(0.f, 0.f, 0.f);
+    xa = (tl == 0) ? x.T : make_float3(0.f, 0.f, 0.f);
     for (int lev = 1; lev <= L.h.max_depth; ++lev) {
         const bool mine = isf && depth == lev;
-        const int src = mine ? parent : lane;
-        const float4 Qp = make_float4(shfl(Q.x, src), shfl(Q.y, src), shfl(Q.z, src), shfl(Q.w, src));
-        const float3 xp = make_float3(shfl(xa.x, src), shfl(xa.y, src), shfl(xa.z, src));
+        const int src = mine ? parent : tl;
+        const float4 Qp = make_float4(Tm::shfl(Q.x, src), Tm::shfl(Q.y, src), Tm::shfl(Q.z, src), Tm::shfl(Q.w, src));
+        const float3 xp = make_float3(Tm::shfl(xa.x, src), Tm::shfl(xa.y, src), Tm::shfl(xa.z, src));
         if (mine) {
             Q = quat_mul(Qp, ql);
             // anchor: parent's anchor + parent rotation applied to the offset, v + 2w(u x v) + 2u x (u x v)
@@ -85,14 +123,14 @@ __device__ __forceinline__ void warp_fk(const PvLigBlob& L, WarpScratch& S, cons
     const int n = L.h.n_atoms;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const int a = lane + 32 * h;
+        const int a = tl + LANES * h;
         float4 loc = a < n ? L.atom[a] : make_float4(0.f, 0.f, 0.f, 0.f);
         const int w = __float_as_int(loc.w);
-        const int fa = a < n ? (w & 255) : lane;
+        const int fa = a < n ? (w & 255) : tl;
         Mat3 Mf;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) Mf.m[k] = shfl(M.m[k], fa);
-        float3 xf = make_float3(shfl(xa.x, fa), shfl(xa.y, fa), shfl(xa.z, fa));
+        for (int k = 0; k < 9; ++k) Mf.m[k] = Tm::shfl(M.m[k], fa);
+        float3 xf = make_float3(Tm::shfl(xa.x, fa), Tm::shfl(xa.y, fa), Tm::shfl(xa.z, fa));
         if (a < n) {
             float3 p = mat_vec(Mf, f3(loc)) + xf;
             const float4 q = make_float4(p.x, p.y, p.z, xs_radius((w >> 8) & 255));
@@ -103,22 +141,42 @@ __device__ __forceinline__ void warp_fk(const PvLigBlob& L, WarpScratch& S, cons
     axw = mat_vec(M, axis);   // the hinge axis in the world frame (rotating about it keeps it)
 }
 
+// One round of the pair loop: the lane's pair (source atom xi, partner position xj).
+__device__ __forceinline__ void pair_round(uint32_t pw, const float4& xi, const float4& xj, WarpScratch& S,
+                                           float& e_intra, float3& acc) {
+    const float3 d = make_float3(xi.x - xj.x, xi.y - xj.y, xi.z - xj.z);
+    const float r2 = dot3(d, d);
+    const bool live = (pw >> 31) && r2 < kCutoff2;
+    float c;
+    const float e = vina_pair_r2(r2, xi.w + xj.w, (float)((pw >> 16) & 1), (float)((pw >> 17) & 1), c);
+    if (live) {
+        e_intra += e;
+        const float3 f = c * d;
+        acc = acc + f;
+        const int t = pw & 63;
+        const float4 gj = S.g[t];
+        S.g[t] = make_float4(gj.x - f.x, gj.y - f.y, gj.z - f.z, 0.f);
+    }
+}
+
 // SF = e_inter + e_intra (Eq. 3) and, if want_grad, its tangent gradient (lane k holds
 // component k). parts (optional, lane-uniform): e_inter, e_intra.
-static __device__ __forceinline__ float warp_eval(const PvLigBlob& L, WarpScratch& S, const Site& site,
-                                               const Pose& x, float& grad, bool want_grad,
-                                               float* parts = nullptr) {
-    const int lane = threadIdx.x & 31;
+template <int LANES>
+__device__ __forceinline__ float team_eval(const PvLigBlob& L, WarpScratch& S, const Site& site,
+                                           const Pose& x, float& grad, bool want_grad,
+                                           float* parts = nullptr) {
+    using Tm = Team<LANES>;
+    const int tl = Tm::lane();
     const int n = L.h.n_atoms;
     float3 axw, xa;
     float4 own[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
-    warp_fk(L, S, x, axw, xa, own);
+    team_fk<LANES>(L, S, x, axw, xa, own);
     const PvPocket& P = *site.P;
     float e_inter = 0.f, e_intra = 0.f;
     float3 acc[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const int a = lane + 32 * h;
+        const int a = tl + LANES * h;
         acc[h] = make_float3(0.f, 0.f, 0.f);
         if (a < n) {
             const int w = __float_as_int(L.atom[a].w);
@@ -127,55 +185,31 @@ static __device__ __forceinline__ float warp_eval(const PvLigBlob& L, WarpScratc
             S.g[a] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
-    __syncwarp();
+    Tm::sync();
     // Pair rounds. Positions and pair words are read-only here, so the next round's word and
-    // partner position are loaded before the current round's force update and its __syncwarp
+    // partner position are loaded before the current round's force update and its sync
     // (which orders only the force scatter).
-    const int rounds = L.h.n_rounds;
+    int rounds;
+    const uint32_t* pr = pair_rounds<LANES>(L, rounds);
     if (rounds > 0) {
-        uint32_t pw = L.pairs[lane];
+        uint32_t pw = pr[tl];
         float4 xj = S.x[pw & 63];
-        if (n <= 32) {                        // every source is the lane's first atom
+        if (n <= LANES) {                     // every source is the lane's first atom
             for (int r = 0; r < rounds; ++r) {
-                const uint32_t pw_n = r + 1 < rounds ? L.pairs[(r + 1) * 32 + lane] : 0u;
+                const uint32_t pw_n = r + 1 < rounds ? pr[(r + 1) * LANES + tl] : 0u;
                 const float4 xj_n = S.x[pw_n & 63];
-                const float3 d = make_float3(own[0].x - xj.x, own[0].y - xj.y, own[0].z - xj.z);
-                const float r2 = dot3(d, d);
-                const bool live = (pw >> 31) && r2 < kCutoff2;
-                float c;
-                const float e = vina_pair_r2(r2, own[0].w + xj.w, (float)((pw >> 16) & 1), (float)((pw >> 17) & 1), c);
-                if (live) {
-                    e_intra += e;
-                    const float3 f = c * d;
-                    acc[0] = acc[0] + f;
-                    const int t = pw & 63;
-                    const float4 gj = S.g[t];
-                    S.g[t] = make_float4(gj.x - f.x, gj.y - f.y, gj.z - f.z, 0.f);
-                }
-                __syncwarp();
+                pair_round(pw, own[0], xj, S, e_intra, acc[0]);
+                Tm::sync();
                 pw = pw_n;
                 xj = xj_n;
             }
         } else {
             for (int r = 0; r < rounds; ++r) {
-                const uint32_t pw_n = r + 1 < rounds ? L.pairs[(r + 1) * 32 + lane] : 0u;
+                const uint32_t pw_n = r + 1 < rounds ? pr[(r + 1) * LANES + tl] : 0u;
                 const float4 xj_n = S.x[pw_n & 63];
-                const int h = (pw >> 6) & 1;
-                const float4 xi = h ? own[1] : own[0];
-                const float3 d = make_float3(xi.x - xj.x, xi.y - xj.y, xi.z - xj.z);
-                const float r2 = dot3(d, d);
-                const bool live = (pw >> 31) && r2 < kCutoff2;
-                float c;
-                const float e = vina_pair_r2(r2, xi.w + xj.w, (float)((pw >> 16) & 1), (float)((pw >> 17) & 1), c);
-                if (live) {
-                    e_intra += e;
-                    const float3 f = c * d;
-                    if (h) acc[1] = acc[1] + f; else acc[0] = acc[0] + f;
-                    const int t = pw & 63;
-                    const float4 gj = S.g[t];
-                    S.g[t] = make_float4(gj.x - f.x, gj.y - f.y, gj.z - f.z, 0.f);
-                }
-                __syncwarp();
+                if ((pw >> 6) & 1) pair_round(pw, own[1], xj, S, e_intra, acc[1]);
+                else pair_round(pw, own[0], xj, S, e_intra, acc[0]);
+                Tm::sync();
                 pw = pw_n;
                 xj = xj_n;
             }
@@ -184,182 +218,104 @@ static __device__ __forceinline__ float warp_eval(const PvLigBlob& L, WarpScratc
     // total dSF/dx of the lane's atoms: own share (registers) + shares received as a target
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const int a = lane + 32 * h;
+        const int a = tl + LANES * h;
         if (a < n) {
             const float4 gt = S.g[a];
             acc[h] = acc[h] + f3(gt);
             S.g[a] = make_float4(acc[h].x, acc[h].y, acc[h].z, 0.f);
         }
     }
-    float ei = warp_sum(e_inter), ej = warp_sum(e_intra);
-    if (parts) { parts[0] = ei; parts[1] = ej; }
+    float ei, ej;
+    if (parts) {
+        ei = Tm::sum(e_inter);
+        ej = Tm::sum(e_intra);
+        parts[0] = ei;
+        parts[1] = ej;
+    } else {
+        ei = Tm::sum(e_inter + e_intra);
+        ej = 0.f;
+    }
     if (want_grad) {
-        __syncwarp();
+        Tm::sync();
         // root: total force and torque about the origin atom (butterfly sums over all atoms)
         float3 F = make_float3(0.f, 0.f, 0.f), tau = F;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int a = lane + 32 * h;
+            const int a = tl + LANES * h;
             if (a < n) {
                 F = F + acc[h];
                 tau = tau + cross3(f3(own[h]) - x.T, acc[h]);
             }
         }
-        F = warp_sum3(F);
-        tau = warp_sum3(tau);
+        F = Tm::sum3(F);
+        tau = Tm::sum3(tau);
         // torsions: fragment lane sums torque of its subtree (a contiguous atom range) about
         // its anchor, projected on its world hinge axis
         float gpsi = 0.f;
         const int nf = L.h.n_frag;
-        if (lane > 0 && lane < nf) {
-            const int a0 = L.frag_a0[lane], a1 = L.frag_a1[lane];
+        if (tl > 0 && tl < nf) {
+            const int a0 = L.frag_a0[tl], a1 = L.frag_a1[tl];
             float3 t = make_float3(0.f, 0.f, 0.f);
             for (int a = a0; a < a1; ++a) t = t + cross3(f3(S.x[a]) - xa, f3(S.g[a]));
             gpsi = dot3(axw, t);
         }
         const int nt = 6 + L.h.n_rot;
-        const int src = (lane >= 6 && lane < nt) ? L.tor_frag[lane - 6] : lane;
-        float gp = shfl(gpsi, src);
+        const int src = (tl >= 6 && tl < nt) ? L.tor_frag[tl - 6] : tl;
+        float gp = Tm::shfl(gpsi, src);
         float c3[6] = {F.x, F.y, F.z, tau.x, tau.y, tau.z};
-        grad = lane < 6 ? c3[lane] : (lane < nt ? gp : 0.f);
+        grad = tl < 6 ? c3[tl] : (tl < nt ? gp : 0.f);
     }
-    __syncwarp();
+    Tm::sync();
     return ei + ej;
 }
 
 // x (+) step: translation += step[0:3]; q <- exp(step[3:6]/2) (x) q; psi += step[6:].
-__device__ __forceinline__ Pose retract(const Pose& x, float step, int n_tan) {
-    const int lane = threadIdx.x & 31;
+template <int LANES>
+__device__ __forceinline__ Pose team_retract(const Pose& x, float step, int n_tan) {
+    using Tm = Team<LANES>;
+    const int tl = Tm::lane();
     Pose y;
-    y.T = x.T + make_float3(shfl(step, 0), shfl(step, 1), shfl(step, 2));
-    y.q = quat_rotate_by(x.q, make_float3(shfl(step, 3), shfl(step, 4), shfl(step, 5)));
-    y.psi = x.psi + ((lane >= 6 && lane < n_tan) ? step : 0.f);
+    y.T = x.T + make_float3(Tm::shfl(step, 0), Tm::shfl(step, 1), Tm::shfl(step, 2));
+    y.q = quat_rotate_by(x.q, make_float3(Tm::shfl(step, 3), Tm::shfl(step, 4), Tm::shfl(step, 5)));
+    y.psi = x.psi + ((tl >= 6 && tl < n_tan) ? step : 0.f);
     return y;
 }
 
-struct ChainCtx {
-    const PvLigBlob* L;
-    WarpScratch* S;
-    Site site;
-    uint32_t evals;
-};
-
-__device__ __forceinline__ float eval_pose(ChainCtx& c, const Pose& x, float& g) {
-    c.evals++;
-    return warp_eval(*c.L, *c.S, c.site, x, g, true);
-}
-
 // L-BFGS two-loop recursion (Eq. 10-11 history, newest pair first) for the direction d = -H g.
+template <int LANES>
 __device__ __forceinline__ float lbfgs_direction(const float* Hs, const float* Hy, float rh, float& al,
                                                  float g, int stored, int head, int m) {
-    const int lane = threadIdx.x & 31;
+    using Tm = Team<LANES>;
+    const int tl = Tm::lane();
     float q = g;
     for (int a = 0; a < stored; ++a) {
         int k = head - 1 - a;
         if (k < 0) k += m;
-        const float alpha = shfl(rh, k) * warp_sum(Hs[k * 32 + lane] * q);
-        if (lane == k) al = alpha;
-        q -= alpha * Hy[k * 32 + lane];
+        const float alpha = Tm::shfl(rh, k) * Tm::sum(Hs[k * 32 + tl] * q);
+        if (tl == k) al = alpha;
+        q -= alpha * Hy[k * 32 + tl];
     }
     if (stored > 0) {
         const int k = head == 0 ? m - 1 : head - 1;
-        const float sk = Hs[k * 32 + lane], yk = Hy[k * 32 + lane];
-        const float sy = warp_sum(sk * yk), yy = warp_sum(yk * yk);
+        const float sk = Hs[k * 32 + tl], yk = Hy[k * 32 + tl];
+        const float sy = Tm::sum(sk * yk), yy = Tm::sum(yk * yk);
         q *= sy / yy;
     }
     for (int a = stored - 1; a >= 0; --a) {
         int k = head - 1 - a;
         if (k < 0) k += m;
-        const float b = shfl(rh, k) * warp_sum(Hy[k * 32 + lane] * q);
-        q += Hs[k * 32 + lane] * (shfl(al, k) - b);
+        const float b = Tm::shfl(rh, k) * Tm::sum(Hy[k * 32 + tl] * q);
+        q += Hs[k * 32 + tl] * (Tm::shfl(al, k) - b);
     }
     return -q;
 }
 
-// RILC-BFGS (Eq. 6-12): L-BFGS two-loop recursion over the m most recent curvature pairs,
-// Lewis-Overton line search (Eq. 7-8 as failure tests of Armijo / weak Wolfe), curvature-
-// guarded history update (Eq. 11), stop on ||g|| <= eps (Eq. 12), non-descent, or max_iter.
-// Updates x in place and returns SF(x). All control flow is warp-uniform. The history lives in
-// the warp's shared scratch (a ring of m slots); rho and alpha of slot k sit in lane k.
-// Written as one loop with a single evaluation site (the start point, then every line-search
-// trial), so the evaluator's code appears once.
-__device__ __forceinline__ float warp_bfgs(ChainCtx& c, Pose& x, const PvSearchConst& C, int max_iter, int m) {
-    const int lane = threadIdx.x & 31;
-    const int n_tan = 6 + c.L->h.n_rot;
-    float* Hs = &c.S->hs[0][0];
-    float* Hy = &c.S->hy[0][0];
-    float rh = 0.f, al = 0.f;
-    int stored = 0, head = 0, it = 0, tr = 0;
-    float f = 0.f, g = 0.f, d = 0.f, gd = 0.f;
-    float lam = 1.f, lo = 0.f, hi = -1.f, flo = 0.f, glo = 0.f;
-    bool have_lo = false, start = true;
-    Pose xt = x;
-    for (;;) {
-        float ge;
-        const float fe = eval_pose(c, xt, ge);
-        bool next_iter = false, done = false;
-        if (start) {                        // the start point: f, g at x
-            start = false;
-            f = fe;
-            g = ge;
-            next_iter = true;
-        } else {                            // a line-search trial at x + lam d
-            const float gtd = warp_sum(ge * d);
-            bool take = false;
-            float ft = fe, gt = ge;
-            if (!(fe <= f + lam * C.rho * gd)) {
-                hi = lam;                                   // Eq. 7 holds: Armijo fails
-            } else if (gtd < C.sigma * gd) {
-                lo = lam; have_lo = true; flo = fe; glo = ge;   // Eq. 8 holds: Wolfe fails
-            } else {
-                take = true;
-            }
-            if (!take) {
-                ++tr;
-                if (tr < C.bfgs_max_trials) {
-                    lam = hi < 0.f ? 2.f * lam : 0.5f * (lo + hi);
-                    xt = retract(x, lam * d, n_tan);
-                    continue;
-                }
-                if (!have_lo) break;                        // no acceptable step: stop here
-                lam = lo; ft = flo; gt = glo;
-                xt = retract(x, lam * d, n_tan);            // the same arithmetic as that trial
-                take = true;
-            }
-            // accepted step: curvature-guarded history update, move, convergence test
-            const float s = lam * d, y = gt - g;
-            const float ys = warp_sum(y * s), ss = warp_sum(s * s), gn = sqrtf(warp_sum(g * g));
-            if (ss > 0.f && ys / ss > C.eps * gn) {
-                Hs[head * 32 + lane] = s;
-                Hy[head * 32 + lane] = y;
-                if (lane == head) rh = 1.f / ys;
-                head = head + 1 == m ? 0 : head + 1;
-                stored = min(stored + 1, m);
-            }
-            x = xt; g = gt; f = ft;
-            ++it;
-            if (sqrtf(warp_sum(g * g)) <= C.eps) done = true;
-            next_iter = !done;
-        }
-        if (done) break;
-        if (next_iter) {
-            if (it >= max_iter) break;
-            d = lbfgs_direction(Hs, Hy, rh, al, g, stored, head, m);
-            gd = warp_sum(g * d);
-            if (!(gd < 0.f)) break;
-            lam = 1.f; lo = 0.f; hi = -1.f; have_lo = false; tr = 0;
-            xt = retract(x, lam * d, n_tan);
-        }
-    }
-    __syncwarp();
-    return f;
-}
-
 // Random conformation (Algorithm 2): draws 0-2 translation uniform in the box, 3-5 a uniform
 // quaternion (Shoemake), 6 + t torsion t uniform in [-pi, pi).
+template <int LANES>
 __device__ __forceinline__ Pose random_pose(const PvLigBlob& L, const PvPocket& P, uint32_t chain,
                                             uint32_t pair, const PvSearchConst& C) {
-    const int lane = threadIdx.x & 31;
+    const int tl = Team<LANES>::lane();
     uint4 b0 = philox4x32_10(make_uint4(chain, pair, 0u, 0u), C.seed_lo, C.seed_hi);
     uint4 b1 = philox4x32_10(make_uint4(chain, pair, 0u, 1u), C.seed_lo, C.seed_hi);
     Pose x;
@@ -373,8 +329,8 @@ __device__ __forceinline__ Pose random_pose(const PvLigBlob& L, const PvPocket& 
     float a = sqrtf(1.f - u1), b = sqrtf(u1);
     x.q = make_float4(a * s2, a * c2, b * s3, b * c3);
     x.psi = 0.f;
-    if (lane >= 6 && lane < 6 + L.h.n_rot) {
-        const int i = lane;   // draw index 6 + t with t = lane - 6
+    if (tl >= 6 && tl < 6 + L.h.n_rot) {
+        const int i = tl;   // draw index 6 + t with t = tl - 6
         uint32_t w = pick(philox4x32_10(make_uint4(chain, pair, 0u, (uint32_t)(i >> 2)), C.seed_lo, C.seed_hi), i & 3);
         x.psi = -PV_PI + 2.f * PV_PI * u01(w);
     }
@@ -386,9 +342,10 @@ __device__ __forceinline__ Pose random_pose(const PvLigBlob& L, const PvPocket& 
 // ball (z = 2a - 1, phi = 2 pi b, r = cbrt(c)); position += amplitude p, or orientation
 // rotated by (amplitude / R_gyr) p, or the torsion redrawn from draw 4. Returns draw 5
 // (the Metropolis uniform).
+template <int LANES>
 __device__ __forceinline__ float mutate(const PvLigBlob& L, Pose& x, uint32_t chain, uint32_t pair,
                                         int step, const PvSearchConst& C) {
-    const int lane = threadIdx.x & 31;
+    const int tl = Team<LANES>::lane();
     const uint32_t st = (uint32_t)step + 1u;
     uint4 b0 = philox4x32_10(make_uint4(chain, pair, st, 0u), C.seed_lo, C.seed_hi);
     uint4 b1 = philox4x32_10(make_uint4(chain, pair, st, 1u), C.seed_lo, C.seed_hi);
@@ -404,10 +361,39 @@ __device__ __forceinline__ float mutate(const PvLigBlob& L, Pose& x, uint32_t ch
     } else if (entity == 1) {
         float sc = L.h.rgyr > 1e-9f ? C.amplitude / L.h.rgyr : 0.f;
         x.q = quat_rotate_by(x.q, sc * p);
-    } else if (lane == 6 + (entity - 2)) {
+    } else if (tl == 6 + (entity - 2)) {
         x.psi = -PV_PI + 2.f * PV_PI * u01(b1.x);
     }
     return u01(b1.y);
 }
+
+// POT record <-> team pose: lanes 0-6 hold (x, y, z, qw, qx, qy, qz), lane 6 + t holds psi_t.
+template <int LANES>
+__device__ __forceinline__ void store_pose(float* dst, const Pose& x, int n_rot) {
+    const int tl = Team<LANES>::lane();
+    float v[7] = {x.T.x, x.T.y, x.T.z, x.q.x, x.q.y, x.q.z, x.q.w};
+    if (tl < 7) dst[tl] = v[tl];
+    if (tl >= 6 && tl < 6 + n_rot) dst[tl + 1] = x.psi;
+}
+template <int LANES>
+__device__ __forceinline__ Pose load_pose(const float* src, int n_rot) {
+    const int tl = Team<LANES>::lane();
+    Pose x;
+    x.T = make_float3(src[0], src[1], src[2]);
+    x.q = make_float4(src[3], src[4], src[5], src[6]);
+    x.psi = (tl >= 6 && tl < 6 + n_rot) ? src[tl + 1] : 0.f;
+    return x;
+}
+
+// Whole-warp names used by the selection and scoring kernels.
+static __device__ __forceinline__ float warp_eval(const PvLigBlob& L, WarpScratch& S, const Site& site,
+                                                  const Pose& x, float& grad, bool want_grad,
+                                                  float* parts = nullptr) {
+    return team_eval<32>(L, S, site, x, grad, want_grad, parts);
+}
+__device__ __forceinline__ void warp_fk(const PvLigBlob& L, WarpScratch& S, const Pose& x, float3& axw, float3& xa) {
+    team_fk<32>(L, S, x, axw, xa);
+}
+__device__ __forceinline__ float shfl(float v, int src) { return __shfl_sync(PV_FULL, v, src); }
 
 }  // namespace pv

@@ -13,6 +13,18 @@ import pvsynth as S
 ABS_TOL, REL_TOL = 1e-3, 1e-4
 # Gradient tolerance: |gpu - oracle| <= 1e-3 * max(|oracle|, 1).
 GRAD_TOL = 1e-3
+# Pose -> atom coordinates (Eq. 1) in FP32 vs FP64, in Angstrom.
+COORD_TOL = 2e-4
+# The pair terms stop at 8 A without smoothing, so the SF jumps there by one pair's term (about
+# 3e-3 kcal/mol for two heavy atoms). Two places meet that edge in FP32 vs FP64:
+#  - intra pairs: local optimisation seeks the edge (the step that brings a pair inside the cutoff
+#    lowers the SF), and the same pose posed by two FP32 kernels can put the pair a few ulps to
+#    either side;
+#  - grid nodes: a receptor atom at 8 A from a node, to within rounding, counts on one side only
+#    (about 1e-4 of the nodes of a pocket), and an atom interpolating there inherits its jump times
+#    the corner's weight.
+# A pair or a (node, receptor atom) within CUTOFF_EDGE of 8 A adds its jump to the tolerance.
+CUTOFF, CUTOFF_EDGE = 8.0, 1e-4
 
 
 def close(gpu, ref, abs_tol=ABS_TOL, rel_tol=REL_TOL):
@@ -48,3 +60,62 @@ def receptor32(rec):
 def ligand32(lig):
     import dataclasses
     return dataclasses.replace(lig, xyz=np.asarray(lig.xyz, np.float32).astype(np.float64))
+
+
+def pose_coords(ctx, pl, pots):
+    """The GPU's FP32 atom coordinates [n, atoms, 3] of POTs [n, 7 + n_rot] (input atom order)."""
+    import torch
+    p = torch.tensor(np.ascontiguousarray(pots, np.float32), device="cuda")
+    return ctx.pose_coords(pl, p).cpu().numpy().astype(np.float64)
+
+
+def check_pose_scores(L, og, pots, es, xyz_gpu, site=None):
+    """Scores reported for poses, checked in two steps. (1) The GPU's atom coordinates equal the
+    oracle's kinematics of the same POT within COORD_TOL. (2) The reported SF equals the oracle's SF
+    at the GPU's own coordinates within ABS_TOL / REL_TOL. Scoring the oracle's coordinates instead
+    would add |force| x the FP32 coordinate rounding to the comparison: at a clash, forces of
+    hundreds of kcal/mol/A times 1e-5 A of rounding move the SF by a few 1e-3 kcal/mol."""
+    pots = np.asarray(pots, np.float64)
+    ref_xyz = np.stack([L.fk(p) for p in pots])
+    dx = np.abs(xyz_gpu - ref_xyz).max()
+    assert dx <= COORD_TOL, dx
+    ref = np.array([L.score_atoms(og, x)[0] for x in xyz_gpu])
+    diff = np.abs(np.asarray(es, np.float64) - ref)
+    ok = close(es, ref)
+    for k in np.nonzero(~ok)[0]:        # the cutoff edges, only where the strict test fails
+        slack = cutoff_slack(L, xyz_gpu[k]) + (node_cutoff_slack(L, xyz_gpu[k], *site) if site else 0.0)
+        ok[k] = diff[k] <= slack + ABS_TOL
+    assert ok.all(), (np.nonzero(~ok)[0], diff.max())
+    return ref_xyz
+
+
+def cutoff_slack(L, xyz):
+    """Sum of the cutoff jumps of the intra pairs within CUTOFF_EDGE of the cutoff at xyz."""
+    if L.n_pairs == 0:
+        return 0.0
+    i, j = L.pairs[:, 0], L.pairs[:, 1]
+    r = np.linalg.norm(xyz[i] - xyz[j], axis=1)
+    near = np.nonzero(np.abs(r - CUTOFF) < CUTOFF_EDGE)[0]
+    return float(sum(abs(O.pair_energy(int(L.xs[i[k]]), int(L.xs[j[k]]), CUTOFF - 1e-9)[0]) for k in near))
+
+
+def node_cutoff_slack(L, xyz, rec, rec_types, box):
+    """Sum over the ligand atoms' interpolation corners of weight x the cutoff jumps of the receptor
+    atoms within CUTOFF_EDGE of 8 A from that node (the grid's cutoff edge)."""
+    origin, dims = O.grid_geometry(box)
+    sp = float(box.spacing)
+    rxyz = np.asarray(rec.xyz, np.float64)
+    total = 0.0
+    for a in range(L.n):
+        g = np.clip((xyz[a] - origin) / sp, 0, dims - 1)
+        i = np.minimum(np.floor(g).astype(int), dims - 2)
+        f = g - i
+        for dz in (0, 1):
+            for dy in (0, 1):
+                for dx in (0, 1):
+                    w = (f[0] if dx else 1 - f[0]) * (f[1] if dy else 1 - f[1]) * (f[2] if dz else 1 - f[2])
+                    node = origin + sp * (i + np.array([dx, dy, dz]))
+                    r = np.linalg.norm(rxyz - node, axis=1)
+                    for j in np.nonzero(np.abs(r - CUTOFF) < CUTOFF_EDGE)[0]:
+                        total += w * abs(O.pair_energy(int(L.xs[a]), int(rec_types[j]), CUTOFF - 1e-9)[0])
+    return total

@@ -16,6 +16,10 @@ from tests import _gpu as G
 
 pytestmark = pytest.mark.gpu
 
+# the batched search with whole-warp teams (chosen automatically for this 20-atom ligand), with
+# half-warp teams, and the plain thread-per-chain form
+FORMS = (dict(mode="batched"), dict(mode="batched", search_variant=4, warps_per_cta=4), dict(mode="plain"))
+
 
 def _tiny_site():
     w = S.tiny()
@@ -38,13 +42,13 @@ def tiny():
     ctx = G.context()
     rec, box, lig = _tiny_site()
     gs, pls, Ls, ogs = _setup(ctx, rec, [box], [lig])
-    return ctx, box, gs, pls[0], Ls[0], ogs[0]
+    return ctx, box, gs, pls[0], Ls[0], ogs[0], rec
 
 
 def test_random_starts_match_oracle(tiny):
-    ctx, box, gs, pl, L, og = tiny
-    for mode in ("batched", "plain"):
-        r = ctx.dock(gs, [pl], [0], chains=40, steps=0, seed=7, mode=mode)
+    ctx, box, gs, pl, L, og, rec = tiny
+    for form in FORMS:
+        r = ctx.dock(gs, [pl], [0], chains=40, steps=0, seed=7, **form)
         pots, es = r.chain_records()
         for c in range(40):
             ref = O.random_conformation(L, box, 7, 0, c)
@@ -58,28 +62,28 @@ def test_first_mc_steps_in_lockstep(tiny):
     states agree with the oracle's. (With the full BFGS budget they do not: the FP64 oracle
     perturbed by 1e-7 agrees with itself on under 10 % of chains after one step, because BFGS
     from a clashing random start has not converged within its iteration budget.)"""
-    ctx, box, gs, pl, L, og = tiny
+    ctx, box, gs, pl, L, og, rec = tiny
     p = O.SearchParams(seed=3, steps=3, max_iter=1, max_trials=1)
     ref_pots, ref_es, _ = O.mc_chains(L, og, box, p, unit=0, n_chains=64, threads=G.threads())
-    for mode in ("batched", "plain"):
-        r = ctx.dock(gs, [pl], [0], chains=64, steps=3, seed=3, mode=mode, bfgs_max_iter=1, bfgs_max_trials=1)
+    for form in FORMS:
+        r = ctx.dock(gs, [pl], [0], chains=64, steps=3, seed=3, bfgs_max_iter=1, bfgs_max_trials=1, **form)
         pots, es = r.chain_records()
         agree = G.close(es[0], ref_es, abs_tol=1e-3, rel_tol=1e-4)
-        assert agree.mean() >= 0.95, (mode, agree.mean())
+        assert agree.mean() >= 0.95, (form, agree.mean())
         same = np.abs(pots[0, :, :L.n_pot] - ref_pots).max(axis=1) <= 1e-3
-        assert same.mean() >= 0.95, (mode, same.mean())
+        assert same.mean() >= 0.95, (form, same.mean())
 
 
-def test_reported_poses_are_valid_and_selection_matches_oracle(tiny):
-    ctx, box, gs, pl, L, og = tiny
-    r = ctx.dock(gs, [pl], [0], chains=48, steps=60, seed=11, top_k=9, rmsd_min=1.0)
+@pytest.mark.parametrize("variant", [-1, 4])
+def test_reported_poses_are_valid_and_selection_matches_oracle(tiny, variant):
+    ctx, box, gs, pl, L, og, rec = tiny
+    r = ctx.dock(gs, [pl], [0], chains=48, steps=60, seed=11, top_k=9, rmsd_min=1.0, search_variant=variant)
     pots, es = r.chain_records()
     pots64 = pots[0, :, :L.n_pot].astype(np.float64)
     # every chain's best is what the oracle scores for that pose
-    ref = np.array([L.score(og, q, False)[0] for q in pots64])
-    assert G.close(es[0], ref).all()
+    xyz = G.check_pose_scores(L, og, pots64, es[0], G.pose_coords(ctx, pl, pots[0, :, :L.n_pot]),
+                              (rec, O.xs_type_receptor(rec), box))
     # top-k: the oracle's sort + RMSD filter on the GPU's chain bests picks the same chains
-    xyz = np.stack([L.fk(q) for q in pots64])
     kept = O.topk(es[0].astype(np.float64), xyz, 9, 1.0)
     n = r.n_kept[0]
     assert list(r.poses[0]["chain"][:n]) == list(kept)
@@ -99,7 +103,7 @@ def test_tiny_workload_best_score_parity(tiny):
     0.2 kcal/mol of the oracle's. Sampled with 64 chains, where the oracle's own best varies by
     about 0.01 kcal/mol across seeds (with the workload's 8 chains it varies by about 0.2, so the
     comparison would measure sampling noise, not parity)."""
-    ctx, box, gs, pl, L, og = tiny
+    ctx, box, gs, pl, L, og, rec = tiny
     p = O.SearchParams(seed=0, steps=1000)
     _, ref_es, _ = O.mc_chains(L, og, box, p, unit=0, n_chains=64, threads=G.threads())
     r = ctx.dock(gs, [pl], [0], chains=64, steps=1000, seed=0)
@@ -109,7 +113,7 @@ def test_tiny_workload_best_score_parity(tiny):
 
 
 def test_bitwise_determinism_across_launch_settings(tiny):
-    ctx, box, gs, pl, L, og = tiny
+    ctx, box, gs, pl, L, og, rec = tiny
     base = ctx.dock(gs, [pl], [0], chains=24, steps=40, seed=5)
     b_pots, b_es = base.chain_records()
     for kw in (dict(use_graph=False), dict(steps_per_round=7), dict(warps_per_cta=8),
@@ -119,6 +123,30 @@ def test_bitwise_determinism_across_launch_settings(tiny):
         np.testing.assert_array_equal(es, b_es, err_msg=str(kw))
         np.testing.assert_array_equal(pots, b_pots, err_msg=str(kw))
         assert (r.poses == base.poses).all()
+
+
+def test_register_variants_agree_bitwise_within_a_team_width(tiny):
+    """Variants 0-3 (a chain per warp) agree bitwise among themselves, and so do 4-7 (a chain per
+    half warp); the autotuned default is the whole-warp group for this 20-atom ligand and the
+    half-warp group for ligands of at most 16 atoms."""
+    ctx, box, gs, pl, L, og, rec = tiny
+    base = {}
+    for v, w in ((0, 2), (1, 4), (2, 4), (3, 4), (4, 2), (5, 4), (6, 4), (7, 4)):
+        r = ctx.dock(gs, [pl], [0], chains=40, steps=30, seed=6, search_variant=v, warps_per_cta=w)
+        assert r.launch_shape() == (v, w)
+        pots, es = r.chain_records()
+        g = v // 4
+        if g not in base:
+            base[g] = (pots, es)
+        else:
+            np.testing.assert_array_equal(es, base[g][1], err_msg=str(v))
+            np.testing.assert_array_equal(pots, base[g][0], err_msg=str(v))
+    r = ctx.dock(gs, [pl], [0], chains=40, steps=30, seed=6)
+    assert r.launch_shape()[0] < 4
+    np.testing.assert_array_equal(r.chain_records()[1], base[0][1])
+    small = ctx.ligand(G.ligand32(S.ligand_centered(S.make_ligand(14, 3, 8))))
+    gs_all = ctx.build_grids(rec, [box], list(range(11)))
+    assert ctx.dock(gs_all, [small], [0], chains=40, steps=5, seed=6).launch_shape()[0] >= 4
 
 
 def test_multi_pocket_merge_and_pocket_parity():
@@ -156,7 +184,7 @@ def test_multi_pocket_merge_and_pocket_parity():
 
 
 def test_plain_path_is_valid(tiny):
-    ctx, box, gs, pl, L, og = tiny
+    ctx, box, gs, pl, L, og, rec = tiny
     r = ctx.dock(gs, [pl], [0], chains=16, steps=30, seed=2, mode="plain")
     pots, es = r.chain_records()
     ref = np.array([L.score(og, q, False)[0] for q in pots[0, :, :L.n_pot].astype(np.float64)])
@@ -166,7 +194,7 @@ def test_plain_path_is_valid(tiny):
 
 
 def test_watchdog_timeout_returns_status_and_context_survives(tiny):
-    ctx, box, gs, pl, L, og = tiny
+    ctx, box, gs, pl, L, og, rec = tiny
     from paper_2506_20043_gb300 import _capi as A
     r = ctx.dock(gs, [pl], [0], chains=8, steps=100000, seed=1, timeout_s=0.02)
     assert r.status_code == A.PV_ERR_TIMEOUT
@@ -178,10 +206,14 @@ def test_watchdog_timeout_returns_status_and_context_survives(tiny):
 
 
 def test_dock_argument_errors(tiny):
-    ctx, box, gs, pl, L, og = tiny
+    ctx, box, gs, pl, L, og, rec = tiny
     from paper_2506_20043_gb300.api import PVError
     for kw in (dict(chains=0), dict(top_k=0), dict(top_k=33), dict(bfgs_m=9), dict(warps_per_cta=17)):
         with pytest.raises(PVError):
             ctx.dock(gs, [pl], [0], steps=1, **kw)
     with pytest.raises(PVError):
         ctx.dock(gs, [pl], [3], steps=1)
+    # half-warp variants refuse a ligand of more than 32 atoms
+    big = ctx.ligand(G.ligand32(S.ligand_centered(S.make_ligand(40, 4, 3))))
+    with pytest.raises(PVError):
+        ctx.dock(gs, [big], [0], steps=1, search_variant=5, warps_per_cta=4)

@@ -204,3 +204,16 @@ def test_rigid_and_edge_ligands():
         ctx.score(gs_c, pl, 0, p)
     with pytest.raises(PVError):
         ctx.score(gs, pl, 5, p)
+
+
+def test_gather_microbenchmark_runs_and_rejects_bad_arguments():
+    """The gather probe (the interpolation step alone) times real launches on a pocket's maps."""
+    from paper_2506_20043_gb300.api import PVError
+    ctx = G.context()
+    rec, box, lig = _site(n_rec=2000, box_size=12.0, n_atoms=12, n_rot=2, seed=5)
+    gs = ctx.build_grids(rec, [box], [0, 1, 2])
+    ms, pts, gbs = ctx.measure_gather(gs, 0, n_points=1 << 20, reps=3)
+    assert ms > 0 and pts > 1e8 and gbs == pytest.approx(32 * pts / 1e9)
+    for kw in (dict(pocket=1), dict(n_points=0), dict(reps=0)):
+        with pytest.raises(PVError):
+            ctx.measure_gather(gs, **{**dict(pocket=0, n_points=1024, reps=1), **kw})

@@ -1,0 +1,87 @@
+"""The intra-pair schedules of the library's ligand records (host code, no GPU): built by the
+library's own ligand builder, decoded, and checked against the oracle's pair list (C-intra: pairs
+in different rigid fragments more than three bonds apart).
+
+Each schedule (the warp's 32 lanes, and the half warp's 16 lanes for ligands that fit one) must
+hold every oracle pair exactly once, give a target at most one pair per round (the format gives a
+lane at most one), carry the pair's hydrophobic / H-bond flags, and use no more rounds than the
+largest lane or target load of its orientation (a proper edge colouring of a bipartite graph,
+Koenig's theorem)."""
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle as O
+import pvsynth as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2506_20043_gb300", "csrc")
+XS = ["C_H", "C_P", "N_P", "N_D", "N_A", "N_DA", "O_P", "O_D", "O_A", "O_DA", "S_P"]
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    out = str(tmp_path_factory.mktemp("sched") / "libsched.so")
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", "-I", CSRC, "-I", cuda_inc,
+                           os.path.join(ROOT, "tests", "csrc", "ligand_schedule.cpp"),
+                           os.path.join(CSRC, "pv_ligand.cpp"), "-o", out])
+    L = C.CDLL(out)
+    L.lig_schedule.restype = C.c_int
+    return L
+
+
+def _decode(lib, lig, lanes):
+    xyz = np.ascontiguousarray(lig.xyz, np.float32)
+    el, don, acc = (np.ascontiguousarray(a, np.uint8) for a in (lig.element, lig.donor, lig.acceptor))
+    bonds = np.ascontiguousarray(lig.bonds, np.int32).reshape(-1, 2)
+    rot = np.ascontiguousarray(lig.rotatable, np.uint8)
+    out = np.zeros((4096, 6), np.int32)
+    info = np.zeros(4, np.int32)
+    p = lambda a, t: a.ctypes.data_as(C.POINTER(t))   # noqa: E731
+    k = lib.lig_schedule(len(xyz), p(xyz, C.c_float), p(el, C.c_uint8), p(don, C.c_uint8), p(acc, C.c_uint8),
+                         len(bonds), p(bonds, C.c_int32), p(rot, C.c_uint8), lanes, p(out, C.c_int32), len(out),
+                         p(info, C.c_int32))
+    assert k >= 0, k
+    return out[:k], info
+
+
+CASES = [(n, r, s) for s, (n, r) in enumerate([(5, 0), (8, 2), (12, 3), (16, 4), (20, 4), (24, 6), (30, 6), (32, 8),
+                                               (32, 10), (31, 9), (40, 8), (48, 12), (60, 15), (64, 20)])]
+
+
+@pytest.mark.parametrize("n_atoms,n_rot,seed", CASES + [(int(n), int(r), 100 + i) for i, (n, r) in enumerate(
+    zip(np.random.default_rng(4).integers(6, 33, 24), np.random.default_rng(5).integers(0, 11, 24)))])
+def test_schedules_hold_every_oracle_pair_once(lib, n_atoms, n_rot, seed):
+    lig = S.ligand_centered(S.make_ligand(n_atoms, n_rot, seed))
+    L = O.OracleLigand(lig)
+    ref = {(min(int(a), int(b)), max(int(a), int(b))) for a, b in L.pairs}
+    assert len(ref) == L.n_pairs
+    xs = [XS[t] for t in L.xs]
+    donor = {t for t in XS if t.endswith("_D") or t.endswith("_DA")}
+    acceptor = {t for t in XS if t.endswith("_A") or t.endswith("_DA")}
+    _, info = _decode(lib, lig, 32)
+    widths = [32] + ([16] if info[2] else [])
+    # a half-warp team holds up to 32 atoms (two per lane) and 16 tangent coordinates
+    assert bool(info[2]) == (n_atoms <= 32 and 6 + L.n_rot <= 16)
+    for lanes in widths:
+        rows, info = _decode(lib, lig, lanes)
+        got = [(min(s, t), max(s, t)) for _, _, s, t, _, _ in rows]
+        assert len(got) == len(set(got)) == len(ref), lanes
+        assert set(got) == ref, lanes
+        for rnd, lane, s, t, hyd, hb in rows:
+            assert s != t and s >= 0 and t >= 0
+            assert hyd == int(xs[s] == "C_H" and xs[t] == "C_H")
+            assert hb == int((xs[s] in donor and xs[t] in acceptor) or (xs[s] in acceptor and xs[t] in donor))
+        n_rounds = info[0] if lanes == 32 else info[1]
+        seen = set()
+        for rnd, lane, s, t, _, _ in rows:
+            assert (rnd, t) not in seen, ("target twice in a round", lanes, rnd, t)
+            seen.add((rnd, t))
+        if len(rows):
+            lane_load = np.bincount(rows[:, 1], minlength=lanes).max()
+            tgt_load = np.bincount(rows[:, 3]).max()
+            assert n_rounds == max(lane_load, tgt_load), lanes
