@@ -474,8 +474,8 @@ def run_batch_workload(args):
 
 def run_small_case(args):
     """One short untimed pass for profiler captures: the multi-pocket workload (10 pockets x 1,000
-    chains) for 20 MC steps with a fixed launch shape (--variant, --warps; no autotuning), plus one
-    score launch over the 65,536 microbenchmark poses."""
+    chains) for --small-steps MC steps in one search launch with a fixed launch shape (--variant,
+    --warps; no autotuning), plus one score launch over the 65,536 microbenchmark poses."""
     import torch
     import paper_2506_20043_gb300 as pv
     pv.build()
@@ -484,8 +484,8 @@ def run_small_case(args):
     rec, boxes, lig_src = workload(seed=0)
     lig = ctx.ligand(lig_src)
     gs = ctx.build_grids(rec, boxes, sorted(set(lig.xs_types.tolist())))
-    r = ctx.dock(gs, [lig], list(range(len(boxes))), chains=CHAINS, steps=20, seed=0, host_copy=False,
-                 search_variant=args.variant, warps_per_cta=args.warps, steps_per_round=20)
+    r = ctx.dock(gs, [lig], list(range(len(boxes))), chains=CHAINS, steps=args.small_steps, seed=0, host_copy=False,
+                 search_variant=args.variant, warps_per_cta=args.warps, steps_per_round=args.small_steps)
     ev, sec, st = r.stats()
     mrec, mbox, mlig_src, mposes = S.score_microbench()
     mlig = ctx.ligand(mlig_src)
@@ -512,7 +512,8 @@ def main():
     ap.add_argument("--case", choices=["full", "small"], default="full",
                     help="small: one untimed small pass for profiler captures")
     ap.add_argument("--variant", type=int, default=0, help="search kernel variant of --case small")
-    ap.add_argument("--warps", type=int, default=2, help="chains per CTA of --case small")
+    ap.add_argument("--warps", type=int, default=2, help="warps per CTA of --case small")
+    ap.add_argument("--small-steps", type=int, default=20, help="MC steps of --case small (one launch)")
     args = ap.parse_args()
     if args.case == "small":
         out = run_small_case(args)

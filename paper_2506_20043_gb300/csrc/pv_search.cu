@@ -224,6 +224,160 @@ __device__ __forceinline__ void run_chain(const SearchArgs& A, const PvLigBlob& 
     flags_out = flags;
 }
 
+// RILC-BFGS (Eq. 6-12) of one whole-warp chain from x (updated in place); returns SF(x). One
+// evaluation call site: the start point, then every line-search trial.
+__device__ __forceinline__ float warp_local_search(const PvLigBlob& L, WarpScratch& S, const Site& site, Pose& x,
+                                                   const PvSearchConst& C, int max_iter, uint32_t& evals) {
+    using Tm = Team<32>;
+    const int tl = Tm::lane();
+    const int n_tan = 6 + L.h.n_rot, m = C.bfgs_m;
+    float* Hs = &S.hs[0][0];
+    float* Hy = &S.hy[0][0];
+    float rh = 0.f, al = 0.f;
+    int stored = 0, head = 0, it = 0, tr = 0;
+    float f = 0.f, g = 0.f, d = 0.f, gd = 0.f, lam = 1.f, lo = 0.f, hi = -1.f, flo = 0.f, glo = 0.f;
+    bool have_lo = false, start = true;
+    Pose xt = x;
+    for (;;) {
+        float ge;
+        const float fe = team_eval<32>(L, S, site, xt, ge, true);
+        ++evals;
+        bool next_iter = false;
+        if (start) {
+            start = false;
+            f = fe; g = ge;
+            next_iter = true;
+        } else {
+            const float gtd = Tm::sum(ge * d);
+            bool take = false;
+            float ft = fe, gt = ge;
+            if (!(fe <= f + lam * C.rho * gd)) {
+                hi = lam;                                       // Eq. 7 holds: Armijo fails
+            } else if (gtd < C.sigma * gd) {
+                lo = lam; have_lo = true; flo = fe; glo = ge;   // Eq. 8 holds: Wolfe fails
+            } else {
+                take = true;
+            }
+            if (!take) {
+                ++tr;
+                if (tr < C.bfgs_max_trials) {
+                    lam = hi < 0.f ? 2.f * lam : 0.5f * (lo + hi);
+                    xt = team_retract<32>(x, lam * d, n_tan);
+                    continue;
+                }
+                if (!have_lo) break;                            // no acceptable step: stop at x
+                lam = lo; ft = flo; gt = glo;
+                xt = team_retract<32>(x, lam * d, n_tan);       // the same arithmetic as that trial
+            }
+            const float sv = lam * d, yv = gt - g;
+            const float ys = Tm::sum(yv * sv), ss = Tm::sum(sv * sv), gn = sqrtf(Tm::sum(g * g));
+            if (ss > 0.f && ys / ss > C.eps * gn) {
+                Hs[head * 32 + tl] = sv;
+                Hy[head * 32 + tl] = yv;
+                if (tl == head) rh = 1.f / ys;
+                head = head + 1 == m ? 0 : head + 1;
+                stored = min(stored + 1, m);
+            }
+            x = xt; g = gt; f = ft;
+            ++it;
+            if (sqrtf(Tm::sum(g * g)) <= C.eps) break;
+            next_iter = true;
+        }
+        if (next_iter) {
+            if (it >= max_iter) break;
+            d = lbfgs_direction<32>(Hs, Hy, rh, al, g, stored, head, m);
+            gd = Tm::sum(g * d);
+            if (!(gd < 0.f)) break;
+            lam = 1.f; lo = 0.f; hi = -1.f; have_lo = false; tr = 0;
+            xt = team_retract<32>(x, lam * d, n_tan);
+        }
+    }
+    Tm::sync();
+    return f;
+}
+
+// The whole-warp chain runner: the same steps as run_chain with the local search as an inner
+// loop (no other team shares the warp, so nothing needs to stay converged across chains).
+__device__ __forceinline__ void run_chain_warp(const SearchArgs& A, const PvLigBlob& L, WarpScratch& S,
+                                               const Site& site, int pair, int chain, uint32_t& evals_out,
+                                               int& flags_out) {
+    using Tm = Team<32>;
+    const int tl = Tm::lane();
+    const PvSearchConst& C = A.C;
+    const int n_rot = L.h.n_rot;
+    const int max_iter = C.bfgs_max_iter > 0 ? C.bfgs_max_iter : L.h.bfgs_iters;
+    float* rec = A.chains + ((size_t)pair * C.chains + chain) * PV_CHAIN_STRIDE;
+    float* curs = S.cur;
+    float e_cur = 0.f, e_best = 0.f, u = 0.f;
+    uint32_t evals = 0, evals_before = 0;
+    if (A.step0 != 0) {
+        for (int i = tl; i < 7 + n_rot; i += 32) curs[i] = rec[PV_CH_CUR + i];
+        e_cur = rec[PV_CH_ECUR];
+        e_best = rec[PV_CH_EBEST];
+        evals_before = __float_as_uint(rec[PV_CH_EVALS]);
+    }
+    Tm::sync();
+    int flags = 0, s = A.step0, stage = A.step0 == 0 ? 0 : 1;   // 0 start, 1 MC step, 2 refine
+    Pose cand;
+    if (stage == 0) cand = random_pose<32>(L, *site.P, (uint32_t)chain, (uint32_t)pair, C);
+    while (stage == 0 || s < A.step1) {
+        if (stage == 1) {
+            cand = load_pose<32>(curs, n_rot);
+            u = mutate<32>(L, cand, (uint32_t)chain, (uint32_t)pair, s, C);
+        }
+        const float e_new = warp_local_search(L, S, site, cand, C, stage == 0 ? 0 : max_iter, evals);
+        if (stage == 0) {
+            e_cur = e_new;
+            e_best = e_new;
+            store_pose<32>(curs, cand, n_rot);
+            store_pose<32>(rec + PV_CH_BEST, cand, n_rot);
+            Tm::sync();
+            stage = 1;
+            continue;
+        }
+        if (stage == 1) {
+            if (!(e_new < e_cur || u < expf((e_cur - e_new) / C.temperature))) {
+                ++s;                                            // rejected
+            } else if (e_new < e_best) {
+                stage = 2;                                      // accepted, a new best: refine first
+                continue;
+            } else {
+                e_cur = e_new;                                  // accepted
+                Tm::sync();
+                store_pose<32>(curs, cand, n_rot);
+                Tm::sync();
+                ++s;
+            }
+        } else {                                                // the refined new best
+            e_cur = e_new;
+            e_best = e_new;
+            store_pose<32>(rec + PV_CH_BEST, cand, n_rot);
+            Tm::sync();
+            store_pose<32>(curs, cand, n_rot);
+            Tm::sync();
+            stage = 1;
+            ++s;
+        }
+        if (A.timeout_ns) {
+            unsigned long long now = tl == 0 ? globaltimer() : 0ull;
+            now = __shfl_sync(PV_FULL, now, 0);
+            if (now - *A.t0 > A.timeout_ns) { flags |= PV_EBIT_TIMEOUT; break; }
+        }
+    }
+    if (!(e_best == e_best)) flags |= PV_EBIT_NAN;
+    Tm::sync();
+    for (int i = tl; i < 7 + n_rot; i += 32) rec[PV_CH_CUR + i] = curs[i];
+    if (tl == 0) {
+        rec[PV_CH_ECUR] = e_cur;
+        rec[PV_CH_EBEST] = e_best;
+        rec[PV_CH_EVALS] = __uint_as_float(evals_before + evals);
+        const int old = A.step0 == 0 ? 0 : __float_as_int(rec[PV_CH_FLAGS]);
+        rec[PV_CH_FLAGS] = __int_as_float(old | flags);
+    }
+    evals_out = evals;
+    flags_out = flags;
+}
+
 // One round of MC steps [step0, step1) for every chain of every pair (batched form). Compiled
 // for several (threads per CTA, minimum CTAs per SM) bounds, i.e. register budgets, and team
 // widths (a chain per warp, or per half warp); the runtime picks one (search variant).
@@ -262,7 +416,11 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) search_round_kernel(SearchA
         site.P = &s_pocket;
         uint32_t evals = 0;
         int flags = 0;
-        run_chain<LANES>(A, L, scratch[team], site, item.pair, chain, chain < A.C.chains, evals, flags);
+        if constexpr (LANES == 32) {
+            if (chain < A.C.chains) run_chain_warp(A, L, scratch[team], site, item.pair, chain, evals, flags);
+        } else {
+            run_chain<LANES>(A, L, scratch[team], site, item.pair, chain, chain < A.C.chains, evals, flags);
+        }
         if (Team<LANES>::lane() == 0 && evals) {
             atomicAdd(A.evals, (unsigned long long)evals);
             if (flags) atomicOr(A.err, flags);
