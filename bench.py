@@ -115,15 +115,17 @@ def kernel_source_hash() -> str:
 
 
 def stored_traffic():
-    """Per-evaluation DRAM traffic of the search kernel from the committed ncu summary, if that
-    summary was taken on the current kernel sources (else None)."""
+    """DRAM bytes (read + write) of one search launch from the committed ncu summary, if that
+    summary was taken on the current kernel sources (else None). The launch's traffic is one read of
+    the pockets' maps plus the chain records, the same for a 20-, 100- or 500-step launch (the maps
+    stay L2-resident), so the captured launch stands for the bench's launches."""
     p = os.path.join(ROOT, "profiles", "search_round_kernel_multipocket.md")
     if not os.path.exists(p):
         return None
     txt = open(p).read()
     import re
     m_hash = re.search(r"kernel source hash:\s*`?([0-9a-f]{16})", txt)
-    m_tr = re.search(r"dram bytes per evaluation:\s*([0-9.eE+]+)", txt)
+    m_tr = re.search(r"dram bytes per launch:\s*([0-9.eE+]+)", txt)
     if not (m_hash and m_tr) or m_hash.group(1) != kernel_source_hash():
         return None
     return float(m_tr.group(1))
@@ -201,7 +203,7 @@ def run_ours(args):
         max_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
         peak_tflops = n_sm * 128 * 2 * max_mhz * 1e6 / 1e12
         achieved = evals * flops / search_s / 1e12
-        per_eval_traffic = stored_traffic()
+        launch_traffic = stored_traffic()
         evals_per_launch = evals / max(launches, 1)
         n_rounds = launches // max(args.steps, 1)
         _, _, gather_gbs = ctx.measure_gather(gs, 0, n_points=1 << 24, reps=10)
@@ -223,9 +225,10 @@ def run_ours(args):
             "evals_per_step_per_gpu": evals // max(args.steps, 1),
             "roofline": {"kernel": "search_round_kernel", "bound": "alu", "achieved": round(achieved, 3),
                          "peak": round(peak_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
-                         "traffic": (round(per_eval_traffic * evals_per_launch) if per_eval_traffic else None),
+                         "traffic": (round(launch_traffic) if launch_traffic else None),
                          "peak_source": f"FP32 FMA peak = {n_sm} SMs x 128 lanes x 2 x {max_mhz:.0f} MHz",
-                         "flops_per_eval": flops, "launch_ms": round(search_s / max(launches, 1) * 1e3, 3),
+                         "flops_per_eval": flops, "evals_per_launch": round(evals_per_launch),
+                         "launch_ms": round(search_s / max(launches, 1) * 1e3, 3),
                          "l2_gather_gbs": round(search_gather_gbs, 1),
                          "gather_ceiling_gbs": round(gather_gbs, 1),
                          "gather_frac": round(search_gather_gbs / gather_gbs, 4)},

@@ -52,7 +52,8 @@ class BfgsParams(C.Structure):
 
 class McParams(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("steps", C.c_int), ("temperature", C.c_double),
-                ("amplitude", C.c_double), ("bfgs", BfgsParams)]
+                ("amplitude", C.c_double), ("bfgs", BfgsParams), ("focc", C.c_int),
+                ("focc_min_delta", C.c_double)]
 
 
 EVAL_FN = C.CFUNCTYPE(C.c_double, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double))
@@ -121,6 +122,9 @@ def lib():
                                       C.c_uint32, dp, dp, C.POINTER(C.c_long)]
             L.or_mc_chains.argtypes = [vp, C.POINTER(Grid), dp, dp, C.POINTER(McParams), C.c_uint32,
                                        C.c_int, dp, dp, C.POINTER(C.c_long), C.c_int]
+            L.or_tangent_delta.argtypes = [C.c_int, dp, dp, dp]
+            L.or_focc_pass.restype = C.c_int
+            L.or_focc_pass.argtypes = [vp, dp, C.c_double, dp, C.c_int, dp, dp, dp, C.c_double]
             L.or_topk.restype = C.c_int
             L.or_topk.argtypes = [C.c_int, dp, dp, C.c_int, C.c_int, C.c_double, ip]
             L.or_affinity.restype = C.c_double
@@ -344,12 +348,15 @@ class SearchParams:
     eps: float = 1e-3
     top_k: int = 9
     rmsd_min: float = 1.0
+    focc: int = 0              # first-order consistency check (Eq. 4-5): neighbours kept, 0 = off
+    focc_min_delta: float = 1e-4
 
     def bfgs(self) -> BfgsParams:
         return BfgsParams(self.m, self.max_iter, self.max_trials, self.rho, self.sigma, self.eps)
 
     def mc(self) -> McParams:
-        return McParams(self.seed, self.steps, self.temperature, self.amplitude, self.bfgs())
+        return McParams(self.seed, self.steps, self.temperature, self.amplitude, self.bfgs(), self.focc,
+                        self.focc_min_delta)
 
 
 def bfgs_generic(f_and_grad, retract, x0, n_tan: int, params: SearchParams):
@@ -437,6 +444,26 @@ def mc_chains(lig: OracleLigand, grid: OracleGrid, box, params: SearchParams, un
                               int(chain0 + i), _p(row), C.byref(e), C.byref(n))
             pots[i], es[i], ev[i] = row, e.value, n.value
     return pots, es, ev
+
+
+def tangent_delta(n_rot: int, a, b) -> np.ndarray:
+    """a - b in the optimiser's tangent space (translation, rotation vector, wrapped torsions)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    out = np.zeros(6 + n_rot)
+    lib().or_tangent_delta(int(n_rot), _p(a), _p(b), _p(out))
+    return out
+
+
+def focc_pass(lig: OracleLigand, pot_i, f_i: float, g_i, nb_pots, nb_f, nb_g, min_delta: float = 1e-4) -> bool:
+    """First-order consistency check (Eq. 4-5) of a candidate against stored neighbours."""
+    pot_i = np.ascontiguousarray(pot_i, dtype=np.float64)
+    g_i = np.ascontiguousarray(g_i, dtype=np.float64)
+    nb_pots = np.ascontiguousarray(np.reshape(nb_pots, (-1, lig.n_pot)), dtype=np.float64)
+    nb_g = np.ascontiguousarray(np.reshape(nb_g, (-1, 6 + lig.n_rot)), dtype=np.float64)
+    nb_f = np.ascontiguousarray(nb_f, dtype=np.float64)
+    return bool(lib().or_focc_pass(lig.ptr, _p(pot_i), float(f_i), _p(g_i), len(nb_f), _p(nb_pots), _p(nb_f),
+                                   _p(nb_g), float(min_delta)))
 
 
 def topk(scores, xyz, k: int, rmsd_min: float) -> np.ndarray:

@@ -798,6 +798,8 @@ typedef struct {
     double temperature;   /* Metropolis temperature (Eq. 13 reading) */
     double amplitude;     /* translation mutation radius, A */
     or_bfgs_params bfgs;  /* max_iter <= 0: floor((25 + N_atoms) / 3) */
+    int focc;             /* first-order consistency check: neighbours kept (0 = off, <= 4) */
+    double focc_min_delta;/* coordinates closer than this carry no sign information */
 } or_mc_params;
 
 /* Random conformation (Algorithm 2, random_conformation): draws 0-2 translation uniform in the
@@ -857,35 +859,124 @@ int or_metropolis_accept(double e_cur, double e_new, double temperature, double 
     return (e_new < e_cur) || (u < exp((e_cur - e_new) / temperature));
 }
 
+/* ------------------------------------------- first-order consistency check (Eq. 4-5) --- */
+#define OR_FOCC_MAX 4
+
+/* Tangent-space difference a - b of two POTs: translation difference, the rotation vector w
+ * with q_a = exp(w / 2) (x) q_b (shortest rotation; both quaternions normalised first), torsion
+ * differences wrapped into [-pi, pi). */
+void or_tangent_delta(int n_rot, const double* a, const double* b, double* out) {
+    for (int c = 0; c < 3; ++c) out[c] = a[c] - b[c];
+    double qa[4], qb[4], na = 0, nb = 0;
+    for (int k = 0; k < 4; ++k) { na += a[3 + k] * a[3 + k]; nb += b[3 + k] * b[3 + k]; }
+    na = sqrt(na); nb = sqrt(nb);
+    qa[0] = a[3] / na; qb[0] = b[3] / nb;
+    for (int k = 1; k < 4; ++k) { qa[k] = a[3 + k] / na; qb[k] = -b[3 + k] / nb; }   /* qb <- conj */
+    double r[4];
+    quat_mul(qa, qb, r);
+    if (r[0] < 0) for (int k = 0; k < 4; ++k) r[k] = -r[k];
+    double vn = sqrt(r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
+    double scale = vn > 1e-15 ? 2.0 * atan2(vn, r[0]) / vn : 2.0;
+    for (int c = 0; c < 3; ++c) out[3 + c] = scale * r[1 + c];
+    for (int k = 0; k < n_rot; ++k) {
+        double d = a[7 + k] - b[7 + k];
+        d = d - 2 * OR_PI * floor((d + OR_PI) / (2 * OR_PI));
+        out[6 + k] = d;
+    }
+}
+
+static int sgn(double v) { return (v > 0) - (v < 0); }
+
+/* The check of Eq. 4-5 for a candidate C_i' (SF f_i, tangent gradient g_i) against stored
+ * neighbours C_j (SF f_j, gradient g_j). Reading (the paper leaves the neighbours and the
+ * quantifiers open): along a tangent coordinate p where the two differ by more than min_delta,
+ * Eq. 4 (the derivative changes sign between them) or Eq. 5 (the secant slope
+ * (SF_i - SF_j) / (C_i - C_j)_p disagrees in sign with the derivative at C_i') means a stationary
+ * point may lie between them. The candidate passes (is worth a local search) if every neighbour
+ * has such a coordinate; it fails if some neighbour has none, i.e. the candidate lies on a
+ * slope that runs down to that neighbour along every coordinate and would roll back to it.
+ * No neighbour: pass. Returns 1 (pass) or 0 (fail). */
+int or_focc_pass(const or_ligand* L, const double* pot_i, double f_i, const double* g_i, int n_nb,
+                 const double* pots, const double* fs, const double* gs, double min_delta) {
+    int n_rot = L->n_rot, n_tan = 6 + n_rot, np = 7 + n_rot;
+    for (int j = 0; j < n_nb; ++j) {
+        double dl[OR_MAXN];
+        or_tangent_delta(n_rot, pot_i, pots + (size_t)j * np, dl);
+        int evidence = 0;
+        for (int p = 0; p < n_tan && !evidence; ++p) {
+            if (!(fabs(dl[p]) > min_delta)) continue;
+            int gi = sgn(g_i[p]), gj = sgn(gs[(size_t)j * n_tan + p]);
+            if (gi * gj <= 0) evidence = 1;                                   /* Eq. 4 */
+            else if (gi * sgn((f_i - fs[j]) * dl[p]) <= 0) evidence = 1;      /* Eq. 5 */
+        }
+        if (!evidence) return 0;
+    }
+    return 1;
+}
+
+/* The last H current conformations of a chain with SF and gradient (the neighbours of Eq. 4-5),
+ * stored contiguously in push order modulo H. */
+typedef struct {
+    int H, n, head, np, n_tan;
+    double pot[OR_FOCC_MAX * OR_MAXN * 2], g[OR_FOCC_MAX * OR_MAXN], f[OR_FOCC_MAX];
+} focc_ring;
+
+static void focc_push(focc_ring* r, const double* pot, const double* g, double f) {
+    if (r->H == 0) return;
+    memcpy(r->pot + (size_t)r->head * r->np, pot, sizeof(double) * r->np);
+    memcpy(r->g + (size_t)r->head * r->n_tan, g, sizeof(double) * r->n_tan);
+    r->f[r->head] = f;
+    r->head = (r->head + 1) % r->H;
+    if (r->n < r->H) r->n++;
+}
+
 /* One chain of Algorithm 2: start C_cur = C_best = random conformation; each step mutate,
  * optimise (RILC-BFGS), accept with p = min(1, exp((e_cur - e_new) / T)); an accepted candidate
  * that beats the best is refined by a second RILC-BFGS run and becomes both the current and the
- * best conformation. Outputs the chain's best POT and SF, and its evaluation count. */
+ * best conformation. With the first-order consistency check on (focc > 0), each mutated candidate
+ * is first evaluated with its gradient and checked (Eq. 4-5, or_focc_pass) against the chain's
+ * last `focc` current conformations (the start and every accepted or refined one, with SF and
+ * gradient); a candidate that fails skips the local search and enters the Metropolis test with
+ * its own SF. Outputs the chain's best POT and SF, and its evaluation count. */
 void or_mc_chain(const or_ligand* L, const or_grid* G, const double center[3], const double size[3],
                  const or_mc_params* mp, uint32_t unit, uint32_t chain, double* best_pot,
                  double* best_e, long* evals) {
-    int np = 7 + L->n_rot;
+    int np = 7 + L->n_rot, n_tan = 6 + L->n_rot;
     or_bfgs_params bp = mp->bfgs;
     if (bp.max_iter <= 0) bp.max_iter = (25 + L->n) / 3;
     double cur[OR_MAXN * 2], cand[OR_MAXN * 2], best[OR_MAXN * 2];
+    double g_cur[OR_MAXN], g_cand[OR_MAXN];
+    focc_ring nb;
+    nb.H = mp->focc < 0 ? 0 : (mp->focc > OR_FOCC_MAX ? OR_FOCC_MAX : mp->focc);
+    nb.n = 0; nb.head = 0; nb.np = np; nb.n_tan = n_tan;
     long ev = 0;
     or_random_conformation(L, center, size, mp->seed, unit, chain, cur);
-    double e_cur = or_score(L, G, cur, NULL, NULL);
+    double e_cur = or_score(L, G, cur, nb.H ? g_cur : NULL, NULL);
     ev++;
     memcpy(best, cur, sizeof(double) * np);
     double e_best = e_cur;
+    focc_push(&nb, cur, g_cur, e_cur);
     for (int st = 0; st < mp->steps; ++st) {
         or_mutate(L, cur, mp->amplitude, mp->seed, unit, chain, st, cand);
-        double e_new = or_bfgs_pose(L, G, &bp, cand, NULL, &ev);
+        double e_new;
+        int optimise = 1;
+        if (nb.H) {
+            e_new = or_score(L, G, cand, g_cand, NULL);
+            ev++;
+            optimise = or_focc_pass(L, cand, e_new, g_cand, nb.n, nb.pot, nb.f, nb.g, mp->focc_min_delta);
+        }
+        if (optimise) e_new = or_bfgs_pose(L, G, &bp, cand, g_cand, &ev);
         double u = or_metropolis_uniform(mp->seed, unit, chain, st);
         if (or_metropolis_accept(e_cur, e_new, mp->temperature, u)) {
             memcpy(cur, cand, sizeof(double) * np);
+            memcpy(g_cur, g_cand, sizeof(double) * n_tan);
             e_cur = e_new;
             if (e_cur < e_best) {
-                e_cur = or_bfgs_pose(L, G, &bp, cur, NULL, &ev);
+                e_cur = or_bfgs_pose(L, G, &bp, cur, g_cur, &ev);
                 memcpy(best, cur, sizeof(double) * np);
                 e_best = e_cur;
             }
+            focc_push(&nb, cur, g_cur, e_cur);
         }
     }
     memcpy(best_pot, best, sizeof(double) * np);
