@@ -152,7 +152,7 @@ def run_ours(args):
                          torch.tensor(rec.element, device="cuda"), torch.tensor(rec.donor, device="cuda"),
                          torch.tensor(rec.acceptor, device="cuda"))
     pockets = list(range(len(boxes)))
-    params = api.DockParams(chains=CHAINS, steps=STEPS, seed=rank, top_k=TOP_K, host_copy=False)
+    params = api.DockParams(chains=CHAINS, steps=STEPS, seed=rank, top_k=TOP_K, host_copy=False, focc=args.focc)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def step(mid=None):
@@ -186,6 +186,9 @@ def run_ours(args):
             search_s += s_s
             launches += n_l
             evals += ev
+    # search quality of the last timed step: per pocket, the best SF over its chains
+    _, chain_best = r.chain_records()
+    best_sf = chain_best.min(axis=1)
     step_t = np.array(times)
     if world > 1:
         t = torch.tensor(step_t, device="cuda", dtype=torch.float64)
@@ -217,7 +220,9 @@ def run_ours(args):
                        "intra_pairs": lig.n_pairs, "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "inputs": "receptor, ligand and boxes resident in HBM; grids rebuilt every step",
                        "parallelism": f"{world} independent receptors, one per GPU",
-                       "search_launch": {"variant": shape[0], "warps_per_cta": shape[1], "chains_per_warp": 2 if shape[0] >= 4 else 1}},
+                       "search_launch": {"variant": shape[0], "warps_per_cta": shape[1], "chains_per_warp": 2 if shape[0] >= 4 else 1},
+                       "focc": args.focc},
+            "best_sf_per_pocket": {"mean": round(float(best_sf.mean()), 4), "min": round(float(best_sf.min()), 4)},
             "evals_per_s": round(evals / total_t * world, 1),
             "breakdown": {"grid_maps_ms": round(float(np.mean(grid_t)) * 1e3, 3),
                           "dock_ms": round((total_t / args.steps - float(np.mean(grid_t))) * 1e3, 3),
@@ -511,6 +516,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", choices=["multipocket", "uneven", "screening"], default="multipocket",
                     help="multipocket: the headline line; uneven / screening: the batch shapes, their own line")
+    ap.add_argument("--focc", type=int, default=0,
+                    help="consistency check (Eq. 4-5) with this many neighbours per chain; 0 = off (headline)")
     ap.add_argument("--ligands-per-receptor", type=int, default=10, help="screening: ligands docked per receptor")
     ap.add_argument("--case", choices=["full", "small"], default="full",
                     help="small: one untimed small pass for profiler captures")

@@ -216,7 +216,7 @@ typedef struct {
     float amplitude;           /* mutation radius, A (translation; orientation amplitude/R_gyr) */
     int32_t steps_per_round;   /* batched: MC steps per kernel launch (round); 0 = automatic */
     int32_t use_graph;         /* batched: capture the launch sequence in a CUDA graph */
-    int32_t warps_per_cta;     /* batched: chains per CTA; 0 = autotuned */
+    int32_t warps_per_cta;     /* batched: warps per CTA; 0 = autotuned */
     int32_t search_variant;    /* batched: search kernel variant; 0..3 one chain per warp, 4..7
                                   one chain per half warp (ligands of <= 32 atoms and <= 10
                                   torsions); within each group decreasing register budgets and
@@ -226,11 +226,19 @@ typedef struct {
                                   else within the whole-warp group */
     int32_t host_copy;         /* 1: copy results to host memory before returning */
     double timeout_s;          /* watchdog per launch; 0 = none. Overrun -> PV_ERR_TIMEOUT */
+    int32_t focc;              /* batched: first-order consistency check (Eq. 4-5), 0..4: a mutated
+                                  candidate is evaluated and checked against the chain's last
+                                  `focc` current conformations (start, accepted, refined); a
+                                  candidate with no sign of a stationary point between it and
+                                  some neighbour along any differing coordinate skips the local
+                                  search. 0 = off (every mutation is optimised) */
+    float focc_min_delta;      /* tangent coordinates closer than this (A, rad) carry no sign */
 } pv_dock_params;
 
 /* Defaults: chains 64, steps 1000, seed 0, top_k 9, rmsd_min 1.0, BATCHED, m 5, max_iter 0,
  * max_trials 10, eps 1e-3, rho 1e-4, sigma 0.1, temperature 1.2, amplitude 2.0,
- * steps_per_round 0, use_graph 1, warps_per_cta 0, search_variant -1, host_copy 1, timeout_s 0.
+ * steps_per_round 0, use_graph 1, warps_per_cta 0, search_variant -1, host_copy 1, timeout_s 0,
+ * focc 0, focc_min_delta 1e-4.
  * Autotuning (warps_per_cta 0 or search_variant -1): the first batched dock of a ligand-size
  * bucket on a context times each candidate launch shape on eight MC steps of its own work items
  * (results are unaffected: the dock itself restarts every chain) and keeps the fastest. */

@@ -37,7 +37,7 @@ class pv_dock_params(C.Structure):
                 ("temperature", C.c_float), ("amplitude", C.c_float), ("steps_per_round", C.c_int32),
                 ("use_graph", C.c_int32), ("warps_per_cta", C.c_int32), ("search_variant", C.c_int32),
                 ("host_copy", C.c_int32),
-                ("timeout_s", C.c_double)]
+                ("timeout_s", C.c_double), ("focc", C.c_int32), ("focc_min_delta", C.c_float)]
 
 
 class pv_pose(C.Structure):

@@ -54,6 +54,8 @@ class DockParams:
     search_variant: int = -1
     host_copy: bool = True
     timeout_s: float = 0.0
+    focc: int = 0                  # first-order consistency check (Eq. 4-5): neighbours kept, 0 = off
+    focc_min_delta: float = 1e-4
 
     def to_c(self) -> A.pv_dock_params:
         p = A.pv_dock_params()

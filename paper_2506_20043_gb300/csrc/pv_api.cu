@@ -32,7 +32,8 @@ struct pv_context {
     int sms = 0;
     cudaStream_t capture_stream = nullptr;   // graphs are captured here (the caller's stream may
                                              // be the legacy default stream, which cannot capture)
-    // autotuned (search variant, warps per CTA) per (ligand atoms / 8 and team width, pair rounds / 4)
+    // autotuned (search variant, warps per CTA) per (ligand atoms / 8, check on/off and team width,
+    // pair rounds / 4)
     std::map<std::pair<int, int>, std::pair<int, int>> tuned;
 };
 
@@ -601,6 +602,8 @@ extern "C" void pv_dock_params_default(pv_dock_params* p) {
     p->use_graph = 1;
     p->warps_per_cta = 0;
     p->search_variant = -1;
+    p->focc = 0;
+    p->focc_min_delta = 1e-4f;
     p->host_copy = 1;
     p->timeout_s = 0.0;
 }
@@ -629,6 +632,10 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     if (p.bfgs_max_trials < 1 || p.bfgs_max_iter < 0) return fail(ctx, PV_ERR_ARG, "bad BFGS limits");
     if (p.mode != PV_MODE_BATCHED && p.mode != PV_MODE_PLAIN) return fail(ctx, PV_ERR_ARG, "unknown mode");
     if (p.warps_per_cta < 0 || p.warps_per_cta > 16) return fail(ctx, PV_ERR_ARG, "warps_per_cta must be 0..16");
+    if (p.focc < 0 || p.focc > PV_FOCC_MAX || !(p.focc_min_delta >= 0.f))
+        return fail(ctx, PV_ERR_ARG, "focc must be 0..4 and focc_min_delta >= 0");
+    if (p.focc > 0 && p.mode != PV_MODE_BATCHED)
+        return fail(ctx, PV_ERR_ARG, "the consistency check (focc) runs in batched mode only");
     if (p.search_variant < -1 || p.search_variant >= kSearchVariants)
         return fail(ctx, PV_ERR_ARG, "search_variant must be -1..7");
     if (p.search_variant >= 0 && p.warps_per_cta * 32 > search_variant_max_warps(p.search_variant) * 32)
@@ -703,7 +710,8 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     const bool autotune = p.mode == PV_MODE_BATCHED && (p.search_variant < 0 || p.warps_per_cta == 0);
     int max_rounds = 0;
     for (int i = 0; i < n_ligs; ++i) max_rounds = std::max(max_rounds, ligs[i]->rec.n_rounds);
-    const std::pair<int, int> tune_key{2 * ((max_atoms + 7) / 8) + (auto_lanes == 16 ? 1 : 0), (max_rounds + 3) / 4};
+    const std::pair<int, int> tune_key{4 * ((max_atoms + 7) / 8) + 2 * (p.focc > 0 ? 1 : 0) + (auto_lanes == 16 ? 1 : 0),
+                                       (max_rounds + 3) / 4};
     bool need_tune = false;
     if (autotune) {
         auto it = ctx->tuned.find(tune_key);
@@ -736,7 +744,8 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
                  o_xyz = Lw.take<float>((size_t)n_pairs * p.top_k * R->atom_stride * 3),
                  o_nkept = Lw.take<int>(n_pairs), o_status = Lw.take<int>(n_pairs),
                  o_rank = Lw.take<int>((size_t)n_ligs * R->rank_stride), o_lps = Lw.take<int>(n_ligs + 1),
-                 o_lp = Lw.take<int>(n_pairs);
+                 o_lp = Lw.take<int>(n_pairs),
+                 o_ring = Lw.take<float>(p.focc > 0 ? (size_t)n_pairs * p.chains * PV_RING_STRIDE : 0);
     const size_t small_end = o_items + std::max(items.size(), items_cap) * sizeof(PvItem);
     char* w = (char*)dalloc(ctx, Lw.off);
     if (!w) {
@@ -784,6 +793,8 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     C.temperature = p.temperature;
     C.amplitude = p.amplitude;
     C.rmsd_min = p.rmsd_min;
+    C.focc = p.focc;
+    C.focc_min_delta = p.focc_min_delta;
     C.pot_stride = R->pot_stride;
     C.atom_stride = R->atom_stride;
     SearchArgs A;
@@ -796,6 +807,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     A.slots_lo = pack_slots(set->slot, 0);
     A.slots_hi = pack_slots(set->slot, 1);
     A.chains = R->d_chains;
+    A.ring = p.focc > 0 ? (float*)(w + o_ring) : nullptr;
     A.C = C;
     A.lig_smem_bytes = max_blob;
     A.t0 = evals + 1;
@@ -842,7 +854,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
             if (lanes_c == 16 && !all_team16) continue;
             if (p.search_variant < 0 && lanes_c != auto_lanes) continue;
             int occ_c = 0;
-            if (search_max_ctas_per_sm(v, wc, search_smem_bytes(max_blob, wc, lanes_c), &occ_c) != cudaSuccess ||
+            if (search_max_ctas_per_sm(v, p.focc > 0, wc, search_smem_bytes(max_blob, wc, lanes_c), &occ_c) != cudaSuccess ||
                 occ_c < 1) {
                 cudaGetLastError();
                 continue;
@@ -901,7 +913,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     // grid of the persistent rounds: every SM filled to its occupancy
     int occ = 0;
     const int smem = search_smem_bytes(max_blob, W, search_variant_lanes(variant));
-    e = search_max_ctas_per_sm(variant, W, smem, &occ);
+    e = search_max_ctas_per_sm(variant, p.focc > 0, W, smem, &occ);
     if (e != cudaSuccess || occ < 1) {
         result_free(R);
         return e != cudaSuccess ? cuda_fail(ctx, e, "occupancy") : fail(ctx, PV_ERR_ARG, "search kernel does not fit");

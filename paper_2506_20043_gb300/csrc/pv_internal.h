@@ -58,6 +58,7 @@ struct SearchArgs {
     const PvPocket* pockets;
     uint64_t slots_lo, slots_hi;   // XS type -> map slot, 8 bits per type
     float* chains;                 // [n_pairs * chains][PV_CHAIN_STRIDE]
+    float* ring;                   // [n_pairs * chains][PV_RING_STRIDE] when C.focc > 0, else null
     PvSearchConst C;
     int step0, step1;
     int lig_smem_bytes;            // staging capacity for one ligand
@@ -73,7 +74,9 @@ int search_smem_bytes(int lig_bytes, int warps, int lanes);
 constexpr int kSearchVariants = 8;
 int search_variant_max_warps(int variant);
 int search_variant_lanes(int variant);
-cudaError_t search_max_ctas_per_sm(int variant, int warps, int smem, int* out);
+cudaError_t search_max_ctas_per_sm(int variant, bool focc, int warps, int smem, int* out);
+// The round kernel of a variant with the consistency check (Eq. 4-5) compiled in (pv_search_focc.cu).
+const void* search_focc_kernel(int variant);
 cudaError_t launch_search_round(const SearchArgs& a, int variant, int grid, int warps, cudaStream_t s);
 cudaError_t launch_plain_search(const SearchArgs& a, int pair, const PvLigBlob* lig_dev,
                                 cudaStream_t s);

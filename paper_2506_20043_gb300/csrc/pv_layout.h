@@ -69,7 +69,16 @@ struct PvSearchConst {
     float eps, rho, sigma, temperature;
     float amplitude, rmsd_min;
     int32_t pot_stride, atom_stride;
+    int32_t focc;                  // consistency check (Eq. 4-5): neighbours kept, 0 = off
+    float focc_min_delta;
 };
+
+// Neighbour ring of the consistency check, per chain in global memory (PV_RING_STRIDE floats):
+//   [0, 160)   POT of neighbour k at 40 k      [160, 288) tangent gradient of k at 160 + 32 k
+//   [288, 292) SF of k    [292] count (int bits)    [293] next slot (int bits)
+#define PV_FOCC_MAX 4
+#define PV_RING_STRIDE 296
+enum { PV_RING_POT = 0, PV_RING_G = 160, PV_RING_F = 288, PV_RING_N = 292, PV_RING_HEAD = 293 };
 
 // Chain record in global memory (PV_CHAIN_STRIDE floats):
 //   [0, 33)  current POT      [40, 73) best POT

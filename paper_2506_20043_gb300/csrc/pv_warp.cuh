@@ -385,6 +385,69 @@ __device__ __forceinline__ Pose load_pose(const float* src, int n_rot) {
     return x;
 }
 
+// ---- first-order consistency check (Eq. 4-5) ----
+// The lane's tangent coordinate p of x - nb (nb a POT in memory): translation difference, the
+// rotation vector w with q_x = exp(w / 2) (x) q_nb (shortest; both normalised), torsion difference
+// wrapped into [-pi, pi); 0 for lanes past the tangent coordinates.
+template <int LANES>
+__device__ __forceinline__ float tangent_delta(const Pose& x, const float* nb, int n_tan) {
+    const int tl = Team<LANES>::lane();
+    if (tl < 3) return (tl == 0 ? x.T.x : (tl == 1 ? x.T.y : x.T.z)) - nb[tl];
+    if (tl < 6) {
+        const float4 a = quat_normalize(x.q);
+        const float4 b = quat_normalize(make_float4(nb[3], -nb[4], -nb[5], -nb[6]));   // conjugate
+        float4 r = quat_mul(a, b);
+        if (r.x < 0.f) r = make_float4(-r.x, -r.y, -r.z, -r.w);
+        const float vn = sqrtf(r.y * r.y + r.z * r.z + r.w * r.w);
+        const float scale = vn > 1e-7f ? 2.f * atan2f(vn, r.x) / vn : 2.f;
+        return scale * (tl == 3 ? r.y : (tl == 4 ? r.z : r.w));
+    }
+    if (tl < n_tan) {
+        const float d = x.psi - nb[tl + 1];
+        return d - 2.f * PV_PI * floorf((d + PV_PI) / (2.f * PV_PI));
+    }
+    return 0.f;
+}
+
+__device__ __forceinline__ int sgnf(float v) { return (v > 0.f) - (v < 0.f); }
+
+// Whether candidate x (SF f, lane gradient g) passes the check against the n neighbours of a
+// chain's ring: every neighbour must show, along some tangent coordinate where the two differ by
+// more than min_delta, a derivative sign change (Eq. 4) or a secant slope whose sign disagrees with
+// the derivative at x (Eq. 5). Team-uniform result.
+template <int LANES>
+__device__ __forceinline__ bool focc_pass(const Pose& x, float f, float g, const float* ring, int n, int n_rot,
+                                          float min_delta) {
+    using Tm = Team<LANES>;
+    const int tl = Tm::lane(), n_tan = 6 + n_rot;
+    for (int j = 0; j < n; ++j) {
+        const float* nb = ring + PV_RING_POT + 40 * j;
+        const float dl = tangent_delta<LANES>(x, nb, n_tan);
+        bool ev = false;
+        if (tl < n_tan && fabsf(dl) > min_delta) {
+            const int gi = sgnf(g), gj = sgnf(ring[PV_RING_G + 32 * j + tl]);
+            ev = gi * gj <= 0 || gi * sgnf((f - ring[PV_RING_F + j]) * dl) <= 0;
+        }
+        if (!__any_sync(Tm::mask(), ev)) return false;
+    }
+    return true;
+}
+
+// Appends (x, f, g) to the chain's ring of the last `cap` current conformations.
+template <int LANES>
+__device__ __forceinline__ void focc_push(float* ring, const Pose& x, float f, float g, int n_rot, int cap,
+                                          int& n, int& head) {
+    using Tm = Team<LANES>;
+    const int tl = Tm::lane();
+    Tm::sync();
+    store_pose<LANES>(ring + PV_RING_POT + 40 * head, x, n_rot);
+    if (tl < 6 + n_rot) ring[PV_RING_G + 32 * head + tl] = g;
+    if (tl == 0) ring[PV_RING_F + head] = f;
+    head = head + 1 == cap ? 0 : head + 1;
+    n = min(n + 1, cap);
+    Tm::sync();
+}
+
 // Whole-warp names used by the selection and scoring kernels.
 static __device__ __forceinline__ float warp_eval(const PvLigBlob& L, WarpScratch& S, const Site& site,
                                                   const Pose& x, float& grad, bool want_grad,

@@ -217,3 +217,57 @@ def test_dock_argument_errors(tiny):
     big = ctx.ligand(G.ligand32(S.ligand_centered(S.make_ligand(40, 4, 3))))
     with pytest.raises(PVError):
         ctx.dock(gs, [big], [0], steps=1, search_variant=5, warps_per_cta=4)
+
+
+# ---------------------------------------------------------------- consistency check (Eq. 4-5) --
+HALF = dict(search_variant=4, warps_per_cta=4)
+
+
+@pytest.mark.parametrize("form", [dict(), HALF], ids=["warp", "half-warp"])
+def test_focc_first_mc_steps_in_lockstep(tiny, form):
+    """With the consistency check on (4 neighbours), three MC steps of a 1-iteration / 1-trial BFGS
+    agree with the oracle's chains run with the same switch (the check's decisions included)."""
+    ctx, box, gs, pl, L, og, rec = tiny
+    p = O.SearchParams(seed=3, steps=3, max_iter=1, max_trials=1, focc=4)
+    ref_pots, ref_es, _ = O.mc_chains(L, og, box, p, unit=0, n_chains=64, threads=G.threads())
+    r = ctx.dock(gs, [pl], [0], chains=64, steps=3, seed=3, bfgs_max_iter=1, bfgs_max_trials=1, focc=4, **form)
+    pots, es = r.chain_records()
+    agree = G.close(es[0], ref_es, abs_tol=1e-3, rel_tol=1e-4)
+    assert agree.mean() >= 0.95, agree.mean()
+    same = np.abs(pots[0, :, :L.n_pot] - ref_pots).max(axis=1) <= 1e-3
+    assert same.mean() >= 0.95, same.mean()
+
+
+@pytest.mark.parametrize("form", [dict(), HALF], ids=["warp", "half-warp"])
+def test_focc_results_valid_deterministic_and_cheaper(tiny, form):
+    ctx, box, gs, pl, L, og, rec = tiny
+    base = ctx.dock(gs, [pl], [0], chains=32, steps=40, seed=8, focc=4, **form)
+    pots, es = base.chain_records()
+    G.check_pose_scores(L, og, pots[0, :, :L.n_pot], es[0], G.pose_coords(ctx, pl, pots[0, :, :L.n_pot]),
+                        (rec, O.xs_type_receptor(rec), box))
+    # the neighbour rings survive round boundaries and graph replay: the same bits
+    for kw in (dict(steps_per_round=7), dict(use_graph=False, steps_per_round=13)):
+        r = ctx.dock(gs, [pl], [0], chains=32, steps=40, seed=8, focc=4, **form, **kw)
+        np.testing.assert_array_equal(r.chain_records()[1], es, err_msg=str(kw))
+        np.testing.assert_array_equal(r.chain_records()[0], pots, err_msg=str(kw))
+    off = ctx.dock(gs, [pl], [0], chains=32, steps=40, seed=8, **form)
+    assert base.stats()[0] < off.stats()[0]          # fewer evaluations with the check on
+
+
+def test_focc_tiny_workload_best_score_parity(tiny):
+    """With the check on, the GPU's best SF over 64 chains x 1,000 steps is within 0.2 kcal/mol of
+    the oracle's with the same switch."""
+    ctx, box, gs, pl, L, og, rec = tiny
+    p = O.SearchParams(seed=0, steps=1000, focc=4)
+    _, ref_es, _ = O.mc_chains(L, og, box, p, unit=0, n_chains=64, threads=G.threads())
+    r = ctx.dock(gs, [pl], [0], chains=64, steps=1000, seed=0, focc=4)
+    _, es = r.chain_records()
+    assert abs(es[0].min() - ref_es.min()) <= 0.2, (es[0].min(), ref_es.min())
+
+
+def test_focc_argument_errors(tiny):
+    ctx, box, gs, pl, L, og, rec = tiny
+    from paper_2506_20043_gb300.api import PVError
+    for kw in (dict(focc=5), dict(focc=-1), dict(focc=2, focc_min_delta=-1.0), dict(focc=2, mode="plain")):
+        with pytest.raises(PVError):
+            ctx.dock(gs, [pl], [0], steps=1, **kw)
