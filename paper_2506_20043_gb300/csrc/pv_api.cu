@@ -731,8 +731,11 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
         pdesc[q] = PvPairDesc{pair_lig[q], pair_pocket[q], ligs[pair_lig[q]]->rec.n_rounds, 0};
     std::vector<const void*> ligptr(n_ligs);
     for (int i = 0; i < n_ligs; ++i) ligptr[i] = ligs[i]->d_blob;
-    const int S_r = p.steps_per_round > 0 ? p.steps_per_round : std::max(1, std::min(p.steps, 500));
+    // one launch (round) covers all MC steps unless steps_per_round asks for more; a launch's steps
+    // are cut into chained step blocks of about 1/16 of them (at least 25)
+    const int S_r = p.steps_per_round > 0 ? p.steps_per_round : std::max(1, p.steps);
     const int n_rounds = p.steps > 0 ? (p.steps + S_r - 1) / S_r : 1;
+    const int block_steps = std::max(25, (S_r + 15) / 16);
     // one workspace allocation
     Layout Lw;
     const size_t o_pairs = Lw.take<PvPairDesc>(n_pairs), o_ligs = Lw.take<const void*>(n_ligs),
@@ -744,7 +747,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
                  o_xyz = Lw.take<float>((size_t)n_pairs * p.top_k * R->atom_stride * 3),
                  o_nkept = Lw.take<int>(n_pairs), o_status = Lw.take<int>(n_pairs),
                  o_rank = Lw.take<int>((size_t)n_ligs * R->rank_stride), o_lps = Lw.take<int>(n_ligs + 1),
-                 o_lp = Lw.take<int>(n_pairs),
+                 o_lp = Lw.take<int>(n_pairs), o_prog = Lw.take<int>(std::max(items.size(), items_cap)),
                  o_ring = Lw.take<float>(p.focc > 0 ? (size_t)n_pairs * p.chains * PV_RING_STRIDE : 0);
     const size_t small_end = o_items + std::max(items.size(), items_cap) * sizeof(PvItem);
     char* w = (char*)dalloc(ctx, Lw.off);
@@ -808,6 +811,9 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     A.slots_hi = pack_slots(set->slot, 1);
     A.chains = R->d_chains;
     A.ring = p.focc > 0 ? (float*)(w + o_ring) : nullptr;
+    A.items_per_block = (int)items.size();
+    A.block_steps = block_steps;
+    A.progress = (int*)(w + o_prog);
     A.C = C;
     A.lig_smem_bytes = max_blob;
     A.t0 = evals + 1;
@@ -867,6 +873,8 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
             a.queue = ctr + 1;
             a.step0 = 0;
             a.step1 = std::min(p.steps, 8);
+            a.items_per_block = n_trial;         // one step block of 8 steps
+            a.block_steps = 8;
             cudaError_t x = cudaMemcpyAsync((char*)R->d_work + o_items, trial.data(), sizeof(PvItem) * n_trial,
                                             cudaMemcpyHostToDevice, ctx->stream);
             if (x == cudaSuccess) x = cudaMemsetAsync(ctr, 0, sizeof(int) * 2, ctx->stream);
@@ -909,7 +917,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
             return cuda_fail(ctx, e, "item upload");
         }
     }
-    A.n_items = (int)items.size();
+    A.items_per_block = (int)items.size();
     // grid of the persistent rounds: every SM filled to its occupancy
     int occ = 0;
     const int smem = search_smem_bytes(max_blob, W, search_variant_lanes(variant));
@@ -918,6 +926,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
         result_free(R);
         return e != cudaSuccess ? cuda_fail(ctx, e, "occupancy") : fail(ctx, PV_ERR_ARG, "search kernel does not fit");
     }
+    // at most one step block of each work item can run at a time
     const int grid = std::max(1, std::min((int)items.size(), ctx->sms * occ));
     R->search_variant = variant;
     R->warps_per_cta = W;
@@ -948,7 +957,10 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
                 a.queue = ctr + 2 + r;
                 a.step0 = r * S_r;
                 a.step1 = std::min(p.steps, (r + 1) * S_r);
-                x = launch_search_round(a, variant, grid, W, s);
+                const int n_blocks = a.step1 > a.step0 ? (a.step1 - a.step0 + block_steps - 1) / block_steps : 1;
+                a.n_items = n_blocks * a.items_per_block;
+                x = cudaMemsetAsync(a.progress, 0, sizeof(int) * (size_t)a.items_per_block, s);
+                if (x == cudaSuccess) x = launch_search_round(a, variant, grid, W, s);
             }
             if (x == cudaSuccess) x = cudaEventRecordWithFlags(evs1, s, ev_flags);
             if (x == cudaSuccess) x = launch_topk(T, n_pairs, s);
@@ -1039,6 +1051,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     *out = R;
     if (err_bits & PV_EBIT_TIMEOUT) return fail(ctx, PV_ERR_TIMEOUT, "search exceeded timeout_s");
     if (err_bits & PV_EBIT_NAN) return fail(ctx, PV_ERR_NAN, "non-finite energy in a chain");
+    if (err_bits & PV_EBIT_WAIT) return fail(ctx, PV_ERR_STATE, "a step block waited 30 s for its predecessor");
     return PV_OK;
 }
 

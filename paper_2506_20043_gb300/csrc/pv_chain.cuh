@@ -17,7 +17,8 @@ namespace pv {
 // chain (have == false) only take part in the loop's warp vote.
 template <int LANES, bool FOCC>
 __device__ __forceinline__ void run_chain(const SearchArgs& A, const PvLigBlob& L, WarpScratch& S, const Site& site,
-                                          int pair, int chain, bool have, uint32_t& evals_out, int& flags_out) {
+                                          int pair, int chain, bool have, int step0, int step1, uint32_t& evals_out,
+                                          int& flags_out) {
     using Tm = Team<LANES>;
     const int tl = Tm::lane();
     const PvSearchConst& C = A.C;
@@ -30,8 +31,8 @@ __device__ __forceinline__ void run_chain(const SearchArgs& A, const PvLigBlob& 
     float* Hs = &S.hs[0][0];
     float* Hy = &S.hy[0][0];
     enum { kStart = 0, kOptimise = 1, kRefine = 2, kDone = 3 };
-    int stage = !have ? kDone : (A.step0 == 0 ? kStart : kOptimise);
-    int s = A.step0, flags = 0;
+    int stage = !have ? kDone : (step0 == 0 ? kStart : kOptimise);
+    int s = step0, flags = 0;
     uint32_t evals = 0, evals_before = 0;
     float e_cur = 0.f, e_best = 0.f, u = 0.f;
     // local-search state
@@ -44,16 +45,16 @@ __device__ __forceinline__ void run_chain(const SearchArgs& A, const PvLigBlob& 
         xt = random_pose<LANES>(L, *site.P, (uint32_t)chain, (uint32_t)pair, C);
         iters = 0;
     } else if (stage == kOptimise) {
-        for (int i = tl; i < 7 + n_rot; i += LANES) curs[i] = rec[PV_CH_CUR + i];
-        e_cur = rec[PV_CH_ECUR];
-        e_best = rec[PV_CH_EBEST];
-        evals_before = __float_as_uint(rec[PV_CH_EVALS]);
+        for (int i = tl; i < 7 + n_rot; i += LANES) curs[i] = __ldcg(rec + PV_CH_CUR + i);
+        e_cur = __ldcg(rec + PV_CH_ECUR);
+        e_best = __ldcg(rec + PV_CH_EBEST);
+        evals_before = __float_as_uint(__ldcg(rec + PV_CH_EVALS));
         if (FOCC) {
-            nb_n = __float_as_int(ring[PV_RING_N]);
-            nb_head = __float_as_int(ring[PV_RING_HEAD]);
+            nb_n = __float_as_int(__ldcg(ring + PV_RING_N));
+            nb_head = __float_as_int(__ldcg(ring + PV_RING_HEAD));
         }
         Tm::sync();
-        if (s < A.step1) {
+        if (s < step1) {
             xt = load_pose<LANES>(curs, n_rot);
             u = mutate<LANES>(L, xt, (uint32_t)chain, (uint32_t)pair, s, C);
             iters = max_iter;
@@ -183,7 +184,7 @@ __device__ __forceinline__ void run_chain(const SearchArgs& A, const PvLigBlob& 
                 continue;
             }
         }
-        if (s < A.step1) {                                      // the next MC step
+        if (s < step1) {                                        // the next MC step
             xt = load_pose<LANES>(curs, n_rot);
             u = mutate<LANES>(L, xt, (uint32_t)chain, (uint32_t)pair, s, C);
             bstart = true;
@@ -204,7 +205,7 @@ __device__ __forceinline__ void run_chain(const SearchArgs& A, const PvLigBlob& 
             rec[PV_CH_ECUR] = e_cur;
             rec[PV_CH_EBEST] = e_best;
             rec[PV_CH_EVALS] = __uint_as_float(evals_before + evals);
-            const int old = A.step0 == 0 ? 0 : __float_as_int(rec[PV_CH_FLAGS]);
+            const int old = step0 == 0 ? 0 : __float_as_int(__ldcg(rec + PV_CH_FLAGS));
             rec[PV_CH_FLAGS] = __int_as_float(old | flags);
         }
     }
@@ -294,8 +295,8 @@ __device__ __forceinline__ float warp_local_search(const PvLigBlob& L, WarpScrat
 // loop (no other team shares the warp, so nothing needs to stay converged across chains).
 template <bool FOCC>
 __device__ __forceinline__ void run_chain_warp(const SearchArgs& A, const PvLigBlob& L, WarpScratch& S,
-                                               const Site& site, int pair, int chain, uint32_t& evals_out,
-                                               int& flags_out) {
+                                               const Site& site, int pair, int chain, int step0, int step1,
+                                               uint32_t& evals_out, int& flags_out) {
     using Tm = Team<32>;
     const int tl = Tm::lane();
     const PvSearchConst& C = A.C;
@@ -307,21 +308,21 @@ __device__ __forceinline__ void run_chain_warp(const SearchArgs& A, const PvLigB
     float e_cur = 0.f, e_best = 0.f, u = 0.f, g_new = 0.f;
     uint32_t evals = 0, evals_before = 0;
     int nb_n = 0, nb_head = 0;
-    if (A.step0 != 0) {
-        for (int i = tl; i < 7 + n_rot; i += 32) curs[i] = rec[PV_CH_CUR + i];
-        e_cur = rec[PV_CH_ECUR];
-        e_best = rec[PV_CH_EBEST];
-        evals_before = __float_as_uint(rec[PV_CH_EVALS]);
+    if (step0 != 0) {
+        for (int i = tl; i < 7 + n_rot; i += 32) curs[i] = __ldcg(rec + PV_CH_CUR + i);
+        e_cur = __ldcg(rec + PV_CH_ECUR);
+        e_best = __ldcg(rec + PV_CH_EBEST);
+        evals_before = __float_as_uint(__ldcg(rec + PV_CH_EVALS));
         if (FOCC) {
-            nb_n = __float_as_int(ring[PV_RING_N]);
-            nb_head = __float_as_int(ring[PV_RING_HEAD]);
+            nb_n = __float_as_int(__ldcg(ring + PV_RING_N));
+            nb_head = __float_as_int(__ldcg(ring + PV_RING_HEAD));
         }
     }
     Tm::sync();
-    int flags = 0, s = A.step0, stage = A.step0 == 0 ? 0 : 1;   // 0 start, 1 MC step, 2 refine
+    int flags = 0, s = step0, stage = step0 == 0 ? 0 : 1;       // 0 start, 1 MC step, 2 refine
     Pose cand;
     if (stage == 0) cand = random_pose<32>(L, *site.P, (uint32_t)chain, (uint32_t)pair, C);
-    while (stage == 0 || s < A.step1) {
+    while (stage == 0 || s < step1) {
         if (stage == 1) {
             cand = load_pose<32>(curs, n_rot);
             u = mutate<32>(L, cand, (uint32_t)chain, (uint32_t)pair, s, C);
@@ -380,16 +381,44 @@ __device__ __forceinline__ void run_chain_warp(const SearchArgs& A, const PvLigB
         rec[PV_CH_ECUR] = e_cur;
         rec[PV_CH_EBEST] = e_best;
         rec[PV_CH_EVALS] = __uint_as_float(evals_before + evals);
-        const int old = A.step0 == 0 ? 0 : __float_as_int(rec[PV_CH_FLAGS]);
+        const int old = step0 == 0 ? 0 : __float_as_int(__ldcg(rec + PV_CH_FLAGS));
         rec[PV_CH_FLAGS] = __int_as_float(old | flags);
     }
     evals_out = evals;
     flags_out = flags;
 }
 
-// One round of MC steps [step0, step1) for every chain of every pair (batched form). Compiled
-// for several (threads per CTA, minimum CTAs per SM) bounds, i.e. register budgets, and team
-// widths (a chain per warp, or per half warp); the runtime picks one (search variant).
+__device__ __forceinline__ int load_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void store_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Waits until the chain block's previous step block is published (`*progress >= blk`). Every CTA
+// of the launch is resident and a block is taken from the queue only after all blocks before it,
+// by CTAs that are running, so the wait ends; it is still bounded (30 s), after which the block
+// runs anyway and the launch reports PV_EBIT_WAIT.
+__device__ __forceinline__ bool wait_block(const int* progress, int blk) {
+    if (load_acquire(progress) >= blk) return true;
+    const unsigned long long t0 = globaltimer();
+    unsigned ns = 64;
+    while (load_acquire(progress) < blk) {
+        if (globaltimer() - t0 > 30000000000ull) return false;
+        __nanosleep(ns);
+        if (ns < 4096) ns <<= 1;
+    }
+    return true;
+}
+
+// One launch of the batched search: MC steps [step0, step1) of every chain of every pair, cut into
+// step blocks of block_steps; the queue hands out all work items (a pair's chain block) of block
+// 0, then of block 1, and so on, so no SM idles at a block boundary while the chains of the last
+// wave finish (the blocks of one chain block run in order through `progress`). Compiled for
+// several (threads per CTA, minimum CTAs per SM) bounds, i.e. register budgets, and team widths (a
+// chain per warp, or per half warp); the runtime picks one (search variant).
 template <int THREADS, int MIN_CTAS, int LANES, bool FOCC>
 __global__ void __launch_bounds__(THREADS, MIN_CTAS) search_round_kernel(SearchArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -407,7 +436,11 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) search_round_kernel(SearchA
         __syncthreads();
         const int it = s_item;
         if (it >= A.n_items) break;
-        const PvItem item = A.items[it];
+        // item `it` = step block `blk` of the work item `j` (a pair's chain block); the blocks of one
+        // chain block run in order, the first waiting, if need be, for its predecessor
+        const int blk = it / A.items_per_block, j = it - blk * A.items_per_block;
+        const int step0 = A.step0 + blk * A.block_steps, step1 = min(A.step1, step0 + A.block_steps);
+        const PvItem item = A.items[j];
         const PvPairDesc pd = A.pairs[item.pair];
         const bool reload = pd.ligand != s_lig;
         if (threadIdx.x < (int)(sizeof(PvPocket) / 4))
@@ -418,6 +451,7 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) search_round_kernel(SearchA
             stage_ligand(&L, A.ligs[pd.ligand], A.slots_lo, A.slots_hi);
             if (threadIdx.x == 0) s_lig = pd.ligand;
         }
+        if (blk > 0 && threadIdx.x == 0 && !wait_block(A.progress + j, blk)) atomicOr(A.err, PV_EBIT_WAIT);
         __syncthreads();
         const int chain = item.chain0 + team;
         Site site;
@@ -426,9 +460,11 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) search_round_kernel(SearchA
         uint32_t evals = 0;
         int flags = 0;
         if constexpr (LANES == 32) {
-            if (chain < A.C.chains) run_chain_warp<FOCC>(A, L, scratch[team], site, item.pair, chain, evals, flags);
+            if (chain < A.C.chains)
+                run_chain_warp<FOCC>(A, L, scratch[team], site, item.pair, chain, step0, step1, evals, flags);
         } else {
-            run_chain<LANES, FOCC>(A, L, scratch[team], site, item.pair, chain, chain < A.C.chains, evals, flags);
+            run_chain<LANES, FOCC>(A, L, scratch[team], site, item.pair, chain, chain < A.C.chains, step0, step1,
+                                   evals, flags);
         }
         if (Team<LANES>::lane() == 0 && evals) {
             atomicAdd(A.evals, (unsigned long long)evals);
@@ -436,6 +472,12 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) search_round_kernel(SearchA
         }
         __syncwarp();
         (void)lane;
+        // the chain records of this block are written: publish it to the next block's item
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            store_release(A.progress + j, blk + 1);
+        }
     }
 }
 

@@ -60,7 +60,10 @@ struct SearchArgs {
     float* chains;                 // [n_pairs * chains][PV_CHAIN_STRIDE]
     float* ring;                   // [n_pairs * chains][PV_RING_STRIDE] when C.focc > 0, else null
     PvSearchConst C;
-    int step0, step1;
+    int step0, step1;              // the launch's MC steps
+    int items_per_block;           // batched: work items of one step block (the items array)
+    int block_steps;               // batched: MC steps per block; block b covers step0 + b * block_steps ..
+    int* progress;                 // batched: [items_per_block] step blocks finished per work item
     int lig_smem_bytes;            // staging capacity for one ligand
     const unsigned long long* t0;  // start time of the dock (globaltimer)
     unsigned long long timeout_ns; // 0 = none

@@ -101,7 +101,7 @@ struct PvPairDesc {
 };
 
 // Device-side error bits
-enum { PV_EBIT_TIMEOUT = 1, PV_EBIT_NAN = 2, PV_EBIT_ARG = 4 };
+enum { PV_EBIT_TIMEOUT = 1, PV_EBIT_NAN = 2, PV_EBIT_ARG = 4, PV_EBIT_WAIT = 8 };
 
 // Output record of a kept pose (matches pv_pose in the public header).
 struct PvPoseRec {

@@ -392,10 +392,11 @@ __device__ __forceinline__ Pose load_pose(const float* src, int n_rot) {
 template <int LANES>
 __device__ __forceinline__ float tangent_delta(const Pose& x, const float* nb, int n_tan) {
     const int tl = Team<LANES>::lane();
-    if (tl < 3) return (tl == 0 ? x.T.x : (tl == 1 ? x.T.y : x.T.z)) - nb[tl];
+    if (tl < 3) return (tl == 0 ? x.T.x : (tl == 1 ? x.T.y : x.T.z)) - __ldcg(nb + tl);
     if (tl < 6) {
         const float4 a = quat_normalize(x.q);
-        const float4 b = quat_normalize(make_float4(nb[3], -nb[4], -nb[5], -nb[6]));   // conjugate
+        const float4 b = quat_normalize(make_float4(__ldcg(nb + 3), -__ldcg(nb + 4), -__ldcg(nb + 5),
+                                                    -__ldcg(nb + 6)));                 // conjugate
         float4 r = quat_mul(a, b);
         if (r.x < 0.f) r = make_float4(-r.x, -r.y, -r.z, -r.w);
         const float vn = sqrtf(r.y * r.y + r.z * r.z + r.w * r.w);
@@ -403,7 +404,7 @@ __device__ __forceinline__ float tangent_delta(const Pose& x, const float* nb, i
         return scale * (tl == 3 ? r.y : (tl == 4 ? r.z : r.w));
     }
     if (tl < n_tan) {
-        const float d = x.psi - nb[tl + 1];
+        const float d = x.psi - __ldcg(nb + tl + 1);
         return d - 2.f * PV_PI * floorf((d + PV_PI) / (2.f * PV_PI));
     }
     return 0.f;
@@ -412,7 +413,7 @@ __device__ __forceinline__ float tangent_delta(const Pose& x, const float* nb, i
 __device__ __forceinline__ int sgnf(float v) { return (v > 0.f) - (v < 0.f); }
 
 // Whether candidate x (SF f, lane gradient g) passes the check against the n neighbours of a
-// chain's ring: every neighbour must show, along some tangent coordinate where the two differ by
+// chain's ring (read past L1: another SM may have written it in the previous step block): every neighbour must show, along some tangent coordinate where the two differ by
 // more than min_delta, a derivative sign change (Eq. 4) or a secant slope whose sign disagrees with
 // the derivative at x (Eq. 5). Team-uniform result.
 template <int LANES>
@@ -425,8 +426,8 @@ __device__ __forceinline__ bool focc_pass(const Pose& x, float f, float g, const
         const float dl = tangent_delta<LANES>(x, nb, n_tan);
         bool ev = false;
         if (tl < n_tan && fabsf(dl) > min_delta) {
-            const int gi = sgnf(g), gj = sgnf(ring[PV_RING_G + 32 * j + tl]);
-            ev = gi * gj <= 0 || gi * sgnf((f - ring[PV_RING_F + j]) * dl) <= 0;
+            const int gi = sgnf(g), gj = sgnf(__ldcg(ring + PV_RING_G + 32 * j + tl));
+            ev = gi * gj <= 0 || gi * sgnf((f - __ldcg(ring + PV_RING_F + j)) * dl) <= 0;
         }
         if (!__any_sync(Tm::mask(), ev)) return false;
     }
