@@ -245,6 +245,7 @@ def run_ours(args):
             out["batched_vs_plain"] = round(value / world / out["plain"]["value"], 2)
         if not args.no_micro:
             out["score_microbench"] = run_score_microbench(ctx, api, torch)
+        out["rescoring"] = run_rescore_check(ctx, gs, lig, pockets, params)
         out["e2e"] = run_e2e(ctx, api, torch, rec, boxes, lig_src, types, pockets, args.steps, rank)
         if world == 1 and not args.no_cpu:
             out["cpu_baseline"] = run_cpu_baseline(rec, boxes, lig_src, budget_s=args.cpu_budget)
@@ -267,6 +268,20 @@ def run_plain_sample(ctx, api, gs, lig, pockets, sample_steps=20):
     return {"value": round(1.0 / per_pair, 5), "unit": UNIT, "evals_per_s": round(ev / s_s, 1),
             "sample": f"1 pocket x {CHAINS} chains x {sample_steps} MC steps, time x {STEPS // sample_steps}",
             "batched_same_sample_evals_per_s": round(evb / tb, 1)}
+
+
+def run_rescore_check(ctx, gs, lig, pockets, params):
+    """One untimed dock of the workload with rescoring of the kept poses by direct summation over
+    the receptor: the grid's interpolation error on the final poses (e_inter grid vs direct)."""
+    import dataclasses
+    r = ctx.dock(gs, [lig], pockets, dataclasses.replace(params, rescore=True, host_copy=True))
+    err = []
+    for q in range(r.n_pairs):
+        n = int(r.n_kept[q])
+        err.extend(np.abs(r.poses[q]["e_inter"][:n] - r.poses[q]["e_inter_grid"][:n]).tolist())
+    err = np.array(err)
+    return {"kept_poses": int(len(err)), "mean_abs_e_inter_grid_error": round(float(err.mean()), 5),
+            "max_abs_e_inter_grid_error": round(float(err.max()), 5), "unit": "kcal/mol"}
 
 
 def run_score_microbench(ctx, api, torch, reps=20):

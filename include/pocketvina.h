@@ -233,12 +233,17 @@ typedef struct {
                                   some neighbour along any differing coordinate skips the local
                                   search. 0 = off (every mutation is optimised) */
     float focc_min_delta;      /* tangent coordinates closer than this (A, rad) carry no sign */
+    int32_t rescore;           /* 1: rescore the kept poses (Algorithm 2, "rescoring") with e_inter
+                                  summed directly over the receptor's atoms (8 A cutoff, no grid,
+                                  no box penalty), then sort each pair's poses and the per-ligand
+                                  ranking by that SF; the grid values stay in score_grid and
+                                  e_inter_grid */
 } pv_dock_params;
 
 /* Defaults: chains 64, steps 1000, seed 0, top_k 9, rmsd_min 1.0, BATCHED, m 5, max_iter 0,
  * max_trials 10, eps 1e-3, rho 1e-4, sigma 0.1, temperature 1.2, amplitude 2.0,
  * steps_per_round 0, use_graph 1, warps_per_cta 0, search_variant -1, host_copy 1, timeout_s 0,
- * focc 0, focc_min_delta 1e-4.
+ * focc 0, focc_min_delta 1e-4, rescore 0.
  * Autotuning (warps_per_cta 0 or search_variant -1): the first batched dock of a ligand-size
  * bucket on a context times each candidate launch shape on eight MC steps of its own work items
  * (results are unaffected: the dock itself restarts every chain) and keeps the fastest. */
@@ -263,7 +268,8 @@ pv_status pv_dock_pairs(pv_context* ctx, const pv_grid_set* set, pv_ligand* cons
                         int32_t n_pairs, const pv_dock_params* params, pv_dock_result** out);
 
 typedef struct {
-    float score;               /* SF = e_inter + e_intra, the search objective */
+    float score;               /* SF = e_inter + e_intra: the search objective (grid e_inter), or
+                                  with rescore the directly summed e_inter */
     float e_inter;
     float e_intra;
     float affinity;            /* e_inter / (1 + 0.0585 N_rot), Vina's reported form */
@@ -271,6 +277,9 @@ typedef struct {
     int32_t ligand;
     int32_t pocket;            /* pocket id in the grid set */
     int32_t chain;
+    float score_grid;          /* SF and e_inter from the grid maps (equal to score and e_inter */
+    float e_inter_grid;        /* without rescore) */
+    int32_t pad[2];
 } pv_pose;
 
 /* Sizes: pairs, top_k, POT stride (7 + max n_rot), coordinate stride (max n_atoms). */

@@ -125,6 +125,8 @@ def lib():
             L.or_tangent_delta.argtypes = [C.c_int, dp, dp, dp]
             L.or_focc_pass.restype = C.c_int
             L.or_focc_pass.argtypes = [vp, dp, C.c_double, dp, C.c_int, dp, dp, dp, C.c_double]
+            L.or_direct_inter.restype = C.c_double
+            L.or_direct_inter.argtypes = [vp, C.c_int, dp, ip, dp]
             L.or_topk.restype = C.c_int
             L.or_topk.argtypes = [C.c_int, dp, dp, C.c_int, C.c_int, C.c_double, ip]
             L.or_affinity.restype = C.c_double
@@ -324,6 +326,12 @@ class OracleLigand:
         g = np.zeros_like(xyz)
         e = lib().or_score_atoms(self.ptr, C.byref(grid.struct), _p(xyz), _p(g))
         return e, g
+
+    def direct_inter(self, rec, rec_types, xyz) -> float:
+        """e_inter of posed atoms (input order) summed directly over the receptor (no grid)."""
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        return lib().or_direct_inter(self.ptr, rec.n, _p(np.ascontiguousarray(rec.xyz, np.float64)),
+                                     _p(np.ascontiguousarray(rec_types, np.int32), C.c_int32), _p(xyz))
 
     def retract(self, pot, step) -> np.ndarray:
         pot = np.ascontiguousarray(pot, dtype=np.float64)

@@ -999,6 +999,21 @@ void or_mc_chains(const or_ligand* L, const or_grid* G, const double center[3], 
     (void)n_threads;
 }
 
+/* ------------------------------------------------- rescoring of selected poses (Alg. 2) --- */
+/* e_inter of a posed ligand (atom coordinates in input order) summed directly over the receptor
+ * atoms: sum_i sum_j E(type_i, type_j, |x_i - x_j|) with the 8 A cutoff; no grid, no box. */
+double or_direct_inter(const or_ligand* L, int n_rec, const double* rec_xyz, const int32_t* rec_types,
+                       const double* lig_xyz) {
+    double e = 0.0;
+    for (int i = 0; i < L->n; ++i)
+        for (int j = 0; j < n_rec; ++j) {
+            double d[3];
+            v_sub(lig_xyz + 3 * i, rec_xyz + 3 * j, d);
+            e += or_pair_energy(L->xs[i], rec_types[j], v_norm(d), NULL);
+        }
+    return e;
+}
+
 /* ------------------------------------------------------- top-k selection (Algorithm 2) --- */
 /* Sort candidates by SF ascending (ties: lower index first), keep a candidate if its RMSD to
  * every kept one (fixed atom correspondence) is >= rmsd_min, stop at k. Returns the count. */

@@ -37,13 +37,15 @@ class pv_dock_params(C.Structure):
                 ("temperature", C.c_float), ("amplitude", C.c_float), ("steps_per_round", C.c_int32),
                 ("use_graph", C.c_int32), ("warps_per_cta", C.c_int32), ("search_variant", C.c_int32),
                 ("host_copy", C.c_int32),
-                ("timeout_s", C.c_double), ("focc", C.c_int32), ("focc_min_delta", C.c_float)]
+                ("timeout_s", C.c_double), ("focc", C.c_int32), ("focc_min_delta", C.c_float),
+                ("rescore", C.c_int32)]
 
 
 class pv_pose(C.Structure):
     _fields_ = [("score", C.c_float), ("e_inter", C.c_float), ("e_intra", C.c_float),
                 ("affinity", C.c_float), ("pair", C.c_int32), ("ligand", C.c_int32),
-                ("pocket", C.c_int32), ("chain", C.c_int32)]
+                ("pocket", C.c_int32), ("chain", C.c_int32), ("score_grid", C.c_float),
+                ("e_inter_grid", C.c_float), ("pad", C.c_int32 * 2)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)

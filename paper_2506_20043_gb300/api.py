@@ -56,6 +56,7 @@ class DockParams:
     timeout_s: float = 0.0
     focc: int = 0                  # first-order consistency check (Eq. 4-5): neighbours kept, 0 = off
     focc_min_delta: float = 1e-4
+    rescore: bool = False          # rescore kept poses by direct receptor summation (no grid)
 
     def to_c(self) -> A.pv_dock_params:
         p = A.pv_dock_params()
@@ -349,10 +350,11 @@ class DockResult:
                 self.h, poses, kept.ctypes.data_as(C.POINTER(C.c_int32)),
                 pots.ctypes.data_as(C.POINTER(C.c_float)), xyz.ctypes.data_as(C.POINTER(C.c_float))),
                 "pv_dock_result_poses")
-            rec = np.array([(p.score, p.e_inter, p.e_intra, p.affinity, p.pair, p.ligand, p.pocket, p.chain)
-                            for p in poses], dtype=[("score", "f4"), ("e_inter", "f4"), ("e_intra", "f4"),
-                                                    ("affinity", "f4"), ("pair", "i4"), ("ligand", "i4"),
-                                                    ("pocket", "i4"), ("chain", "i4")])
+            rec = np.array([(p.score, p.e_inter, p.e_intra, p.affinity, p.pair, p.ligand, p.pocket, p.chain,
+                             p.score_grid, p.e_inter_grid) for p in poses],
+                           dtype=[("score", "f4"), ("e_inter", "f4"), ("e_intra", "f4"), ("affinity", "f4"),
+                                  ("pair", "i4"), ("ligand", "i4"), ("pocket", "i4"), ("chain", "i4"),
+                                  ("score_grid", "f4"), ("e_inter_grid", "f4")])
             self._host = (rec.reshape(self.n_pairs, self.top_k), kept, pots, xyz)
         return self._host
 

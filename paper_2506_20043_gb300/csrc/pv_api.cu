@@ -256,15 +256,20 @@ static pv_status add_receptor(pv_context* ctx, pv_grid_set* set, const pv_recept
         const int tx = (pk[p].dims[0] + 7) / 8, ty = (pk[p].dims[1] + 7) / 8, tz = (pk[p].dims[2] + 7) / 8;
         for (int t = 0; t < tx * ty * tz; ++t) tiles.push_back(make_int2(first + p, t));
     }
-    // maps arena
+    // maps arena, and the typed receptor kept for direct rescoring of poses
     float* arena = (float*)dalloc(ctx, map_floats * sizeof(float));
     if (!arena) return fail(ctx, PV_ERR_OOM, "map allocation failed");
     set->arenas.push_back(arena);
     set->bytes += (int64_t)(map_floats * sizeof(float));
+    float4* typed = (float4*)dalloc(ctx, sizeof(float4) * (size_t)n);
+    if (!typed) return fail(ctx, PV_ERR_OOM, "receptor allocation failed");
+    set->arenas.push_back(typed);
     size_t off = 0;
     for (int p = 0; p < n_pockets; ++p) {
         pk[p].maps = arena + off;
         off += (size_t)pk[p].nxyz * set->n_maps;
+        pk[p].rec_atoms = typed;
+        pk[p].rec_n = n;
     }
     // pocket table (all pockets of the set)
     set->pockets.insert(set->pockets.end(), pk.begin(), pk.end());
@@ -275,7 +280,7 @@ static pv_status add_receptor(pv_context* ctx, pv_grid_set* set, const pv_recept
     // scratch
     Layout L;
     const size_t o_xyz = L.take<float>(3 * (size_t)n), o_el = L.take<uint8_t>(n), o_don = L.take<uint8_t>(n),
-                 o_acc = L.take<uint8_t>(n), o_typed = L.take<float4>(n), o_sorted = L.take<float4>(n),
+                 o_acc = L.take<uint8_t>(n), o_sorted = L.take<float4>(n),
                  o_cof = L.take<int>(n), o_rank = L.take<int>(n), o_cnt = L.take<int>(n_cells),
                  o_start = L.take<int>(n_cells + 1), o_tiles = L.take<int2>(tiles.size());
     char* w = (char*)dalloc(ctx, L.off);
@@ -300,11 +305,11 @@ static pv_status add_receptor(pv_context* ctx, pv_grid_set* set, const pv_recept
     }
     if (e == cudaSuccess) {
         stage = "receptor typing";
-        e = launch_receptor_type(xyz, el, don, acc, n, (float4*)(w + o_typed), ctx->stream);
+        e = launch_receptor_type(xyz, el, don, acc, n, typed, ctx->stream);
     }
     if (e == cudaSuccess) {
         stage = "receptor binning";
-        e = launch_receptor_bin((const float4*)(w + o_typed), n, flo, kCellEdge, cd, (int*)(w + o_cof),
+        e = launch_receptor_bin(typed, n, flo, kCellEdge, cd, (int*)(w + o_cof),
                                 (int*)(w + o_rank), (int*)(w + o_cnt), (int*)(w + o_start),
                                 (float4*)(w + o_sorted), ctx->stream);
     }
@@ -604,6 +609,7 @@ extern "C" void pv_dock_params_default(pv_dock_params* p) {
     p->search_variant = -1;
     p->focc = 0;
     p->focc_min_delta = 1e-4f;
+    p->rescore = 0;
     p->host_copy = 1;
     p->timeout_s = 0.0;
 }
@@ -798,6 +804,8 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     C.rmsd_min = p.rmsd_min;
     C.focc = p.focc;
     C.focc_min_delta = p.focc_min_delta;
+    C.rescore = p.rescore ? 1 : 0;
+    C.pad = 0;
     C.pot_stride = R->pot_stride;
     C.atom_stride = R->atom_stride;
     SearchArgs A;

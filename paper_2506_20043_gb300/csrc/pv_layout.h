@@ -54,6 +54,9 @@ struct PvPocket {
     float* maps;                // this pocket's maps, slot-major, each [z][y][x]
     int32_t nxy, nxyz;
     int32_t pad[2];
+    const float4* rec_atoms;    // the pocket's receptor: xyz and XS type (int bits), for rescoring
+    int32_t rec_n;
+    int32_t pad2;
 };
 
 // XS type -> map slot of a grid set (-1: no map)
@@ -71,6 +74,8 @@ struct PvSearchConst {
     int32_t pot_stride, atom_stride;
     int32_t focc;                  // consistency check (Eq. 4-5): neighbours kept, 0 = off
     float focc_min_delta;
+    int32_t rescore;               // rescore kept poses by direct receptor summation
+    int32_t pad;
 };
 
 // Neighbour ring of the consistency check, per chain in global memory (PV_RING_STRIDE floats):
@@ -107,4 +112,6 @@ enum { PV_EBIT_TIMEOUT = 1, PV_EBIT_NAN = 2, PV_EBIT_ARG = 4, PV_EBIT_WAIT = 8 }
 struct PvPoseRec {
     float score, e_inter, e_intra, affinity;
     int32_t pair, ligand, pocket, chain;
+    float score_grid, e_inter_grid;
+    int32_t pad[2];
 };

@@ -145,6 +145,37 @@ __device__ void bitonic_sort(unsigned long long* keys, int n) {
     }
 }
 
+// e_inter of the pose in S.x summed directly over the pocket's receptor atoms within the 8 A
+// cutoff (no grid, no box): the whole warp, lanes over ligand atoms, receptor atoms broadcast.
+__device__ float direct_inter(const PvLigBlob& L, const WarpScratch& S, const PvPocket& P) {
+    const int lane = threadIdx.x & 31, n = L.h.n_atoms;
+    float4 xi[2];
+    int ti[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int a = lane + 32 * h;
+        xi[h] = a < n ? S.x[a] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+        ti[h] = a < n ? ((__float_as_int(L.atom[a].w) >> 8) & 255) : 0;
+    }
+    float e = 0.f;
+    for (int j = 0; j < P.rec_n; ++j) {
+        const float4 r = __ldg(P.rec_atoms + j);
+        const int tj = __float_as_int(r.w);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float dx = xi[h].x - r.x, dy = xi[h].y - r.y, dz = xi[h].z - r.z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < kCutoff2) {
+                const bool hyd = xs_hydrophobic(ti[h]) && xs_hydrophobic(tj);
+                const bool hb = (xs_donor(ti[h]) && xs_acceptor(tj)) || (xs_acceptor(ti[h]) && xs_donor(tj));
+                float c;
+                e += vina_pair_r2(r2, xi[h].w + xs_radius(tj), hyd ? 1.f : 0.f, hb ? 1.f : 0.f, c);
+            }
+        }
+    }
+    return warp_sum(e);
+}
+
 __global__ void __launch_bounds__(kTopkThreads) topk_kernel(TopkArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const PvSearchConst& C = A.C;
@@ -215,27 +246,68 @@ __global__ void __launch_bounds__(kTopkThreads) topk_kernel(TopkArgs A) {
     }
     __syncthreads();
     const int kept = s_nkept;
-    // rescoring of the kept poses, one warp each: e_inter, e_intra, affinity
+    // the kept poses' SF parts from the grid, one warp each; with C.rescore also e_inter summed
+    // directly over the receptor's atoms (Algorithm 2's rescoring of the selected poses)
+    __shared__ float s_e[kMaxTopK], s_ei[kMaxTopK], s_ej[kMaxTopK], s_ed[kMaxTopK];
+    __shared__ int s_order[kMaxTopK];
+    Site site;
+    site.maps = s_pocket.maps;
+    site.P = &s_pocket;
     for (int slot = warp; slot < kept; slot += W) {
         const int ch = s_kept[slot];
-        const float* best = chains + (size_t)ch * PV_CHAIN_STRIDE + PV_CH_BEST;
-        Pose x = load_pose<32>(best, n_rot);
-        Site site;
-        site.maps = s_pocket.maps;
-        site.P = &s_pocket;
+        Pose x = load_pose<32>(chains + (size_t)ch * PV_CHAIN_STRIDE + PV_CH_BEST, n_rot);
         float g, parts[2];
-        float e = warp_eval(L, scratch[warp], site, x, g, false, parts);
-        const size_t o = (size_t)pair * C.top_k + slot;
+        const float e = warp_eval(L, scratch[warp], site, x, g, false, parts);
+        const float ed = C.rescore ? direct_inter(L, scratch[warp], s_pocket) : 0.f;
+        if (lane == 0) {
+            s_e[slot] = e;
+            s_ei[slot] = parts[0];
+            s_ej[slot] = parts[1];
+            s_ed[slot] = ed;
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // output order: the selection's order, or sorted by the rescored SF (ties: chain id); the kept
+    // poses are pairwise at least rmsd_min apart, so the RMSD filter keeps all of them in any order
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kept; ++i) {
+            int j = i;
+            if (C.rescore) {
+                const float si = s_ej[i] + s_ed[i];
+                while (j > 0) {
+                    const int o = s_order[j - 1];
+                    const float so = s_ej[o] + s_ed[o];
+                    if (so < si || (so == si && s_kept[o] < s_kept[i])) break;
+                    s_order[j] = o;
+                    --j;
+                }
+            }
+            s_order[j] = i;
+        }
+    }
+    __syncthreads();
+    for (int out = warp; out < kept; out += W) {
+        const int src = s_order[out], ch = s_kept[src];
+        const float* best = chains + (size_t)ch * PV_CHAIN_STRIDE + PV_CH_BEST;
+        const Pose x = load_pose<32>(best, n_rot);
+        float3 axw, xa;
+        warp_fk(L, scratch[warp], x, axw, xa);
+        __syncwarp();
+        const size_t o = (size_t)pair * C.top_k + out;
         if (lane == 0) {
             PvPoseRec r;
-            r.score = e;
-            r.e_inter = parts[0];
-            r.e_intra = parts[1];
-            r.affinity = parts[0] / (1.f + kWRot * (float)n_rot);
+            r.e_inter = C.rescore ? s_ed[src] : s_ei[src];
+            r.e_intra = s_ej[src];
+            r.score = C.rescore ? s_ed[src] + s_ej[src] : s_e[src];
+            r.affinity = r.e_inter / (1.f + kWRot * (float)n_rot);
             r.pair = pair;
             r.ligand = pd.ligand;
             r.pocket = pd.pocket;
             r.chain = ch;
+            r.score_grid = s_e[src];
+            r.e_inter_grid = s_ei[src];
+            r.pad[0] = r.pad[1] = 0;
             A.poses[o] = r;
         }
         for (int i = lane; i < 7 + n_rot; i += 32) A.pots[o * C.pot_stride + i] = best[i];
@@ -250,6 +322,7 @@ __global__ void __launch_bounds__(kTopkThreads) topk_kernel(TopkArgs A) {
         PvPoseRec r;
         r.score = 0.f; r.e_inter = 0.f; r.e_intra = 0.f; r.affinity = 0.f;
         r.pair = -1; r.ligand = -1; r.pocket = -1; r.chain = -1;
+        r.score_grid = 0.f; r.e_inter_grid = 0.f; r.pad[0] = r.pad[1] = 0;
         A.poses[(size_t)pair * C.top_k + slot] = r;
     }
     if (threadIdx.x == 0) {

@@ -119,3 +119,40 @@ def node_cutoff_slack(L, xyz, rec, rec_types, box):
                     for j in np.nonzero(np.abs(r - CUTOFF) < CUTOFF_EDGE)[0]:
                         total += w * abs(O.pair_energy(int(L.xs[a]), int(rec_types[j]), CUTOFF - 1e-9)[0])
     return total
+
+
+def direct_cutoff_slack(L, xyz, rec, rec_types):
+    """Cutoff jumps of the (ligand atom, receptor atom) pairs within CUTOFF_EDGE of 8 A, for
+    directly summed e_inter."""
+    rxyz = np.asarray(rec.xyz, np.float64)
+    total = 0.0
+    for a in range(L.n):
+        r = np.linalg.norm(rxyz - xyz[a], axis=1)
+        for j in np.nonzero(np.abs(r - CUTOFF) < CUTOFF_EDGE)[0]:
+            total += abs(O.pair_energy(int(L.xs[a]), int(rec_types[j]), CUTOFF - 1e-9)[0])
+    return total
+
+
+def check_rescored(r, q, L, rec, rec_types, base=None):
+    """Pair q of a result docked with rescore: e_inter equals the oracle's direct sum at the
+    reported coordinates, score = e_inter + e_intra, affinity from it, poses sorted by score; the
+    grid values equal those of the same dock without rescoring (base), chain by chain."""
+    n = int(r.n_kept[q])
+    poses = r.poses[q]
+    for slot in range(n):
+        p = poses[slot]
+        xyz = r.xyz[q, slot, :L.n].astype(np.float64)
+        ref = L.direct_inter(rec, rec_types, xyz)
+        d = abs(float(p["e_inter"]) - ref)
+        assert close(p["e_inter"], ref) or d <= direct_cutoff_slack(L, xyz, rec, rec_types) + ABS_TOL, (q, slot, d)
+        assert float(p["score"]) == pytest.approx(float(p["e_inter"]) + float(p["e_intra"]), abs=2e-6)
+        assert close(p["affinity"], O.affinity(ref, L.n_rot))
+    sc = poses["score"][:n]
+    assert (np.diff(sc) >= 0).all()
+    if base is not None:
+        assert int(base.n_kept[q]) == n
+        by_chain = {int(b["chain"]): b for b in base.poses[q][:n]}
+        assert set(by_chain) == {int(c) for c in poses["chain"][:n]}
+        for p in poses[:n]:
+            b = by_chain[int(p["chain"])]
+            assert p["score_grid"] == b["score"] and p["e_inter_grid"] == b["e_inter"]

@@ -176,3 +176,8 @@ def test_appended_receptors_and_pair_list():
     for li in range(len(ligs)):
         pk = {int(flat[i]["pocket"]) for i in r.ranking(li)}
         assert pk <= {pair_pocket[q] for q in range(18) if pair_lig[q] == li}
+    # rescoring uses each pocket's own receptor
+    rr = ctx.dock_pairs(gs, pls, pair_lig, pair_pocket, chains=chains, steps=20, seed=2, top_k=4, rescore=True)
+    for q in range(18):
+        rec = recs[pair_box[q] // 3]
+        G.check_rescored(rr, q, Ls[pair_lig[q]], rec, O.xs_type_receptor(rec), r)

@@ -271,3 +271,22 @@ def test_focc_argument_errors(tiny):
     for kw in (dict(focc=5), dict(focc=-1), dict(focc=2, focc_min_delta=-1.0), dict(focc=2, mode="plain")):
         with pytest.raises(PVError):
             ctx.dock(gs, [pl], [0], steps=1, **kw)
+
+
+def test_rescoring_by_direct_summation(tiny):
+    """Algorithm 2's rescoring of the selected poses: e_inter summed over the receptor's atoms
+    (no grid), poses re-sorted by it, grid values kept alongside."""
+    ctx, box, gs, pl, L, og, rec = tiny
+    base = ctx.dock(gs, [pl], [0], chains=48, steps=60, seed=11, top_k=9)
+    r = ctx.dock(gs, [pl], [0], chains=48, steps=60, seed=11, top_k=9, rescore=True)
+    G.check_rescored(r, 0, L, rec, O.xs_type_receptor(rec), base)
+    # without rescoring the grid and reported values coincide
+    assert (base.poses[0]["score_grid"] == base.poses[0]["score"]).all()
+    # the merged ranking follows the rescored SF
+    flat = r.poses.reshape(-1)
+    sc = [float(flat[i]["score"]) for i in r.ranking(0)]
+    assert sc == sorted(sc)
+    # the grid's interpolation error on final poses is small next to the SF
+    n = r.n_kept[0]
+    err = np.abs(r.poses[0]["e_inter"][:n] - r.poses[0]["e_inter_grid"][:n])
+    assert err.max() < 0.5, err
