@@ -414,7 +414,14 @@ def run_batch_workload(args):
     from paper_2506_20043_gb300 import api
     ctx = api.Context(0)
     t_gen = time.perf_counter()
-    if args.workload == "uneven":
+    if args.workload == "boxsweep":
+        w = S.box_sweep(seed=0)
+        recs, boxes = w.receptors, w.boxes
+        pair_lig = [0] * len(boxes[0])
+        pair_pocket = list(range(len(boxes[0])))
+        desc = ("box sweep: 5,000-atom receptor, its 5 top-ranked pockets each in boxes of 15-30 A by 1 A "
+                "(80 boxes, 0.375 A), one ligand of 30 atoms / 6 torsions, 256 chains x 1,000 MC steps, top-9")
+    elif args.workload == "uneven":
         w = S.uneven(seed=0)
         recs, boxes = w.receptors, w.boxes
         pair_lig = [li for li in range(len(w.ligands)) for _ in range(len(boxes[0]))]
@@ -471,6 +478,11 @@ def run_batch_workload(args):
             map_bytes = gs.bytes
     total_t = float(np.sum(times))
     n_pairs = len(pair_lig)
+    extra = {}
+    if args.workload == "boxsweep":
+        _, es = r.chain_records()
+        best = es.min(axis=1).reshape(-1, 16)            # [pocket, size]
+        extra["best_sf_by_box_size"] = {f"{15 + k} A": round(float(best[:, k].mean()), 3) for k in range(16)}
     # roofline of the search kernel: the pair-weighted mean cost of the batch's ligands
     costs = [l.cost() for l in ligs]
     w_flops = float(np.mean([costs[li][0] for li in pair_lig]))
@@ -492,7 +504,7 @@ def run_batch_workload(args):
             "roofline": {"kernel": "search_round_kernel", "bound": "alu", "achieved": round(achieved, 3),
                          "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
                          "flops_per_eval": round(w_flops, 1)},
-            "clocks": clocks}
+            "clocks": clocks, **extra}
 
 
 def run_small_case(args):
@@ -529,8 +541,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-micro", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", choices=["multipocket", "uneven", "screening"], default="multipocket",
-                    help="multipocket: the headline line; uneven / screening: the batch shapes, their own line")
+    ap.add_argument("--workload", choices=["multipocket", "uneven", "screening", "boxsweep"], default="multipocket",
+                    help="multipocket: the headline line; uneven / screening / boxsweep: other shapes, their own line")
     ap.add_argument("--focc", type=int, default=0,
                     help="consistency check (Eq. 4-5) with this many neighbours per chain; 0 = off (headline)")
     ap.add_argument("--ligands-per-receptor", type=int, default=10, help="screening: ligands docked per receptor")

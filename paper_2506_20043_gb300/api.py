@@ -232,6 +232,14 @@ class Context:
         st = self.lib.pv_dock(self.h, grids.h, hs, len(ligands), pk, len(pocket_ids), C.byref(cp), C.byref(h))
         return self._result(st, h, len(ligands), "pv_dock")
 
+    def dock_top_pockets(self, grids: "GridSet", ligands: Sequence["Ligand"], ranked_pocket_ids: Sequence[int],
+                         max_pockets: int = 5, params: Optional[DockParams] = None, **kw) -> "DockResult":
+        """Docks into the best-ranked pockets only (pocket ids ordered by the pocket predictor's
+        score, best first): the first max_pockets of them, as the paper suggests five suffice."""
+        if max_pockets < 1:
+            raise PVError("max_pockets must be >= 1")
+        return self.dock(grids, ligands, list(ranked_pocket_ids)[:max_pockets], params, **kw)
+
     def dock_pairs(self, grids: "GridSet", ligands: Sequence["Ligand"], pair_ligand: Sequence[int],
                    pair_pocket: Sequence[int], params: Optional[DockParams] = None, **kw) -> "DockResult":
         p = dataclasses.replace(params or DockParams(), **kw)

@@ -324,3 +324,15 @@ def screening(seed: int = 0, n_receptors: int = 256, ligands_per_receptor: int =
         subsets.append(ids)
     return Workload("screening", recs, boxes, ligs, chains=chains, steps=steps, top_k=9, seed=seed,
                     ligands_per_receptor=subsets)
+
+
+def box_sweep(seed: int = 0, sizes: Sequence[float] = tuple(range(15, 31)), n_pockets: int = 5,
+              chains: int = 256, steps: int = 1000) -> Workload:
+    """5,000-atom receptor with ``n_pockets`` pockets (radius 6-10 A, listed in rank order), each
+    docked in boxes of every edge in ``sizes`` (15-30 A by 1 A by default) centred on the pocket;
+    one 30-atom / 6-torsion ligand. Boxes are pocket-major: box i = pocket i // len(sizes), size
+    sizes[i % len(sizes)]."""
+    rec, centres = _carved(5000, n_pockets, (6.0, 10.0), seed, 24.0)
+    boxes = [Box(np.array(b.center), np.array([float(s)] * 3)) for b in centres for s in sizes]
+    lig = ligand_centered(make_ligand(30, 6, seed))
+    return Workload("box_sweep", [rec], [boxes], [lig], chains=chains, steps=steps, top_k=9, seed=seed)

@@ -181,3 +181,31 @@ def test_appended_receptors_and_pair_list():
     for q in range(18):
         rec = recs[pair_box[q] // 3]
         G.check_rescored(rr, q, Ls[pair_lig[q]], rec, O.xs_type_receptor(rec), r)
+
+
+def test_mixed_box_sizes_in_one_launch():
+    """Boxes of 15, 21.5 and 30 A around two pocket centres (41, 59 and 81 nodes per axis) in one
+    grid set and one launch (the box-size sweep): chain bests valid against the oracle, the
+    selection and the per-ligand merge equal to the oracle's."""
+    ctx = G.context()
+    rec0, centres = S._carved(3000, 2, (6.5, 7.5), 41, 14.0)
+    rec = G.receptor32(rec0)
+    boxes = [G.box32(S.Box(np.array(c.center), np.array([s] * 3))) for c in centres for s in (15.0, 21.5, 30.0)]
+    ligs = [G.ligand32(S.ligand_centered(S.make_ligand(22, 5, 71)))]
+    Ls = [O.OracleLigand(l) for l in ligs]
+    gs = ctx.build_grids(rec, boxes, list(range(11)))
+    assert [int(gs.geometry(p, 0)[0][0]) for p in range(6)] == [41, 59, 81, 41, 59, 81]
+    pls = [ctx.ligand(l) for l in ligs]
+    r = ctx.dock(gs, pls, list(range(6)), chains=12, steps=25, seed=3, top_k=4)
+    _, _, st = r.stats()
+    assert (st == 0).all()
+    pair_lig, pair_box = [0] * 6, list(range(6))
+    coords = _coords(ctx, r, pls, Ls, pair_lig)
+    ogs = _lazy_grids(lambda b: rec, boxes, coords, pair_box)
+    sites = [(rec, O.xs_type_receptor(rec), b) for b in boxes]
+    _check_pairs(r, Ls, ogs, coords, pair_lig, pair_box, sites)
+    results = [O.PairResult(0, q, None, None, 0, r.poses[q]["chain"][:r.n_kept[q]],
+                            r.poses[q]["score"][:r.n_kept[q]].astype(np.float64), None, None, None) for q in range(6)]
+    flat = r.poses.reshape(-1)
+    got = [(int(flat[i]["pocket"]), int(flat[i]["chain"])) for i in r.ranking(0)]
+    assert got == [(m[1], m[2]) for m in O.merge_pockets(results)]
