@@ -220,27 +220,31 @@ __device__ __forceinline__ void run_chain(const SearchArgs& A, const PvLigBlob& 
 template <bool FOCC>
 __device__ __forceinline__ float warp_local_search(const PvLigBlob& L, WarpScratch& S, const Site& site, Pose& x,
                                                    const PvSearchConst& C, int max_iter, uint32_t& evals,
-                                                   float& g_out, const float* ring, int n_nb) {
+                                                   float& g_out, const float* ring) {
     using Tm = Team<32>;
     const int tl = Tm::lane();
     const int n_tan = 6 + L.h.n_rot, m = C.bfgs_m;
     float* Hs = &S.hs[0][0];
     float* Hy = &S.hy[0][0];
-    float rh = 0.f, al = 0.f;
-    int stored = 0, head = 0, it = 0, tr = 0;
-    float f = 0.f, g = 0.f, d = 0.f, gd = 0.f, lam = 1.f, lo = 0.f, hi = -1.f, flo = 0.f, glo = 0.f;
-    bool have_lo = false, start = true;
+    // The line search's uniform scalars live in S.cs between evaluations: each iteration loads them
+    // after the evaluation's team barrier and stores them back before the next evaluation, so no
+    // lane reads a slot another lane has already rewritten in the same iteration.
+    ChainScalars& Q = S.cs;
+    float rh = 0.f, al = 0.f, g = 0.f, d = 0.f;
+    bool start = true;
     Pose xt = x;
     for (;;) {
         float ge;
         const float fe = team_eval<32>(L, S, site, xt, ge, true);
         ++evals;
-        bool next_iter = false;
+        float f = Q.f, gd = Q.gd, lam = Q.lam, lo = Q.lo, hi = Q.hi, flo = Q.flo;
+        int it = Q.it, tr = Q.tr, stored = Q.stored, head = Q.head, have_lo = Q.have_lo;
+        bool next_iter = false, stop = false, retry = false;
         if (start) {
             start = false;
-            f = fe; g = ge;
-            if (FOCC && ring && !focc_pass<32>(x, f, g, ring, n_nb, L.h.n_rot, C.focc_min_delta)) break;
-            next_iter = true;
+            f = fe; g = ge; it = 0; stored = 0; head = 0;
+            if (FOCC && ring && !focc_pass<32>(x, fe, g, ring, Q.nb_n, L.h.n_rot, C.focc_min_delta)) stop = true;
+            else next_iter = true;
         } else {
             const float gtd = Tm::sum(ge * d);
             bool take = false;
@@ -248,7 +252,8 @@ __device__ __forceinline__ float warp_local_search(const PvLigBlob& L, WarpScrat
             if (!(fe <= f + lam * C.rho * gd)) {
                 hi = lam;                                       // Eq. 7 holds: Armijo fails
             } else if (gtd < C.sigma * gd) {
-                lo = lam; have_lo = true; flo = fe; glo = ge;   // Eq. 8 holds: Wolfe fails
+                lo = lam; have_lo = 1; flo = fe;                // Eq. 8 holds: Wolfe fails
+                S.glo[tl] = ge;
             } else {
                 take = true;
             }
@@ -257,42 +262,56 @@ __device__ __forceinline__ float warp_local_search(const PvLigBlob& L, WarpScrat
                 if (tr < C.bfgs_max_trials) {
                     lam = hi < 0.f ? 2.f * lam : 0.5f * (lo + hi);
                     xt = team_retract<32>(x, lam * d, n_tan);
-                    continue;
+                    retry = true;
+                } else if (!have_lo) {
+                    stop = true;                                // no acceptable step: stop at x
+                } else {
+                    lam = lo; ft = flo; gt = S.glo[tl];
+                    xt = team_retract<32>(x, lam * d, n_tan);   // the same arithmetic as that trial
+                    take = true;
                 }
-                if (!have_lo) break;                            // no acceptable step: stop at x
-                lam = lo; ft = flo; gt = glo;
-                xt = team_retract<32>(x, lam * d, n_tan);       // the same arithmetic as that trial
             }
-            const float sv = lam * d, yv = gt - g;
-            const float ys = Tm::sum(yv * sv), ss = Tm::sum(sv * sv), gn = sqrtf(Tm::sum(g * g));
-            if (ss > 0.f && ys / ss > C.eps * gn) {
-                Hs[head * 32 + tl] = sv;
-                Hy[head * 32 + tl] = yv;
-                if (tl == head) rh = 1.f / ys;
-                head = head + 1 == m ? 0 : head + 1;
-                stored = min(stored + 1, m);
+            if (take) {
+                const float sv = lam * d, yv = gt - g;
+                const float ys = Tm::sum(yv * sv), ss = Tm::sum(sv * sv), gn = sqrtf(Tm::sum(g * g));
+                if (ss > 0.f && ys / ss > C.eps * gn) {
+                    Hs[head * 32 + tl] = sv;
+                    Hy[head * 32 + tl] = yv;
+                    if (tl == head) rh = 1.f / ys;
+                    head = head + 1 == m ? 0 : head + 1;
+                    stored = min(stored + 1, m);
+                }
+                x = xt; g = gt; f = ft;
+                ++it;
+                if (sqrtf(Tm::sum(g * g)) <= C.eps) stop = true;
+                else next_iter = true;
             }
-            x = xt; g = gt; f = ft;
-            ++it;
-            if (sqrtf(Tm::sum(g * g)) <= C.eps) break;
-            next_iter = true;
         }
         if (next_iter) {
-            if (it >= max_iter) break;
-            d = lbfgs_direction<32>(Hs, Hy, rh, al, g, stored, head, m);
-            gd = Tm::sum(g * d);
-            if (!(gd < 0.f)) break;
-            lam = 1.f; lo = 0.f; hi = -1.f; have_lo = false; tr = 0;
-            xt = team_retract<32>(x, lam * d, n_tan);
+            if (it >= max_iter) {
+                stop = true;
+            } else {
+                d = lbfgs_direction<32>(Hs, Hy, rh, al, g, stored, head, m);
+                gd = Tm::sum(g * d);
+                if (!(gd < 0.f)) {
+                    stop = true;
+                } else {
+                    lam = 1.f; lo = 0.f; hi = -1.f; have_lo = 0; tr = 0;
+                    xt = team_retract<32>(x, lam * d, n_tan);
+                }
+            }
         }
+        if (stop) {
+            Tm::sync();
+            g_out = g;
+            return f;
+        }
+        (void)retry;
+        Tm::sync();                       // every lane has read this iteration's scalars
+        Q.f = f; Q.gd = gd; Q.lam = lam; Q.lo = lo; Q.hi = hi; Q.flo = flo;
+        Q.it = it; Q.tr = tr; Q.stored = stored; Q.head = head; Q.have_lo = have_lo;
     }
-    Tm::sync();
-    g_out = g;
-    return f;
 }
-
-// The whole-warp chain runner: the same steps as run_chain with the local search as an inner
-// loop (no other team shares the warp, so nothing needs to stay converged across chains).
 template <bool FOCC>
 __device__ __forceinline__ void run_chain_warp(const SearchArgs& A, const PvLigBlob& L, WarpScratch& S,
                                                const Site& site, int pair, int chain, int step0, int step1,
@@ -305,30 +324,47 @@ __device__ __forceinline__ void run_chain_warp(const SearchArgs& A, const PvLigB
     float* rec = A.chains + ((size_t)pair * C.chains + chain) * PV_CHAIN_STRIDE;
     float* ring = FOCC ? A.ring + ((size_t)pair * C.chains + chain) * PV_RING_STRIDE : nullptr;
     float* curs = S.cur;
-    float e_cur = 0.f, e_best = 0.f, u = 0.f, g_new = 0.f;
-    uint32_t evals = 0, evals_before = 0;
-    int nb_n = 0, nb_head = 0;
-    if (step0 != 0) {
-        for (int i = tl; i < 7 + n_rot; i += 32) curs[i] = __ldcg(rec + PV_CH_CUR + i);
-        e_cur = __ldcg(rec + PV_CH_ECUR);
-        e_best = __ldcg(rec + PV_CH_EBEST);
-        evals_before = __float_as_uint(__ldcg(rec + PV_CH_EVALS));
-        if (FOCC) {
-            nb_n = __float_as_int(__ldcg(ring + PV_RING_N));
-            nb_head = __float_as_int(__ldcg(ring + PV_RING_HEAD));
+    // The MC step's uniform scalars live in S.cs across the local search (whose evaluations end
+    // with team barriers): loaded after it returns, stored back before the next one.
+    ChainScalars& Q = S.cs;
+    uint32_t evals = 0;
+    float g_new = 0.f;
+    {
+        float e_cur = 0.f, e_best = 0.f;
+        uint32_t evals_before = 0;
+        int nb_n = 0, nb_head = 0;
+        if (step0 != 0) {
+            for (int i = tl; i < 7 + n_rot; i += 32) curs[i] = __ldcg(rec + PV_CH_CUR + i);
+            e_cur = __ldcg(rec + PV_CH_ECUR);
+            e_best = __ldcg(rec + PV_CH_EBEST);
+            evals_before = __float_as_uint(__ldcg(rec + PV_CH_EVALS));
+            if (FOCC) {
+                nb_n = __float_as_int(__ldcg(ring + PV_RING_N));
+                nb_head = __float_as_int(__ldcg(ring + PV_RING_HEAD));
+            }
         }
+        Tm::sync();
+        Q.e_cur = e_cur; Q.e_best = e_best; Q.u = 0.f; Q.evals_before = evals_before;
+        Q.nb_n = nb_n; Q.nb_head = nb_head; Q.flags = 0; Q.s = step0; Q.stage = step0 == 0 ? 0 : 1;
+        Tm::sync();
     }
-    Tm::sync();
-    int flags = 0, s = step0, stage = step0 == 0 ? 0 : 1;       // 0 start, 1 MC step, 2 refine
     Pose cand;
-    if (stage == 0) cand = random_pose<32>(L, *site.P, (uint32_t)chain, (uint32_t)pair, C);
-    while (stage == 0 || s < step1) {
-        if (stage == 1) {
+    if (step0 == 0) cand = random_pose<32>(L, *site.P, (uint32_t)chain, (uint32_t)pair, C);
+    for (;;) {
+        const int stage0 = Q.stage, s0 = Q.s;                   // 0 start, 1 MC step, 2 refine
+        if (!(stage0 == 0 || s0 < step1)) break;
+        if (stage0 == 1) {
             cand = load_pose<32>(curs, n_rot);
-            u = mutate<32>(L, cand, (uint32_t)chain, (uint32_t)pair, s, C);
+            const float u = mutate<32>(L, cand, (uint32_t)chain, (uint32_t)pair, s0, C);
+            Tm::sync();
+            Q.u = u;
         }
-        const float e_new = warp_local_search<FOCC>(L, S, site, cand, C, stage == 0 ? 0 : max_iter, evals, g_new,
-                                              FOCC && stage == 1 ? ring : nullptr, nb_n);
+        const float e_new = warp_local_search<FOCC>(L, S, site, cand, C, stage0 == 0 ? 0 : max_iter, evals, g_new,
+                                                    FOCC && stage0 == 1 ? ring : nullptr);
+        float e_cur = Q.e_cur, e_best = Q.e_best;
+        const float u = Q.u;
+        int s = Q.s, stage = Q.stage, flags = Q.flags, nb_n = Q.nb_n, nb_head = Q.nb_head;
+        bool stop = false;
         if (stage == 0) {
             e_cur = e_new;
             e_best = e_new;
@@ -337,22 +373,17 @@ __device__ __forceinline__ void run_chain_warp(const SearchArgs& A, const PvLigB
             Tm::sync();
             if (FOCC) focc_push<32>(ring, cand, e_new, g_new, n_rot, C.focc, nb_n, nb_head);
             stage = 1;
-            continue;
-        }
-        if (stage == 1) {
-            if (!(e_new < e_cur || u < expf((e_cur - e_new) / C.temperature))) {
-                ++s;                                            // rejected
-            } else if (e_new < e_best) {
-                stage = 2;                                      // accepted, a new best: refine first
-                continue;
-            } else {
-                e_cur = e_new;                                  // accepted
-                Tm::sync();
-                store_pose<32>(curs, cand, n_rot);
-                Tm::sync();
-                if (FOCC) focc_push<32>(ring, cand, e_new, g_new, n_rot, C.focc, nb_n, nb_head);
-                ++s;
-            }
+        } else if (stage == 1 && !(e_new < e_cur || u < expf((e_cur - e_new) / C.temperature))) {
+            ++s;                                                // rejected
+        } else if (stage == 1 && e_new < e_best) {
+            stage = 2;                                          // accepted, a new best: refine first
+        } else if (stage == 1) {
+            e_cur = e_new;                                      // accepted
+            Tm::sync();
+            store_pose<32>(curs, cand, n_rot);
+            Tm::sync();
+            if (FOCC) focc_push<32>(ring, cand, e_new, g_new, n_rot, C.focc, nb_n, nb_head);
+            ++s;
         } else {                                                // the refined new best
             e_cur = e_new;
             e_best = e_new;
@@ -364,26 +395,33 @@ __device__ __forceinline__ void run_chain_warp(const SearchArgs& A, const PvLigB
             stage = 1;
             ++s;
         }
-        if (A.timeout_ns) {
+        if (A.timeout_ns && stage != 2) {
             unsigned long long now = tl == 0 ? globaltimer() : 0ull;
             now = __shfl_sync(PV_FULL, now, 0);
-            if (now - *A.t0 > A.timeout_ns) { flags |= PV_EBIT_TIMEOUT; break; }
+            if (now - *A.t0 > A.timeout_ns) { flags |= PV_EBIT_TIMEOUT; stop = true; }
         }
+        Tm::sync();
+        Q.e_cur = e_cur; Q.e_best = e_best; Q.s = s; Q.stage = stop ? 3 : stage; Q.flags = flags;
+        Q.nb_n = nb_n; Q.nb_head = nb_head;
+        Tm::sync();
+        if (stop) break;
     }
+    const float e_cur = Q.e_cur, e_best = Q.e_best;
+    int flags = Q.flags;
     if (!(e_best == e_best)) flags |= PV_EBIT_NAN;
-    Tm::sync();
     for (int i = tl; i < 7 + n_rot; i += 32) rec[PV_CH_CUR + i] = curs[i];
     if (tl == 0) {
         if (FOCC) {
-            ring[PV_RING_N] = __int_as_float(nb_n);
-            ring[PV_RING_HEAD] = __int_as_float(nb_head);
+            ring[PV_RING_N] = __int_as_float(Q.nb_n);
+            ring[PV_RING_HEAD] = __int_as_float(Q.nb_head);
         }
         rec[PV_CH_ECUR] = e_cur;
         rec[PV_CH_EBEST] = e_best;
-        rec[PV_CH_EVALS] = __uint_as_float(evals_before + evals);
+        rec[PV_CH_EVALS] = __uint_as_float(Q.evals_before + evals);
         const int old = step0 == 0 ? 0 : __float_as_int(__ldcg(rec + PV_CH_FLAGS));
         rec[PV_CH_FLAGS] = __int_as_float(old | flags);
     }
+    Tm::sync();
     evals_out = evals;
     flags_out = flags;
 }

@@ -20,12 +20,23 @@
 
 namespace pv {
 
+// Team-uniform scalars of a chain's MC step and of its line search, kept in shared memory rather
+// than registers: they are used between evaluations only, and every evaluation ends with a team
+// barrier, so registers holding them across it would only lower the kernel's occupancy.
+struct ChainScalars {
+    float e_cur, e_best, u, f, gd, lam, lo, hi, flo;
+    int s, stage, flags, nb_n, nb_head, it, tr, stored, head, have_lo;
+    uint32_t evals_before;
+};
+
 struct WarpScratch {            // one per team
     float4 x[64];               // posed coordinates; w = XS radius
     float4 g[64];               // dSF/dx
     float hs[PV_MAX_M][32];     // L-BFGS history: s vectors, lane = tangent coordinate
     float hy[PV_MAX_M][32];     //                 y vectors
     float cur[40];              // the chain's current POT (MC state)
+    float glo[32];              // line search: gradient at the largest Armijo-satisfying trial
+    ChainScalars cs;
 };
 
 template <int LANES>
