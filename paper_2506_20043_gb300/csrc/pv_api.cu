@@ -32,8 +32,8 @@ struct pv_context {
     int sms = 0;
     cudaStream_t capture_stream = nullptr;   // graphs are captured here (the caller's stream may
                                              // be the legacy default stream, which cannot capture)
-    // autotuned (search variant, warps per CTA) per (ligand atoms / 8, check on/off and team width,
-    // pair rounds / 4)
+    // autotuned (search variant, warps per CTA) per (ligand atoms / 8, check on/off and team width;
+    // pair rounds / 4 and the caller's fixed variant or CTA size)
     std::map<std::pair<int, int>, std::pair<int, int>> tuned;
 };
 
@@ -716,8 +716,10 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     const bool autotune = p.mode == PV_MODE_BATCHED && (p.search_variant < 0 || p.warps_per_cta == 0);
     int max_rounds = 0;
     for (int i = 0; i < n_ligs; ++i) max_rounds = std::max(max_rounds, ligs[i]->rec.n_rounds);
+    // the parameters the caller fixed (a variant or a CTA size) are part of the key: a shape tuned
+    // with one of them free may not suit the other fixed
     const std::pair<int, int> tune_key{4 * ((max_atoms + 7) / 8) + 2 * (p.focc > 0 ? 1 : 0) + (auto_lanes == 16 ? 1 : 0),
-                                       (max_rounds + 3) / 4};
+                                       ((max_rounds + 3) / 4) * 1024 + p.warps_per_cta * 16 + (p.search_variant + 1)};
     bool need_tune = false;
     if (autotune) {
         auto it = ctx->tuned.find(tune_key);
