@@ -61,6 +61,13 @@ struct Team {
         }
         return v;
     }
+    static __device__ __forceinline__ float3 shfl3(float3 v, int src) {
+        return make_float3(shfl(v.x, src), shfl(v.y, src), shfl(v.z, src));
+    }
+    static __device__ __forceinline__ float3 xor3(float3 v, int o) {
+        return make_float3(__shfl_xor_sync(mask(), v.x, o, LANES), __shfl_xor_sync(mask(), v.y, o, LANES),
+                           __shfl_xor_sync(mask(), v.z, o, LANES));
+    }
     static __device__ __forceinline__ void sync() { __syncwarp(mask()); }
 };
 
@@ -260,18 +267,24 @@ __device__ __forceinline__ float team_eval(const PvLigBlob& L, WarpScratch& S, c
         }
         F = Tm::sum3(F);
         tau = Tm::sum3(tau);
-        // torsions: fragment lane sums torque of its subtree (a contiguous atom range) about
-        // its anchor, projected on its world hinge axis
-        float gpsi = 0.f;
+        // torsions: the torque of each fragment's subtree (a contiguous atom range) about its
+        // anchor, on its world hinge axis. k lanes share a fragment (k the largest power of two
+        // with k * n_frag <= LANES), each summing every k-th atom of the range, then a butterfly
+        // within the group; fragment f's anchor and axis come from lane f.
         const int nf = L.h.n_frag;
-        if (tl > 0 && tl < nf) {
-            const int a0 = L.frag_a0[tl], a1 = L.frag_a1[tl];
-            float3 t = make_float3(0.f, 0.f, 0.f);
-            for (int a = a0; a < a1; ++a) t = t + cross3(f3(S.x[a]) - xa, f3(S.g[a]));
-            gpsi = dot3(axw, t);
+        int k = LANES;
+        while (k * nf > LANES) k >>= 1;
+        const int f = tl / k, sub = tl & (k - 1);
+        const float3 xa_f = Tm::shfl3(xa, f < nf ? f : 0), ax_f = Tm::shfl3(axw, f < nf ? f : 0);
+        float3 t = make_float3(0.f, 0.f, 0.f);
+        if (f > 0 && f < nf) {
+            const int a0 = L.frag_a0[f], a1 = L.frag_a1[f];
+            for (int a = a0 + sub; a < a1; a += k) t = t + cross3(f3(S.x[a]) - xa_f, f3(S.g[a]));
         }
+        for (int o = 1; o < k; o <<= 1) t = t + Tm::xor3(t, o);
+        const float gpsi = dot3(ax_f, t);
         const int nt = 6 + L.h.n_rot;
-        const int src = (tl >= 6 && tl < nt) ? L.tor_frag[tl - 6] : tl;
+        const int src = (tl >= 6 && tl < nt) ? L.tor_frag[tl - 6] * k : tl;
         float gp = Tm::shfl(gpsi, src);
         float c3[6] = {F.x, F.y, F.z, tau.x, tau.y, tau.z};
         grad = tl < 6 ? c3[tl] : (tl < nt ? gp : 0.f);
