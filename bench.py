@@ -114,21 +114,27 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def stored_traffic():
-    """DRAM bytes (read + write) of one search launch from the committed ncu summary, if that
-    summary was taken on the current kernel sources (else None). The launch's traffic is one read of
-    the pockets' maps plus the chain records, the same for a 20-, 100- or 500-step launch (the maps
-    stay L2-resident), so the captured launch stands for the bench's launches."""
+def stored_profile():
+    """Figures of the committed ncu summary of the search kernel, if it was taken on the current
+    kernel sources (else {}): 'traffic' = DRAM bytes (read + write) of one launch of the bench's
+    shape (16 step blocks, each sweeping the pockets' maps once; captured at 400 steps, which
+    makes the same sweeps), 'inst' = warp instructions per evaluation."""
     p = os.path.join(ROOT, "profiles", "search_round_kernel_multipocket.md")
     if not os.path.exists(p):
-        return None
+        return {}
     txt = open(p).read()
     import re
-    m_hash = re.search(r"kernel source hash:\s*`?([0-9a-f]{16})", txt)
+    m_hash = re.search(r"kernel source hash at capture:\s*`?([0-9a-f]{16})", txt, re.I)
+    if not m_hash or m_hash.group(1) != kernel_source_hash():
+        return {}
+    out = {}
     m_tr = re.search(r"dram bytes per launch:\s*([0-9.eE+]+)", txt)
-    if not (m_hash and m_tr) or m_hash.group(1) != kernel_source_hash():
-        return None
-    return float(m_tr.group(1))
+    m_in = re.search(r"warp instructions per evaluation:\s*([0-9.eE+]+)", txt)
+    if m_tr:
+        out["traffic"] = float(m_tr.group(1))
+    if m_in:
+        out["inst"] = float(m_in.group(1))
+    return out
 
 
 # ------------------------------------------------------------------------------ our arm --
@@ -206,10 +212,11 @@ def run_ours(args):
         max_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
         peak_tflops = n_sm * 128 * 2 * max_mhz * 1e6 / 1e12
         achieved = evals * flops / search_s / 1e12
-        launch_traffic = stored_traffic()
+        prof = stored_profile()
+        launch_traffic = prof.get("traffic")
         evals_per_launch = evals / max(launches, 1)
         n_rounds = launches // max(args.steps, 1)
-        _, _, gather_gbs = ctx.measure_gather(gs, 0, n_points=1 << 24, reps=10)
+        _, _, gather_gbs = ctx.measure_gather(gs, -1, n_points=1 << 24, reps=10)   # the 10 pockets' map set
         search_gather_gbs = evals * gbytes / search_s / 1e9
         out = {
             "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -236,7 +243,13 @@ def run_ours(args):
                          "launch_ms": round(search_s / max(launches, 1) * 1e3, 3),
                          "l2_gather_gbs": round(search_gather_gbs, 1),
                          "gather_ceiling_gbs": round(gather_gbs, 1),
-                         "gather_frac": round(search_gather_gbs / gather_gbs, 4)},
+                         "gather_frac": round(search_gather_gbs / gather_gbs, 4),
+                         "issue": ({"warp_inst_per_eval": prof["inst"],
+                                    "achieved_ginst_s": round(evals / search_s * prof["inst"] / 1e9, 1),
+                                    "peak_ginst_s": round(n_sm * 4 * max_mhz * 1e6 / 1e9, 1),
+                                    "frac": round(evals / search_s * prof["inst"] / (n_sm * 4 * max_mhz * 1e6), 4),
+                                    "note": "warp instructions issued per second vs 4 per SM per clock"}
+                                   if "inst" in prof else None)},
             "gpu_launches": args.steps * (6 + 1 + n_rounds + 2),
             "clocks": clocks,
         }

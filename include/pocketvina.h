@@ -188,9 +188,10 @@ pv_status pv_pose_coords(pv_context* ctx, const pv_ligand* lig, int32_t n_poses,
 
 /* Microbenchmark of the trilinear gather alone (Eq. 3's e_inter from the grid cache, with its
  * gradient), the ceiling of that step inside pv_score and the search: each launch interpolates
- * n_points hashed positions in the pocket's box on hashed map slots of the set. One untimed
- * launch, then `reps` launches timed with events on the context stream; *ms_per_launch = their
- * mean device time. Algorithmic bytes: 32 per point (8 corner values of 4 bytes).
+ * n_points hashed positions in the pocket's box on hashed map slots of the set (pocket -1: in the
+ * box of a hashed pocket of the whole set, i.e. over the whole map set). One untimed launch, then
+ * `reps` launches timed with events on the context stream; *ms_per_launch = their mean device
+ * time. Algorithmic bytes: 32 per point (8 corner values of 4 bytes).
  * PV_ERR_ARG for a bad pocket, n_points < 1, reps < 1 or a null output. Synchronous. */
 pv_status pv_measure_gather(pv_context* ctx, const pv_grid_set* set, int32_t pocket, int64_t n_points,
                             int32_t reps, float* ms_per_launch);

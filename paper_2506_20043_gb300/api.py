@@ -213,8 +213,9 @@ class Context:
         return out
 
     def measure_gather(self, grids: "GridSet", pocket: int = 0, n_points: int = 1 << 24, reps: int = 10):
-        """The trilinear gather alone (value + gradient at hashed positions in the pocket's box):
-        returns (milliseconds per launch, points per second, algorithmic GB/s at 32 B per point)."""
+        """The trilinear gather alone (value + gradient at hashed positions in the pocket's box;
+        pocket -1: over every pocket of the set): returns (milliseconds per launch, points per
+        second, algorithmic GB/s at 32 B per point)."""
         ms = C.c_float()
         self._check(self.lib.pv_measure_gather(self.h, grids.h, int(pocket), int(n_points), int(reps), C.byref(ms)),
                     "pv_measure_gather")

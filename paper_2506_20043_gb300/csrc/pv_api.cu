@@ -557,20 +557,21 @@ extern "C" pv_status pv_measure_gather(pv_context* ctx, const pv_grid_set* set, 
                                        int32_t reps, float* ms_per_launch) {
     if (!ctx || ctx->magic != kCtxMagic) return PV_ERR_STATE;
     if (!set || set->ctx != ctx) return fail(ctx, PV_ERR_STATE, "grid set of another context");
-    if (pocket < 0 || pocket >= (int)set->pockets.size() || n_points < 1 || reps < 1 || !ms_per_launch)
+    if (pocket < -1 || pocket >= (int)set->pockets.size() || n_points < 1 || reps < 1 || !ms_per_launch)
         return fail(ctx, PV_ERR_ARG, "bad arguments");
     DeviceGuard g(ctx->device);
-    const PvPocket& P = set->pockets[pocket];
+    const PvPocket* table = pocket < 0 ? set->d_pockets : set->d_pockets + pocket;
+    const int n_table = pocket < 0 ? (int)set->pockets.size() : 1;
     float* sink = nullptr;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     sink = (float*)dalloc(ctx, sizeof(float));
     if (!sink) return fail(ctx, PV_ERR_OOM, "device allocation failed");
     cudaError_t e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
-    if (e == cudaSuccess) e = launch_gather_probe(P, set->n_maps, n_points, 1u, sink, ctx->sms, ctx->stream);
+    if (e == cudaSuccess) e = launch_gather_probe(table, n_table, set->n_maps, n_points, 1u, sink, ctx->sms, ctx->stream);
     if (e == cudaSuccess) e = cudaEventRecord(t0, ctx->stream);
     for (int r = 0; r < reps && e == cudaSuccess; ++r)
-        e = launch_gather_probe(P, set->n_maps, n_points, 2u + (uint32_t)r * 977u, sink, ctx->sms, ctx->stream);
+        e = launch_gather_probe(table, n_table, set->n_maps, n_points, 2u + (uint32_t)r * 977u, sink, ctx->sms, ctx->stream);
     if (e == cudaSuccess) e = cudaEventRecord(t1, ctx->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(t1);
     float ms = 0.f;

@@ -43,10 +43,11 @@ cudaError_t launch_pose_coords(const PvLigBlob* lig, int lig_bytes, int n_poses,
                                const float* pose, float* xyz, cudaStream_t s);
 
 // ---- gather microbenchmark (pv_probe.cu) ----
-// n_points trilinear interpolations (value + gradient) at hashed positions in the pocket's box,
-// on hashed map slots in [0, n_slots); sink is written only in a case that does not occur.
-cudaError_t launch_gather_probe(const PvPocket& P, int n_slots, long long n_points, uint32_t seed,
-                                float* sink, int n_sm, cudaStream_t s);
+// n_points trilinear interpolations (value + gradient) at hashed positions in the box of a hashed
+// pocket of the device table, on hashed map slots in [0, n_slots); sink is written only in a case
+// that does not occur.
+cudaError_t launch_gather_probe(const PvPocket* pockets_dev, int n_pockets, int n_slots, long long n_points,
+                                uint32_t seed, float* sink, int n_sm, cudaStream_t s);
 
 // ---- search (pv_search.cu) ----
 struct SearchArgs {

@@ -1,6 +1,7 @@
 // pv_probe.cu -- microbenchmark of the trilinear map gather alone (Eq. 3's e_inter from the grid
-// cache, with its gradient): the rate at which one pocket's maps serve interpolations at random
-// positions, i.e. the ceiling of the gather step inside the score and search kernels.
+// cache, with its gradient): the rate at which a pocket's maps (or every pocket's of a grid set)
+// serve interpolations at random positions, i.e. the ceiling of the gather step inside the score
+// and search kernels.
 #include <algorithm>
 
 #include "pv_internal.h"
@@ -19,13 +20,15 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
     return x;
 }
 
-__global__ void __launch_bounds__(256) gather_probe_kernel(PvPocket P, int n_slots, long long n_points,
-                                                           uint32_t seed, float* sink) {
+__global__ void __launch_bounds__(256) gather_probe_kernel(const PvPocket* __restrict__ pockets, int n_pockets,
+                                                           int n_slots, long long n_points, uint32_t seed,
+                                                           float* sink) {
     float acc = 0.f;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_points; i += stride) {
         const uint32_t h0 = hash32((uint32_t)i * 4u + seed), h1 = hash32(h0 ^ 0x9e3779b9u);
         const uint32_t h2 = hash32(h1 ^ 0x9e3779b9u), h3 = hash32(h2 ^ 0x9e3779b9u);
+        const PvPocket& P = pockets[n_pockets > 1 ? (int)__umulhi(hash32(h3 ^ 0x9e3779b9u), (uint32_t)n_pockets) : 0];
         const float3 p = make_float3(P.center[0] + (u01(h0) - 0.5f) * P.size[0],
                                      P.center[1] + (u01(h1) - 0.5f) * P.size[1],
                                      P.center[2] + (u01(h2) - 0.5f) * P.size[2]);
@@ -38,12 +41,12 @@ __global__ void __launch_bounds__(256) gather_probe_kernel(PvPocket P, int n_slo
     if (acc == 1234567.0f) sink[0] = acc;
 }
 
-cudaError_t launch_gather_probe(const PvPocket& P, int n_slots, long long n_points, uint32_t seed,
-                                float* sink, int n_sm, cudaStream_t s) {
+cudaError_t launch_gather_probe(const PvPocket* pockets_dev, int n_pockets, int n_slots, long long n_points,
+                                uint32_t seed, float* sink, int n_sm, cudaStream_t s) {
     const int threads = 256;
     const long long blocks_needed = (n_points + threads - 1) / threads;
     const int grid = (int)std::min<long long>(blocks_needed, (long long)n_sm * 8);
-    gather_probe_kernel<<<std::max(grid, 1), threads, 0, s>>>(P, n_slots, n_points, seed, sink);
+    gather_probe_kernel<<<std::max(grid, 1), threads, 0, s>>>(pockets_dev, n_pockets, n_slots, n_points, seed, sink);
     return cudaGetLastError();
 }
 

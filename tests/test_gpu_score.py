@@ -214,6 +214,8 @@ def test_gather_microbenchmark_runs_and_rejects_bad_arguments():
     gs = ctx.build_grids(rec, [box], [0, 1, 2])
     ms, pts, gbs = ctx.measure_gather(gs, 0, n_points=1 << 20, reps=3)
     assert ms > 0 and pts > 1e8 and gbs == pytest.approx(32 * pts / 1e9)
-    for kw in (dict(pocket=1), dict(n_points=0), dict(reps=0)):
+    ms_all, _, _ = ctx.measure_gather(gs, -1, n_points=1 << 20, reps=3)   # every pocket of the set
+    assert ms_all > 0
+    for kw in (dict(pocket=1), dict(pocket=-2), dict(n_points=0), dict(reps=0)):
         with pytest.raises(PVError):
             ctx.measure_gather(gs, **{**dict(pocket=0, n_points=1024, reps=1), **kw})
