@@ -36,6 +36,7 @@ struct WarpScratch {            // one per team
     float hy[PV_MAX_M][32];     //                 y vectors
     float cur[40];              // the chain's current POT (MC state)
     float glo[32];              // line search: gradient at the largest Armijo-satisfying trial
+    float4 fm[3 * PV_MAX_FRAGS];// per fragment: world rotation rows (xyz) with the anchor (w)
     ChainScalars cs;
 };
 
@@ -138,19 +139,28 @@ __device__ __forceinline__ void team_fk(const PvLigBlob& L, WarpScratch& S, cons
         }
     }
     const Mat3 M = unit_quat_to_mat(Q.x, Q.y, Q.z, Q.w);
+    // each fragment's rotation rows and anchor go through shared memory once; an atom then reads
+    // its fragment's three rows as 16-byte words
+    if (isf) {
+        S.fm[3 * tl + 0] = make_float4(M.m[0], M.m[1], M.m[2], xa.x);
+        S.fm[3 * tl + 1] = make_float4(M.m[3], M.m[4], M.m[5], xa.y);
+        S.fm[3 * tl + 2] = make_float4(M.m[6], M.m[7], M.m[8], xa.z);
+    }
+    Tm::sync();
     const int n = L.h.n_atoms;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
+        if (h == 1 && n <= LANES) break;
         const int a = tl + LANES * h;
-        float4 loc = a < n ? L.atom[a] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const int w = __float_as_int(loc.w);
-        const int fa = a < n ? (w & 255) : tl;
-        Mat3 Mf;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Mf.m[k] = Tm::shfl(M.m[k], fa);
-        float3 xf = make_float3(Tm::shfl(xa.x, fa), Tm::shfl(xa.y, fa), Tm::shfl(xa.z, fa));
         if (a < n) {
-            float3 p = mat_vec(Mf, f3(loc)) + xf;
+            const float4 loc = L.atom[a];
+            const int w = __float_as_int(loc.w);
+            const int fa = w & 255;
+            const float4 r0 = S.fm[3 * fa], r1 = S.fm[3 * fa + 1], r2 = S.fm[3 * fa + 2];
+            const float3 p = make_float3(r0.x * loc.x + r0.y * loc.y + r0.z * loc.z,
+                                         r1.x * loc.x + r1.y * loc.y + r1.z * loc.z,
+                                         r2.x * loc.x + r2.y * loc.y + r2.z * loc.z) +
+                             make_float3(r0.w, r1.w, r2.w);
             const float4 q = make_float4(p.x, p.y, p.z, xs_radius((w >> 8) & 255));
             S.x[a] = q;
             if (own) own[h] = q;
