@@ -427,7 +427,13 @@ def run_batch_workload(args):
     from paper_2506_20043_gb300 import api
     ctx = api.Context(0)
     t_gen = time.perf_counter()
-    if args.workload == "boxsweep":
+    if args.workload == "tiny":
+        w = S.tiny()
+        recs, boxes = w.receptors, w.boxes
+        pair_lig, pair_pocket = [0], [0]
+        desc = ("tiny: 2,000-atom receptor, one 8 A pocket in a 20 A box (0.375 A), one ligand of 20 atoms / "
+                "4 torsions, 8 chains x 1,000 MC steps")
+    elif args.workload == "boxsweep":
         w = S.box_sweep(seed=0)
         recs, boxes = w.receptors, w.boxes
         pair_lig = [0] * len(boxes[0])
@@ -517,7 +523,52 @@ def run_batch_workload(args):
             "roofline": {"kernel": "search_round_kernel", "bound": "alu", "achieved": round(achieved, 3),
                          "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
                          "flops_per_eval": round(w_flops, 1)},
-            "clocks": clocks, **extra}
+            "clocks": clocks, **extra,
+            "cpu_baseline": (None if args.no_cpu else
+                             oracle_pairs_sample(w, pair_lig, pair_pocket, args.workload, budget_s=args.cpu_budget,
+                                                 n_pairs=1 if len(pair_lig) == 1 else 3))}
+
+
+def oracle_pairs_sample(w, pair_lig, pair_pocket, name, budget_s=12.0, n_pairs=3, seed=7):
+    """The FP64 oracle on a seeded sample of the workload's pairs: for each sampled pair, the
+    pocket's full grid maps (their cost shared by the pairs docked into that pocket) and as many
+    full-length chains as fit the budget, extrapolated to the pair's chain count."""
+    import oracle as O
+    cores = len(os.sched_getaffinity(0))
+    rng = np.random.default_rng(seed)
+    picks = rng.choice(len(pair_lig), size=min(n_pairs, len(pair_lig)), replace=False)
+    rec_of = []
+    for r, bx in enumerate(w.boxes):
+        rec_of += [r] * len(bx)
+    flat_boxes = [b for bx in w.boxes for b in bx]
+    pairs_per_pocket = np.bincount(np.asarray(pair_pocket), minlength=len(flat_boxes))
+    per_pair, evals, secs, chains_run = [], 0, 0.0, []
+    for q in picks:
+        L = O.OracleLigand(w.ligands[pair_lig[q]])
+        k = pair_pocket[q]
+        rec, box = w.receptors[rec_of[k]], flat_boxes[k]
+        t0 = time.perf_counter()
+        og = O.OracleGrid(rec, box, L.xs, rec_types=O.xs_type_receptor(rec), threads=cores)
+        t_grid = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        _, _, ev = O.mc_chains(L, og, box, O.SearchParams(seed=0, steps=min(w.steps, 50)), unit=int(q),
+                               n_chains=cores, threads=cores)
+        per_chain = (time.perf_counter() - t0) / cores * (w.steps / min(w.steps, 50)) * cores
+        n_ch = int(min(w.chains, max(cores, (budget_s / n_pairs) * cores / max(per_chain, 1e-9) // cores * cores)))
+        t0 = time.perf_counter()
+        _, _, ev = O.mc_chains(L, og, box, O.SearchParams(seed=0, steps=w.steps), unit=int(q), n_chains=n_ch,
+                               threads=cores)
+        t_dock = time.perf_counter() - t0
+        per_pair.append(t_grid / pairs_per_pocket[k] + t_dock * w.chains / n_ch)
+        evals += int(ev.sum())
+        secs += t_dock
+        chains_run.append(n_ch)
+    value = 1.0 / float(np.mean(per_pair))
+    return {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"{len(picks)} seeded pairs of the {name} workload: each pocket's full FP64 grid maps "
+                       f"(shared by its {int(np.median(pairs_per_pocket[pairs_per_pocket > 0]))} pairs) + "
+                       f"{'/'.join(map(str, chains_run))} of {w.chains} chains x {w.steps} MC steps, scaled to the pair"),
+            "evals_per_s": round(evals / secs, 1)}
 
 
 def run_small_case(args):
@@ -554,7 +605,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-micro", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", choices=["multipocket", "uneven", "screening", "boxsweep"], default="multipocket",
+    ap.add_argument("--workload", choices=["multipocket", "tiny", "uneven", "screening", "boxsweep"], default="multipocket",
                     help="multipocket: the headline line; uneven / screening / boxsweep: other shapes, their own line")
     ap.add_argument("--focc", type=int, default=0,
                     help="consistency check (Eq. 4-5) with this many neighbours per chain; 0 = off (headline)")
