@@ -732,7 +732,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
         }
     }
     // the items buffer is sized for the smallest CTA a candidate may use
-    const int W_min = autotune ? (p.warps_per_cta > 0 ? p.warps_per_cta : 2) : W;
+    const int W_min = autotune ? (p.warps_per_cta > 0 ? p.warps_per_cta : 1) : W;
     std::vector<PvItem> items = make_items(W * (32 / search_variant_lanes(variant)));
     const size_t items_cap = make_items(W_min).size();
     std::vector<PvPairDesc> pdesc(n_pairs);
@@ -856,8 +856,8 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     M.ranking = R->d_ranking;
     // autotuning: time each candidate launch shape on eight MC steps of its own first work items
     if (need_tune) {
-        static const int cand[][2] = {{0, 2}, {0, 4}, {0, 8}, {1, 4}, {2, 4}, {3, 4},
-                                      {4, 2}, {4, 4}, {5, 4}, {6, 4}, {7, 4}};
+        static const int cand[][2] = {{0, 1}, {0, 2}, {0, 4}, {0, 8}, {1, 4}, {2, 4}, {3, 4},
+                                      {4, 1}, {4, 2}, {4, 4}, {5, 4}, {6, 4}, {7, 4}};
         cudaEvent_t t0, t1;
         cudaEventCreate(&t0);
         cudaEventCreate(&t1);
