@@ -37,9 +37,11 @@ struct PvLigBlob {
     int32_t tor_frag[PV_MAX_FRAGS];  // fragment of torsion k
     int32_t atom_src[64];            // input index of device atom i
     uint32_t pairs[1];               // n_rounds * 32 words (warp schedule), then n_rounds16 * 16
-                                     // words (half-warp schedule); word l of a round is lane l's
-                                     // pair: target atom (bits 0-5), source atom l + LANES * bit 6,
-                                     // hydrophobic (bit 16), H-bond (bit 17), valid (bit 31)
+                                     // words (half-warp schedule); word l of a round is lane l's:
+                                     // pair sent: target atom (bits 0-5), source atom l + LANES *
+                                     // bit 6, hydrophobic (bit 16), H-bond (bit 17), valid (bit 31);
+                                     // pair received: source lane (bits 8-12), valid (bit 13),
+                                     // receiving atom l + LANES * bit 14
 };
 #define PV_LIG_FIXED_BYTES ((int)offsetof(PvLigBlob, pairs))
 

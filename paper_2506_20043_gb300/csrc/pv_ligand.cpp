@@ -25,7 +25,7 @@ static bool is_acc(int t) { return t == 4 || t == 5 || t == 8 || t == 9; }
 // Orients every pair so that, per atom, sources and targets split its pairs evenly (an Euler
 // circuit of the pair graph, with a dummy vertex joined to the odd-degree atoms, enters and
 // leaves each atom equally often), then flips single pairs while that lowers the larger of a
-// lane's source load (atoms l and l + 32 share lane l) and a target's load.
+// lane's source load and its target load (atoms l and l + lanes share lane l).
 static void orient_pairs(int n, std::vector<std::pair<int, int>>& edges, int lanes) {
     const int m = (int)edges.size();
     if (m == 0) return;
@@ -58,17 +58,17 @@ static void orient_pairs(int n, std::vector<std::pair<int, int>>& edges, int lan
         }
     }
     const int lm = lanes - 1;
-    std::vector<int> load(lanes, 0), ind(64, 0);
-    for (auto& e : edges) { load[e.first & lm]++; ind[e.second]++; }
+    std::vector<int> load(lanes, 0), ind(lanes, 0);   // per lane: pairs as source, as target
+    for (auto& e : edges) { load[e.first & lm]++; ind[e.second & lm]++; }
     for (bool changed = true; changed;) {
         changed = false;
         for (auto& e : edges) {
             const int s = e.first, t = e.second, ls = s & lm, lt = t & lm;
             if (ls == lt) continue;
-            const int before = std::max(std::max(load[ls], load[lt]), std::max(ind[s], ind[t]));
-            const int after = std::max(std::max(load[ls] - 1, load[lt] + 1), std::max(ind[s] + 1, ind[t] - 1));
-            if (after < before || (after == before && load[lt] + 1 < load[ls] && ind[s] + 1 < ind[t])) {
-                load[ls]--; load[lt]++; ind[s]++; ind[t]--;
+            const int before = std::max(std::max(load[ls], load[lt]), std::max(ind[ls], ind[lt]));
+            const int after = std::max(std::max(load[ls] - 1, load[lt] + 1), std::max(ind[ls] + 1, ind[lt] - 1));
+            if (after < before || (after == before && load[lt] + 1 < load[ls] && ind[ls] + 1 < ind[lt])) {
+                load[ls]--; load[lt]++; ind[ls]++; ind[lt]--;
                 e = {t, s};
                 changed = true;
             }
@@ -76,20 +76,21 @@ static void orient_pairs(int n, std::vector<std::pair<int, int>>& edges, int lan
     }
 }
 
-// Edge colouring of the bipartite graph lanes x targets with as many colours (rounds) as its
-// largest degree (Koenig): a pair gets a colour free at both ends, else the alternating path
-// of the two candidate colours from its target is swapped first.
+// Edge colouring of the bipartite multigraph source lanes x target lanes with as many colours
+// (rounds) as its largest degree (Koenig): a pair gets a colour free at both ends, else the
+// alternating path of the two candidate colours from its target lane is swapped first. In a round
+// every lane then sends at most one pair and receives at most one.
 static int colour_rounds(const std::vector<std::pair<int, int>>& edges, std::vector<int>& col, int lanes) {
     const int m = (int)edges.size();
     const int lm = lanes - 1;
     col.assign(m, -1);
     if (m == 0) return 0;
-    std::vector<int> dl(lanes, 0), dr(64, 0);
-    for (auto& e : edges) { dl[e.first & lm]++; dr[e.second]++; }
+    std::vector<int> dl(lanes, 0), dr(lanes, 0);
+    for (auto& e : edges) { dl[e.first & lm]++; dr[e.second & lm]++; }
     const int D = std::max(*std::max_element(dl.begin(), dl.end()), *std::max_element(dr.begin(), dr.end()));
-    std::vector<int> Lc(lanes * D, -1), Rc(64 * D, -1);   // edge holding colour c at a lane / target
+    std::vector<int> Lc(lanes * D, -1), Rc(lanes * D, -1);   // edge holding colour c at a source / target lane
     for (int e = 0; e < m; ++e) {
-        const int u = edges[e].first & lm, v = edges[e].second;
+        const int u = edges[e].first & lm, v = edges[e].second & lm;
         int a = 0, b = 0;
         while (Lc[u * D + a] >= 0) ++a;
         while (Rc[v * D + b] >= 0) ++b;
@@ -101,18 +102,18 @@ static int colour_rounds(const std::vector<std::pair<int, int>>& edges, std::vec
                 const int f = right ? Rc[x * D + c] : Lc[x * D + c];
                 if (f < 0) break;
                 path.push_back(f);
-                x = right ? (edges[f].first & lm) : edges[f].second;
+                x = right ? (edges[f].first & lm) : (edges[f].second & lm);
                 right = !right;
                 c = c == a ? b : a;
             }
             for (int f : path) {
                 Lc[(edges[f].first & lm) * D + col[f]] = -1;
-                Rc[edges[f].second * D + col[f]] = -1;
+                Rc[(edges[f].second & lm) * D + col[f]] = -1;
             }
             for (int f : path) {
                 col[f] = col[f] == a ? b : a;
                 Lc[(edges[f].first & lm) * D + col[f]] = f;
-                Rc[edges[f].second * D + col[f]] = f;
+                Rc[(edges[f].second & lm) * D + col[f]] = f;
             }
         }
         col[e] = a;
@@ -246,10 +247,10 @@ bool build_ligand(const LigandInput& in, LigandRecord& out, std::string& err) {
         for (int j = i + 1; j < n; ++j)
             if (frag[i] != frag[j] && !(dist[j] >= 0 && dist[j] <= 3)) pairs.push_back({i, j});
     }
-    // Schedule the pairs for the warp: each pair is owned by the lane of one of its atoms (the
-    // source), which keeps that atom's force in registers; the other atom (the target) receives
-    // its force through shared memory. A round gives every lane at most one pair and every
-    // target at most one pair, so a round needs no atomics.
+    // Schedule the pairs for the team: each pair is computed by the lane of one of its atoms (the
+    // source), which keeps that atom's force in registers; the other atom's lane (the target's)
+    // receives the opposite force by a shuffle from the source lane. A round gives every lane at
+    // most one pair to send and one to receive, so a round needs neither atomics nor shared memory.
     // A warp schedule (32 lanes) always; a half-warp schedule (16 lanes) when the ligand fits a
     // half-warp team (at most 32 atoms, 16 fragments, 6 + n_rot <= 16 tangent coordinates).
     auto schedule = [&](int lanes, std::vector<std::vector<uint32_t>>& rounds) {
@@ -265,8 +266,9 @@ bool build_ligand(const LigandInput& in, LigandRecord& out, std::string& err) {
             const uint32_t hyd = (is_hyd(ti) && is_hyd(tj)) ? 1u : 0u;
             const uint32_t hb = ((is_don(ti) && is_acc(tj)) || (is_acc(ti) && is_don(tj))) ? 1u : 0u;
             const uint32_t half = (uint32_t)(src / lanes);
-            const uint32_t w = (uint32_t)tgt | (half << 6) | (hyd << 16) | (hb << 17) | (1u << 31);
-            rounds[colour[e]][src % lanes] = w;
+            rounds[colour[e]][src % lanes] |= (uint32_t)tgt | (half << 6) | (hyd << 16) | (hb << 17) | (1u << 31);
+            // the target's lane: which lane sends to it this round, and which of its atoms
+            rounds[colour[e]][tgt % lanes] |= ((uint32_t)(src % lanes) << 8) | (1u << 13) | ((uint32_t)(tgt / lanes) << 14);
         }
         return nr;
     };

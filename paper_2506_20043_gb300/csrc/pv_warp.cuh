@@ -169,22 +169,16 @@ __device__ __forceinline__ void team_fk(const PvLigBlob& L, WarpScratch& S, cons
     axw = mat_vec(M, axis);   // the hinge axis in the world frame (rotating about it keeps it)
 }
 
-// One round of the pair loop: the lane's pair (source atom xi, partner position xj).
-__device__ __forceinline__ void pair_round(uint32_t pw, const float4& xi, const float4& xj, WarpScratch& S,
-                                           float& e_intra, float3& acc) {
+// The lane's pair of one round (source atom xi, partner position xj): its energy and the force
+// on the source, which the target's lane receives with the opposite sign.
+__device__ __forceinline__ float3 pair_force(uint32_t pw, const float4& xi, const float4& xj, float& e_intra) {
     const float3 d = make_float3(xi.x - xj.x, xi.y - xj.y, xi.z - xj.z);
     const float r2 = dot3(d, d);
     const bool live = (pw >> 31) && r2 < kCutoff2;
     float c;
     const float e = vina_pair_r2(r2, xi.w + xj.w, (float)((pw >> 16) & 1), (float)((pw >> 17) & 1), c);
-    if (live) {
-        e_intra += e;
-        const float3 f = c * d;
-        acc = acc + f;
-        const int t = pw & 63;
-        const float4 gj = S.g[t];
-        S.g[t] = make_float4(gj.x - f.x, gj.y - f.y, gj.z - f.z, 0.f);
-    }
+    if (live) e_intra += e;
+    return live ? c * d : make_float3(0.f, 0.f, 0.f);
 }
 
 // SF = e_inter + e_intra (Eq. 3) and, if want_grad, its tangent gradient (lane k holds
@@ -210,24 +204,26 @@ __device__ __forceinline__ float team_eval(const PvLigBlob& L, WarpScratch& S, c
             const int w = __float_as_int(L.atom[a].w);
             const int slot = (w >> 16) & 255;
             e_inter += grid_eval(site.maps + (long long)slot * P.nxyz, P, f3(own[h]), acc[h]);
-            S.g[a] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
     Tm::sync();
-    // Pair rounds. Positions and pair words are read-only here, so the next round's word and
-    // partner position are loaded before the current round's force update and its sync
-    // (which orders only the force scatter).
+    // Pair rounds. Each lane computes the pair it sends (its atom is the source) and takes the
+    // opposite force of the pair it receives from the sending lane by a shuffle, so forces stay in
+    // registers and rounds need no barrier; positions and pair words are read-only here, so the
+    // next round's word and partner position are loaded ahead.
     int rounds;
     const uint32_t* pr = pair_rounds<LANES>(L, rounds);
     if (rounds > 0) {
         uint32_t pw = pr[tl];
         float4 xj = S.x[pw & 63];
-        if (n <= LANES) {                     // every source is the lane's first atom
+        if (n <= LANES) {                     // every atom of a pair is its lane's first
             for (int r = 0; r < rounds; ++r) {
                 const uint32_t pw_n = r + 1 < rounds ? pr[(r + 1) * LANES + tl] : 0u;
                 const float4 xj_n = S.x[pw_n & 63];
-                pair_round(pw, own[0], xj, S, e_intra, acc[0]);
-                Tm::sync();
+                const float3 f = pair_force(pw, own[0], xj, e_intra);
+                const float3 fi = Tm::shfl3(f, (pw >> 8) & (LANES - 1));
+                acc[0] = acc[0] + f;
+                if ((pw >> 13) & 1) acc[0] = acc[0] - fi;
                 pw = pw_n;
                 xj = xj_n;
             }
@@ -235,23 +231,25 @@ __device__ __forceinline__ float team_eval(const PvLigBlob& L, WarpScratch& S, c
             for (int r = 0; r < rounds; ++r) {
                 const uint32_t pw_n = r + 1 < rounds ? pr[(r + 1) * LANES + tl] : 0u;
                 const float4 xj_n = S.x[pw_n & 63];
-                if ((pw >> 6) & 1) pair_round(pw, own[1], xj, S, e_intra, acc[1]);
-                else pair_round(pw, own[0], xj, S, e_intra, acc[0]);
-                Tm::sync();
+                const bool hs = (pw >> 6) & 1, hr = (pw >> 14) & 1;
+                const float3 f = pair_force(pw, hs ? own[1] : own[0], xj, e_intra);
+                const float3 fi = Tm::shfl3(f, (pw >> 8) & (LANES - 1));
+                if (hs) acc[1] = acc[1] + f;
+                else acc[0] = acc[0] + f;
+                if ((pw >> 13) & 1) {
+                    if (hr) acc[1] = acc[1] - fi;
+                    else acc[0] = acc[0] - fi;
+                }
                 pw = pw_n;
                 xj = xj_n;
             }
         }
     }
-    // total dSF/dx of the lane's atoms: own share (registers) + shares received as a target
+    // total dSF/dx of the lane's atoms, kept in shared memory for the torque sums
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int a = tl + LANES * h;
-        if (a < n) {
-            const float4 gt = S.g[a];
-            acc[h] = acc[h] + f3(gt);
-            S.g[a] = make_float4(acc[h].x, acc[h].y, acc[h].z, 0.f);
-        }
+        if (a < n) S.g[a] = make_float4(acc[h].x, acc[h].y, acc[h].z, 0.f);
     }
     float ei, ej;
     if (parts) {

@@ -3,10 +3,10 @@ library's own ligand builder, decoded, and checked against the oracle's pair lis
 in different rigid fragments more than three bonds apart).
 
 Each schedule (the warp's 32 lanes, and the half warp's 16 lanes for ligands that fit one) must
-hold every oracle pair exactly once, give a target at most one pair per round (the format gives a
-lane at most one), carry the pair's hydrophobic / H-bond flags, and use no more rounds than the
-largest lane or target load of its orientation (a proper edge colouring of a bipartite graph,
-Koenig's theorem)."""
+hold every oracle pair exactly once, carry the pair's hydrophobic / H-bond flags, have every pair
+received by its target atom's lane from its sending lane, let a lane send and receive at most one
+pair per round, and use no more rounds than the largest sending or receiving load of a lane (a
+proper edge colouring of a bipartite multigraph, Koenig's theorem)."""
 import ctypes as C
 import os
 import subprocess
@@ -35,18 +35,35 @@ def lib(tmp_path_factory):
 
 
 def _decode(lib, lig, lanes):
+    """Rows (round, lane, source input atom, target input atom, hyd, hb) of the pairs sent, rows
+    (round, lane, sending lane, receiving input atom) of the pairs received, the header and the
+    round count."""
     xyz = np.ascontiguousarray(lig.xyz, np.float32)
     el, don, acc = (np.ascontiguousarray(a, np.uint8) for a in (lig.element, lig.donor, lig.acceptor))
     bonds = np.ascontiguousarray(lig.bonds, np.int32).reshape(-1, 2)
     rot = np.ascontiguousarray(lig.rotatable, np.uint8)
-    out = np.zeros((4096, 6), np.int32)
-    info = np.zeros(4, np.int32)
+    words = np.zeros(8192, np.uint32)
+    src = np.zeros(64, np.int32)
+    info = np.zeros(5, np.int32)
     p = lambda a, t: a.ctypes.data_as(C.POINTER(t))   # noqa: E731
-    k = lib.lig_schedule(len(xyz), p(xyz, C.c_float), p(el, C.c_uint8), p(don, C.c_uint8), p(acc, C.c_uint8),
-                         len(bonds), p(bonds, C.c_int32), p(rot, C.c_uint8), lanes, p(out, C.c_int32), len(out),
-                         p(info, C.c_int32))
-    assert k >= 0, k
-    return out[:k], info
+    nr = lib.lig_schedule(len(xyz), p(xyz, C.c_float), p(el, C.c_uint8), p(don, C.c_uint8), p(acc, C.c_uint8),
+                          len(bonds), p(bonds, C.c_int32), p(rot, C.c_uint8), lanes, p(words, C.c_uint32),
+                          len(words), p(src, C.c_int32), p(info, C.c_int32))
+    assert nr >= 0, nr
+    n = int(info[4])
+    sent, recv = [], []
+    for r in range(nr):
+        for l in range(lanes):
+            w = int(words[r * lanes + l])
+            if w >> 31:
+                s_dev, t_dev = l + lanes * ((w >> 6) & 1), w & 63
+                assert s_dev < n and t_dev < n
+                sent.append((r, l, int(src[s_dev]), int(src[t_dev]), (w >> 16) & 1, (w >> 17) & 1))
+            if (w >> 13) & 1:
+                a_dev = l + lanes * ((w >> 14) & 1)
+                assert a_dev < n
+                recv.append((r, l, (w >> 8) & 31, int(src[a_dev])))
+    return np.array(sent, dtype=np.int64).reshape(-1, 6), np.array(recv, dtype=np.int64).reshape(-1, 4), info, nr
 
 
 CASES = [(n, r, s) for s, (n, r) in enumerate([(5, 0), (8, 2), (12, 3), (16, 4), (20, 4), (24, 6), (30, 6), (32, 8),
@@ -63,12 +80,12 @@ def test_schedules_hold_every_oracle_pair_once(lib, n_atoms, n_rot, seed):
     xs = [XS[t] for t in L.xs]
     donor = {t for t in XS if t.endswith("_D") or t.endswith("_DA")}
     acceptor = {t for t in XS if t.endswith("_A") or t.endswith("_DA")}
-    _, info = _decode(lib, lig, 32)
+    _, _, info, _ = _decode(lib, lig, 32)
     widths = [32] + ([16] if info[2] else [])
     # a half-warp team holds up to 32 atoms (two per lane) and 16 tangent coordinates
     assert bool(info[2]) == (n_atoms <= 32 and 6 + L.n_rot <= 16)
     for lanes in widths:
-        rows, info = _decode(lib, lig, lanes)
+        rows, recv, info, n_rounds = _decode(lib, lig, lanes)
         got = [(min(s, t), max(s, t)) for _, _, s, t, _, _ in rows]
         assert len(got) == len(set(got)) == len(ref), lanes
         assert set(got) == ref, lanes
@@ -76,12 +93,14 @@ def test_schedules_hold_every_oracle_pair_once(lib, n_atoms, n_rot, seed):
             assert s != t and s >= 0 and t >= 0
             assert hyd == int(xs[s] == "C_H" and xs[t] == "C_H")
             assert hb == int((xs[s] in donor and xs[t] in acceptor) or (xs[s] in acceptor and xs[t] in donor))
-        n_rounds = info[0] if lanes == 32 else info[1]
-        seen = set()
-        for rnd, lane, s, t, _, _ in rows:
-            assert (rnd, t) not in seen, ("target twice in a round", lanes, rnd, t)
-            seen.add((rnd, t))
+        assert n_rounds == (info[0] if lanes == 32 else info[1])
+        # every pair sent is received once, by the lane of its target atom, from its sending lane;
+        # a lane sends at most one pair and receives at most one per round
+        want = sorted((rnd, lane, t) for rnd, lane, s, t, _, _ in rows)
+        got_recv = sorted((rnd, sl, a) for rnd, l, sl, a in recv)
+        assert want == got_recv, lanes
+        assert len({(rnd, l) for rnd, l, _, _ in recv}) == len(recv)
         if len(rows):
-            lane_load = np.bincount(rows[:, 1], minlength=lanes).max()
-            tgt_load = np.bincount(rows[:, 3]).max()
-            assert n_rounds == max(lane_load, tgt_load), lanes
+            src_load = np.bincount(rows[:, 1], minlength=lanes).max()
+            tgt_load = np.bincount(recv[:, 1], minlength=lanes).max()
+            assert n_rounds == max(src_load, tgt_load), lanes
