@@ -8,11 +8,11 @@
 //   fragments:  lane tl owns rigid fragment tl (n_frag <= LANES): its world rotation and anchor
 //   tangent:    lane k owns tangent coordinate k (0-2 translation, 3-5 rotation vector,
 //               6 + t torsion t); the torsion angle psi_t itself lives in lane 6 + t
-//   pairs:      every intra pair is owned by the lane of one of its atoms (its source), which
-//               adds that atom's share of the force in registers; the other atom (its target)
-//               receives its share through shared memory. Rounds give each lane one pair and
-//               each target one pair, so no atomics are needed and the order of accumulation
-//               is fixed (bitwise reproducible).
+//   pairs:      every intra pair is computed by the lane of one of its atoms (its source), which
+//               adds that atom's share of the force in registers; the other atom's lane (its
+//               target's) receives the opposite force by a shuffle. Rounds give each lane at most
+//               one pair to send and one to receive, so forces never leave registers and the
+//               order of accumulation is fixed (bitwise reproducible).
 // Half-warp teams (LANES = 16) serve ligands of at most 32 atoms and 10 torsions: two chains share
 // a warp and stay converged at the evaluator (one evaluation per loop iteration).
 #pragma once
