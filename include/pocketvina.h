@@ -182,6 +182,16 @@ pv_status pv_score_backward(pv_context* ctx, const pv_grid_set* set, const pv_li
                             const float* dev_grad_energy, float* dev_grad_pose,
                             float* dev_grad_xyz);
 
+/* SF (Eq. 3) of posed ligands given by their atom coordinates rather than POTs, for automatic
+ * differentiation over ligand coordinates: dev_xyz [n][n_atoms][3] float32, input atom order.
+ * e_inter is interpolated from the pocket's maps as in pv_score (same out-of-grid rule), e_intra
+ * sums the ligand's intra pairs at these coordinates (the bond geometry is not checked).
+ * dev_energy (nullable) [n]; dev_grad_xyz (nullable) [n][n_atoms][3] = s[n] * dSF/dx with
+ * s = dev_grad_energy[n] (nullable: s = 1). At least one output. One warp per ligand. */
+pv_status pv_score_xyz(pv_context* ctx, const pv_grid_set* set, const pv_ligand* lig, int32_t pocket,
+                       int32_t n_poses, const float* dev_xyz, const float* dev_grad_energy,
+                       float* dev_energy, float* dev_grad_xyz);
+
 /* Posed atom coordinates: dev_xyz[n][n_atoms][3] in input atom order (forward kinematics). */
 pv_status pv_pose_coords(pv_context* ctx, const pv_ligand* lig, int32_t n_poses,
                          const float* dev_pose, float* dev_xyz);

@@ -77,6 +77,7 @@ SIGNATURES = {
     "pv_score": (i32, [vp, vp, vp, i32, i32, vp, vp, vp, vp]),
     "pv_score_backward": (i32, [vp, vp, vp, i32, i32, vp, vp, vp, vp]),
     "pv_pose_coords": (i32, [vp, vp, i32, vp, vp]),
+    "pv_score_xyz": (i32, [vp, vp, vp, i32, i32, vp, vp, vp, vp]),
     "pv_measure_gather": (i32, [vp, vp, i32, i64, i32, vp]),
     "pv_dock_params_default": (None, [C.POINTER(pv_dock_params)]),
     "pv_dock": (i32, [vp, vp, C.POINTER(vp), i32, pi32, i32, C.POINTER(pv_dock_params), C.POINTER(vp)]),

@@ -204,6 +204,22 @@ class Context:
                                                gx.data_ptr() if gx is not None else None), "pv_score_backward")
         return gp, gx
 
+    def score_xyz(self, grids: "GridSet", lig: "Ligand", pocket: int, xyz, grad: bool = True, grad_energy=None):
+        """SF (Eq. 3) of posed atom coordinates xyz [n, n_atoms, 3] (input order, cuda float32).
+        Returns (energy [n] or None when grad_energy is given, dSF/dxyz [n, n_atoms, 3] scaled by
+        grad_energy [n] if given, or None)."""
+        torch = self.torch
+        xyz = xyz.to(device=f"cuda:{self.device}", dtype=torch.float32).contiguous()
+        n = xyz.shape[0]
+        ge = grad_energy.to(device=xyz.device, dtype=torch.float32).contiguous() if grad_energy is not None else None
+        e = torch.empty(n, device=xyz.device, dtype=torch.float32) if ge is None else None
+        g = torch.empty_like(xyz) if grad or ge is not None else None
+        self._check(self.lib.pv_score_xyz(self.h, grids.h, lig.h, int(pocket), n, xyz.data_ptr(),
+                                          ge.data_ptr() if ge is not None else None,
+                                          e.data_ptr() if e is not None else None,
+                                          g.data_ptr() if g is not None else None), "pv_score_xyz")
+        return e, g
+
     def pose_coords(self, lig: "Ligand", poses):
         torch = self.torch
         poses = poses.to(device=f"cuda:{self.device}", dtype=torch.float32).contiguous()
@@ -460,3 +476,34 @@ class PVScore:
 
             cls._fn = _F
         return cls._fn.apply(pose, ctx, grids, lig, pocket)
+
+
+class PVScoreXYZ:
+    """torch.autograd.Function over ligand atom coordinates: energy = SF(xyz) for posed atoms
+    [n, n_atoms, 3] of one ligand in one pocket; backward is the library's coordinate gradient
+    (dSF/dx_i scaled by the incoming gradient in the kernel)."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, xyz, ctx: Context, grids: GridSet, lig: Ligand, pocket: int):
+        if cls._fn is None:
+            import torch
+
+            class _F(torch.autograd.Function):
+                @staticmethod
+                def forward(fctx, xyz_t, pv_ctx, grids_, lig_, pocket_):
+                    e, _ = pv_ctx.score_xyz(grids_, lig_, pocket_, xyz_t.detach(), grad=False)
+                    fctx.save_for_backward(xyz_t)
+                    fctx.pv = (pv_ctx, grids_, lig_, pocket_)
+                    return e
+
+                @staticmethod
+                def backward(fctx, ge):
+                    (xyz_t,) = fctx.saved_tensors
+                    pv_ctx, grids_, lig_, pocket_ = fctx.pv
+                    _, gx = pv_ctx.score_xyz(grids_, lig_, pocket_, xyz_t.detach(), grad_energy=ge.contiguous())
+                    return gx.to(xyz_t.dtype), None, None, None, None
+
+            cls._fn = _F
+        return cls._fn.apply(xyz, ctx, grids, lig, pocket)

@@ -541,6 +541,20 @@ extern "C" pv_status pv_score_backward(pv_context* ctx, const pv_grid_set* set, 
     return PV_OK;
 }
 
+extern "C" pv_status pv_score_xyz(pv_context* ctx, const pv_grid_set* set, const pv_ligand* lig, int32_t pocket,
+                                  int32_t n_poses, const float* dev_xyz, const float* dev_grad_energy,
+                                  float* dev_energy, float* dev_grad_xyz) {
+    pv_status st = check_score_args(ctx, set, lig, pocket, n_poses);
+    if (st != PV_OK) return st;
+    if (n_poses == 0) return PV_OK;
+    if (!dev_xyz || (!dev_energy && !dev_grad_xyz)) return fail(ctx, PV_ERR_ARG, "coordinates and an output required");
+    DeviceGuard g(ctx->device);
+    PV_CU(ctx, launch_score_xyz((const PvLigBlob*)lig->d_blob, (int)lig->rec.blob.size(), set->d_pockets + pocket,
+                                slots_of(set), n_poses, dev_xyz, dev_grad_energy, dev_energy, dev_grad_xyz,
+                                ctx->stream));
+    return PV_OK;
+}
+
 extern "C" pv_status pv_pose_coords(pv_context* ctx, const pv_ligand* lig, int32_t n_poses, const float* dev_pose,
                                     float* dev_xyz) {
     if (!ctx || ctx->magic != kCtxMagic) return PV_ERR_STATE;

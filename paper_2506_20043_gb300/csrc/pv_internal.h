@@ -39,6 +39,11 @@ cudaError_t launch_score(const PvLigBlob* lig, int lig_bytes, const PvPocket* po
                          const float* pose, float* energy, float* grad, float* parts,
                          const float* grad_energy, float* grad_pose, float* grad_xyz,
                          cudaStream_t s);
+// SF of posed atom coordinates [n][n_atoms][3] (input order); energy and grad_xyz nullable,
+// grad_xyz scaled by grad_energy (nullable: 1).
+cudaError_t launch_score_xyz(const PvLigBlob* lig, int lig_bytes, const PvPocket* pocket, PvSlots slots,
+                             int n_poses, const float* xyz, const float* grad_energy, float* energy,
+                             float* grad_xyz, cudaStream_t s);
 cudaError_t launch_pose_coords(const PvLigBlob* lig, int lig_bytes, int n_poses, int pot_stride,
                                const float* pose, float* xyz, cudaStream_t s);
 

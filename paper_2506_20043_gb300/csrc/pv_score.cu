@@ -1,5 +1,7 @@
 // pv_score.cu -- batched scoring of given poses (Eq. 3) with the adjoint gradient, one warp per
 // pose; the vector-Jacobian product used by automatic differentiation; forward kinematics only.
+#include <algorithm>
+
 #include "pv_internal.h"
 #include "pv_stage.cuh"
 #include "pv_warp.cuh"
@@ -141,6 +143,92 @@ cudaError_t launch_score(const PvLigBlob* lig, int lig_bytes, const PvPocket* po
     a.energy = energy; a.grad = grad; a.parts = parts;
     a.grad_energy = grad_energy; a.grad_pose = grad_pose; a.grad_xyz = grad_xyz;
     return launch(a, s);
+}
+
+// SF of posed ligands given by their atom coordinates (input order), one warp per ligand: the atoms
+// go to S.x in device order, then the same interpolation and pair rounds as for a pose; the
+// coordinate gradient, scaled by grad_energy when given, comes from S.g.
+struct ScoreXyzArgs {
+    const PvLigBlob* lig;
+    int lig_bytes;
+    const PvPocket* pocket;
+    uint64_t slots_lo, slots_hi;
+    int n_poses;
+    const float* xyz;
+    const float* grad_energy;   // nullable: scale 1
+    float* energy;              // nullable
+    float* grad_xyz;            // nullable
+};
+
+__global__ void __launch_bounds__(kScoreWarps * 32) score_xyz_kernel(ScoreXyzArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    PvLigBlob& L = *reinterpret_cast<PvLigBlob*>(smem);
+    WarpScratch* scratch = reinterpret_cast<WarpScratch*>(smem + ((A.lig_bytes + 127) & ~127));
+    __shared__ PvPocket s_pocket;
+    if (threadIdx.x < (int)(sizeof(PvPocket) / 4))
+        reinterpret_cast<int*>(&s_pocket)[threadIdx.x] = reinterpret_cast<const int*>(A.pocket)[threadIdx.x];
+    stage_ligand(&L, A.lig, A.slots_lo, A.slots_hi);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = L.h.n_atoms;
+    WarpScratch& S = scratch[warp];
+    Site site;
+    site.maps = s_pocket.maps;
+    site.P = &s_pocket;
+    const Pose none{};
+    for (int i = blockIdx.x * kScoreWarps + warp; i < A.n_poses; i += gridDim.x * kScoreWarps) {
+        for (int a = lane; a < n; a += 32) {
+            const float* src = A.xyz + ((size_t)i * n + L.atom_src[a]) * 3;
+            const int t = (__float_as_int(L.atom[a].w) >> 8) & 255;
+            S.x[a] = make_float4(src[0], src[1], src[2], xs_radius(t));
+        }
+        __syncwarp();
+        float g = 0.f;
+        const float e = team_eval<32, false>(L, S, site, none, g, false);
+        if (A.energy && lane == 0) A.energy[i] = e;
+        if (A.grad_xyz) {
+            const float s = A.grad_energy ? A.grad_energy[i] : 1.f;
+            for (int a = lane; a < n; a += 32) {
+                float* dst = A.grad_xyz + ((size_t)i * n + L.atom_src[a]) * 3;
+                const float4 gg = S.g[a];
+                dst[0] = s * gg.x; dst[1] = s * gg.y; dst[2] = s * gg.z;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_score_xyz(const PvLigBlob* lig, int lig_bytes, const PvPocket* pocket, PvSlots slots,
+                             int n_poses, const float* xyz, const float* grad_energy, float* energy,
+                             float* grad_xyz, cudaStream_t s) {
+    ScoreXyzArgs a{};
+    a.lig = lig; a.lig_bytes = lig_bytes; a.pocket = pocket;
+    uint64_t lo = 0, hi = 0;
+    for (int t = 0; t < 16; ++t) {
+        uint64_t b = (uint64_t)(uint8_t)slots.slot[t];
+        if (t < 8) lo |= b << (8 * t); else hi |= b << (8 * (t - 8));
+    }
+    a.slots_lo = lo; a.slots_hi = hi;
+    a.n_poses = n_poses; a.xyz = xyz; a.grad_energy = grad_energy; a.energy = energy; a.grad_xyz = grad_xyz;
+    const int smem = ((lig_bytes + 127) & ~127) + kScoreWarps * (int)sizeof(WarpScratch);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    static int configured[64];
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (smem > configured[dev]) {
+        e = cudaFuncSetAttribute(score_xyz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured[dev] = smem;
+    }
+    int sms = 0, occ = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, score_xyz_kernel, kScoreWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    const int need = (n_poses + kScoreWarps - 1) / kScoreWarps;
+    const int grid = std::min(need, sms * (occ > 0 ? occ : 1));
+    if (grid < 1) return cudaSuccess;
+    score_xyz_kernel<<<grid, kScoreWarps * 32, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pose_coords(const PvLigBlob* lig, int lig_bytes, int n_poses, int pot_stride,

@@ -182,17 +182,26 @@ __device__ __forceinline__ float3 pair_force(uint32_t pw, const float4& xi, cons
 }
 
 // SF = e_inter + e_intra (Eq. 3) and, if want_grad, its tangent gradient (lane k holds
-// component k). parts (optional, lane-uniform): e_inter, e_intra.
-template <int LANES>
+// component k). parts (optional, lane-uniform): e_inter, e_intra. On return S.g holds dSF/dx of
+// every atom (device order). FK = false: the atoms are already posed in S.x (device order, w = XS
+// radius, written and synced by the caller), x is not used and there is no tangent gradient.
+template <int LANES, bool FK = true>
 __device__ __forceinline__ float team_eval(const PvLigBlob& L, WarpScratch& S, const Site& site,
                                            const Pose& x, float& grad, bool want_grad,
                                            float* parts = nullptr) {
     using Tm = Team<LANES>;
     const int tl = Tm::lane();
     const int n = L.h.n_atoms;
-    float3 axw, xa;
+    float3 axw = make_float3(0.f, 0.f, 0.f), xa = axw;
     float4 own[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
-    team_fk<LANES>(L, S, x, axw, xa, own);
+    if constexpr (FK) {
+        team_fk<LANES>(L, S, x, axw, xa, own);
+    } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (tl + LANES * h < n) own[h] = S.x[tl + LANES * h];
+        want_grad = false;
+    }
     const PvPocket& P = *site.P;
     float e_inter = 0.f, e_intra = 0.f;
     float3 acc[2];

@@ -219,3 +219,68 @@ def test_gather_microbenchmark_runs_and_rejects_bad_arguments():
     for kw in (dict(pocket=1), dict(pocket=-2), dict(n_points=0), dict(reps=0)):
         with pytest.raises(PVError):
             ctx.measure_gather(gs, **{**dict(pocket=0, n_points=1024, reps=1), **kw})
+
+
+def test_score_of_coordinates_matches_pose_score_and_oracle():
+    """pv_score_xyz: the SF of posed atom coordinates equals pv_score of the pose they come from,
+    and the oracle's SF and coordinate gradient at those coordinates (atoms within 2e-4 cells of
+    a face excluded from the gradient check: the field's gradient jumps there)."""
+    torch = pytest.importorskip("torch")
+    ctx = G.context()
+    rec, box, lig = _site(n_rec=3000, box_size=12.0, n_atoms=40, n_rot=7, seed=8)
+    L = O.OracleLigand(lig)
+    gs = ctx.build_grids(rec, [box], sorted(set(L.xs.tolist())))
+    pl = ctx.ligand(lig)
+    poses = torch.tensor(S.random_poses(400, box, L.n_rot, seed=9), dtype=torch.float32, device="cuda")
+    xyz = ctx.pose_coords(pl, poses)
+    e_pose, _, _ = ctx.score(gs, pl, 0, poses, grad=False)
+    e, g = ctx.score_xyz(gs, pl, 0, xyz)
+    assert G.close(e.cpu().numpy(), e_pose.cpu().numpy(), abs_tol=1e-5, rel_tol=1e-6).all()
+    x64 = xyz.double().cpu().numpy()
+    og = O.OracleGrid.lazy(rec, box, L.xs, O.xs_type_receptor(rec), x64.reshape(-1, 3), threads=G.threads())
+    ref = [L.score_atoms(og, x) for x in x64]
+    er = np.array([r[0] for r in ref])
+    assert G.close(e.cpu().numpy(), er).all(), np.abs(e.cpu().numpy() - er).max()
+    gr = np.stack([r[1] for r in ref])
+    gg = g.cpu().numpy()
+    far = ~_near_face(x64, box)
+    d = np.abs(gg[far] - gr[far])
+    assert (d <= G.GRAD_TOL * np.maximum(np.abs(gr[far]), 1.0)).all(), d.max()
+    # the scaled form (a vector-Jacobian product) is the plain gradient times the scale
+    w = torch.linspace(0.25, 2.0, 400, device="cuda")
+    _, gw = ctx.score_xyz(gs, pl, 0, xyz, grad_energy=w)
+    np.testing.assert_allclose(gw.cpu().numpy(), gg * w.cpu().numpy()[:, None, None], rtol=1e-6, atol=1e-6)
+
+
+def test_autograd_over_coordinates_vs_fd():
+    """PVScoreXYZ backward against FP64 central differences of the oracle over the coordinates."""
+    torch = pytest.importorskip("torch")
+    from paper_2506_20043_gb300.api import PVScoreXYZ
+    ctx = G.context()
+    rec, box, lig = _site(n_rec=3000, box_size=10.0, n_atoms=20, n_rot=4, seed=11)
+    L = O.OracleLigand(lig)
+    gs = ctx.build_grids(rec, [box], sorted(set(L.xs.tolist())))
+    pl = ctx.ligand(lig)
+    poses = torch.tensor(S.random_poses(32, box, L.n_rot, seed=12), dtype=torch.float32, device="cuda")
+    x = ctx.pose_coords(pl, poses).clone().requires_grad_(True)
+    e = PVScoreXYZ.apply(x, ctx, gs, pl, 0)
+    w = torch.linspace(0.5, 1.5, 32, device="cuda")
+    (e * w).sum().backward()
+    got = x.grad.cpu().numpy() / w.cpu().numpy()[:, None, None]
+    x64 = x.detach().double().cpu().numpy()
+    og = O.OracleGrid(rec, box, L.xs, rec_types=O.xs_type_receptor(rec), threads=G.threads())
+    checked = 0
+    for i in range(32):
+        if _near_face(x64[i][None], box, tol=1e-3)[0]:
+            continue
+        h = 1e-6
+        fd = np.zeros_like(x64[i])
+        for a in range(L.n):
+            for k in range(3):
+                p, m = x64[i].copy(), x64[i].copy()
+                p[a, k] += h
+                m[a, k] -= h
+                fd[a, k] = (L.score_atoms(og, p)[0] - L.score_atoms(og, m)[0]) / (2 * h)
+        assert (np.abs(got[i] - fd) <= G.GRAD_TOL * np.maximum(np.abs(fd), 1.0)).all(), (i, np.abs(got[i] - fd).max())
+        checked += 1
+    assert checked >= 16
