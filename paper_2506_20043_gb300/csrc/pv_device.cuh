@@ -33,9 +33,12 @@ __host__ __device__ inline bool xs_donor(int t) { return t == 3 || t == 5 || t =
 __host__ __device__ inline bool xs_acceptor(int t) { return t == 4 || t == 5 || t == 8 || t == 9; }
 
 // Weighted pair energy at distance r and (dE/dr) / r, from r^2 (< cutoff^2, checked by the caller):
-// one reciprocal square root gives both r and the force scale; the piecewise terms are written as
-// clamps with matching one-sided derivatives (the same values as vina_pair below).
-__device__ __forceinline__ float vina_pair_r2(float r2, float rsum, float hyd, float hb, float& dedr_over_r) {
+// one reciprocal square root gives both r and the force scale. The hydrophobic and H-bond terms
+// never meet in one pair (a hydrophobic carbon is neither donor nor acceptor), so they are one
+// clamped ramp sat((p1 - d) p2) with the pair's weight: p1 = 1.5, p2 = 1 for hydrophobic pairs,
+// p1 = 0, p2 = 1 / 0.7 for H-bond pairs; its derivative is -p2 on the ramp (the same values and
+// one-sided derivatives as vina_pair below).
+__device__ __forceinline__ float vina_pair_r2(float r2, float rsum, bool hyd, bool hb, float& dedr_over_r) {
     const float rinv = rsqrtf(fmaxf(r2, 1e-12f));
     const float r = r2 * rinv;
     const float d = r - rsum;
@@ -44,14 +47,13 @@ __device__ __forceinline__ float vina_pair_r2(float r2, float rsum, float hyd, f
     const float b = 0.5f * (d - 3.0f);           // (d - 3) / 2
     const float g2 = __expf(-b * b);
     const float rep = fminf(d, 0.0f);
-    const float hydv = __saturatef(1.5f - d);
-    const float hbv = __saturatef(d * (-1.0f / 0.7f));
-    const float dhyd = (d >= 0.5f && d < 1.5f) ? -1.0f : 0.0f;
-    const float dhb = (d >= -0.7f && d < 0.0f) ? (-1.0f / 0.7f) : 0.0f;
-    const float e = kWGauss1 * g1 + kWGauss2 * g2 + kWRepulsion * rep * rep +
-                    hyd * (kWHydrophobic * hydv) + hb * (kWHBond * hbv);
-    const float de = kWGauss1 * g1 * (-4.0f * a) + kWGauss2 * g2 * (-b) + (2.0f * kWRepulsion) * rep +
-                     hyd * (kWHydrophobic * dhyd) + hb * (kWHBond * dhb);
+    const float p1 = hyd ? 1.5f : 0.0f, p2 = hyd ? 1.0f : (1.0f / 0.7f);
+    const float w = hyd ? kWHydrophobic : (hb ? kWHBond : 0.0f);
+    const float t = (p1 - d) * p2;
+    const float v = __saturatef(t);
+    const float dv = (t > 0.0f && t <= 1.0f) ? -p2 : 0.0f;
+    const float e = kWGauss1 * g1 + kWGauss2 * g2 + kWRepulsion * rep * rep + w * v;
+    const float de = kWGauss1 * g1 * (-4.0f * a) + kWGauss2 * g2 * (-b) + (2.0f * kWRepulsion) * rep + w * dv;
     dedr_over_r = r2 > 1e-12f ? de * rinv : 0.0f;
     return e;
 }

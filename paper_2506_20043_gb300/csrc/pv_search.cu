@@ -169,7 +169,7 @@ __device__ float direct_inter(const PvLigBlob& L, const WarpScratch& S, const Pv
                 const bool hyd = xs_hydrophobic(ti[h]) && xs_hydrophobic(tj);
                 const bool hb = (xs_donor(ti[h]) && xs_acceptor(tj)) || (xs_acceptor(ti[h]) && xs_donor(tj));
                 float c;
-                e += vina_pair_r2(r2, xi[h].w + xs_radius(tj), hyd ? 1.f : 0.f, hb ? 1.f : 0.f, c);
+                e += vina_pair_r2(r2, xi[h].w + xs_radius(tj), hyd, hb, c);
             }
         }
     }

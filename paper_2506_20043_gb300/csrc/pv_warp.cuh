@@ -176,9 +176,10 @@ __device__ __forceinline__ float3 pair_force(uint32_t pw, const float4& xi, cons
     const float r2 = dot3(d, d);
     const bool live = (pw >> 31) && r2 < kCutoff2;
     float c;
-    const float e = vina_pair_r2(r2, xi.w + xj.w, (float)((pw >> 16) & 1), (float)((pw >> 17) & 1), c);
-    if (live) e_intra += e;
-    return live ? c * d : make_float3(0.f, 0.f, 0.f);
+    const float e = vina_pair_r2(r2, xi.w + xj.w, (pw >> 16) & 1, (pw >> 17) & 1, c);
+    e_intra += live ? e : 0.f;
+    c = live ? c : 0.f;
+    return c * d;
 }
 
 // SF = e_inter + e_intra (Eq. 3) and, if want_grad, its tangent gradient (lane k holds
