@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pv_oracle.c")
+_SRCS = (_SRC, os.path.join(_HERE, "pv_oracle_pocket.c"))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libpv_oracle.so")
 _lock = threading.Lock()
@@ -30,12 +31,14 @@ XS_NAMES = ("C_H", "C_P", "N_P", "N_D", "N_A", "N_DA", "O_P", "O_D", "O_A", "O_D
 
 
 def build(force: bool = False) -> str:
-    """Compile ``pv_oracle.c`` into ``oracle/_build/libpv_oracle.so`` (gcc, OpenMP)."""
+    """Compile ``pv_oracle.c`` and ``pv_oracle_pocket.c`` into ``oracle/_build/libpv_oracle.so``
+    (gcc, OpenMP)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(f) for f in _SRCS)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
         tmp = _SO + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-                               "-Wall", "-Wno-unused-function", "-o", tmp, _SRC, "-lm"])
+                               "-Wall", "-Wno-unused-function", "-o", tmp, *_SRCS, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -131,6 +134,13 @@ def lib():
             L.or_topk.argtypes = [C.c_int, dp, dp, C.c_int, C.c_int, C.c_double, ip]
             L.or_affinity.restype = C.c_double
             L.or_affinity.argtypes = [C.c_double, C.c_int]
+            L.or_sphere_lattice.argtypes = [C.c_int, dp]
+            L.or_sas_points.argtypes = [C.c_int, dp, dp, C.c_double, C.c_int, C.c_int, ip, u8p, dp, dp]
+            L.or_point_features.argtypes = [C.c_int, dp, C.c_int, dp, C.c_int, dp, C.c_double,
+                                            C.c_double, dp, ip]
+            L.or_cluster_points.restype = C.c_int
+            L.or_cluster_points.argtypes = [C.c_int, dp, dp, C.c_double, C.c_double, ip, ip, dp, dp,
+                                            ip, ip]
             _lib = L
     return _lib
 
@@ -523,3 +533,63 @@ def merge_pockets(results: List[PairResult]):
         for s, c in zip(r.scores, r.kept):
             rows.append((float(s), int(r.pocket), int(c)))
     return sorted(rows)
+
+
+# ------------------------------------------------- pocket side (Supplementary Algorithm 1) --
+
+def sphere_lattice(n: int) -> np.ndarray:
+    """The n directions of the spherical Fibonacci lattice, float64 [n, 3]."""
+    out = np.zeros((max(n, 1), 3))
+    lib().or_sphere_lattice(int(n), _p(out))
+    return out[:n]
+
+
+def sas_points(xyz, radius, probe: float, n_sphere: int, atoms=None):
+    """Step 1 (numerical SAS). Returns (keep uint8, points float64 [., 3], margin float64), rows
+    ordered (atom, lattice direction) over ``atoms`` (default: every atom)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    radius = np.ascontiguousarray(radius, dtype=np.float64)
+    sel = None if atoms is None else np.ascontiguousarray(atoms, dtype=np.int32)
+    rows = (xyz.shape[0] if sel is None else sel.shape[0]) * n_sphere
+    keep = np.zeros(max(rows, 1), np.uint8)
+    pts = np.zeros((max(rows, 1), 3))
+    margin = np.zeros(max(rows, 1))
+    lib().or_sas_points(xyz.shape[0], _p(xyz), _p(radius), float(probe), int(n_sphere),
+                        0 if sel is None else sel.shape[0], None if sel is None else _p(sel, C.c_int32),
+                        _p(keep, C.c_uint8), _p(pts), _p(margin))
+    return keep[:rows], pts[:rows], margin[:rows]
+
+
+def point_features(xyz, props, pts, r_feat: float = 6.0, r_prot: float = 10.0):
+    """Step 2: Eq. 1 sums [n_pts, n_props] and protrusion counts [n_pts] at the given points."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    props = np.ascontiguousarray(props, dtype=np.float64).reshape(xyz.shape[0], -1)
+    pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+    feat = np.zeros((max(pts.shape[0], 1), props.shape[1]))
+    prot = np.zeros(max(pts.shape[0], 1), np.int32)
+    lib().or_point_features(xyz.shape[0], _p(xyz), props.shape[1], _p(props), pts.shape[0], _p(pts),
+                            float(r_feat), float(r_prot), _p(feat), _p(prot, C.c_int32))
+    return feat[:pts.shape[0]], prot[:pts.shape[0]]
+
+
+@dataclasses.dataclass
+class Clusters:
+    root: np.ndarray       # [n] lowest point index of the point's cluster, -1 below threshold
+    cluster: np.ndarray    # [n] rank of the point's cluster, -1 below threshold
+    score: np.ndarray      # [K] Eq. 2 score, descending
+    center: np.ndarray     # [K, 3]
+    size: np.ndarray       # [K]
+    first: np.ndarray      # [K] lowest point index
+
+
+def cluster_points(pts, score, theta: float, link: float = 3.0) -> Clusters:
+    """Steps 4-5: threshold, single-linkage clusters, Eq. 2 scores, centres, ranking."""
+    pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+    score = np.ascontiguousarray(score, dtype=np.float64)
+    n = pts.shape[0]
+    m = max(n, 1)
+    root, cl = np.zeros(m, np.int32), np.zeros(m, np.int32)
+    cs, cc, sz, fi = np.zeros(m), np.zeros((m, 3)), np.zeros(m, np.int32), np.zeros(m, np.int32)
+    k = lib().or_cluster_points(n, _p(pts), _p(score), float(theta), float(link), _p(root, C.c_int32),
+                                _p(cl, C.c_int32), _p(cs), _p(cc), _p(sz, C.c_int32), _p(fi, C.c_int32))
+    return Clusters(root[:n], cl[:n], cs[:k], cc[:k], sz[:k], fi[:k])
