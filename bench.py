@@ -535,6 +535,149 @@ def run_batch_workload(args):
                                                  n_pairs=1 if len(pair_lig) == 1 else 3))}
 
 
+def run_pocket_workload(args):
+    """Pocket prediction (Supplementary Algorithm 1, Steps 1, 2, 4, 5; the classifier of Step 3 is
+    replaced by a synthetic score given as input): each step takes 16 receptors of 8,000 atoms
+    with 10 carved pockets each to SAS points (100 lattice points per atom, 1.6 A probe, Bondi
+    radii), their Eq. 1 sums over 7 property columns with the protrusion count, and the ranked
+    single-linkage clusters of the points scoring >= 0.5. Its own JSON line: receptors/s, with
+    the feature kernel's roofline."""
+    import torch
+    import paper_2506_20043_gb300 as pv
+    pv.build()
+    from paper_2506_20043_gb300 import api
+    ctx = api.Context(0)
+    n_rec, n_atoms, n_pockets = 16, 8000, 10
+    prm = api.PocketParams(n_sphere=100)
+    sites = [S.pocket_site(seed, n_atoms, n_pockets) for seed in range(n_rec)]
+    dev = torch.device("cuda", 0)
+    recs = [S.Receptor(torch.tensor(s.receptor.xyz, dtype=torch.float32, device=dev),
+                       torch.tensor(s.receptor.element, device=dev), torch.tensor(s.receptor.donor, device=dev),
+                       torch.tensor(s.receptor.acceptor, device=dev)) for s in sites]
+    host_recs = [S.Receptor(np.asarray(s.receptor.xyz, np.float32), s.receptor.element, s.receptor.donor,
+                            s.receptor.acceptor) for s in sites]
+    props_h = [S.atom_properties(s.receptor, i) for i, s in enumerate(sites)]
+    props = [torch.tensor(p, device=dev) for p in props_h]
+    # the stand-in scores of every receptor's points (an input of Step 4, computed once)
+    scores_h = []
+    for i, r in enumerate(recs):
+        surf = ctx.surface(r, params=prm)
+        scores_h.append(S.ligandability(surf.points().cpu().numpy(), sites[i], i))
+    scores = [torch.tensor(x, device=dev) for x in scores_h]
+    stream = ctx.stream
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    feat_ms = []
+
+    def step(timed_features=False):
+        out = []
+        for i in range(n_rec):
+            surf = ctx.surface(recs[i], params=prm)
+            if timed_features:
+                f0.record(stream)
+            feat, prot = surf.features(props[i], params=prm)
+            if timed_features:
+                f1.record(stream)
+                f1.synchronize()
+                feat_ms.append(f0.elapsed_time(f1))
+            cl = ctx.cluster(surf.points(), scores[i], prm)
+            out.append((surf, feat, prot, cl))
+        return out
+
+    def step_e2e():
+        h2d = d2h = 0
+        for i in range(n_rec):
+            r = host_recs[i]
+            surf = ctx.surface(r, params=prm)
+            feat, prot = surf.features(props_h[i], params=prm)
+            cl = ctx.cluster(surf.points(), scores_h[i], prm)
+            res = cl.read()
+            feat_h = feat.cpu().numpy()
+            h2d += r.xyz.nbytes + r.element.nbytes + props_h[i].nbytes + scores_h[i].nbytes
+            d2h += feat_h.nbytes + sum(v.nbytes for v in res.values()) + 8
+        return h2d, d2h
+
+    for _ in range(args.warmup):
+        out = step()
+    torch.cuda.synchronize()
+    n_points = sum(o[0].n_points for o in out)
+    n_clusters = [o[3].n_clusters for o in out]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) * 1e-3)
+        e2e_t = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h2d, d2h = step_e2e()
+            torch.cuda.synchronize()
+            e2e_t.append(time.perf_counter() - t0)
+    clocks = clk.summary()
+    # the feature kernel alone (events around its one launch), and its algorithmic work: the
+    # distance test of every (point, atom) pair within r_protrusion, plus the weight and the
+    # 2 x 7 property FLOPs of every pair within r_feature (counted with r_protrusion = r_feature)
+    for _ in range(2):
+        step(timed_features=True)
+    feat_s = float(np.mean(feat_ms)) * 1e-3
+    pairs10 = pairs6 = 0
+    n6 = api.PocketParams(n_sphere=100, r_protrusion=6.0)
+    for i in range(n_rec):
+        surf = out[i][0]
+        pairs10 += int(out[i][2].to(torch.int64).sum())
+        pairs6 += int(surf.features(props[i][:, :1], params=n6)[1].to(torch.int64).sum())
+    flops = (pairs10 * 8 + pairs6 * (4 + 2 * 7)) / n_rec
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    max_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = n_sm * 128 * 2 * max_mhz * 1e6 / 1e12
+    achieved = flops / feat_s / 1e12
+    total_t = float(np.sum(times))
+    cpu = None
+    if not args.no_cpu:
+        import oracle as O
+        s0 = sites[0]
+        rec = s0.receptor
+        xyz = np.asarray(rec.xyz, np.float32).astype(np.float64)
+        rad = np.asarray(S.vdw_radii(rec), np.float32).astype(np.float64)
+        t0 = time.perf_counter()
+        keep, pts, _ = O.sas_points(xyz, rad, prm.probe, prm.n_sphere)
+        pts = pts[keep == 1]
+        O.point_features(xyz, props_h[0].astype(np.float64), pts)
+        O.cluster_points(pts, S.ligandability(pts, s0, 0).astype(np.float64), prm.threshold, prm.link)
+        dt = time.perf_counter() - t0
+        cpu = {"value": round(1.0 / dt, 4), "unit": "receptors/s", "cores": len(os.sched_getaffinity(0)),
+               "kind": "oracle", "sample": "one whole 8,000-atom receptor: FP64 SAS points, Eq. 1 sums and "
+                                           "protrusion at its points, clusters (brute force over all pairs)"}
+    return {"metric": "pocket predictions/sec (SAS points, Eq. 1 features, Eq. 2 clusters) at 1 GB300",
+            "value": round(n_rec * args.steps / total_t, 2), "unit": "receptors/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_t / args.steps * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "pocket prediction: 16 receptors of 8,000 atoms (0.05 per cubic A) with 10 carved "
+                                   "pockets each; 100 lattice points per atom, 1.6 A probe, Bondi radii; Eq. 1 over 7 "
+                                   "property columns (6 A), protrusion (10 A); clusters of points scoring >= 0.5 "
+                                   "(synthetic score), 3 A single linkage",
+                       "points_per_receptor": round(n_points / n_rec, 1),
+                       "clusters_per_receptor": round(float(np.mean(n_clusters)), 1),
+                       "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                       "inputs": "receptors, property columns and scores resident in HBM"},
+            "points_per_s": round(n_points * args.steps / total_t, 1),
+            "roofline": {"kernel": "feature_kernel", "bound": "alu", "achieved": round(achieved, 4),
+                         "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 5),
+                         "traffic": None, "launch_ms": round(feat_s * 1e3, 4),
+                         "flops_per_launch": round(flops, 1)},
+            "e2e": {"value": round(n_rec * args.steps / float(np.sum(e2e_t)), 2), "unit": "receptors/s",
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "clocks": clocks, "cpu_baseline": cpu}
+
+
 def oracle_pairs_sample(w, pair_lig, pair_pocket, name, budget_s=12.0, n_pairs=3, seed=7):
     """The FP64 oracle on a seeded sample of the workload's pairs: for each sampled pair, the
     pocket's full grid maps (their cost shared by the pairs docked into that pocket) and as many
@@ -611,7 +754,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-micro", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", choices=["multipocket", "tiny", "uneven", "screening", "boxsweep"], default="multipocket",
+    ap.add_argument("--workload", choices=["multipocket", "tiny", "uneven", "screening", "boxsweep", "pockets"],
+                    default="multipocket",
                     help="multipocket: the headline line; uneven / screening / boxsweep: other shapes, their own line")
     ap.add_argument("--focc", type=int, default=0,
                     help="consistency check (Eq. 4-5) with this many neighbours per chain; 0 = off (headline)")
@@ -624,6 +768,8 @@ def main():
     args = ap.parse_args()
     if args.case == "small":
         out = run_small_case(args)
+    elif args.workload == "pockets" and args.impl == "ours":
+        out = run_pocket_workload(args)
     elif args.workload != "multipocket" and args.impl == "ours":
         out = run_batch_workload(args)
     else:

@@ -339,6 +339,86 @@ pv_status pv_dock_result_read_chains(const pv_dock_result* r, float* dst);
 
 void pv_dock_result_destroy(pv_dock_result* r);
 
+/* ---------------------------------------------- pocket side (Supplementary Algorithm 1) --- */
+
+/* The pocket prediction that feeds the docking (Methods "Pocket Prediction with P2Rank",
+ * Supplementary Algorithm 1): solvent-accessible surface (SAS) points of the receptor (Step 1),
+ * the distance-weighted property sums of Eq. 1 and the protrusion count at points (Step 2),
+ * and, given a ligandability score per point (Step 3's Random Forest is not part of this
+ * library: its scores are an input), the single-linkage clusters of the high-scoring points with
+ * their Eq. 2 scores, centres and ranking (Steps 4-5). The cluster centres are the pocket
+ * centres that pv_build_grids' boxes are placed on (Algorithm 3). */
+typedef struct pv_surface pv_surface;
+typedef struct pv_clusters pv_clusters;
+
+#define PV_MAX_SPHERE_POINTS 1024
+#define PV_MAX_PROPS 64
+
+typedef struct {
+    float probe;               /* solvent probe radius added to every atom radius, A (1.6) */
+    int32_t n_sphere;          /* lattice points per atom sphere, 1 .. PV_MAX_SPHERE_POINTS (100) */
+    float r_feature;           /* Eq. 1 neighbourhood: weight max(0, 1 - d / r_feature), A (6.0) */
+    float r_protrusion;        /* protrusion = atoms with d <= r_protrusion, A (10.0) */
+    float threshold;           /* points with score >= threshold are clustered (0.5) */
+    float link;                /* single-linkage distance: hops of at most link A join (3.0) */
+} pv_pocket_params;
+
+pv_status pv_pocket_params_default(pv_pocket_params* p);
+
+/* Step 1. The numerical SAS: every atom i carries n_sphere points x_i + a_i u_k on its expanded
+ * sphere, a_i = R_i + probe, u_k (k = 0 .. n_sphere-1) the spherical Fibonacci lattice
+ * (z_k = 1 - (2k + 1) / n_sphere, azimuth k pi (3 - sqrt 5)); a point is kept unless it lies
+ * strictly inside another atom's expanded sphere (|p - x_j| < a_j, float32 arithmetic).
+ *   - radius: per-atom vdW radii R_i [n_atoms] in the receptor's memory kind, or NULL for the
+ *     Bondi radii by element (C 1.70, N 1.55, O 1.52, S 1.80 A). Only xyz and element of the
+ *     receptor are read (element only when radius is NULL); at most 200,000 atoms.
+ *   - The kept points are ordered by atom index, then k. The surface keeps the binned atoms for
+ *     pv_surface_features. Synchronous (it returns the point count).
+ * Errors: PV_ERR_ARG on sizes, an element > 3, a radius outside (0, 10] A or a non-finite
+ * coordinate; PV_ERR_OOM; PV_ERR_CUDA. */
+pv_status pv_surface_create(pv_context* ctx, const pv_receptor* receptor, const float* radius,
+                            const pv_pocket_params* p, pv_surface** out);
+pv_status pv_surface_info(const pv_surface* s, int32_t* n_atoms, int32_t* n_points);
+/* Copies the points (float32 [n_points][3]) and, if src is not NULL, each point's source
+ * (atom * n_sphere + k, int32 [n_points]) into host or device memory (mem). Synchronous. */
+pv_status pv_surface_read(pv_context* ctx, const pv_surface* s, float* xyz, int32_t* src, int32_t mem);
+/* The surface's points on the device (borrowed, valid until destroy): float32 [n_points][3]. */
+pv_status pv_surface_points(const pv_surface* s, const float** dev_xyz);
+
+/* Step 2 at n_points points: features[p][q] = sum over receptor atoms a of
+ * max(0, 1 - |x_a - p| / r_feature) * props[a][q] (Eq. 1) and protrusion[p] = the number of
+ * atoms with |x_a - p| <= r_protrusion (float32 arithmetic).
+ *   - xyz: float32 [n_points][3] in memory kind xyz_mem, or NULL for the surface's own points
+ *     (n_points must then equal its count). props: float32 [n_atoms][n_props] in receptor atom
+ *     order, memory kind props_mem, 1 <= n_props <= PV_MAX_PROPS.
+ *   - dev_features: float32 [n_points][n_props]; dev_protrusion: int32 [n_points] (nullable).
+ *   - Points are handled 32 at a time over the cells their bounding box reaches: keep nearby
+ *     points adjacent (the surface's order is) for speed; any order gives the same sums.
+ *   Asynchronous. Errors: PV_ERR_ARG, PV_ERR_OOM, PV_ERR_CUDA. */
+pv_status pv_surface_features(pv_context* ctx, const pv_surface* s, int32_t n_points,
+                              const float* xyz, int32_t xyz_mem, int32_t n_props, const float* props,
+                              int32_t props_mem, const pv_pocket_params* p, float* dev_features,
+                              int32_t* dev_protrusion);
+void pv_surface_destroy(pv_surface* s);
+
+/* Steps 4-5 over n_points points (dev_xyz float32 [n][3], dev_score float32 [n], device memory):
+ * points with score >= threshold (a NaN score is below it) are joined when a chain of such points
+ * links them with every hop |p - q| <= link (float32 arithmetic); each cluster K gets the Eq. 2
+ * score S_K = sum of s_p^2 (accumulated in float64), its centre (the mean of its points), its
+ * size and its lowest point index; clusters are ranked by S_K descending, ties by the lowest
+ * point index. Synchronous (it returns the cluster count). Ranking costs O(K^2) for K clusters.
+ * Errors: PV_ERR_ARG on sizes, link <= 0, or a clustered point with a non-finite coordinate or
+ * one beyond 2^30 link lengths from the origin; PV_ERR_OOM; PV_ERR_CUDA. */
+pv_status pv_cluster_points(pv_context* ctx, int32_t n_points, const float* dev_xyz,
+                            const float* dev_score, const pv_pocket_params* p, pv_clusters** out);
+pv_status pv_clusters_info(const pv_clusters* c, int32_t* n_points, int32_t* n_clusters);
+/* Copies, into host or device memory (mem), each nullable: cluster[n_points] (the rank of the
+ * point's cluster, -1 below the threshold), and per cluster in rank order score[K],
+ * center[K][3], size[K], first[K] (lowest point index). Synchronous. */
+pv_status pv_clusters_read(pv_context* ctx, const pv_clusters* c, int32_t* cluster, float* score,
+                           float* center, int32_t* size, int32_t* first, int32_t mem);
+void pv_clusters_destroy(pv_clusters* c);
+
 /* -------------------------------------------------------- allocation-free grid build --- */
 
 /* Sizes of the fixed device scratch used by pv_build_grid_noalloc. */

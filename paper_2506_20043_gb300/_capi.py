@@ -48,6 +48,11 @@ class pv_pose(C.Structure):
                 ("e_inter_grid", C.c_float), ("pad", C.c_int32 * 2)]
 
 
+class pv_pocket_params(C.Structure):
+    _fields_ = [("probe", C.c_float), ("n_sphere", C.c_int32), ("r_feature", C.c_float),
+                ("r_protrusion", C.c_float), ("threshold", C.c_float), ("link", C.c_float)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
@@ -94,6 +99,17 @@ SIGNATURES = {
     "pv_dock_result_read_chains": (i32, [vp, vp]),
     "pv_dock_result_destroy": (None, [vp]),
     "pv_build_grid_noalloc": (i32, [vp, C.POINTER(pv_receptor), C.POINTER(pv_box), C.POINTER(C.c_uint8), i32, vp]),
+    "pv_pocket_params_default": (i32, [C.POINTER(pv_pocket_params)]),
+    "pv_surface_create": (i32, [vp, C.POINTER(pv_receptor), vp, C.POINTER(pv_pocket_params), C.POINTER(vp)]),
+    "pv_surface_info": (i32, [vp, pi32, pi32]),
+    "pv_surface_read": (i32, [vp, vp, vp, vp, i32]),
+    "pv_surface_points": (i32, [vp, C.POINTER(vp)]),
+    "pv_surface_features": (i32, [vp, vp, i32, vp, i32, i32, vp, i32, C.POINTER(pv_pocket_params), vp, vp]),
+    "pv_surface_destroy": (None, [vp]),
+    "pv_cluster_points": (i32, [vp, i32, vp, vp, C.POINTER(pv_pocket_params), C.POINTER(vp)]),
+    "pv_clusters_info": (i32, [vp, pi32, pi32]),
+    "pv_clusters_read": (i32, [vp, vp, vp, vp, vp, vp, vp, i32]),
+    "pv_clusters_destroy": (None, [vp]),
 }
 
 _lib = None

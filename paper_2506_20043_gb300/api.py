@@ -71,6 +71,23 @@ class DockParams:
         return p
 
 
+@dataclasses.dataclass
+class PocketParams:
+    """Parameters of the pocket-side steps (Supplementary Algorithm 1)."""
+    probe: float = 1.6             # solvent probe radius added to the atom radii, A
+    n_sphere: int = 100            # lattice points per atom sphere
+    r_feature: float = 6.0         # Eq. 1 neighbourhood radius, A
+    r_protrusion: float = 10.0     # protrusion count radius, A
+    threshold: float = 0.5         # points with score >= threshold are clustered
+    link: float = 3.0              # single-linkage distance, A
+
+    def to_c(self) -> A.pv_pocket_params:
+        p = A.pv_pocket_params()
+        for f in dataclasses.fields(self):
+            setattr(p, f.name, getattr(self, f.name))
+        return p
+
+
 class Context:
     """A library context on one CUDA device, issuing work on a torch stream and allocating
     device memory through torch's caching allocator."""
@@ -161,6 +178,45 @@ class Context:
         self._check(self.lib.pv_build_grids(self.h, C.byref(r), bx, len(boxes), types, len(lig_types), C.byref(h)),
                     "pv_build_grids")
         return GridSet(self, h)
+
+    # ---------------------------------------------------------------------- pocket side --
+    def surface(self, receptor, radius=None, params: Optional[PocketParams] = None) -> "Surface":
+        """Step 1 of Supplementary Algorithm 1: the receptor's SAS points (pv_surface_create).
+        radius: per-atom vdW radii in the receptor's memory kind, or None for the Bondi radii."""
+        torch = self.torch
+        keep: list = []
+        r = self._receptor(receptor, keep)
+        rad = None
+        if radius is not None:
+            if isinstance(radius, torch.Tensor):
+                rad = radius.to(torch.float32).contiguous()
+                if rad.is_cuda != (r.mem == A.PV_MEM_DEVICE):
+                    raise PVError("radius must live where the receptor does")
+            else:
+                if r.mem != A.PV_MEM_HOST:
+                    raise PVError("radius must live where the receptor does")
+                rad = _np(radius, np.float32)
+            keep.append(rad)
+        p = (params or PocketParams()).to_c()
+        h = C.c_void_p()
+        self._check(self.lib.pv_surface_create(self.h, C.byref(r), None if rad is None else _ptr(rad), C.byref(p),
+                                               C.byref(h)), "pv_surface_create")
+        return Surface(self, h)
+
+    def cluster(self, points, scores, params: Optional[PocketParams] = None) -> "Clusters":
+        """Steps 4-5: threshold, single-linkage clusters, Eq. 2 scores, centres and ranking of the
+        points (pv_cluster_points). points [n, 3] and scores [n] are moved to the device."""
+        torch = self.torch
+        dev = torch.device("cuda", self.device)
+        pts = torch.as_tensor(points, dtype=torch.float32).to(dev).contiguous().reshape(-1, 3)
+        sc = torch.as_tensor(scores, dtype=torch.float32).to(dev).contiguous().reshape(-1)
+        if sc.shape[0] != pts.shape[0]:
+            raise PVError("one score per point required")
+        p = (params or PocketParams()).to_c()
+        h = C.c_void_p()
+        self._check(self.lib.pv_cluster_points(self.h, int(pts.shape[0]), pts.data_ptr(), sc.data_ptr(), C.byref(p),
+                                               C.byref(h)), "pv_cluster_points")
+        return Clusters(self, h)
 
     # --------------------------------------------------------------------------- ligands --
     def ligand(self, lig) -> "Ligand":
@@ -507,3 +563,94 @@ class PVScoreXYZ:
 
             cls._fn = _F
         return cls._fn.apply(xyz, ctx, grids, lig, pocket)
+
+
+class Surface:
+    """Solvent-accessible surface points of a receptor (pv_surface_*)."""
+
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+        na, npt = C.c_int32(), C.c_int32()
+        ctx.lib.pv_surface_info(h, C.byref(na), C.byref(npt))
+        self.n_atoms, self.n_points = na.value, npt.value
+
+    def points(self):
+        """float32 [n_points, 3] device tensor (a copy), ordered by atom, then lattice point."""
+        torch = self.ctx.torch
+        out = torch.empty((self.n_points, 3), dtype=torch.float32, device=torch.device("cuda", self.ctx.device))
+        self.ctx._check(self.ctx.lib.pv_surface_read(self.ctx.h, self.h, out.data_ptr(), None, A.PV_MEM_DEVICE),
+                        "pv_surface_read")
+        return out
+
+    def sources(self) -> np.ndarray:
+        """int32 [n_points]: atom * n_sphere + lattice index of every point."""
+        out = np.zeros(max(self.n_points, 1), dtype=np.int32)
+        self.ctx._check(self.ctx.lib.pv_surface_read(self.ctx.h, self.h, None, out.ctypes.data, A.PV_MEM_HOST),
+                        "pv_surface_read")
+        return out[:self.n_points]
+
+    def features(self, props, points=None, params: Optional[PocketParams] = None):
+        """Step 2 (Eq. 1 and protrusion) at the surface's points, or at given points [n, 3].
+        props: [n_atoms, n_props] in receptor atom order. Returns device tensors
+        (features float32 [n, n_props], protrusion int32 [n])."""
+        torch = self.ctx.torch
+        dev = torch.device("cuda", self.ctx.device)
+        pr = torch.as_tensor(props, dtype=torch.float32).to(dev).contiguous()
+        if pr.ndim != 2 or pr.shape[0] != self.n_atoms:
+            raise PVError("props must be [n_atoms, n_props]")
+        if points is None:
+            n, xp = self.n_points, None
+        else:
+            pts = torch.as_tensor(points, dtype=torch.float32).to(dev).contiguous().reshape(-1, 3)
+            n, xp = int(pts.shape[0]), pts
+        feat = torch.empty((n, pr.shape[1]), dtype=torch.float32, device=dev)
+        prot = torch.empty(n, dtype=torch.int32, device=dev)
+        if n == 0 and xp is not None and pr.shape[1] > 0:
+            return feat, prot          # an empty tensor's pointer is NULL, which means "the surface's points"
+        p = (params or PocketParams()).to_c()
+        self.ctx._check(self.ctx.lib.pv_surface_features(
+            self.ctx.h, self.h, n, None if xp is None else xp.data_ptr(), A.PV_MEM_DEVICE, int(pr.shape[1]),
+            pr.data_ptr(), A.PV_MEM_DEVICE, C.byref(p), feat.data_ptr(), prot.data_ptr()), "pv_surface_features")
+        return feat, prot
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.ctx.h:
+            self.ctx.lib.pv_surface_destroy(self.h)
+            self.h = None
+
+
+class Clusters:
+    """Ranked single-linkage clusters of high-scoring points (pv_clusters_*)."""
+
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+        n, k = C.c_int32(), C.c_int32()
+        ctx.lib.pv_clusters_info(h, C.byref(n), C.byref(k))
+        self.n_points, self.n_clusters = n.value, k.value
+
+    def read(self) -> dict:
+        """Host arrays: cluster [n_points] (rank of the point's cluster, -1 below the threshold),
+        and per cluster in rank order score [K] (Eq. 2), center [K, 3], size [K], first [K]."""
+        n, k = self.n_points, self.n_clusters
+        out = {"cluster": np.zeros(max(n, 1), np.int32), "score": np.zeros(max(k, 1), np.float32),
+               "center": np.zeros((max(k, 1), 3), np.float32), "size": np.zeros(max(k, 1), np.int32),
+               "first": np.zeros(max(k, 1), np.int32)}
+        self.ctx._check(self.ctx.lib.pv_clusters_read(self.ctx.h, self.h, *(out[x].ctypes.data for x in
+                                                                              ("cluster", "score", "center", "size", "first")),
+                                                      A.PV_MEM_HOST), "pv_clusters_read")
+        out["cluster"] = out["cluster"][:n]
+        for x in ("score", "center", "size", "first"):
+            out[x] = out[x][:k]
+        return out
+
+    def boxes(self, size: float = 20.0, spacing: float = 0.375, max_pockets: int = 0) -> list:
+        """Search boxes centred on the ranked cluster centres (Algorithm 3), best first."""
+        c = self.read()["center"]
+        if max_pockets > 0:
+            c = c[:max_pockets]
+        return [(tuple(float(v) for v in x), (size, size, size), spacing) for x in c]
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.ctx.h:
+            self.ctx.lib.pv_clusters_destroy(self.h)
+            self.h = None

@@ -1,0 +1,1087 @@
+// pv_pocket.cu -- the pocket side of PocketVina (Methods "Pocket Prediction with P2Rank",
+// Eq. 1-2, Supplementary Algorithm 1): solvent-accessible surface points of a receptor, the
+// distance-weighted property sums of Eq. 1 with the protrusion count at points, and the
+// single-linkage clusters of high-scoring points with their Eq. 2 scores, centres and ranking.
+//
+// Layout. Receptor atoms are binned into cubic cells of kCell A over their bounding box (CSR,
+// input order kept within a cell, so every sum below runs in a fixed order). The SAS kernel runs
+// one warp per atom: the warp gathers the atoms whose expanded spheres can reach its sphere into
+// a shared-memory list (ballot compaction) and each lane tests the lattice points
+// lane + 32 m against it, keeping one burial bit per point in a register. The feature kernel runs
+// one warp per 32 consecutive points: the atoms of the cells within reach of the warp's bounding
+// box are staged 32 at a time in shared memory with one chunk of their property columns, and every
+// lane accumulates its point's sums in registers. Clustering hashes points into link-sized cells,
+// joins neighbours with a lock-free union-find that always hooks the larger root under the smaller
+// (so a component's root is its lowest index), and reduces per root in float64.
+//
+// Device memory comes from the stream-ordered pool (cudaMallocAsync on the context's stream) and
+// goes back to it on that stream when the handle is destroyed.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pocketvina.h"
+#include "pv_internal.h"
+
+namespace {
+
+constexpr int kSurfaceMagic = 0x53524631;
+constexpr int kClustersMagic = 0x434c5331;
+constexpr float kCell = 4.0f;            // atom binning cell edge, A
+constexpr int kMaxAtoms = 200000;
+constexpr int kNb = 128;                 // neighbour list capacity per warp (SAS kernel)
+constexpr int kSasWarps = 4;
+constexpr int kFeatWarps = 4;
+constexpr int kPropChunk = 8;            // property columns per feature launch row
+constexpr double kPi = 3.14159265358979323846;
+
+// Bondi (J. Phys. Chem. 68, 441, 1964) van der Waals radii by element: C, N, O, S.
+__constant__ float c_bondi[4] = {1.70f, 1.55f, 1.52f, 1.80f};
+
+struct AtomGrid {
+    float lo[3];
+    float inv_cell;
+    int cd[3];
+};
+
+enum : int { kErrElement = 1, kErrRadius = 2, kErrCoord = 4, kErrUnion = 8 };
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+__device__ __forceinline__ int cell_coord(float x, float lo, float inv, int cd) {
+    return clampi(__float2int_rd((x - lo) * inv), 0, cd - 1);
+}
+
+// One lattice point of atom A (radius a): the same expression wherever a point is formed.
+__device__ __forceinline__ float3 sphere_point(const float4& A, float a, const float* dirs, int k) {
+    return make_float3(fmaf(a, __ldg(dirs + 3 * k), A.x), fmaf(a, __ldg(dirs + 3 * k + 1), A.y),
+                       fmaf(a, __ldg(dirs + 3 * k + 2), A.z));
+}
+
+// ------------------------------------------------------------------------------ binning ---
+
+// Atoms in input order as (x, y, z, index bits), expanded radius a_i = R_i + probe, cell key.
+__global__ void prep_atoms_kernel(const float* __restrict__ xyz, const uint8_t* __restrict__ element,
+                                  const float* __restrict__ radius, float probe, int n, AtomGrid G,
+                                  float4* __restrict__ atoms, float* __restrict__ arad,
+                                  int* __restrict__ key, int* __restrict__ count, int* __restrict__ err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+    float r;
+    if (radius) {
+        r = radius[i];
+        if (!(r > 0.f && r <= 10.f)) atomicOr(err, kErrRadius);
+    } else {
+        const int e = element[i];
+        if (e > 3) atomicOr(err, kErrElement);
+        r = c_bondi[e & 3];
+    }
+    if (!(isfinite(x) && isfinite(y) && isfinite(z))) atomicOr(err, kErrCoord);
+    atoms[i] = make_float4(x, y, z, __int_as_float(i));
+    arad[i] = r + probe;
+    const int c = (cell_coord(z, G.lo[2], G.inv_cell, G.cd[2]) * G.cd[1] +
+                   cell_coord(y, G.lo[1], G.inv_cell, G.cd[1])) * G.cd[0] +
+                  cell_coord(x, G.lo[0], G.inv_cell, G.cd[0]);
+    key[i] = c;
+    atomicAdd(&count[c], 1);
+}
+
+// Exclusive scan of count[0 .. n) into start[0 .. n] by one CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) scan_kernel(const int* __restrict__ count, int n,
+                                                    int* __restrict__ start) {
+    __shared__ int s_warp[32];
+    __shared__ int s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int base = 0; base < n; base += 1024) {
+        const int i = base + threadIdx.x;
+        const int v = i < n ? count[i] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = s_warp[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        const int carry = s_carry;
+        const int incl = x + (warp ? s_warp[warp - 1] : 0) + carry;
+        if (i < n) start[i] = incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) s_carry = incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) start[n] = s_carry;
+}
+
+// Unstable placement: each element with key >= 0 takes a slot of its key's segment.
+__global__ void scatter_kernel(const int* __restrict__ key, int n, const int* __restrict__ start,
+                               int* __restrict__ cursor, int* __restrict__ slot_elem) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int k = key[i];
+    if (k < 0) return;
+    slot_elem[start[k] + atomicAdd(&cursor[k], 1)] = i;
+}
+
+// Stable order: within a segment, an element's rank is the number of lower indices in it.
+// Only the start[n_keys] placed slots are read.
+__global__ void stable_kernel(const int* __restrict__ key, const int* __restrict__ slot_elem, int n,
+                              const int* __restrict__ start, int n_keys, int* __restrict__ order) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n || s >= start[n_keys]) return;
+    const int i = slot_elem[s];
+    const int k = key[i], b = start[k], e = start[k + 1];
+    int r = 0;
+    for (int t = b; t < e; ++t) r += slot_elem[t] < i;
+    order[b + r] = i;
+}
+
+__global__ void gather_atoms_kernel(const int* __restrict__ order, int n, const float4* __restrict__ atoms,
+                                    float4* __restrict__ sorted) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) sorted[s] = atoms[order[s]];
+}
+
+// Stable CSR of n keys in [0, n_keys) (key < 0: left out): start[n_keys + 1], order[count].
+cudaError_t bin_keys(const int* key, int n, int n_keys, const int* count, int* start, int* cursor,
+                     int* slot_elem, int* order, cudaStream_t s) {
+    scan_kernel<<<1, 1024, 0, s>>>(count, n_keys, start);
+    cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(int) * n_keys, s);
+    if (e != cudaSuccess) return e;
+    const int b = (n + 255) / 256;
+    if (b > 0) {
+        scatter_kernel<<<b, 256, 0, s>>>(key, n, start, cursor, slot_elem);
+        stable_kernel<<<b, 256, 0, s>>>(key, slot_elem, n, start, n_keys, order);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------- Step 1: SAS ---
+
+struct SasArgs {
+    const float4* atoms;     // input order
+    const float4* sorted;    // cell order
+    const float* arad;       // a_i, input order
+    const int* cell_start;
+    AtomGrid G;
+    const float* dirs;       // [n_sphere][3]
+    int n_atoms, n_sphere;
+    float reach_max;         // largest a_j plus a margin
+    uint32_t* kept;          // [n_atoms][32]: bit m of lane's word = point lane + 32 m kept
+    int* n_kept;             // [n_atoms]
+};
+
+__device__ __forceinline__ uint32_t bury(const float4* nb, int cnt, const float4& A, float a,
+                                         const float* dirs, int n_sphere, int lane, uint32_t buried) {
+    const int M = (n_sphere + 31) >> 5;
+    for (int m = 0; m < M; ++m) {
+        const int k = lane + 32 * m;
+        if (k >= n_sphere || ((buried >> m) & 1u)) continue;
+        const float3 p = sphere_point(A, a, dirs, k);
+        for (int t = 0; t < cnt; ++t) {
+            const float4 q = nb[t];
+            const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+            if (dx * dx + dy * dy + dz * dz < q.w) {
+                buried |= 1u << m;
+                break;
+            }
+        }
+    }
+    return buried;
+}
+
+__global__ void __launch_bounds__(kSasWarps * 32) sas_kernel(SasArgs g) {
+    __shared__ float4 s_nb[kSasWarps][kNb];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int s = blockIdx.x * kSasWarps + wib;
+    if (s >= g.n_atoms) return;                         // warp-uniform
+    float4* nb = s_nb[wib];
+    const float4 A = g.sorted[s];
+    const int i = __float_as_int(A.w);
+    const float a = g.arad[i];
+    const float reach = a + g.reach_max;
+    int c0[3], c1[3];
+    const float pa[3] = {A.x, A.y, A.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        c0[k] = cell_coord(pa[k] - reach, g.G.lo[k], g.G.inv_cell, g.G.cd[k]);
+        c1[k] = cell_coord(pa[k] + reach, g.G.lo[k], g.G.inv_cell, g.G.cd[k]);
+    }
+    uint32_t buried = 0;
+    int cnt = 0;
+    for (int cz = c0[2]; cz <= c1[2]; ++cz)
+        for (int cy = c0[1]; cy <= c1[1]; ++cy) {
+            const int row = (cz * g.G.cd[1] + cy) * g.G.cd[0];
+            const int b = g.cell_start[row + c0[0]], e = g.cell_start[row + c1[0] + 1];
+            for (int base = b; base < e; base += 32) {
+                const int j = base + lane;
+                bool take = false;
+                float4 B = make_float4(0.f, 0.f, 0.f, 0.f);
+                float aj = 0.f;
+                if (j < e) {
+                    B = g.sorted[j];
+                    const int idx = __float_as_int(B.w);
+                    aj = g.arad[idx];
+                    const float dx = B.x - A.x, dy = B.y - A.y, dz = B.z - A.z;
+                    const float lim = a + aj + 1e-3f;   // spheres that can overlap, with slack
+                    take = idx != i && dx * dx + dy * dy + dz * dz < lim * lim;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, take);
+                if (take) nb[cnt + __popc(bal & ((1u << lane) - 1u))] = make_float4(B.x, B.y, B.z, aj * aj);
+                cnt += __popc(bal);
+                if (cnt > kNb - 32) {
+                    __syncwarp();
+                    buried = bury(nb, cnt, A, a, g.dirs, g.n_sphere, lane, buried);
+                    __syncwarp();
+                    cnt = 0;
+                }
+            }
+        }
+    __syncwarp();
+    buried = bury(nb, cnt, A, a, g.dirs, g.n_sphere, lane, buried);
+    const int M = (g.n_sphere + 31) >> 5;
+    uint32_t valid = 0;
+    for (int m = 0; m < M; ++m)
+        if (lane + 32 * m < g.n_sphere) valid |= 1u << m;
+    const uint32_t keep = valid & ~buried;
+    g.kept[(size_t)i * 32 + lane] = keep;
+    int c = __popc(keep);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) g.n_kept[i] = c;
+}
+
+// Kept points in (atom, k) order.
+__global__ void __launch_bounds__(128) sas_write_kernel(const float4* __restrict__ atoms,
+                                                        const float* __restrict__ arad,
+                                                        const float* __restrict__ dirs, int n_atoms,
+                                                        int n_sphere, const uint32_t* __restrict__ kept,
+                                                        const int* __restrict__ offset, float* __restrict__ pts,
+                                                        int* __restrict__ src) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (i >= n_atoms) return;
+    const float4 A = atoms[i];
+    const float a = arad[i];
+    const uint32_t word = kept[(size_t)i * 32 + lane];
+    int base = offset[i];
+    const int M = (n_sphere + 31) >> 5;
+    for (int m = 0; m < M; ++m) {
+        const bool on = (word >> m) & 1u;
+        const unsigned bal = __ballot_sync(0xffffffffu, on);
+        if (on) {
+            const int k = lane + 32 * m;
+            const int pos = base + __popc(bal & ((1u << lane) - 1u));
+            const float3 p = sphere_point(A, a, dirs, k);
+            pts[3 * (size_t)pos] = p.x;
+            pts[3 * (size_t)pos + 1] = p.y;
+            pts[3 * (size_t)pos + 2] = p.z;
+            src[pos] = i * n_sphere + k;
+        }
+        base += __popc(bal);
+    }
+}
+
+// ------------------------------------------------------------ Step 2: Eq. 1 + protrusion ---
+
+struct FeatArgs {
+    const float4* sorted;
+    const int* cell_start;
+    AtomGrid G;
+    const float* pts;
+    int n_pts;
+    const float* props;      // [n_atoms][n_props], input atom order
+    int n_props;
+    float inv_rf, rf2, rp2, reach;
+    float* feat;             // [n_pts][n_props]
+    int* prot;               // [n_pts] or null
+};
+
+__global__ void __launch_bounds__(kFeatWarps * 32) feature_kernel(FeatArgs g) {
+    __shared__ float4 s_at[kFeatWarps][32];
+    __shared__ float s_pr[kFeatWarps][32][kPropChunk + 1];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int p0 = (blockIdx.x * kFeatWarps + wib) * 32;
+    if (p0 >= g.n_pts) return;                          // warp-uniform
+    const int q0 = blockIdx.y * kPropChunk;
+    const int nq = min(kPropChunk, g.n_props - q0);
+    const int pi = p0 + lane;
+    const bool live = pi < g.n_pts;
+    float px = 0.f, py = 0.f, pz = 0.f;
+    if (live) {
+        px = g.pts[3 * (size_t)pi];
+        py = g.pts[3 * (size_t)pi + 1];
+        pz = g.pts[3 * (size_t)pi + 2];
+    }
+    // the warp's bounding box (non-finite points take no part)
+    const bool fin = live && isfinite(px) && isfinite(py) && isfinite(pz);
+    float lo3[3] = {fin ? px : INFINITY, fin ? py : INFINITY, fin ? pz : INFINITY};
+    float hi3[3] = {fin ? px : -INFINITY, fin ? py : -INFINITY, fin ? pz : -INFINITY};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo3[k] = fminf(lo3[k], __shfl_xor_sync(0xffffffffu, lo3[k], o));
+            hi3[k] = fmaxf(hi3[k], __shfl_xor_sync(0xffffffffu, hi3[k], o));
+        }
+    float acc[kPropChunk];
+#pragma unroll
+    for (int q = 0; q < kPropChunk; ++q) acc[q] = 0.f;
+    int count = 0;
+    if (lo3[0] <= hi3[0]) {                             // at least one finite point
+        int c0[3], c1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            c0[k] = cell_coord(lo3[k] - g.reach, g.G.lo[k], g.G.inv_cell, g.G.cd[k]);
+            c1[k] = cell_coord(hi3[k] + g.reach, g.G.lo[k], g.G.inv_cell, g.G.cd[k]);
+        }
+        for (int cz = c0[2]; cz <= c1[2]; ++cz)
+            for (int cy = c0[1]; cy <= c1[1]; ++cy) {
+                const int row = (cz * g.G.cd[1] + cy) * g.G.cd[0];
+                const int b = g.cell_start[row + c0[0]], e = g.cell_start[row + c1[0] + 1];
+                for (int base = b; base < e; base += 32) {
+                    const int j = base + lane;
+                    const int nt = min(32, e - base);
+                    __syncwarp();
+                    if (j < e) {
+                        const float4 B = g.sorted[j];
+                        s_at[wib][lane] = B;
+                        const float* pr = g.props + (size_t)__float_as_int(B.w) * g.n_props + q0;
+#pragma unroll
+                        for (int q = 0; q < kPropChunk; ++q) s_pr[wib][lane][q] = q < nq ? __ldg(pr + q) : 0.f;
+                    }
+                    __syncwarp();
+                    for (int t = 0; t < nt; ++t) {
+                        const float4 B = s_at[wib][t];
+                        const float dx = B.x - px, dy = B.y - py, dz = B.z - pz;
+                        const float d2 = dx * dx + dy * dy + dz * dz;
+                        count += d2 <= g.rp2;
+                        if (d2 < g.rf2) {
+                            const float w = 1.0f - sqrtf(d2) * g.inv_rf;
+#pragma unroll
+                            for (int q = 0; q < kPropChunk; ++q) acc[q] = fmaf(w, s_pr[wib][t][q], acc[q]);
+                        }
+                    }
+                }
+            }
+    }
+    if (!live) return;
+    if (!fin) count = 0;
+    float* f = g.feat + (size_t)pi * g.n_props + q0;
+#pragma unroll
+    for (int q = 0; q < kPropChunk; ++q)
+        if (q < nq) f[q] = fin ? acc[q] : 0.f;
+    if (g.prot && blockIdx.y == 0) g.prot[pi] = count;
+}
+
+// ------------------------------------------------------------ Steps 4-5: clusters ---
+
+// Spatial hash of a link-sized cell (Teschner et al., "Optimized Spatial Hashing for Collision
+// Detection of Deformable Objects", VMV 2003).
+__device__ __forceinline__ int cell_hash(int x, int y, int z, uint32_t mask) {
+    return (int)((((uint32_t)x * 73856093u) ^ ((uint32_t)y * 19349663u) ^ ((uint32_t)z * 83492791u)) & mask);
+}
+
+struct ClusterArgs {
+    const float* pts;
+    const float* score;
+    int n;
+    float theta, link2, inv_cell;
+    uint32_t hmask;
+    int* key;                // [n] bucket of a clustered point, -1 otherwise
+    int* count;              // [buckets]
+    int* parent;             // [n]
+    int* err;
+};
+
+__device__ __forceinline__ int3 link_cell(const float* p, float inv) {
+    return make_int3(__float2int_rd(p[0] * inv), __float2int_rd(p[1] * inv), __float2int_rd(p[2] * inv));
+}
+
+__global__ void cl_init_kernel(ClusterArgs g) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    g.parent[i] = i;
+    const float s = g.score[i];
+    int k = -1;
+    if (s >= g.theta) {
+        const float* p = g.pts + 3 * (size_t)i;
+        const float lim = 1073741824.0f;   // 2^30 cells
+        bool ok = true;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ok = ok && isfinite(p[c]) && fabsf(p[c] * g.inv_cell) < lim;
+        if (!ok) {
+            atomicOr(g.err, kErrCoord);
+        } else {
+            const int3 c = link_cell(p, g.inv_cell);
+            k = cell_hash(c.x, c.y, c.z, g.hmask);
+            atomicAdd(&g.count[k], 1);
+        }
+    }
+    g.key[i] = k;
+}
+
+// Root of v: parents only ever point to lower indices, so the walk ends.
+__device__ __forceinline__ int uf_find(int* par, int v) {
+    int cur = __ldcg(par + v);
+    if (cur != v) {
+        int prev = v, next;
+        while (cur > (next = __ldcg(par + cur))) {   // path halving towards the root
+            par[prev] = next;
+            prev = cur;
+            cur = next;
+        }
+    }
+    return cur;
+}
+
+// Joins the components of a and b, hooking the larger root under the smaller. Every failed
+// attempt lowers a + b, so the loop ends; the bound only guards against a broken invariant.
+__device__ __forceinline__ bool uf_unite(int* par, int a, int b) {
+    a = uf_find(par, a);
+    b = uf_find(par, b);
+    for (int it = 0; it < (1 << 26) && a != b; ++it) {
+        if (a > b) { const int t = a; a = b; b = t; }
+        const int old = atomicCAS(par + b, b, a);
+        if (old == b) return true;
+        b = uf_find(par, old);
+        a = uf_find(par, a);
+    }
+    return a == b;
+}
+
+__global__ void cl_union_kernel(ClusterArgs g, const int* __restrict__ start, const int* __restrict__ order) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n || g.key[i] < 0) return;
+    const float* p = g.pts + 3 * (size_t)i;
+    const float px = p[0], py = p[1], pz = p[2];
+    const int3 c = link_cell(p, g.inv_cell);
+    bool ok = true;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int h = cell_hash(c.x + dx, c.y + dy, c.z + dz, g.hmask);
+                const int e = start[h + 1];
+                for (int t = start[h]; t < e; ++t) {
+                    const int j = order[t];
+                    if (j <= i) continue;
+                    const float* q = g.pts + 3 * (size_t)j;
+                    const float ex = q[0] - px, ey = q[1] - py, ez = q[2] - pz;
+                    if (ex * ex + ey * ey + ez * ez <= g.link2) ok = uf_unite(g.parent, i, j) && ok;
+                }
+            }
+    if (!ok) atomicOr(g.err, kErrUnion);
+}
+
+struct StatsArgs {
+    const float* pts;
+    const float* score;
+    const int* key;
+    int* parent;
+    int n;
+    int* root;               // [n]
+    int* is_root;            // [n] 0/1
+    double* s2;              // [n] per root
+    double* sx;              // [n][3] per root
+    int* size;               // [n] per root
+};
+
+__global__ void cl_root_kernel(StatsArgs g) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    const int r = g.key[i] < 0 ? -1 : uf_find(g.parent, i);
+    g.root[i] = r;
+    g.is_root[i] = r == i;
+}
+
+__global__ void cl_stats_kernel(StatsArgs g) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    const int r = g.root[i];
+    if (r < 0) return;
+    const double s = g.score[i];
+    atomicAdd(g.s2 + r, s * s);
+    for (int c = 0; c < 3; ++c) atomicAdd(g.sx + 3 * (size_t)r + c, (double)g.pts[3 * (size_t)i + c]);
+    atomicAdd(g.size + r, 1);
+}
+
+struct RankArgs {
+    const int* is_root;
+    const int* cid;          // [n + 1] exclusive scan of is_root; cid[n] = K
+    const double* s2;
+    const double* sx;
+    const int* size;
+    int n;
+    double* c_s2;            // [n] by cluster id (index order of roots)
+    int* c_first;            // [n]
+    int* rank;               // [n] rank of cluster id
+    float* out_score;        // [n] by rank
+    float* out_center;       // [n][3]
+    int* out_size;
+    int* out_first;
+    const int* root;
+    int* cluster;            // [n] per point
+};
+
+__global__ void cl_compact_kernel(RankArgs g) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n || !g.is_root[i]) return;
+    const int c = g.cid[i];
+    g.c_s2[c] = g.s2[i];
+    g.c_first[c] = i;
+}
+
+// rank of cluster c = the number of clusters sorting before it (score desc, first index asc)
+__global__ void __launch_bounds__(256) cl_rank_kernel(RankArgs g) {
+    __shared__ double s_s[256];
+    __shared__ int s_f[256];
+    const int K = g.cid[g.n];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x * blockDim.x >= K) return;           // block-uniform
+    const double sc = c < K ? g.c_s2[c] : 0.0;
+    const int fc = c < K ? g.c_first[c] : 0;
+    int r = 0;
+    for (int base = 0; base < K; base += 256) {
+        __syncthreads();
+        const int t = base + threadIdx.x;
+        if (t < K) {
+            s_s[threadIdx.x] = g.c_s2[t];
+            s_f[threadIdx.x] = g.c_first[t];
+        }
+        __syncthreads();
+        const int m = min(256, K - base);
+        for (int u = 0; u < m; ++u) r += s_s[u] > sc || (s_s[u] == sc && s_f[u] < fc);
+    }
+    if (c < K) g.rank[c] = r;
+}
+
+__global__ void cl_output_kernel(RankArgs g) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    const int r = g.root[i];
+    g.cluster[i] = r < 0 ? -1 : g.rank[g.cid[r]];
+    if (r != i) return;
+    const int k = g.rank[g.cid[i]];
+    const int m = g.size[i];
+    g.out_score[k] = (float)g.s2[i];
+    for (int c = 0; c < 3; ++c) g.out_center[3 * (size_t)k + c] = (float)(g.sx[3 * (size_t)i + c] / m);
+    g.out_size[k] = m;
+    g.out_first[k] = i;
+}
+
+// ------------------------------------------------------------------------- host side ---
+
+struct Pool {
+    cudaStream_t stream;
+    std::vector<void*> ptrs;
+    cudaError_t err = cudaSuccess;
+    explicit Pool(cudaStream_t s) : stream(s) {}
+    template <typename T>
+    T* take(size_t count) {
+        void* p = nullptr;
+        if (err != cudaSuccess) return nullptr;
+        err = cudaMallocAsync(&p, count ? count * sizeof(T) : 16, stream);
+        if (err != cudaSuccess) return nullptr;
+        ptrs.push_back(p);
+        return (T*)p;
+    }
+    void release() {
+        for (void* p : ptrs) cudaFreeAsync(p, stream);
+        ptrs.clear();
+    }
+};
+
+pv_status fail(pv_context* ctx, pv_status s, const char* msg) {
+    pv::context_set_error(ctx, msg);
+    return s;
+}
+
+pv_status cuda_fail(pv_context* ctx, cudaError_t e, const char* what) {
+    static thread_local std::string m;
+    m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(ctx, e == cudaErrorMemoryAllocation ? PV_ERR_OOM : PV_ERR_CUDA, m.c_str());
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetLastError();
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool valid_params(const pv_pocket_params* p) {
+    return p && std::isfinite(p->probe) && p->probe >= 0.f && p->probe <= 10.f && p->n_sphere >= 1 &&
+           p->n_sphere <= PV_MAX_SPHERE_POINTS && p->r_feature > 0.f && std::isfinite(p->r_feature) &&
+           p->r_feature <= 100.f && p->r_protrusion > 0.f && p->r_protrusion <= 100.f &&
+           std::isfinite(p->link) && p->link > 0.f && p->link <= 100.f && !std::isnan(p->threshold);
+}
+
+}  // namespace
+
+struct pv_surface {
+    int magic = kSurfaceMagic;
+    pv_context* ctx = nullptr;
+    int device = 0;
+    Pool pool{nullptr};
+    int n_atoms = 0, n_points = 0, n_sphere = 0;
+    AtomGrid G{};
+    float4* sorted = nullptr;
+    int* cell_start = nullptr;
+    float* points = nullptr;
+    int* src = nullptr;
+};
+
+struct pv_clusters {
+    int magic = kClustersMagic;
+    pv_context* ctx = nullptr;
+    int device = 0;
+    Pool pool{nullptr};
+    int n = 0, K = 0;
+    int* cluster = nullptr;
+    float* score = nullptr;
+    float* center = nullptr;
+    int* size = nullptr;
+    int* first = nullptr;
+};
+
+extern "C" pv_status pv_pocket_params_default(pv_pocket_params* p) {
+    if (!p) return PV_ERR_ARG;
+    p->probe = 1.6f;
+    p->n_sphere = 100;
+    p->r_feature = 6.0f;
+    p->r_protrusion = 10.0f;
+    p->threshold = 0.5f;
+    p->link = 3.0f;
+    return PV_OK;
+}
+
+extern "C" pv_status pv_surface_create(pv_context* ctx, const pv_receptor* r, const float* radius,
+                                       const pv_pocket_params* p, pv_surface** out) {
+    int dev = 0;
+    cudaStream_t st = nullptr;
+    if (!pv::context_device_stream(ctx, &dev, &st)) return PV_ERR_STATE;
+    if (!out) return fail(ctx, PV_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (!valid_params(p)) return fail(ctx, PV_ERR_ARG, "pocket parameters out of range");
+    if (!r || r->n_atoms < 1 || r->n_atoms > kMaxAtoms) return fail(ctx, PV_ERR_ARG, "receptor atom count must be in [1, 200000]");
+    if (!r->xyz || (!radius && !r->element)) return fail(ctx, PV_ERR_ARG, "receptor xyz and element (or radii) required");
+    if (r->mem != PV_MEM_HOST && r->mem != PV_MEM_DEVICE) return fail(ctx, PV_ERR_ARG, "receptor mem kind");
+    DeviceGuard guard(dev);
+    const int n = r->n_atoms;
+    // bounding box on the host
+    std::vector<float> hx;
+    const float* xyz_h = r->xyz;
+    if (r->mem == PV_MEM_DEVICE) {
+        hx.resize(3 * (size_t)n);
+        cudaError_t e = cudaMemcpyAsync(hx.data(), r->xyz, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "receptor read");
+        xyz_h = hx.data();
+    }
+    // the largest vdW radius bounds how far a neighbouring sphere can reach
+    float r_max = 1.80f;
+    if (radius) {
+        std::vector<float> hr;
+        const float* rad_h = radius;
+        if (r->mem == PV_MEM_DEVICE) {
+            hr.resize(n);
+            cudaError_t e = cudaMemcpyAsync(hr.data(), radius, sizeof(float) * n, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "radius read");
+            rad_h = hr.data();
+        }
+        r_max = 0.f;
+        for (int i = 0; i < n; ++i) {
+            if (!(rad_h[i] > 0.f && rad_h[i] <= 10.f)) return fail(ctx, PV_ERR_ARG, "atom radius must be in (0, 10] A");
+            r_max = std::max(r_max, rad_h[i]);
+        }
+    }
+    double lo[3] = {1e30, 1e30, 1e30}, hi[3] = {-1e30, -1e30, -1e30};
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) {
+            const double v = xyz_h[3 * i + k];
+            if (!std::isfinite(v) || std::fabs(v) > 1e6) return fail(ctx, PV_ERR_ARG, "receptor coordinates must be finite (|x| <= 1e6 A)");
+            lo[k] = std::min(lo[k], v);
+            hi[k] = std::max(hi[k], v);
+        }
+    AtomGrid G;
+    long long n_cells = 1;
+    for (int k = 0; k < 3; ++k) {
+        G.lo[k] = (float)(lo[k] - 0.5);
+        G.cd[k] = (int)std::ceil((hi[k] + 0.5 - (double)G.lo[k]) / kCell) + 1;
+        n_cells *= G.cd[k];
+    }
+    G.inv_cell = 1.0f / kCell;
+    if (n_cells > (1 << 24)) return fail(ctx, PV_ERR_ARG, "receptor spans too large a region");
+    // lattice directions (spherical Fibonacci lattice, evaluated in double)
+    const int ns = p->n_sphere;
+    std::vector<float> dirs(3 * (size_t)ns);
+    const double golden_angle = kPi * (3.0 - std::sqrt(5.0));
+    for (int k = 0; k < ns; ++k) {
+        const double z = 1.0 - (2.0 * k + 1.0) / ns, rho = std::sqrt(std::max(0.0, 1.0 - z * z));
+        dirs[3 * k] = (float)(rho * std::cos(golden_angle * k));
+        dirs[3 * k + 1] = (float)(rho * std::sin(golden_angle * k));
+        dirs[3 * k + 2] = (float)z;
+    }
+    pv_surface* S = new (std::nothrow) pv_surface();
+    if (!S) return fail(ctx, PV_ERR_OOM, "host allocation failed");
+    S->ctx = ctx;
+    S->device = dev;
+    S->pool.stream = st;
+    S->n_atoms = n;
+    S->n_sphere = ns;
+    S->G = G;
+    Pool scratch(st);
+    const float* d_xyz = r->xyz;
+    const uint8_t* d_el = r->element;
+    const float* d_rad = radius;
+    if (r->mem == PV_MEM_HOST) {
+        d_xyz = scratch.take<float>(3 * (size_t)n);
+        d_el = r->element ? scratch.take<uint8_t>(n) : nullptr;
+        d_rad = radius ? scratch.take<float>(n) : nullptr;
+    }
+    float4* atoms = scratch.take<float4>(n);
+    float* arad = scratch.take<float>(n);
+    int* key = scratch.take<int>(n);
+    int* count = scratch.take<int>(n_cells);
+    int* cursor = scratch.take<int>(n_cells);
+    int* slot_elem = scratch.take<int>(n);
+    int* order = scratch.take<int>(n);
+    int* err = scratch.take<int>(1);
+    float* d_dirs = scratch.take<float>(3 * (size_t)ns);
+    uint32_t* kept = scratch.take<uint32_t>(32 * (size_t)n);
+    int* n_kept = scratch.take<int>(n);
+    int* offset = scratch.take<int>(n + 1);
+    S->sorted = S->pool.take<float4>(n);
+    S->cell_start = S->pool.take<int>(n_cells + 1);
+    cudaError_t e = scratch.err != cudaSuccess ? scratch.err : S->pool.err;
+    const char* stage = "allocation";
+    auto step = [&](cudaError_t x, const char* what) {
+        if (e == cudaSuccess && x != cudaSuccess) { e = x; stage = what; }
+    };
+    if (e == cudaSuccess && r->mem == PV_MEM_HOST) {
+        step(cudaMemcpyAsync((void*)d_xyz, r->xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st), "receptor upload");
+        if (d_el) step(cudaMemcpyAsync((void*)d_el, r->element, n, cudaMemcpyHostToDevice, st), "receptor upload");
+        if (d_rad) step(cudaMemcpyAsync((void*)d_rad, radius, sizeof(float) * n, cudaMemcpyHostToDevice, st), "radius upload");
+    }
+    int h_err = 0, h_total = 0;
+    if (e == cudaSuccess) {
+        step(cudaMemcpyAsync(d_dirs, dirs.data(), sizeof(float) * dirs.size(), cudaMemcpyHostToDevice, st), "lattice upload");
+        step(cudaMemsetAsync(count, 0, sizeof(int) * n_cells, st), "memset");
+        step(cudaMemsetAsync(err, 0, sizeof(int), st), "memset");
+    }
+    if (e == cudaSuccess) {
+        prep_atoms_kernel<<<(n + 255) / 256, 256, 0, st>>>(d_xyz, d_el, d_rad, p->probe, n, G, atoms, arad, key, count, err);
+        step(cudaGetLastError(), "atom preparation");
+        step(bin_keys(key, n, (int)n_cells, count, S->cell_start, cursor, slot_elem, order, st), "atom binning");
+        gather_atoms_kernel<<<(n + 255) / 256, 256, 0, st>>>(order, n, atoms, S->sorted);
+        step(cudaGetLastError(), "atom binning");
+    }
+    float reach_max = 0.f;
+    if (e == cudaSuccess) {
+        reach_max = r_max + p->probe + 1e-3f;
+        SasArgs a{atoms, S->sorted, arad, S->cell_start, G, d_dirs, n, ns, reach_max, kept, n_kept};
+        sas_kernel<<<(n + kSasWarps - 1) / kSasWarps, kSasWarps * 32, 0, st>>>(a);
+        step(cudaGetLastError(), "surface points");
+        scan_kernel<<<1, 1024, 0, st>>>(n_kept, n, offset);
+        step(cudaGetLastError(), "surface points");
+        step(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st), "readback");
+        step(cudaMemcpyAsync(&h_total, offset + n, sizeof(int), cudaMemcpyDeviceToHost, st), "readback");
+        step(cudaStreamSynchronize(st), "surface points");
+    }
+    if (e == cudaSuccess && h_err) {
+        scratch.release();
+        S->pool.release();
+        delete S;
+        return fail(ctx, PV_ERR_ARG, (h_err & kErrElement) ? "receptor element must be 0..3"
+                                     : (h_err & kErrRadius) ? "atom radius must be in (0, 10] A"
+                                                            : "receptor coordinates must be finite");
+    }
+    if (e == cudaSuccess) {
+        S->n_points = h_total;
+        S->points = S->pool.take<float>(3 * (size_t)(h_total > 0 ? h_total : 1));
+        S->src = S->pool.take<int>(h_total > 0 ? h_total : 1);
+        step(S->pool.err, "point allocation");
+    }
+    if (e == cudaSuccess) {
+        sas_write_kernel<<<(n + 3) / 4, 128, 0, st>>>(atoms, arad, d_dirs, n, ns, kept, offset, S->points, S->src);
+        step(cudaGetLastError(), "surface points");
+        step(cudaStreamSynchronize(st), "surface points");   // the scratch goes back to the pool below
+    }
+    scratch.release();
+    if (e != cudaSuccess) {
+        S->pool.release();
+        delete S;
+        return cuda_fail(ctx, e, (std::string("surface: ") + stage).c_str());
+    }
+    *out = S;
+    return PV_OK;
+}
+
+extern "C" pv_status pv_surface_info(const pv_surface* s, int32_t* n_atoms, int32_t* n_points) {
+    if (!s || s->magic != kSurfaceMagic) return PV_ERR_STATE;
+    if (n_atoms) *n_atoms = s->n_atoms;
+    if (n_points) *n_points = s->n_points;
+    return PV_OK;
+}
+
+extern "C" pv_status pv_surface_points(const pv_surface* s, const float** dev_xyz) {
+    if (!s || s->magic != kSurfaceMagic) return PV_ERR_STATE;
+    if (!dev_xyz) return PV_ERR_ARG;
+    *dev_xyz = s->points;
+    return PV_OK;
+}
+
+extern "C" pv_status pv_surface_read(pv_context* ctx, const pv_surface* s, float* xyz, int32_t* src, int32_t mem) {
+    int dev = 0;
+    cudaStream_t st = nullptr;
+    if (!pv::context_device_stream(ctx, &dev, &st)) return PV_ERR_STATE;
+    if (!s || s->magic != kSurfaceMagic || s->ctx != ctx) return fail(ctx, PV_ERR_STATE, "surface of another context");
+    if (mem != PV_MEM_HOST && mem != PV_MEM_DEVICE) return fail(ctx, PV_ERR_ARG, "mem kind");
+    DeviceGuard guard(dev);
+    const cudaMemcpyKind kind = mem == PV_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    cudaError_t e = cudaSuccess;
+    if (s->n_points > 0 && xyz) e = cudaMemcpyAsync(xyz, s->points, sizeof(float) * 3 * s->n_points, kind, st);
+    if (e == cudaSuccess && s->n_points > 0 && src) e = cudaMemcpyAsync(src, s->src, sizeof(int) * s->n_points, kind, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? PV_OK : cuda_fail(ctx, e, "surface read");
+}
+
+extern "C" pv_status pv_surface_features(pv_context* ctx, const pv_surface* s, int32_t n_points,
+                                         const float* xyz, int32_t xyz_mem, int32_t n_props,
+                                         const float* props, int32_t props_mem, const pv_pocket_params* p,
+                                         float* dev_features, int32_t* dev_protrusion) {
+    int dev = 0;
+    cudaStream_t st = nullptr;
+    if (!pv::context_device_stream(ctx, &dev, &st)) return PV_ERR_STATE;
+    if (!s || s->magic != kSurfaceMagic || s->ctx != ctx) return fail(ctx, PV_ERR_STATE, "surface of another context");
+    if (!valid_params(p)) return fail(ctx, PV_ERR_ARG, "pocket parameters out of range");
+    if (n_points < 0 || (!xyz && n_points != s->n_points)) return fail(ctx, PV_ERR_ARG, "n_points must equal the surface's count when xyz is NULL");
+    if (n_props < 1 || n_props > PV_MAX_PROPS || !props) return fail(ctx, PV_ERR_ARG, "1..64 property columns required");
+    if ((xyz && xyz_mem != PV_MEM_HOST && xyz_mem != PV_MEM_DEVICE) || (props_mem != PV_MEM_HOST && props_mem != PV_MEM_DEVICE))
+        return fail(ctx, PV_ERR_ARG, "mem kind");
+    if (n_points > 0 && !dev_features) return fail(ctx, PV_ERR_ARG, "dev_features is null");
+    if (n_points == 0) return PV_OK;
+    DeviceGuard guard(dev);
+    Pool scratch(st);
+    const float* d_pts = xyz ? xyz : s->points;
+    const float* d_props = props;
+    cudaError_t e = cudaSuccess;
+    if (xyz && xyz_mem == PV_MEM_HOST) {
+        float* t = scratch.take<float>(3 * (size_t)n_points);
+        if (t) e = cudaMemcpyAsync(t, xyz, sizeof(float) * 3 * (size_t)n_points, cudaMemcpyHostToDevice, st);
+        d_pts = t;
+    }
+    if (props_mem == PV_MEM_HOST) {
+        float* t = scratch.take<float>((size_t)s->n_atoms * n_props);
+        if (t && e == cudaSuccess)
+            e = cudaMemcpyAsync(t, props, sizeof(float) * (size_t)s->n_atoms * n_props, cudaMemcpyHostToDevice, st);
+        d_props = t;
+    }
+    if (scratch.err != cudaSuccess) e = scratch.err;
+    if (e == cudaSuccess) {
+        FeatArgs a;
+        a.sorted = s->sorted;
+        a.cell_start = s->cell_start;
+        a.G = s->G;
+        a.pts = d_pts;
+        a.n_pts = n_points;
+        a.props = d_props;
+        a.n_props = n_props;
+        a.inv_rf = (float)(1.0 / (double)p->r_feature);
+        a.rf2 = p->r_feature * p->r_feature;
+        a.rp2 = p->r_protrusion * p->r_protrusion;
+        a.reach = std::max(p->r_feature, p->r_protrusion) + 1e-3f;
+        a.feat = dev_features;
+        a.prot = dev_protrusion;
+        const dim3 grid((unsigned)((n_points + 32 * kFeatWarps - 1) / (32 * kFeatWarps)),
+                        (unsigned)((n_props + kPropChunk - 1) / kPropChunk));
+        feature_kernel<<<grid, kFeatWarps * 32, 0, st>>>(a);
+        e = cudaGetLastError();
+    }
+    scratch.release();   // stream-ordered: the kernel above finishes first
+    return e == cudaSuccess ? PV_OK : cuda_fail(ctx, e, "surface features");
+}
+
+extern "C" void pv_surface_destroy(pv_surface* s) {
+    if (!s || s->magic != kSurfaceMagic) return;
+    DeviceGuard guard(s->device);
+    s->pool.release();
+    s->magic = 0;
+    delete s;
+}
+
+extern "C" pv_status pv_cluster_points(pv_context* ctx, int32_t n, const float* dev_xyz, const float* dev_score,
+                                       const pv_pocket_params* p, pv_clusters** out) {
+    int dev = 0;
+    cudaStream_t st = nullptr;
+    if (!pv::context_device_stream(ctx, &dev, &st)) return PV_ERR_STATE;
+    if (!out) return fail(ctx, PV_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (!valid_params(p)) return fail(ctx, PV_ERR_ARG, "pocket parameters out of range");
+    if (n < 0 || n > (1 << 26)) return fail(ctx, PV_ERR_ARG, "point count must be in [0, 2^26]");
+    if (n > 0 && (!dev_xyz || !dev_score)) return fail(ctx, PV_ERR_ARG, "dev_xyz and dev_score required");
+    DeviceGuard guard(dev);
+    pv_clusters* C = new (std::nothrow) pv_clusters();
+    if (!C) return fail(ctx, PV_ERR_OOM, "host allocation failed");
+    C->ctx = ctx;
+    C->device = dev;
+    C->pool.stream = st;
+    C->n = n;
+    const size_t m = n > 0 ? (size_t)n : 1;
+    C->cluster = C->pool.take<int>(m);
+    C->score = C->pool.take<float>(m);
+    C->center = C->pool.take<float>(3 * m);
+    C->size = C->pool.take<int>(m);
+    C->first = C->pool.take<int>(m);
+    if (C->pool.err != cudaSuccess) {
+        const cudaError_t e = C->pool.err;
+        C->pool.release();
+        delete C;
+        return cuda_fail(ctx, e, "cluster allocation");
+    }
+    if (n == 0) {
+        *out = C;
+        return PV_OK;
+    }
+    uint32_t buckets = 1024;
+    while (buckets < 2u * (uint32_t)n) buckets <<= 1;
+    Pool scratch(st);
+    int* key = scratch.take<int>(m);
+    int* count = scratch.take<int>(buckets);
+    int* start = scratch.take<int>(buckets + 1);
+    int* cursor = scratch.take<int>(buckets);
+    int* slot_elem = scratch.take<int>(m);
+    int* order = scratch.take<int>(m);
+    int* parent = scratch.take<int>(m);
+    int* err = scratch.take<int>(1);
+    int* root = scratch.take<int>(m);
+    int* is_root = scratch.take<int>(m);
+    int* cid = scratch.take<int>(m + 1);
+    double* s2 = scratch.take<double>(m);
+    double* sx = scratch.take<double>(3 * m);
+    int* size = scratch.take<int>(m);
+    double* c_s2 = scratch.take<double>(m);
+    int* c_first = scratch.take<int>(m);
+    int* rank = scratch.take<int>(m);
+    cudaError_t e = scratch.err;
+    const char* stage = "allocation";
+    auto step = [&](cudaError_t x, const char* what) {
+        if (e == cudaSuccess && x != cudaSuccess) { e = x; stage = what; }
+    };
+    int h_err = 0, h_k = 0;
+    if (e == cudaSuccess) {
+        step(cudaMemsetAsync(count, 0, sizeof(int) * buckets, st), "memset");
+        step(cudaMemsetAsync(err, 0, sizeof(int), st), "memset");
+        step(cudaMemsetAsync(s2, 0, sizeof(double) * m, st), "memset");
+        step(cudaMemsetAsync(sx, 0, sizeof(double) * 3 * m, st), "memset");
+        step(cudaMemsetAsync(size, 0, sizeof(int) * m, st), "memset");
+    }
+    if (e == cudaSuccess) {
+        ClusterArgs a;
+        a.pts = dev_xyz;
+        a.score = dev_score;
+        a.n = n;
+        a.theta = p->threshold;
+        a.link2 = p->link * p->link;
+        // cells a little wider than the link so that linked points always sit in adjacent cells
+        a.inv_cell = (float)(1.0 / ((double)p->link * (1.0 + 1e-5)));
+        a.hmask = buckets - 1;
+        a.key = key;
+        a.count = count;
+        a.parent = parent;
+        a.err = err;
+        const int b = (n + 255) / 256;
+        cl_init_kernel<<<b, 256, 0, st>>>(a);
+        step(cudaGetLastError(), "cluster set-up");
+        step(bin_keys(key, n, (int)buckets, count, start, cursor, slot_elem, order, st), "point binning");
+        cl_union_kernel<<<b, 256, 0, st>>>(a, start, order);
+        step(cudaGetLastError(), "single linkage");
+        StatsArgs sa{dev_xyz, dev_score, key, parent, n, root, is_root, s2, sx, size};
+        cl_root_kernel<<<b, 256, 0, st>>>(sa);
+        cl_stats_kernel<<<b, 256, 0, st>>>(sa);
+        step(cudaGetLastError(), "cluster sums");
+        scan_kernel<<<1, 1024, 0, st>>>(is_root, n, cid);
+        RankArgs ra{is_root, cid, s2, sx, size, n, c_s2, c_first, rank, C->score, C->center, C->size, C->first, root, C->cluster};
+        cl_compact_kernel<<<b, 256, 0, st>>>(ra);
+        cl_rank_kernel<<<b, 256, 0, st>>>(ra);
+        cl_output_kernel<<<b, 256, 0, st>>>(ra);
+        step(cudaGetLastError(), "cluster ranking");
+        step(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st), "readback");
+        step(cudaMemcpyAsync(&h_k, cid + n, sizeof(int), cudaMemcpyDeviceToHost, st), "readback");
+        step(cudaStreamSynchronize(st), "clusters");
+    }
+    scratch.release();
+    if (e == cudaSuccess && h_err) {
+        C->pool.release();
+        delete C;
+        return fail(ctx, PV_ERR_ARG, (h_err & kErrCoord) ? "clustered points need finite coordinates within 2^30 link lengths"
+                                                         : "union-find did not converge");
+    }
+    if (e != cudaSuccess) {
+        C->pool.release();
+        delete C;
+        return cuda_fail(ctx, e, (std::string("clusters: ") + stage).c_str());
+    }
+    C->K = h_k;
+    *out = C;
+    return PV_OK;
+}
+
+extern "C" pv_status pv_clusters_info(const pv_clusters* c, int32_t* n_points, int32_t* n_clusters) {
+    if (!c || c->magic != kClustersMagic) return PV_ERR_STATE;
+    if (n_points) *n_points = c->n;
+    if (n_clusters) *n_clusters = c->K;
+    return PV_OK;
+}
+
+extern "C" pv_status pv_clusters_read(pv_context* ctx, const pv_clusters* c, int32_t* cluster, float* score,
+                                      float* center, int32_t* size, int32_t* first, int32_t mem) {
+    int dev = 0;
+    cudaStream_t st = nullptr;
+    if (!pv::context_device_stream(ctx, &dev, &st)) return PV_ERR_STATE;
+    if (!c || c->magic != kClustersMagic || c->ctx != ctx) return fail(ctx, PV_ERR_STATE, "clusters of another context");
+    if (mem != PV_MEM_HOST && mem != PV_MEM_DEVICE) return fail(ctx, PV_ERR_ARG, "mem kind");
+    DeviceGuard guard(dev);
+    const cudaMemcpyKind kind = mem == PV_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    cudaError_t e = cudaSuccess;
+    auto copy = [&](void* dst, const void* srcp, size_t bytes) {
+        if (e == cudaSuccess && dst && bytes) e = cudaMemcpyAsync(dst, srcp, bytes, kind, st);
+    };
+    copy(cluster, c->cluster, sizeof(int) * (size_t)c->n);
+    copy(score, c->score, sizeof(float) * (size_t)c->K);
+    copy(center, c->center, sizeof(float) * 3 * (size_t)c->K);
+    copy(size, c->size, sizeof(int) * (size_t)c->K);
+    copy(first, c->first, sizeof(int) * (size_t)c->K);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? PV_OK : cuda_fail(ctx, e, "clusters read");
+}
+
+extern "C" void pv_clusters_destroy(pv_clusters* c) {
+    if (!c || c->magic != kClustersMagic) return;
+    DeviceGuard guard(c->device);
+    c->pool.release();
+    c->magic = 0;
+    delete c;
+}

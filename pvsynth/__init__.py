@@ -336,3 +336,68 @@ def box_sweep(seed: int = 0, sizes: Sequence[float] = tuple(range(15, 31)), n_po
     boxes = [Box(np.array(b.center), np.array([float(s)] * 3)) for b in centres for s in sizes]
     lig = ligand_centered(make_ligand(30, 6, seed))
     return Workload("box_sweep", [rec], [boxes], [lig], chains=chains, steps=steps, top_k=9, seed=seed)
+
+
+# ------------------------------------------------------------------ pocket-side inputs --
+# Inputs of the pocket prediction (Supplementary Algorithm 1). The Random Forest score of
+# Step 3 is replaced by a synthetic ligandability that is high inside the carved pockets.
+
+# Bondi (J. Phys. Chem. 68, 441, 1964) van der Waals radii by element: C, N, O, S.
+VDW_RADIUS = (1.70, 1.55, 1.52, 1.80)
+PROPERTY_NAMES = ("is_C", "is_N", "is_O", "is_S", "donor", "acceptor", "charge")
+
+
+def vdw_radii(rec: Receptor) -> np.ndarray:
+    return np.asarray(VDW_RADIUS, dtype=np.float64)[rec.element]
+
+
+def atom_properties(rec: Receptor, seed: int) -> np.ndarray:
+    """float32 [n, 7] per-atom property columns (PROPERTY_NAMES): element one-hot, the donor and
+    acceptor flags, and a synthetic partial charge uniform in [-0.5, 0.5]."""
+    rng = np.random.default_rng([seed, 0x9C0])
+    out = np.zeros((rec.n, len(PROPERTY_NAMES)), dtype=np.float32)
+    out[np.arange(rec.n), rec.element] = 1.0
+    out[:, 4] = rec.donor
+    out[:, 5] = rec.acceptor
+    out[:, 6] = rng.uniform(-0.5, 0.5, size=rec.n)
+    return out
+
+
+@dataclasses.dataclass
+class PocketSite:
+    receptor: Receptor
+    centers: np.ndarray     # [P, 3] carved pocket centres
+    radii: np.ndarray       # [P]
+
+
+def pocket_site(seed: int = 0, n_atoms: int = 8000, n_pockets: int = 10,
+                radius_range: Tuple[float, float] = (6.0, 10.0)) -> PocketSite:
+    """A receptor of ``n_atoms`` atoms (0.05 per cubic A) with ``n_pockets`` carved spherical pockets."""
+    side = receptor_side(n_atoms)
+    centers, radii = place_pockets(n_pockets, radius_range, side, seed, margin=min(6.0, side / 4))
+    rec = make_receptor(n_atoms, seed, list(zip(centers, radii)))
+    return PocketSite(rec, centers, radii)
+
+
+def ligandability(points, site: PocketSite, seed: int, noise: float = 0.1) -> np.ndarray:
+    """Synthetic stand-in for the classifier score of each point, float32 in [0, 1]: 1 inside a
+    carved pocket sphere, falling off over about 2 A outside it, mixed with uniform noise."""
+    p = np.asarray(points, dtype=np.float64).reshape(-1, 3)
+    rng = np.random.default_rng([seed, 0x5C0])
+    if p.shape[0] == 0:
+        return np.zeros(0, dtype=np.float32)
+    d = np.linalg.norm(p[:, None, :] - site.centers[None, :, :], axis=2) - site.radii[None, :]
+    base = np.exp(-(np.maximum(d, 0.0) / 2.0) ** 2).max(axis=1)
+    return ((1.0 - noise) * base + noise * rng.random(p.shape[0])).astype(np.float32)
+
+
+def cluster_cloud(seed: int = 0, n_blobs: int = 20, per_blob: int = 500, n_background: int = 5000,
+                  extent: float = 60.0, spread: float = 2.0) -> Tuple[np.ndarray, np.ndarray]:
+    """Points for clustering: ``n_blobs`` Gaussian blobs (sd ``spread`` A) and a uniform background
+    in a cube of edge ``extent``, with uniform scores in [0, 1]. float32 [n, 3], float32 [n]."""
+    rng = np.random.default_rng([seed, 0xC1C])
+    centres = rng.uniform(-extent / 2, extent / 2, size=(n_blobs, 3))
+    blobs = (centres[:, None, :] + rng.normal(scale=spread, size=(n_blobs, per_blob, 3))).reshape(-1, 3)
+    bg = rng.uniform(-extent / 2, extent / 2, size=(n_background, 3))
+    pts = np.concatenate([blobs, bg])[rng.permutation(n_blobs * per_blob + n_background)]
+    return pts.astype(np.float32), rng.random(pts.shape[0]).astype(np.float32)
