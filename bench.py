@@ -569,17 +569,11 @@ def run_pocket_workload(args):
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     feat_ms = []
 
-    def step(timed_features=False):
+    def step():
         out = []
         for i in range(n_rec):
             surf = ctx.surface(recs[i], params=prm)
-            if timed_features:
-                f0.record(stream)
             feat, prot = surf.features(props[i], params=prm)
-            if timed_features:
-                f1.record(stream)
-                f1.synchronize()
-                feat_ms.append(f0.elapsed_time(f1))
             cl = ctx.cluster(surf.points(), scores[i], prm)
             out.append((surf, feat, prot, cl))
         return out
@@ -625,9 +619,41 @@ def run_pocket_workload(args):
     # the feature kernel alone (events around its one launch), and its algorithmic work: the
     # distance test of every (point, atom) pair within r_protrusion, plus the weight and the
     # 2 x 7 property FLOPs of every pair within r_feature (counted with r_protrusion = r_feature)
-    for _ in range(2):
-        step(timed_features=True)
+    # 20 back-to-back launches per receptor through the C ABI (outputs preallocated), so that the
+    # events time the kernel rather than the host's call overhead
+    import ctypes as C
+    cp = prm.to_c()
+    reps = 20
+    for i in range(n_rec):
+        surf = out[i][0]
+        feat = torch.empty((surf.n_points, props[i].shape[1]), dtype=torch.float32, device=dev)
+        prot = torch.empty(surf.n_points, dtype=torch.int32, device=dev)
+        args_c = (ctx.h, surf.h, surf.n_points, None, 1, int(props[i].shape[1]), props[i].data_ptr(), 1, C.byref(cp),
+                  feat.data_ptr(), prot.data_ptr())
+        ctx.lib.pv_surface_features(*args_c)
+        f0.record(stream)
+        for _ in range(reps):
+            ctx.lib.pv_surface_features(*args_c)
+        f1.record(stream)
+        f1.synchronize()
+        feat_ms.append(f0.elapsed_time(f1) / reps)
     feat_s = float(np.mean(feat_ms)) * 1e-3
+    # host-clocked phases of one receptor (each call ends synchronised here)
+    phase = {"surface": [], "features": [], "clusters": []}
+    for i in range(n_rec):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        surf = ctx.surface(recs[i], params=prm)
+        t1 = time.perf_counter()
+        surf.features(props[i], params=prm)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        ctx.cluster(surf.points(), scores[i], prm)
+        t3 = time.perf_counter()
+        phase["surface"].append(t1 - t0)
+        phase["features"].append(t2 - t1)
+        phase["clusters"].append(t3 - t2)
+    breakdown = {k: round(float(np.mean(v)) * 1e3, 4) for k, v in phase.items()}
     pairs10 = pairs6 = 0
     n6 = api.PocketParams(n_sphere=100, r_protrusion=6.0)
     for i in range(n_rec):
@@ -669,6 +695,7 @@ def run_pocket_workload(args):
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "inputs": "receptors, property columns and scores resident in HBM"},
             "points_per_s": round(n_points * args.steps / total_t, 1),
+            "breakdown_ms_per_receptor": breakdown,
             "roofline": {"kernel": "feature_kernel", "bound": "alu", "achieved": round(achieved, 4),
                          "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 5),
                          "traffic": None, "launch_ms": round(feat_s * 1e3, 4),

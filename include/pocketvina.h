@@ -347,7 +347,10 @@ void pv_dock_result_destroy(pv_dock_result* r);
  * and, given a ligandability score per point (Step 3's Random Forest is not part of this
  * library: its scores are an input), the single-linkage clusters of the high-scoring points with
  * their Eq. 2 scores, centres and ranking (Steps 4-5). The cluster centres are the pocket
- * centres that pv_build_grids' boxes are placed on (Algorithm 3). */
+ * centres that pv_build_grids' boxes are placed on (Algorithm 3).
+ * Device memory of these calls comes from a stream-ordered pool per device owned by the library
+ * (not the context's allocator); memory freed by a call or a destroy stays in that pool for the
+ * next call until the process exits. */
 typedef struct pv_surface pv_surface;
 typedef struct pv_clusters pv_clusters;
 

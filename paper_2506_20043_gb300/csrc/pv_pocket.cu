@@ -14,10 +14,11 @@
 // joins neighbours with a lock-free union-find that always hooks the larger root under the smaller
 // (so a component's root is its lowest index), and reduces per root in float64.
 //
-// Device memory comes from the stream-ordered pool (cudaMallocAsync on the context's stream) and
-// goes back to it on that stream when the handle is destroyed.
+// Device memory comes from a library-owned stream-ordered pool per device (allocated and freed on
+// the context's stream); freed blocks stay in the pool for the next call.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -33,9 +34,10 @@ constexpr float kCell = 4.0f;            // atom binning cell edge, A
 constexpr int kMaxAtoms = 200000;
 constexpr int kNb = 128;                 // neighbour list capacity per warp (SAS kernel)
 constexpr int kSasWarps = 4;
-constexpr int kFeatWarps = 4;
+constexpr int kFeatSplit = 4;          // warps sharing one group of 32 points (feature kernel)
 constexpr int kPropChunk = 8;            // property columns per feature launch row
 constexpr double kPi = 3.14159265358979323846;
+constexpr int kHookRounds = 3;           // hooking rounds before the unions (clustering)
 
 // Bondi (J. Phys. Chem. 68, 441, 1964) van der Waals radii by element: C, N, O, S.
 __constant__ float c_bondi[4] = {1.70f, 1.55f, 1.52f, 1.80f};
@@ -89,23 +91,26 @@ __global__ void prep_atoms_kernel(const float* __restrict__ xyz, const uint8_t* 
     atomicAdd(&count[c], 1);
 }
 
-// Exclusive scan of count[0 .. n) into start[0 .. n] by one CTA of 1024 threads.
+// Exclusive scan of count[0 .. n) into start[0 .. n] by one CTA of 1024 threads, over tiles of
+// 4096 elements (four consecutive elements per thread, coalesced loads), carrying the running total.
 __global__ void __launch_bounds__(1024) scan_kernel(const int* __restrict__ count, int n,
                                                     int* __restrict__ start) {
     __shared__ int s_warp[32];
-    __shared__ int s_carry;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int base = 0; base < n; base += 1024) {
-        const int i = base + threadIdx.x;
-        const int v = i < n ? count[i] : 0;
-        int x = v;
+    int carry = 0;
+    for (int base = 0; base < n; base += 4096) {
+        const int i0 = base + 4 * (int)threadIdx.x;
+        int v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = i0 + k < n ? count[i0 + k] : 0;
+        const int sum = v[0] + v[1] + v[2] + v[3];
+        int x = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
+        __syncthreads();                                 // the previous tile is done with s_warp
         if (lane == 31) s_warp[warp] = x;
         __syncthreads();
         if (warp == 0) {
@@ -118,14 +123,15 @@ __global__ void __launch_bounds__(1024) scan_kernel(const int* __restrict__ coun
             s_warp[lane] = w;
         }
         __syncthreads();
-        const int carry = s_carry;
-        const int incl = x + (warp ? s_warp[warp - 1] : 0) + carry;
-        if (i < n) start[i] = incl - v;
-        __syncthreads();
-        if (threadIdx.x == 1023) s_carry = incl;
-        __syncthreads();
+        int run = carry + x - sum + (warp ? s_warp[warp - 1] : 0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (i0 + k < n) start[i0 + k] = run;
+            run += v[k];
+        }
+        carry += s_warp[31];
     }
-    if (threadIdx.x == 0) start[n] = s_carry;
+    if (threadIdx.x == 0) start[n] = carry;
 }
 
 // Unstable placement: each element with key >= 0 takes a slot of its key's segment.
@@ -304,6 +310,7 @@ struct FeatArgs {
     const int* cell_start;
     AtomGrid G;
     const float* pts;
+    const int* perm;         // [n_pts] order in which points are grouped, or null (given order)
     int n_pts;
     const float* props;      // [n_atoms][n_props], input atom order
     int n_props;
@@ -312,23 +319,26 @@ struct FeatArgs {
     int* prot;               // [n_pts] or null
 };
 
-__global__ void __launch_bounds__(kFeatWarps * 32) feature_kernel(FeatArgs g) {
-    __shared__ float4 s_at[kFeatWarps][32];
-    __shared__ float s_pr[kFeatWarps][32][kPropChunk + 1];
+// One CTA per group of 32 points; its kFeatSplit warps share the group and split the cell rows
+// within reach of the group's bounding box (a row's x range trimmed to the box swept by the
+// reach), then add their partial sums in shared memory.
+__global__ void __launch_bounds__(kFeatSplit * 32) feature_kernel(FeatArgs g) {
+    __shared__ float4 s_at[kFeatSplit][32];
+    __shared__ float s_pr[kFeatSplit][32][kPropChunk + 1];
+    __shared__ float s_red[kFeatSplit][kPropChunk + 1][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int p0 = (blockIdx.x * kFeatWarps + wib) * 32;
-    if (p0 >= g.n_pts) return;                          // warp-uniform
+    const int slot = blockIdx.x * 32 + lane;
     const int q0 = blockIdx.y * kPropChunk;
     const int nq = min(kPropChunk, g.n_props - q0);
-    const int pi = p0 + lane;
-    const bool live = pi < g.n_pts;
+    const bool live = slot < g.n_pts;
+    const int pi = live ? (g.perm ? g.perm[slot] : slot) : 0;
     float px = 0.f, py = 0.f, pz = 0.f;
     if (live) {
         px = g.pts[3 * (size_t)pi];
         py = g.pts[3 * (size_t)pi + 1];
         pz = g.pts[3 * (size_t)pi + 2];
     }
-    // the warp's bounding box (non-finite points take no part)
+    // the group's bounding box (non-finite points take no part)
     const bool fin = live && isfinite(px) && isfinite(py) && isfinite(pz);
     float lo3[3] = {fin ? px : INFINITY, fin ? py : INFINITY, fin ? pz : INFINITY};
     float hi3[3] = {fin ? px : -INFINITY, fin ? py : -INFINITY, fin ? pz : -INFINITY};
@@ -343,50 +353,89 @@ __global__ void __launch_bounds__(kFeatWarps * 32) feature_kernel(FeatArgs g) {
 #pragma unroll
     for (int q = 0; q < kPropChunk; ++q) acc[q] = 0.f;
     int count = 0;
-    if (lo3[0] <= hi3[0]) {                             // at least one finite point
+    if (lo3[0] <= hi3[0]) {                             // at least one finite point (CTA-uniform)
+        const float reach2 = g.reach * g.reach;
+        const float cell = 1.0f / g.G.inv_cell;
         int c0[3], c1[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             c0[k] = cell_coord(lo3[k] - g.reach, g.G.lo[k], g.G.inv_cell, g.G.cd[k]);
             c1[k] = cell_coord(hi3[k] + g.reach, g.G.lo[k], g.G.inv_cell, g.G.cd[k]);
         }
-        for (int cz = c0[2]; cz <= c1[2]; ++cz)
-            for (int cy = c0[1]; cy <= c1[1]; ++cy) {
-                const int row = (cz * g.G.cd[1] + cy) * g.G.cd[0];
-                const int b = g.cell_start[row + c0[0]], e = g.cell_start[row + c1[0] + 1];
-                for (int base = b; base < e; base += 32) {
-                    const int j = base + lane;
-                    const int nt = min(32, e - base);
-                    __syncwarp();
-                    if (j < e) {
-                        const float4 B = g.sorted[j];
-                        s_at[wib][lane] = B;
-                        const float* pr = g.props + (size_t)__float_as_int(B.w) * g.n_props + q0;
+        const int ny = c1[1] - c0[1] + 1, n_rows = ny * (c1[2] - c0[2] + 1);
+        for (int rr = wib; rr < n_rows; rr += kFeatSplit) {
+            const int cz = c0[2] + rr / ny, cy = c0[1] + rr % ny;
+            // distance in (y, z) between the box and the row's slab
+            const float ylo = g.G.lo[1] + cy * cell, zlo = g.G.lo[2] + cz * cell;
+            const float dy = fmaxf(0.f, fmaxf(ylo - hi3[1], lo3[1] - (ylo + cell)));
+            const float dz = fmaxf(0.f, fmaxf(zlo - hi3[2], lo3[2] - (zlo + cell)));
+            const float dyz2 = dy * dy + dz * dz;
+            if (dyz2 > reach2) continue;                // warp-uniform
+            const float half = sqrtf(reach2 - dyz2);
+            const int x0 = cell_coord(lo3[0] - half, g.G.lo[0], g.G.inv_cell, g.G.cd[0]);
+            const int x1 = cell_coord(hi3[0] + half, g.G.lo[0], g.G.inv_cell, g.G.cd[0]);
+            const int row = (cz * g.G.cd[1] + cy) * g.G.cd[0];
+            const int b = g.cell_start[row + x0], e = g.cell_start[row + x1 + 1];
+            for (int base = b; base < e; base += 32) {
+                const int j = base + lane;
+                const int nt = min(32, e - base);
+                __syncwarp();
+                if (j < e) {
+                    const float4 B = g.sorted[j];
+                    s_at[wib][lane] = B;
+                    const float* pr = g.props + (size_t)__float_as_int(B.w) * g.n_props + q0;
 #pragma unroll
-                        for (int q = 0; q < kPropChunk; ++q) s_pr[wib][lane][q] = q < nq ? __ldg(pr + q) : 0.f;
-                    }
-                    __syncwarp();
-                    for (int t = 0; t < nt; ++t) {
-                        const float4 B = s_at[wib][t];
-                        const float dx = B.x - px, dy = B.y - py, dz = B.z - pz;
-                        const float d2 = dx * dx + dy * dy + dz * dz;
-                        count += d2 <= g.rp2;
-                        if (d2 < g.rf2) {
-                            const float w = 1.0f - sqrtf(d2) * g.inv_rf;
+                    for (int q = 0; q < kPropChunk; ++q) s_pr[wib][lane][q] = q < nq ? __ldg(pr + q) : 0.f;
+                }
+                __syncwarp();
+                for (int t = 0; t < nt; ++t) {
+                    const float4 B = s_at[wib][t];
+                    const float dx = B.x - px, ey = B.y - py, ez = B.z - pz;
+                    const float d2 = dx * dx + ey * ey + ez * ez;
+                    count += d2 <= g.rp2;
+                    if (d2 < g.rf2) {
+                        const float w = 1.0f - sqrtf(d2) * g.inv_rf;
 #pragma unroll
-                            for (int q = 0; q < kPropChunk; ++q) acc[q] = fmaf(w, s_pr[wib][t][q], acc[q]);
-                        }
+                        for (int q = 0; q < kPropChunk; ++q) acc[q] = fmaf(w, s_pr[wib][t][q], acc[q]);
                     }
                 }
             }
+        }
     }
-    if (!live) return;
-    if (!fin) count = 0;
+#pragma unroll
+    for (int q = 0; q < kPropChunk; ++q) s_red[wib][q][lane] = acc[q];
+    s_red[wib][kPropChunk][lane] = __int_as_float(count);
+    __syncthreads();
+    if (wib != 0 || !live) return;
+    int total = 0;
+#pragma unroll
+    for (int w = 0; w < kFeatSplit; ++w) total += __float_as_int(s_red[w][kPropChunk][lane]);
     float* f = g.feat + (size_t)pi * g.n_props + q0;
 #pragma unroll
-    for (int q = 0; q < kPropChunk; ++q)
-        if (q < nq) f[q] = fin ? acc[q] : 0.f;
-    if (g.prot && blockIdx.y == 0) g.prot[pi] = count;
+    for (int q = 0; q < kPropChunk; ++q) {
+        float v = 0.f;
+#pragma unroll
+        for (int w = 0; w < kFeatSplit; ++w) v += s_red[w][q][lane];
+        if (q < nq) f[q] = fin ? v : 0.f;
+    }
+    if (g.prot && blockIdx.y == 0) g.prot[pi] = fin ? total : 0;
+}
+
+// Points grouped by the cell order of their atoms: perm[base_sorted[s] + t] = offset[i] + t for
+// the t-th point of atom i = order[s].
+__global__ void sorted_counts_kernel(const int* __restrict__ order, const int* __restrict__ n_kept, int n,
+                                     int* __restrict__ cnt) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) cnt[s] = n_kept[order[s]];
+}
+
+__global__ void perm_kernel(const int* __restrict__ order, const int* __restrict__ n_kept,
+                            const int* __restrict__ offset, const int* __restrict__ base_sorted, int n,
+                            int* __restrict__ perm) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int i = order[s], m = n_kept[i], o = offset[i], b = base_sorted[s];
+    for (int t = 0; t < m; ++t) perm[b + t] = o + t;
 }
 
 // ------------------------------------------------------------ Steps 4-5: clusters ---
@@ -465,26 +514,77 @@ __device__ __forceinline__ bool uf_unite(int* par, int a, int b) {
     return a == b;
 }
 
-__global__ void cl_union_kernel(ClusterArgs g, const int* __restrict__ start, const int* __restrict__ order) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n || g.key[i] < 0) return;
-    const float* p = g.pts + 3 * (size_t)i;
-    const float px = p[0], py = p[1], pz = p[2];
-    const int3 c = link_cell(p, g.inv_cell);
+// Clustered points in bucket order as (x, y, z, index bits): a neighbour scan reads each candidate
+// with one contiguous load, and consecutive threads take neighbouring points.
+__global__ void cl_gather_kernel(const int* __restrict__ order, const float* __restrict__ pts,
+                                 const int* __restrict__ total, float4* __restrict__ spts) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= *total) return;
+    const int i = order[t];
+    spts[t] = make_float4(pts[3 * (size_t)i], pts[3 * (size_t)i + 1], pts[3 * (size_t)i + 2], __int_as_float(i));
+}
+
+// One warp per clustered point: lane l < 27 scans link cell l of the 27 around q's cell and calls
+// f(j) for every clustered point j within the link of q there (q included; two cells that share a
+// hash bucket are scanned twice, which changes nothing below).
+template <typename F>
+__device__ __forceinline__ void for_linked_lane(const ClusterArgs& g, const int* __restrict__ start,
+                                                const float4* __restrict__ spts, const float4& q, int lane,
+                                                F&& f) {
+    if (lane >= 27) return;
+    const float p3[3] = {q.x, q.y, q.z};
+    const int3 c = link_cell(p3, g.inv_cell);
+    const int h = cell_hash(c.x + lane % 3 - 1, c.y + (lane / 3) % 3 - 1, c.z + lane / 9 - 1, g.hmask);
+    const int e = start[h + 1];
+    for (int u = start[h]; u < e; ++u) {
+        const float4 o = spts[u];
+        const float ex = o.x - q.x, ey = o.y - q.y, ez = o.z - q.z;
+        if (ex * ex + ey * ey + ez * ez <= g.link2) f(__float_as_int(o.w));
+    }
+}
+
+// One hooking round: every clustered point takes the lowest parent among its linked points and
+// lowers its own tree's root to it (atomicMin keeps parent[x] <= x, and every hook follows a
+// link, so trees only ever join points of one component). From parent[i] = i the first round
+// builds a shallow forest (each point under its lowest-index linked point); after a flattening
+// pass each further round joins neighbouring trees, so their number falls quickly and the
+// lock-free unions that follow have little left to do.
+__global__ void cl_hook_kernel(ClusterArgs g, const int* __restrict__ start, const float4* __restrict__ spts,
+                               int n_buckets) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= start[n_buckets]) return;                  // warp-uniform
+    const float4 q = spts[w];
+    const int ri = __ldcg(g.parent + __float_as_int(q.w));
+    int m = ri;
+    for_linked_lane(g, start, spts, q, lane, [&](int j) { m = min(m, __ldcg(g.parent + j)); });
+    m = __reduce_min_sync(0xffffffffu, m);
+    if (lane == 0 && m < ri) atomicMin(g.parent + ri, m);
+}
+
+// Points every clustered point at the root of its tree (each thread writes only its own entry;
+// a concurrent write elsewhere only shortens the walk), so that most linked pairs are seen to
+// share a tree by one comparison.
+__global__ void cl_flatten_kernel(ClusterArgs g, const int* __restrict__ start, const float4* __restrict__ spts,
+                                  int n_buckets) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= start[n_buckets]) return;
+    const int i = __float_as_int(spts[t].w);
+    int r = __ldcg(g.parent + i);
+    for (int next; (next = __ldcg(g.parent + r)) < r;) r = next;
+    g.parent[i] = r;
+}
+
+__global__ void cl_union_kernel(ClusterArgs g, const int* __restrict__ start, const float4* __restrict__ spts,
+                                int n_buckets) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= start[n_buckets]) return;                  // warp-uniform
+    const float4 q = spts[w];
+    const int i = __float_as_int(q.w);
     bool ok = true;
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int h = cell_hash(c.x + dx, c.y + dy, c.z + dz, g.hmask);
-                const int e = start[h + 1];
-                for (int t = start[h]; t < e; ++t) {
-                    const int j = order[t];
-                    if (j <= i) continue;
-                    const float* q = g.pts + 3 * (size_t)j;
-                    const float ex = q[0] - px, ey = q[1] - py, ez = q[2] - pz;
-                    if (ex * ex + ey * ey + ez * ez <= g.link2) ok = uf_unite(g.parent, i, j) && ok;
-                }
-            }
+    for_linked_lane(g, start, spts, q, lane, [&](int j) {
+        // components only ever merge, so equal parents mean the pair is already joined
+        if (j > i && __ldcg(g.parent + i) != __ldcg(g.parent + j)) ok = uf_unite(g.parent, i, j) && ok;
+    });
     if (!ok) atomicOr(g.err, kErrUnion);
 }
 
@@ -495,7 +595,8 @@ struct StatsArgs {
     int* parent;
     int n;
     int* root;               // [n]
-    int* is_root;            // [n] 0/1
+    int* cid;                // [n] cluster id of a root (order of discovery)
+    int* n_clusters;         // counter
     double* s2;              // [n] per root
     double* sx;              // [n][3] per root
     int* size;               // [n] per root
@@ -506,7 +607,7 @@ __global__ void cl_root_kernel(StatsArgs g) {
     if (i >= g.n) return;
     const int r = g.key[i] < 0 ? -1 : uf_find(g.parent, i);
     g.root[i] = r;
-    g.is_root[i] = r == i;
+    if (r == i) g.cid[i] = atomicAdd(g.n_clusters, 1);
 }
 
 __global__ void cl_stats_kernel(StatsArgs g) {
@@ -520,14 +621,16 @@ __global__ void cl_stats_kernel(StatsArgs g) {
     atomicAdd(g.size + r, 1);
 }
 
+// Cluster ids come from a counter, so their order is arbitrary; everything below depends on the
+// ranking (score, then lowest index) only, which is unique.
 struct RankArgs {
-    const int* is_root;
-    const int* cid;          // [n + 1] exclusive scan of is_root; cid[n] = K
+    const int* cid;
+    const int* n_clusters;
     const double* s2;
     const double* sx;
     const int* size;
     int n;
-    double* c_s2;            // [n] by cluster id (index order of roots)
+    double* c_s2;            // [n] by cluster id
     int* c_first;            // [n]
     int* rank;               // [n] rank of cluster id
     float* out_score;        // [n] by rank
@@ -540,7 +643,7 @@ struct RankArgs {
 
 __global__ void cl_compact_kernel(RankArgs g) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n || !g.is_root[i]) return;
+    if (i >= g.n || g.root[i] != i) return;
     const int c = g.cid[i];
     g.c_s2[c] = g.s2[i];
     g.c_first[c] = i;
@@ -550,7 +653,7 @@ __global__ void cl_compact_kernel(RankArgs g) {
 __global__ void __launch_bounds__(256) cl_rank_kernel(RankArgs g) {
     __shared__ double s_s[256];
     __shared__ int s_f[256];
-    const int K = g.cid[g.n];
+    const int K = *g.n_clusters;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (blockIdx.x * blockDim.x >= K) return;           // block-uniform
     const double sc = c < K ? g.c_s2[c] : 0.0;
@@ -586,16 +689,57 @@ __global__ void cl_output_kernel(RankArgs g) {
 
 // ------------------------------------------------------------------------- host side ---
 
+// Device memory of the pocket side: one stream-ordered pool per device, owned by the library,
+// that keeps freed blocks for reuse until the process exits (the device's default pool hands them
+// back to the driver at every synchronisation, and mapping them again costs more than the
+// kernels of a call).
+cudaMemPool_t pocket_pool(int device, cudaError_t* err) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    if (device < 0 || device >= 64) {
+        *err = cudaErrorInvalidDevice;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[device]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t p = nullptr;
+        *err = cudaMemPoolCreate(&p, &props);
+        if (*err != cudaSuccess) return nullptr;
+        uint64_t keep = ~0ull;
+        *err = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (*err != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return nullptr;
+        }
+        pools[device] = p;
+    }
+    *err = cudaSuccess;
+    return pools[device];
+}
+
+// The allocations of one object or one call, freed together in stream order.
 struct Pool {
-    cudaStream_t stream;
+    cudaStream_t stream = nullptr;
+    cudaMemPool_t mp = nullptr;
     std::vector<void*> ptrs;
     cudaError_t err = cudaSuccess;
-    explicit Pool(cudaStream_t s) : stream(s) {}
+    Pool() = default;
+    Pool(cudaStream_t s, int device) { init(s, device); }
+    void init(cudaStream_t s, int device) {
+        stream = s;
+        mp = pocket_pool(device, &err);
+    }
     template <typename T>
     T* take(size_t count) {
         void* p = nullptr;
         if (err != cudaSuccess) return nullptr;
-        err = cudaMallocAsync(&p, count ? count * sizeof(T) : 16, stream);
+        err = cudaMallocFromPoolAsync(&p, count ? count * sizeof(T) : 16, mp, stream);
         if (err != cudaSuccess) return nullptr;
         ptrs.push_back(p);
         return (T*)p;
@@ -643,20 +787,21 @@ struct pv_surface {
     int magic = kSurfaceMagic;
     pv_context* ctx = nullptr;
     int device = 0;
-    Pool pool{nullptr};
+    Pool pool;
     int n_atoms = 0, n_points = 0, n_sphere = 0;
     AtomGrid G{};
     float4* sorted = nullptr;
     int* cell_start = nullptr;
     float* points = nullptr;
     int* src = nullptr;
+    int* perm = nullptr;      // points grouped by the cell order of their atoms
 };
 
 struct pv_clusters {
     int magic = kClustersMagic;
     pv_context* ctx = nullptr;
     int device = 0;
-    Pool pool{nullptr};
+    Pool pool;
     int n = 0, K = 0;
     int* cluster = nullptr;
     float* score = nullptr;
@@ -748,11 +893,11 @@ extern "C" pv_status pv_surface_create(pv_context* ctx, const pv_receptor* r, co
     if (!S) return fail(ctx, PV_ERR_OOM, "host allocation failed");
     S->ctx = ctx;
     S->device = dev;
-    S->pool.stream = st;
+    S->pool.init(st, dev);
     S->n_atoms = n;
     S->n_sphere = ns;
     S->G = G;
-    Pool scratch(st);
+    Pool scratch(st, dev);
     const float* d_xyz = r->xyz;
     const uint8_t* d_el = r->element;
     const float* d_rad = radius;
@@ -763,7 +908,7 @@ extern "C" pv_status pv_surface_create(pv_context* ctx, const pv_receptor* r, co
     }
     float4* atoms = scratch.take<float4>(n);
     float* arad = scratch.take<float>(n);
-    int* key = scratch.take<int>(n);
+    int* key = scratch.take<int>(n + 1);   // n + 1: reused for a scan below
     int* count = scratch.take<int>(n_cells);
     int* cursor = scratch.take<int>(n_cells);
     int* slot_elem = scratch.take<int>(n);
@@ -822,12 +967,17 @@ extern "C" pv_status pv_surface_create(pv_context* ctx, const pv_receptor* r, co
         S->n_points = h_total;
         S->points = S->pool.take<float>(3 * (size_t)(h_total > 0 ? h_total : 1));
         S->src = S->pool.take<int>(h_total > 0 ? h_total : 1);
+        S->perm = S->pool.take<int>(h_total > 0 ? h_total : 1);
         step(S->pool.err, "point allocation");
     }
     if (e == cudaSuccess) {
         sas_write_kernel<<<(n + 3) / 4, 128, 0, st>>>(atoms, arad, d_dirs, n, ns, kept, offset, S->points, S->src);
         step(cudaGetLastError(), "surface points");
-        step(cudaStreamSynchronize(st), "surface points");   // the scratch goes back to the pool below
+        // the point order of the feature kernel: atoms in cell order (slot_elem is free again)
+        sorted_counts_kernel<<<(n + 255) / 256, 256, 0, st>>>(order, n_kept, n, slot_elem);
+        scan_kernel<<<1, 1024, 0, st>>>(slot_elem, n, key);          // key: n + 1 ints, free again
+        perm_kernel<<<(n + 255) / 256, 256, 0, st>>>(order, n_kept, offset, key, n, S->perm);
+        step(cudaGetLastError(), "point order");
     }
     scratch.release();
     if (e != cudaSuccess) {
@@ -884,7 +1034,7 @@ extern "C" pv_status pv_surface_features(pv_context* ctx, const pv_surface* s, i
     if (n_points > 0 && !dev_features) return fail(ctx, PV_ERR_ARG, "dev_features is null");
     if (n_points == 0) return PV_OK;
     DeviceGuard guard(dev);
-    Pool scratch(st);
+    Pool scratch(st, dev);
     const float* d_pts = xyz ? xyz : s->points;
     const float* d_props = props;
     cudaError_t e = cudaSuccess;
@@ -906,6 +1056,7 @@ extern "C" pv_status pv_surface_features(pv_context* ctx, const pv_surface* s, i
         a.cell_start = s->cell_start;
         a.G = s->G;
         a.pts = d_pts;
+        a.perm = xyz ? nullptr : s->perm;
         a.n_pts = n_points;
         a.props = d_props;
         a.n_props = n_props;
@@ -915,9 +1066,8 @@ extern "C" pv_status pv_surface_features(pv_context* ctx, const pv_surface* s, i
         a.reach = std::max(p->r_feature, p->r_protrusion) + 1e-3f;
         a.feat = dev_features;
         a.prot = dev_protrusion;
-        const dim3 grid((unsigned)((n_points + 32 * kFeatWarps - 1) / (32 * kFeatWarps)),
-                        (unsigned)((n_props + kPropChunk - 1) / kPropChunk));
-        feature_kernel<<<grid, kFeatWarps * 32, 0, st>>>(a);
+        const dim3 grid((unsigned)((n_points + 31) / 32), (unsigned)((n_props + kPropChunk - 1) / kPropChunk));
+        feature_kernel<<<grid, kFeatSplit * 32, 0, st>>>(a);
         e = cudaGetLastError();
     }
     scratch.release();   // stream-ordered: the kernel above finishes first
@@ -947,7 +1097,7 @@ extern "C" pv_status pv_cluster_points(pv_context* ctx, int32_t n, const float* 
     if (!C) return fail(ctx, PV_ERR_OOM, "host allocation failed");
     C->ctx = ctx;
     C->device = dev;
-    C->pool.stream = st;
+    C->pool.init(st, dev);
     C->n = n;
     const size_t m = n > 0 ? (size_t)n : 1;
     C->cluster = C->pool.take<int>(m);
@@ -966,8 +1116,8 @@ extern "C" pv_status pv_cluster_points(pv_context* ctx, int32_t n, const float* 
         return PV_OK;
     }
     uint32_t buckets = 1024;
-    while (buckets < 2u * (uint32_t)n) buckets <<= 1;
-    Pool scratch(st);
+    while (2 * buckets < (uint32_t)n) buckets <<= 1;
+    Pool scratch(st, dev);
     int* key = scratch.take<int>(m);
     int* count = scratch.take<int>(buckets);
     int* start = scratch.take<int>(buckets + 1);
@@ -977,8 +1127,9 @@ extern "C" pv_status pv_cluster_points(pv_context* ctx, int32_t n, const float* 
     int* parent = scratch.take<int>(m);
     int* err = scratch.take<int>(1);
     int* root = scratch.take<int>(m);
-    int* is_root = scratch.take<int>(m);
-    int* cid = scratch.take<int>(m + 1);
+    int* cid = scratch.take<int>(m);
+    int* n_clusters = scratch.take<int>(1);
+    float4* spts = scratch.take<float4>(m);
     double* s2 = scratch.take<double>(m);
     double* sx = scratch.take<double>(3 * m);
     int* size = scratch.take<int>(m);
@@ -997,6 +1148,7 @@ extern "C" pv_status pv_cluster_points(pv_context* ctx, int32_t n, const float* 
         step(cudaMemsetAsync(s2, 0, sizeof(double) * m, st), "memset");
         step(cudaMemsetAsync(sx, 0, sizeof(double) * 3 * m, st), "memset");
         step(cudaMemsetAsync(size, 0, sizeof(int) * m, st), "memset");
+        step(cudaMemsetAsync(n_clusters, 0, sizeof(int), st), "memset");
     }
     if (e == cudaSuccess) {
         ClusterArgs a;
@@ -1016,20 +1168,25 @@ extern "C" pv_status pv_cluster_points(pv_context* ctx, int32_t n, const float* 
         cl_init_kernel<<<b, 256, 0, st>>>(a);
         step(cudaGetLastError(), "cluster set-up");
         step(bin_keys(key, n, (int)buckets, count, start, cursor, slot_elem, order, st), "point binning");
-        cl_union_kernel<<<b, 256, 0, st>>>(a, start, order);
+        cl_gather_kernel<<<b, 256, 0, st>>>(order, dev_xyz, start + buckets, spts);
+        const int bw = (n + 7) / 8;                     // a warp per point: 8 points per CTA of 256
+        for (int round = 0; round < kHookRounds; ++round) {
+            cl_hook_kernel<<<bw, 256, 0, st>>>(a, start, spts, (int)buckets);
+            cl_flatten_kernel<<<b, 256, 0, st>>>(a, start, spts, (int)buckets);
+        }
+        cl_union_kernel<<<bw, 256, 0, st>>>(a, start, spts, (int)buckets);
         step(cudaGetLastError(), "single linkage");
-        StatsArgs sa{dev_xyz, dev_score, key, parent, n, root, is_root, s2, sx, size};
+        StatsArgs sa{dev_xyz, dev_score, key, parent, n, root, cid, n_clusters, s2, sx, size};
         cl_root_kernel<<<b, 256, 0, st>>>(sa);
         cl_stats_kernel<<<b, 256, 0, st>>>(sa);
         step(cudaGetLastError(), "cluster sums");
-        scan_kernel<<<1, 1024, 0, st>>>(is_root, n, cid);
-        RankArgs ra{is_root, cid, s2, sx, size, n, c_s2, c_first, rank, C->score, C->center, C->size, C->first, root, C->cluster};
+        RankArgs ra{cid, n_clusters, s2, sx, size, n, c_s2, c_first, rank, C->score, C->center, C->size, C->first, root, C->cluster};
         cl_compact_kernel<<<b, 256, 0, st>>>(ra);
         cl_rank_kernel<<<b, 256, 0, st>>>(ra);
         cl_output_kernel<<<b, 256, 0, st>>>(ra);
         step(cudaGetLastError(), "cluster ranking");
         step(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st), "readback");
-        step(cudaMemcpyAsync(&h_k, cid + n, sizeof(int), cudaMemcpyDeviceToHost, st), "readback");
+        step(cudaMemcpyAsync(&h_k, n_clusters, sizeof(int), cudaMemcpyDeviceToHost, st), "readback");
         step(cudaStreamSynchronize(st), "clusters");
     }
     scratch.release();
