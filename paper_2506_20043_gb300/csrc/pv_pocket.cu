@@ -34,8 +34,8 @@ constexpr float kCell = 4.0f;            // atom binning cell edge, A
 constexpr int kMaxAtoms = 200000;
 constexpr int kNb = 128;                 // neighbour list capacity per warp (SAS kernel)
 constexpr int kSasWarps = 4;
-constexpr int kFeatSplit = 4;          // warps sharing one group of 32 points (feature kernel)
-constexpr int kPropChunk = 8;            // property columns per feature launch row
+constexpr int kFeatSplit = 16;         // warps sharing one group of 32 points (feature kernel)
+constexpr int kPropChunk = 8;            // property columns per feature launch row (a multiple of 4)
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kHookRounds = 3;           // hooking rounds before the unions (clustering)
 
@@ -324,7 +324,7 @@ struct FeatArgs {
 // reach), then add their partial sums in shared memory.
 __global__ void __launch_bounds__(kFeatSplit * 32) feature_kernel(FeatArgs g) {
     __shared__ float4 s_at[kFeatSplit][32];
-    __shared__ float s_pr[kFeatSplit][32][kPropChunk + 1];
+    __shared__ float4 s_pr[kFeatSplit][32][kPropChunk / 4];   // an atom's chunk: two broadcast loads
     __shared__ float s_red[kFeatSplit][kPropChunk + 1][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int slot = blockIdx.x * 32 + lane;
@@ -384,8 +384,12 @@ __global__ void __launch_bounds__(kFeatSplit * 32) feature_kernel(FeatArgs g) {
                     const float4 B = g.sorted[j];
                     s_at[wib][lane] = B;
                     const float* pr = g.props + (size_t)__float_as_int(B.w) * g.n_props + q0;
+                    float v[kPropChunk];
 #pragma unroll
-                    for (int q = 0; q < kPropChunk; ++q) s_pr[wib][lane][q] = q < nq ? __ldg(pr + q) : 0.f;
+                    for (int q = 0; q < kPropChunk; ++q) v[q] = q < nq ? __ldg(pr + q) : 0.f;
+#pragma unroll
+                    for (int q = 0; q < kPropChunk / 4; ++q)
+                        s_pr[wib][lane][q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
                 }
                 __syncwarp();
                 for (int t = 0; t < nt; ++t) {
@@ -396,7 +400,13 @@ __global__ void __launch_bounds__(kFeatSplit * 32) feature_kernel(FeatArgs g) {
                     if (d2 < g.rf2) {
                         const float w = 1.0f - sqrtf(d2) * g.inv_rf;
 #pragma unroll
-                        for (int q = 0; q < kPropChunk; ++q) acc[q] = fmaf(w, s_pr[wib][t][q], acc[q]);
+                        for (int q = 0; q < kPropChunk / 4; ++q) {
+                            const float4 pv = s_pr[wib][t][q];
+                            acc[4 * q] = fmaf(w, pv.x, acc[4 * q]);
+                            acc[4 * q + 1] = fmaf(w, pv.y, acc[4 * q + 1]);
+                            acc[4 * q + 2] = fmaf(w, pv.z, acc[4 * q + 2]);
+                            acc[4 * q + 3] = fmaf(w, pv.w, acc[4 * q + 3]);
+                        }
                     }
                 }
             }
