@@ -113,10 +113,12 @@ DOCK_SOURCES = ("pv_api.cu", "pv_chain.cuh", "pv_device.cuh", "pv_grid.cu", "pv_
 
 
 def kernel_source_hash() -> str:
+    """Hash of the dock path's sources and of the build script (its compiler flags shape the code)."""
     d = os.path.join(ROOT, "paper_2506_20043_gb300", "csrc")
     h = hashlib.sha256()
     for f in sorted(DOCK_SOURCES):
         h.update(open(os.path.join(d, f), "rb").read())
+    h.update(open(os.path.join(ROOT, "paper_2506_20043_gb300", "build.py"), "rb").read())
     return h.hexdigest()[:16]
 
 
