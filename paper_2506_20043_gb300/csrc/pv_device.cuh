@@ -38,14 +38,22 @@ __host__ __device__ inline bool xs_acceptor(int t) { return t == 4 || t == 5 || 
 // clamped ramp sat((p1 - d) p2) with the pair's weight: p1 = 1.5, p2 = 1 for hydrophobic pairs,
 // p1 = 0, p2 = 1 / 0.7 for H-bond pairs; its derivative is -p2 on the ramp (the same values and
 // one-sided derivatives as vina_pair below).
+// 2^x by the PTX approximation (flush-to-zero); the exponentials below use e^y = 2^(y log2 e) with
+// log2 e folded into their constants.
+__device__ __forceinline__ float exp2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+constexpr float kLog2e = 1.44269504088896341f;
+
 __device__ __forceinline__ float vina_pair_r2(float r2, float rsum, bool hyd, bool hb, float& dedr_over_r) {
     const float rinv = rsqrtf(fmaxf(r2, 1e-12f));
     const float r = r2 * rinv;
     const float d = r - rsum;
-    const float a = 2.0f * d;                    // d / 0.5
-    const float g1 = __expf(-a * a);
-    const float b = 0.5f * (d - 3.0f);           // (d - 3) / 2
-    const float g2 = __expf(-b * b);
+    const float g1 = exp2_approx(d * d * (-4.0f * kLog2e));     // exp(-(d / 0.5)^2)
+    const float b = d - 3.0f;
+    const float g2 = exp2_approx(b * b * (-0.25f * kLog2e));    // exp(-((d - 3) / 2)^2)
     const float rep = fminf(d, 0.0f);
     const float p1 = hyd ? 1.5f : 0.0f, p2 = hyd ? 1.0f : (1.0f / 0.7f);
     const float w = hyd ? kWHydrophobic : (hb ? kWHBond : 0.0f);
@@ -53,7 +61,7 @@ __device__ __forceinline__ float vina_pair_r2(float r2, float rsum, bool hyd, bo
     const float v = __saturatef(t);
     const float dv = (t > 0.0f && t <= 1.0f) ? -p2 : 0.0f;
     const float e = kWGauss1 * g1 + kWGauss2 * g2 + kWRepulsion * rep * rep + w * v;
-    const float de = kWGauss1 * g1 * (-4.0f * a) + kWGauss2 * g2 * (-b) + (2.0f * kWRepulsion) * rep + w * dv;
+    const float de = (-8.0f * kWGauss1) * d * g1 + (-0.5f * kWGauss2) * b * g2 + (2.0f * kWRepulsion) * rep + w * dv;
     dedr_over_r = r2 > 1e-12f ? de * rinv : 0.0f;
     return e;
 }
