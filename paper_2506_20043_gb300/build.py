@@ -26,7 +26,7 @@ def nvcc() -> str:
 
 def _flags():
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
-                   "--expt-relaxed-constexpr", "-ftz=true", "-Xptxas", "-warn-spills"]
+                   "--expt-relaxed-constexpr", "--use_fast_math", "-Xptxas", "-warn-spills"]
 
 
 def _stale(obj: str, src: str) -> bool:

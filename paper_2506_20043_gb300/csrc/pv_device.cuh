@@ -139,6 +139,16 @@ __device__ __forceinline__ float4 quat_mul(float4 a, float4 b) {
                        a.x * b.z - a.y * b.w + a.z * b.x + a.w * b.y,
                        a.x * b.w + a.y * b.z - a.z * b.y + a.w * b.x);
 }
+// x reduced to [-pi, pi] by the two-constant reduction of Cody & Waite ("Software Manual for the
+// Elementary Functions", 1980): x - k 2pi with k = rint(x / 2pi) and 2pi split into its nearest float
+// and the remainder; the fast sine and cosine (the build uses them) are accurate on [-pi, pi], and
+// angles here (torsions that a search moves freely) can lie anywhere.
+__device__ __forceinline__ float wrap_pi(float x) {
+    const float k = rintf(x * (1.0f / (2.0f * PV_PI)));
+    const float r = fmaf(k, -6.28318548e+00f, x);     // 2pi rounded to float
+    return fmaf(k, 1.74845560e-07f, r);               // minus (2pi - that float)
+}
+
 // q <- normalize(exp(omega / 2) (x) q): world-frame rotation by the rotation vector omega.
 __device__ __forceinline__ float4 quat_rotate_by(float4 q, float3 om) {
     float th2 = om.x * om.x + om.y * om.y + om.z * om.z;
@@ -147,7 +157,7 @@ __device__ __forceinline__ float4 quat_rotate_by(float4 q, float3 om) {
         e = make_float4(1.0f, 0.5f * om.x, 0.5f * om.y, 0.5f * om.z);
     } else {
         float th = sqrtf(th2), s, c;
-        sincosf(0.5f * th, &s, &c);
+        sincosf(wrap_pi(0.5f * th), &s, &c);
         s /= th;
         e = make_float4(c, s * om.x, s * om.y, s * om.z);
     }
@@ -165,7 +175,7 @@ __device__ __forceinline__ Mat3 unit_quat_to_mat(float w, float x, float y, floa
 // Rotation by angle t about the unit axis a (Rodrigues).
 __device__ __forceinline__ Mat3 axis_angle(float3 a, float t) {
     float s, c;
-    sincosf(t, &s, &c);
+    sincosf(wrap_pi(t), &s, &c);
     float C = 1.0f - c;
     Mat3 R;
     R.m[0] = c + a.x * a.x * C;        R.m[1] = a.x * a.y * C - a.z * s; R.m[2] = a.x * a.z * C + a.y * s;

@@ -120,7 +120,7 @@ __device__ __forceinline__ void team_fk(const PvLigBlob& L, WarpScratch& S, cons
     // torsion's half-angle quaternion (cos psi/2, sin psi/2 * axis) about its hinge axis; world
     // rotations compose down the tree level by level (Q_f = Q_parent (x) q_f)
     float s2, c2;
-    sincosf(0.5f * (isf ? psi : 0.0f), &s2, &c2);
+    sincosf(wrap_pi(0.5f * (isf ? psi : 0.0f)), &s2, &c2);
     float4 Q = tl == 0 ? quat_normalize(x.q) : make_float4(c2, s2 * axis.x, s2 * axis.y, s2 * axis.z);
     const float4 ql = Q;
     xa = (tl == 0) ? x.T : make_float3(0.f, 0.f, 0.f);
