@@ -890,8 +890,13 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
                 cudaGetLastError();
                 continue;
             }
+            // whole waves of the shape's resident CTAs (up to four) when the work allows, so that a
+            // partly filled last wave, which the chained step blocks of a real launch do not have,
+            // does not weigh on the shapes with fewer, larger CTAs
             std::vector<PvItem> trial = make_items(wc * (32 / lanes_c));
-            const int n_trial = (int)std::min<size_t>(trial.size(), (size_t)4 * ctx->sms * occ_c);
+            const size_t slots = (size_t)ctx->sms * occ_c;
+            size_t n_waves = std::min<size_t>(4, trial.size() / slots);
+            const int n_trial = (int)(n_waves > 0 ? n_waves * slots : trial.size());
             SearchArgs a = A;
             a.items = (const PvItem*)((char*)R->d_work + o_items);
             a.n_items = 0;                       // an empty launch first: loads the variant's code
