@@ -5,7 +5,9 @@
  * receptor grid maps ("Kernel 1"), Vina-style scoring of ligand poses by trilinear
  * interpolation plus intra-ligand terms (Eq. 3) with its analytic gradient over pose, and
  * many independent Monte-Carlo + RILC-BFGS chains per (ligand, pocket) pair ("Kernel 2",
- * Eq. 1-13, Supplementary Algorithm 2), aggregated over pockets (Algorithm 3).
+ * Eq. 1-13, Supplementary Algorithm 2), aggregated over pockets (Algorithm 3); and the pocket
+ * side that places the boxes (Methods "Pocket Prediction with P2Rank", Eq. 1-2, Supplementary
+ * Algorithm 1): surface points, their property sums and the ranked clusters of scored points.
  *
  * Conventions
  *   - Every call returns pv_status; no C++ exception crosses the ABI and nothing aborts.

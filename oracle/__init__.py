@@ -2,8 +2,9 @@
 
 Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
 import this package. It shares no code with the CUDA path: the arithmetic lives in
-``pv_oracle.c`` (plain C, FP64, compiled with gcc here) and this module only marshals numpy
-arrays through ctypes and does the final cross-pocket merge with a plain sort.
+``pv_oracle.c`` (docking) and ``pv_oracle_pocket.c`` (pocket side: surface points, Eq. 1 sums,
+clusters), plain C in FP64 compiled with gcc here, and this module only marshals numpy arrays
+through ctypes and does the final cross-pocket merge with a plain sort.
 
 Parity pins for every function live in ``tests/test_oracle_*.py``.
 """
