@@ -39,3 +39,16 @@ def test_binding_refuses_to_run_without_a_gpu():
     from paper_2506_20043_gb300 import api
     with pytest.raises(api.PVError):
         api.Context(0)
+
+
+def test_pocket_parameter_defaults_agree():
+    # host-only entry point: the binding's defaults are the library's
+    import dataclasses
+    from paper_2506_20043_gb300 import _capi, api
+    lib = _capi.load()
+    p = _capi.pv_pocket_params()
+    assert lib.pv_pocket_params_default(ctypes.byref(p)) == _capi.PV_OK
+    q = api.PocketParams()
+    for f in dataclasses.fields(q):
+        assert getattr(p, f.name) == pytest.approx(getattr(q, f.name)), f.name
+    assert lib.pv_pocket_params_default(None) == _capi.PV_ERR_ARG
