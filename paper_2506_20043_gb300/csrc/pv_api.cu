@@ -868,8 +868,10 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     M.top_k = p.top_k;
     M.rank_stride = R->rank_stride;
     M.ranking = R->d_ranking;
-    // autotuning: time each candidate launch shape on eight MC steps of its own first work items
+    // autotuning: time each candidate launch shape on kTuneSteps MC steps of its own first work
+    // items (long enough that chains which share a CTA even out, as over a real step block)
     if (need_tune) {
+        constexpr int kTuneSteps = 32;
         static const int cand[][2] = {{0, 1}, {0, 2}, {0, 4}, {0, 8}, {1, 4}, {2, 4}, {3, 4},
                                       {4, 1}, {4, 2}, {4, 4}, {5, 4}, {6, 4}, {7, 4}};
         cudaEvent_t t0, t1;
@@ -902,9 +904,9 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
             a.n_items = 0;                       // an empty launch first: loads the variant's code
             a.queue = ctr + 1;
             a.step0 = 0;
-            a.step1 = std::min(p.steps, 8);
-            a.items_per_block = n_trial;         // one step block of 8 steps
-            a.block_steps = 8;
+            a.step1 = std::min(p.steps, kTuneSteps);
+            a.items_per_block = n_trial;         // one step block
+            a.block_steps = kTuneSteps;
             cudaError_t x = cudaMemcpyAsync((char*)R->d_work + o_items, trial.data(), sizeof(PvItem) * n_trial,
                                             cudaMemcpyHostToDevice, ctx->stream);
             if (x == cudaSuccess) x = cudaMemsetAsync(ctr, 0, sizeof(int) * 2, ctx->stream);
