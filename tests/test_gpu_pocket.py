@@ -180,6 +180,27 @@ def test_features_at_surface_points():
     _check_features(rec, props, ref_pts, feat.cpu().numpy()[both], prot.cpu().numpy()[both])
 
 
+def test_features_full_size_sampled():
+    # the bench's configuration (8,000 atoms, 100 points per atom, 7 columns), 1,000 sampled surface
+    # points: GPU sums at the GPU's points against the oracle's at its own points of the same keys
+    ctx = G.context()
+    site = S.pocket_site(0, 8000, 10)
+    rec = _rec32(site.receptor)
+    props = S.atom_properties(rec, 0).astype(np.float64)
+    surf = ctx.surface(rec, params=_params(n_sphere=100))
+    feat, prot = surf.features(props)
+    src = surf.sources()
+    rng = np.random.default_rng(11)
+    rows = np.sort(rng.choice(len(src), 1000, replace=False))
+    atoms = np.unique(src[rows] // 100).astype(np.int32)
+    keep, opts, _ = O.sas_points(rec.xyz, _radii32(rec), 1.6, 100, atoms=atoms)
+    row_of = {int(a) * 100 + k: i * 100 + k for i, a in enumerate(atoms) for k in range(100)}
+    orow = np.array([row_of[int(k)] for k in src[rows]])
+    both = keep[orow] == 1
+    assert both.mean() > 0.99
+    _check_features(rec, props, opts[orow[both]], feat.cpu().numpy()[rows[both]], prot.cpu().numpy()[rows[both]])
+
+
 def test_features_edge_cases():
     torch = pytest.importorskip("torch")
     ctx = G.context()
