@@ -35,6 +35,7 @@ constexpr int kMaxAtoms = 200000;
 constexpr int kNb = 128;                 // neighbour list capacity per warp (SAS kernel)
 constexpr int kSasWarps = 4;
 constexpr int kFeatSplit = 16;         // warps sharing one group of 32 points (feature kernel)
+constexpr int kFeatRows = 256;          // cell rows listed at a time by the feature kernel
 constexpr int kPropChunk = 8;            // property columns per feature launch row (a multiple of 4)
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kHookRounds = 3;           // hooking rounds before the unions (clustering)
@@ -319,13 +320,18 @@ struct FeatArgs {
     int* prot;               // [n_pts] or null
 };
 
-// One CTA per group of 32 points; its kFeatSplit warps share the group and split the cell rows
-// within reach of the group's bounding box (a row's x range trimmed to the box swept by the
-// reach), then add their partial sums in shared memory.
+// One CTA per group of 32 points. The cell rows within reach of the group's bounding box (each
+// row's x range trimmed to the box swept by the reach) are listed with their atom counts, up to
+// kFeatRows at a time, and the concatenated atoms of the listed rows are cut into chunks of 32:
+// the CTA's kFeatSplit warps take the chunks in turn (balanced to within one chunk), each loading
+// its next chunk into registers while it works on the current one; the partial sums are added in
+// shared memory at the end.
 __global__ void __launch_bounds__(kFeatSplit * 32) feature_kernel(FeatArgs g) {
     __shared__ float4 s_at[kFeatSplit][32];
     __shared__ float4 s_pr[kFeatSplit][32][kPropChunk / 4];   // an atom's chunk: two broadcast loads
     __shared__ float s_red[kFeatSplit][kPropChunk + 1][32];
+    __shared__ int s_beg[kFeatRows];                          // first atom of a listed row
+    __shared__ int s_off[kFeatRows + 1];                      // position of its atoms in the list
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int slot = blockIdx.x * 32 + lane;
     const int q0 = blockIdx.y * kPropChunk;
@@ -338,7 +344,7 @@ __global__ void __launch_bounds__(kFeatSplit * 32) feature_kernel(FeatArgs g) {
         py = g.pts[3 * (size_t)pi + 1];
         pz = g.pts[3 * (size_t)pi + 2];
     }
-    // the group's bounding box (non-finite points take no part)
+    // the group's bounding box (non-finite points take no part); every warp computes the same one
     const bool fin = live && isfinite(px) && isfinite(py) && isfinite(pz);
     float lo3[3] = {fin ? px : INFINITY, fin ? py : INFINITY, fin ? pz : INFINITY};
     float hi3[3] = {fin ? px : -INFINITY, fin ? py : -INFINITY, fin ? pz : -INFINITY};
@@ -363,38 +369,78 @@ __global__ void __launch_bounds__(kFeatSplit * 32) feature_kernel(FeatArgs g) {
             c1[k] = cell_coord(hi3[k] + g.reach, g.G.lo[k], g.G.inv_cell, g.G.cd[k]);
         }
         const int ny = c1[1] - c0[1] + 1, n_rows = ny * (c1[2] - c0[2] + 1);
-        for (int rr = wib; rr < n_rows; rr += kFeatSplit) {
-            const int cz = c0[2] + rr / ny, cy = c0[1] + rr % ny;
-            // distance in (y, z) between the box and the row's slab
-            const float ylo = g.G.lo[1] + cy * cell, zlo = g.G.lo[2] + cz * cell;
-            const float dy = fmaxf(0.f, fmaxf(ylo - hi3[1], lo3[1] - (ylo + cell)));
-            const float dz = fmaxf(0.f, fmaxf(zlo - hi3[2], lo3[2] - (zlo + cell)));
-            const float dyz2 = dy * dy + dz * dz;
-            if (dyz2 > reach2) continue;                // warp-uniform
-            const float half = sqrtf(reach2 - dyz2);
-            const int x0 = cell_coord(lo3[0] - half, g.G.lo[0], g.G.inv_cell, g.G.cd[0]);
-            const int x1 = cell_coord(hi3[0] + half, g.G.lo[0], g.G.inv_cell, g.G.cd[0]);
-            const int row = (cz * g.G.cd[1] + cy) * g.G.cd[0];
-            const int b = g.cell_start[row + x0], e = g.cell_start[row + x1 + 1];
-            for (int base = b; base < e; base += 32) {
-                const int j = base + lane;
-                const int nt = min(32, e - base);
-                __syncwarp();
-                if (j < e) {
-                    const float4 B = g.sorted[j];
-                    s_at[wib][lane] = B;
+        for (int rbase = 0; rbase < n_rows; rbase += kFeatRows) {
+            const int nr = min(kFeatRows, n_rows - rbase);
+            // list the rows: begin and atom count (zero for a row out of reach)
+            for (int t = threadIdx.x; t < nr; t += kFeatSplit * 32) {
+                const int rr = rbase + t;
+                const int cz = c0[2] + rr / ny, cy = c0[1] + rr % ny;
+                const float ylo = g.G.lo[1] + cy * cell, zlo = g.G.lo[2] + cz * cell;
+                const float dy = fmaxf(0.f, fmaxf(ylo - hi3[1], lo3[1] - (ylo + cell)));
+                const float dz = fmaxf(0.f, fmaxf(zlo - hi3[2], lo3[2] - (zlo + cell)));
+                const float dyz2 = dy * dy + dz * dz;
+                int b = 0, n = 0;
+                if (dyz2 <= reach2) {
+                    const float half = sqrtf(reach2 - dyz2);
+                    const int x0 = cell_coord(lo3[0] - half, g.G.lo[0], g.G.inv_cell, g.G.cd[0]);
+                    const int x1 = cell_coord(hi3[0] + half, g.G.lo[0], g.G.inv_cell, g.G.cd[0]);
+                    const int row = (cz * g.G.cd[1] + cy) * g.G.cd[0];
+                    b = g.cell_start[row + x0];
+                    n = g.cell_start[row + x1 + 1] - b;
+                }
+                s_beg[t] = b;
+                s_off[t + 1] = n;
+            }
+            __syncthreads();
+            if (wib == 0) {                             // prefix of the counts, 32 rows per pass
+                int carry = 0;
+                for (int t0 = 0; t0 < nr; t0 += 32) {
+                    int v = t0 + lane < nr ? s_off[t0 + lane + 1] : 0;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, v, o);
+                        if (lane >= o) v += y;
+                    }
+                    if (t0 + lane < nr) s_off[t0 + lane + 1] = carry + v;
+                    carry += __shfl_sync(0xffffffffu, v, 31);
+                }
+                if (lane == 0) s_off[0] = 0;
+            }
+            __syncthreads();
+            const int total = s_off[nr], n_chunks = (total + 31) >> 5;
+            // the atom at list position p: its row by binary search over the offsets
+            auto fetch = [&](int c, float4& B, float (&v)[kPropChunk]) {
+                const int p = c * 32 + lane;
+                if (p < total) {
+                    int lo = 0, hi = nr - 1;                // the last row with s_off[row] <= p
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_off[mid] <= p) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    B = g.sorted[s_beg[lo] + (p - s_off[lo])];
                     const float* pr = g.props + (size_t)__float_as_int(B.w) * g.n_props + q0;
-                    float v[kPropChunk];
 #pragma unroll
                     for (int q = 0; q < kPropChunk; ++q) v[q] = q < nq ? __ldg(pr + q) : 0.f;
-#pragma unroll
-                    for (int q = 0; q < kPropChunk / 4; ++q)
-                        s_pr[wib][lane][q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
                 }
+            };
+            float4 B_next = make_float4(0.f, 0.f, 0.f, 0.f);
+            float v_next[kPropChunk];
+#pragma unroll
+            for (int q = 0; q < kPropChunk; ++q) v_next[q] = 0.f;
+            if (wib < n_chunks) fetch(wib, B_next, v_next);
+            for (int c = wib; c < n_chunks; c += kFeatSplit) {
                 __syncwarp();
+                s_at[wib][lane] = B_next;
+#pragma unroll
+                for (int q = 0; q < kPropChunk / 4; ++q)
+                    s_pr[wib][lane][q] = make_float4(v_next[4 * q], v_next[4 * q + 1], v_next[4 * q + 2], v_next[4 * q + 3]);
+                __syncwarp();
+                if (c + kFeatSplit < n_chunks) fetch(c + kFeatSplit, B_next, v_next);
+                const int nt = min(32, total - c * 32);
                 for (int t = 0; t < nt; ++t) {
-                    const float4 B = s_at[wib][t];
-                    const float dx = B.x - px, ey = B.y - py, ez = B.z - pz;
+                    const float4 A = s_at[wib][t];
+                    const float dx = A.x - px, ey = A.y - py, ez = A.z - pz;
                     const float d2 = dx * dx + ey * ey + ez * ez;
                     count += d2 <= g.rp2;
                     if (d2 < g.rf2) {
@@ -410,6 +456,7 @@ __global__ void __launch_bounds__(kFeatSplit * 32) feature_kernel(FeatArgs g) {
                     }
                 }
             }
+            __syncthreads();                            // the row table is rebuilt for the next rows
         }
     }
 #pragma unroll
