@@ -34,8 +34,8 @@ constexpr float kCell = 4.0f;            // atom binning cell edge, A
 constexpr int kMaxAtoms = 200000;
 constexpr int kNb = 128;                 // neighbour list capacity per warp (SAS kernel)
 constexpr int kSasWarps = 4;
-constexpr int kFeatSplit = 16;         // warps sharing one group of 32 points (feature kernel)
-constexpr int kFeatRows = 256;          // cell rows listed at a time by the feature kernel
+constexpr int kFeatSplit = 16;           // warps sharing one group of 32 points (feature kernel)
+constexpr int kFeatRows = 256;           // cell rows listed at a time by the feature kernel
 constexpr int kPropChunk = 8;            // property columns per feature launch row (a multiple of 4)
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kHookRounds = 3;           // hooking rounds before the unions (clustering)
