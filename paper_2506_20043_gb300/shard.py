@@ -5,6 +5,10 @@ data-path collective. Shards are cut by pocket first, so that each GPU builds an
 of its own pockets, then by ligand when there are fewer pocket groups than ranks. The only exchange
 is the final one: each rank's kept poses (a few records per pair) are gathered on the host and merged
 per ligand by score, ties by (pocket, chain) -- the same order the GPU merge uses within a rank.
+
+Pocket prediction (Supplementary Algorithm 1) shards by receptor: receptors are dealt round-robin to
+ranks, each rank predicts the pockets of its own receptors, and the ranked pocket lists are gathered
+on one rank keyed by receptor.
 """
 from __future__ import annotations
 
@@ -63,3 +67,39 @@ def gather_merge(local: Dict[int, List[Record]], group=None, dst: int = 0):
     bucket = [None] * world if rank == dst else None
     dist.gather_object(local, bucket, dst=dst, group=group)
     return merge_records(bucket) if rank == dst else None
+
+
+Pocket = Tuple[float, float, float, float, int]   # (Eq. 2 score, centre x, y, z, points)
+
+
+def plan_receptors(n_receptors: int, world: int) -> List[List[int]]:
+    """Per rank: the receptor indices it predicts pockets for (round-robin)."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    return [list(range(r, max(n_receptors, 0), world)) for r in range(world)]
+
+
+def pockets_from_clusters(clusters) -> List[Pocket]:
+    """The ranked pockets of one receptor from its Clusters (best first)."""
+    c = clusters.read()
+    return [(float(s), float(x[0]), float(x[1]), float(x[2]), int(n))
+            for s, x, n in zip(c["score"], c["center"], c["size"])]
+
+
+def gather_pockets(local: Dict[int, List[Pocket]], group=None, dst: int = 0):
+    """Gathers every rank's {receptor: ranked pockets} on rank `dst` (torch.distributed, any
+    backend); other ranks get None. Receptors are disjoint across ranks, so this is a union."""
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    bucket = [None] * world if rank == dst else None
+    dist.gather_object(local, bucket, dst=dst, group=group)
+    if rank != dst:
+        return None
+    out: Dict[int, List[Pocket]] = {}
+    for part in bucket:
+        for rec, pockets in part.items():
+            if int(rec) in out:
+                raise ValueError(f"receptor {rec} predicted on two ranks")
+            out[int(rec)] = [tuple(p) for p in pockets]
+    return dict(sorted(out.items()))
