@@ -383,6 +383,12 @@ pv_status pv_pocket_params_default(pv_pocket_params* p);
  * coordinate; PV_ERR_OOM; PV_ERR_CUDA. */
 pv_status pv_surface_create(pv_context* ctx, const pv_receptor* receptor, const float* radius,
                             const pv_pocket_params* p, pv_surface** out);
+/* Step 1 for n_receptors receptors at once: the same results as one pv_surface_create per
+ * receptor, with one host synchronisation for all of them. radii: NULL, or n_receptors pointers
+ * (each NULL or per-atom radii in that receptor's memory kind). out receives n_receptors handles,
+ * each destroyed on its own; on any error none is returned. */
+pv_status pv_surface_create_many(pv_context* ctx, int32_t n_receptors, const pv_receptor* receptors,
+                                 const float* const* radii, const pv_pocket_params* p, pv_surface** out);
 pv_status pv_surface_info(const pv_surface* s, int32_t* n_atoms, int32_t* n_points);
 /* Copies the points (float32 [n_points][3]) and, if src is not NULL, each point's source
  * (atom * n_sphere + k, int32 [n_points]) into host or device memory (mem). Synchronous. */
@@ -416,6 +422,12 @@ void pv_surface_destroy(pv_surface* s);
  * one beyond 2^30 link lengths from the origin; PV_ERR_OOM; PV_ERR_CUDA. */
 pv_status pv_cluster_points(pv_context* ctx, int32_t n_points, const float* dev_xyz,
                             const float* dev_score, const pv_pocket_params* p, pv_clusters** out);
+/* Steps 4-5 for n_sets point sets at once (n_points[j] points at dev_xyz[j], dev_score[j]): the same
+ * results as one pv_cluster_points per set, with one host synchronisation for all of them. out
+ * receives n_sets handles; on any error none is returned. */
+pv_status pv_cluster_points_many(pv_context* ctx, int32_t n_sets, const int32_t* n_points,
+                                 const float* const* dev_xyz, const float* const* dev_score,
+                                 const pv_pocket_params* p, pv_clusters** out);
 pv_status pv_clusters_info(const pv_clusters* c, int32_t* n_points, int32_t* n_clusters);
 /* Copies, into host or device memory (mem), each nullable: cluster[n_points] (the rank of the
  * point's cluster, -1 below the threshold), and per cluster in rank order score[K],

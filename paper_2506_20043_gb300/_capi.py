@@ -101,12 +101,14 @@ SIGNATURES = {
     "pv_build_grid_noalloc": (i32, [vp, C.POINTER(pv_receptor), C.POINTER(pv_box), C.POINTER(C.c_uint8), i32, vp]),
     "pv_pocket_params_default": (i32, [C.POINTER(pv_pocket_params)]),
     "pv_surface_create": (i32, [vp, C.POINTER(pv_receptor), vp, C.POINTER(pv_pocket_params), C.POINTER(vp)]),
+    "pv_surface_create_many": (i32, [vp, i32, vp, vp, C.POINTER(pv_pocket_params), C.POINTER(vp)]),
     "pv_surface_info": (i32, [vp, pi32, pi32]),
     "pv_surface_read": (i32, [vp, vp, vp, vp, i32]),
     "pv_surface_points": (i32, [vp, C.POINTER(vp)]),
     "pv_surface_features": (i32, [vp, vp, i32, vp, i32, i32, vp, i32, C.POINTER(pv_pocket_params), vp, vp]),
     "pv_surface_destroy": (None, [vp]),
     "pv_cluster_points": (i32, [vp, i32, vp, vp, C.POINTER(pv_pocket_params), C.POINTER(vp)]),
+    "pv_cluster_points_many": (i32, [vp, i32, vp, vp, vp, C.POINTER(pv_pocket_params), C.POINTER(vp)]),
     "pv_clusters_info": (i32, [vp, pi32, pi32]),
     "pv_clusters_read": (i32, [vp, vp, vp, vp, vp, vp, vp, i32]),
     "pv_clusters_destroy": (None, [vp]),

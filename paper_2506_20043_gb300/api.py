@@ -203,6 +203,67 @@ class Context:
                                                C.byref(h)), "pv_surface_create")
         return Surface(self, h)
 
+    def surfaces(self, receptors: Sequence, radii: Optional[Sequence] = None,
+                 params: Optional[PocketParams] = None) -> List["Surface"]:
+        """Step 1 for several receptors in one call (pv_surface_create_many): the same surfaces as
+        one `surface` call each, with one host synchronisation for all of them."""
+        torch = self.torch
+        k = len(receptors)
+        if k == 0:
+            return []
+        keep: list = []
+        recs = (A.pv_receptor * k)()
+        rad_ptrs = (C.c_void_p * k)()
+        for j, rec in enumerate(receptors):
+            recs[j] = self._receptor(rec, keep)
+            rad = None if radii is None else radii[j]
+            if rad is not None:
+                if isinstance(rad, torch.Tensor):
+                    rad = rad.to(torch.float32).contiguous()
+                    if rad.is_cuda != (recs[j].mem == A.PV_MEM_DEVICE):
+                        raise PVError("radius must live where the receptor does")
+                else:
+                    if recs[j].mem != A.PV_MEM_HOST:
+                        raise PVError("radius must live where the receptor does")
+                    rad = _np(rad, np.float32)
+                keep.append(rad)
+                rad_ptrs[j] = _ptr(rad)
+        p = (params or PocketParams()).to_c()
+        hs = (C.c_void_p * k)()
+        self._check(self.lib.pv_surface_create_many(self.h, k, recs, None if radii is None else rad_ptrs, C.byref(p), hs),
+                    "pv_surface_create_many")
+        return [Surface(self, C.c_void_p(h)) for h in hs]
+
+    def cluster_many(self, sets: Sequence, params: Optional[PocketParams] = None) -> List["Clusters"]:
+        """Steps 4-5 for several point sets in one call (pv_cluster_points_many). sets: (points,
+        scores) pairs, points a [n, 3] array or tensor, or a Surface (its own points, used in place)."""
+        torch = self.torch
+        dev = torch.device("cuda", self.device)
+        k = len(sets)
+        if k == 0:
+            return []
+        keep: list = []
+        ns, xs, ss = (C.c_int32 * k)(), (C.c_void_p * k)(), (C.c_void_p * k)()
+        for j, (pts, sc) in enumerate(sets):
+            if isinstance(pts, Surface):
+                ptr = C.c_void_p()
+                self._check(self.lib.pv_surface_points(pts.h, C.byref(ptr)), "pv_surface_points")
+                n, xp = pts.n_points, ptr.value
+                keep.append(pts)
+            else:
+                t = torch.as_tensor(pts, dtype=torch.float32).to(dev).contiguous().reshape(-1, 3)
+                keep.append(t)
+                n, xp = int(t.shape[0]), t.data_ptr()
+            st = torch.as_tensor(sc, dtype=torch.float32).to(dev).contiguous().reshape(-1)
+            if st.shape[0] != n:
+                raise PVError("one score per point required")
+            keep.append(st)
+            ns[j], xs[j], ss[j] = n, xp, st.data_ptr()
+        p = (params or PocketParams()).to_c()
+        hs = (C.c_void_p * k)()
+        self._check(self.lib.pv_cluster_points_many(self.h, k, ns, xs, ss, C.byref(p), hs), "pv_cluster_points_many")
+        return [Clusters(self, C.c_void_p(h)) for h in hs]
+
     def cluster(self, points, scores, params: Optional[PocketParams] = None) -> "Clusters":
         """Steps 4-5: threshold, single-linkage clusters, Eq. 2 scores, centres and ranking of the
         points (pv_cluster_points). points [n, 3] and scores [n] are moved to the device."""

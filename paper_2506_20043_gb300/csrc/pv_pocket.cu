@@ -878,20 +878,49 @@ extern "C" pv_status pv_pocket_params_default(pv_pocket_params* p) {
     return PV_OK;
 }
 
-extern "C" pv_status pv_surface_create(pv_context* ctx, const pv_receptor* r, const float* radius,
-                                       const pv_pocket_params* p, pv_surface** out) {
-    int dev = 0;
-    cudaStream_t st = nullptr;
-    if (!pv::context_device_stream(ctx, &dev, &st)) return PV_ERR_STATE;
-    if (!out) return fail(ctx, PV_ERR_ARG, "out is null");
-    *out = nullptr;
-    if (!valid_params(p)) return fail(ctx, PV_ERR_ARG, "pocket parameters out of range");
+namespace {
+
+// One receptor of a surface call, through its three phases: prepare (host checks, binning grid),
+// issue (everything up to the point count, asynchronous) and finish (the points, once counted).
+struct SurfaceJob {
+    const pv_receptor* r = nullptr;
+    const float* radius = nullptr;
+    int n = 0;
+    float r_max = 1.80f;
+    AtomGrid G{};
+    long long n_cells = 0;
+    pv_surface* S = nullptr;
+    Pool scratch;
+    float4* atoms = nullptr;
+    float* arad = nullptr;
+    int* key = nullptr;
+    int* slot_elem = nullptr;
+    int* order = nullptr;
+    float* d_dirs = nullptr;
+    uint32_t* kept = nullptr;
+    int* n_kept = nullptr;
+    int* offset = nullptr;
+};
+
+void release_jobs(std::vector<SurfaceJob>& jobs) {
+    for (SurfaceJob& J : jobs) {
+        J.scratch.release();
+        if (J.S) {
+            J.S->pool.release();
+            delete J.S;
+            J.S = nullptr;
+        }
+    }
+}
+
+// Host checks and the binning grid of one receptor; device-resident coordinates (and radii) are
+// read back for the bounding box.
+pv_status surface_prepare(pv_context* ctx, cudaStream_t st, SurfaceJob& J) {
+    const pv_receptor* r = J.r;
     if (!r || r->n_atoms < 1 || r->n_atoms > kMaxAtoms) return fail(ctx, PV_ERR_ARG, "receptor atom count must be in [1, 200000]");
-    if (!r->xyz || (!radius && !r->element)) return fail(ctx, PV_ERR_ARG, "receptor xyz and element (or radii) required");
+    if (!r->xyz || (!J.radius && !r->element)) return fail(ctx, PV_ERR_ARG, "receptor xyz and element (or radii) required");
     if (r->mem != PV_MEM_HOST && r->mem != PV_MEM_DEVICE) return fail(ctx, PV_ERR_ARG, "receptor mem kind");
-    DeviceGuard guard(dev);
-    const int n = r->n_atoms;
-    // bounding box on the host
+    const int n = J.n = r->n_atoms;
     std::vector<float> hx;
     const float* xyz_h = r->xyz;
     if (r->mem == PV_MEM_DEVICE) {
@@ -902,21 +931,20 @@ extern "C" pv_status pv_surface_create(pv_context* ctx, const pv_receptor* r, co
         xyz_h = hx.data();
     }
     // the largest vdW radius bounds how far a neighbouring sphere can reach
-    float r_max = 1.80f;
-    if (radius) {
+    if (J.radius) {
         std::vector<float> hr;
-        const float* rad_h = radius;
+        const float* rad_h = J.radius;
         if (r->mem == PV_MEM_DEVICE) {
             hr.resize(n);
-            cudaError_t e = cudaMemcpyAsync(hr.data(), radius, sizeof(float) * n, cudaMemcpyDeviceToHost, st);
+            cudaError_t e = cudaMemcpyAsync(hr.data(), J.radius, sizeof(float) * n, cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "radius read");
             rad_h = hr.data();
         }
-        r_max = 0.f;
+        J.r_max = 0.f;
         for (int i = 0; i < n; ++i) {
             if (!(rad_h[i] > 0.f && rad_h[i] <= 10.f)) return fail(ctx, PV_ERR_ARG, "atom radius must be in (0, 10] A");
-            r_max = std::max(r_max, rad_h[i]);
+            J.r_max = std::max(J.r_max, rad_h[i]);
         }
     }
     double lo[3] = {1e30, 1e30, 1e30}, hi[3] = {-1e30, -1e30, -1e30};
@@ -927,15 +955,131 @@ extern "C" pv_status pv_surface_create(pv_context* ctx, const pv_receptor* r, co
             lo[k] = std::min(lo[k], v);
             hi[k] = std::max(hi[k], v);
         }
-    AtomGrid G;
-    long long n_cells = 1;
+    J.n_cells = 1;
     for (int k = 0; k < 3; ++k) {
-        G.lo[k] = (float)(lo[k] - 0.5);
-        G.cd[k] = (int)std::ceil((hi[k] + 0.5 - (double)G.lo[k]) / kCell) + 1;
-        n_cells *= G.cd[k];
+        J.G.lo[k] = (float)(lo[k] - 0.5);
+        J.G.cd[k] = (int)std::ceil((hi[k] + 0.5 - (double)J.G.lo[k]) / kCell) + 1;
+        J.n_cells *= J.G.cd[k];
     }
-    G.inv_cell = 1.0f / kCell;
-    if (n_cells > (1 << 24)) return fail(ctx, PV_ERR_ARG, "receptor spans too large a region");
+    J.G.inv_cell = 1.0f / kCell;
+    if (J.n_cells > (1 << 24)) return fail(ctx, PV_ERR_ARG, "receptor spans too large a region");
+    return PV_OK;
+}
+
+// Everything up to the point count, issued on the stream; the receptor's error word and point
+// count are copied to status[0] and status[1] (device memory).
+cudaError_t surface_issue(pv_context* ctx, cudaStream_t st, int dev, const pv_pocket_params* p,
+                          const std::vector<float>& dirs, SurfaceJob& J, int* status, const char** stage) {
+    const pv_receptor* r = J.r;
+    const int n = J.n, ns = p->n_sphere;
+    pv_surface* S = J.S = new (std::nothrow) pv_surface();
+    if (!S) return cudaErrorMemoryAllocation;
+    S->ctx = ctx;
+    S->device = dev;
+    S->pool.init(st, dev);
+    S->n_atoms = n;
+    S->n_sphere = ns;
+    S->G = J.G;
+    J.scratch.init(st, dev);
+    Pool& sc = J.scratch;
+    const float* d_xyz = r->xyz;
+    const uint8_t* d_el = r->element;
+    const float* d_rad = J.radius;
+    if (r->mem == PV_MEM_HOST) {
+        d_xyz = sc.take<float>(3 * (size_t)n);
+        d_el = r->element ? sc.take<uint8_t>(n) : nullptr;
+        d_rad = J.radius ? sc.take<float>(n) : nullptr;
+    }
+    J.atoms = sc.take<float4>(n);
+    J.arad = sc.take<float>(n);
+    J.key = sc.take<int>(n + 1);   // n + 1: reused for a scan when the points are ordered
+    int* count = sc.take<int>(J.n_cells);
+    int* cursor = sc.take<int>(J.n_cells);
+    J.slot_elem = sc.take<int>(n);
+    J.order = sc.take<int>(n);
+    int* err = sc.take<int>(1);
+    J.d_dirs = sc.take<float>(3 * (size_t)ns);
+    J.kept = sc.take<uint32_t>(32 * (size_t)n);
+    J.n_kept = sc.take<int>(n);
+    J.offset = sc.take<int>(n + 1);
+    S->sorted = S->pool.take<float4>(n);
+    S->cell_start = S->pool.take<int>(J.n_cells + 1);
+    cudaError_t e = sc.err != cudaSuccess ? sc.err : S->pool.err;
+    *stage = "allocation";
+    auto step = [&](cudaError_t x, const char* what) {
+        if (e == cudaSuccess && x != cudaSuccess) { e = x; *stage = what; }
+    };
+    if (e == cudaSuccess && r->mem == PV_MEM_HOST) {
+        step(cudaMemcpyAsync((void*)d_xyz, r->xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st), "receptor upload");
+        if (d_el) step(cudaMemcpyAsync((void*)d_el, r->element, n, cudaMemcpyHostToDevice, st), "receptor upload");
+        if (d_rad) step(cudaMemcpyAsync((void*)d_rad, J.radius, sizeof(float) * n, cudaMemcpyHostToDevice, st), "radius upload");
+    }
+    if (e == cudaSuccess) {
+        step(cudaMemcpyAsync(J.d_dirs, dirs.data(), sizeof(float) * dirs.size(), cudaMemcpyHostToDevice, st), "lattice upload");
+        step(cudaMemsetAsync(count, 0, sizeof(int) * J.n_cells, st), "memset");
+        step(cudaMemsetAsync(err, 0, sizeof(int), st), "memset");
+    }
+    if (e == cudaSuccess) {
+        prep_atoms_kernel<<<(n + 255) / 256, 256, 0, st>>>(d_xyz, d_el, d_rad, p->probe, n, J.G, J.atoms, J.arad, J.key,
+                                                            count, err);
+        step(cudaGetLastError(), "atom preparation");
+        step(bin_keys(J.key, n, (int)J.n_cells, count, S->cell_start, cursor, J.slot_elem, J.order, st), "atom binning");
+        gather_atoms_kernel<<<(n + 255) / 256, 256, 0, st>>>(J.order, n, J.atoms, S->sorted);
+        step(cudaGetLastError(), "atom binning");
+    }
+    if (e == cudaSuccess) {
+        SasArgs a{J.atoms, S->sorted, J.arad, S->cell_start, J.G, J.d_dirs, n, ns, J.r_max + p->probe + 1e-3f,
+                  J.kept, J.n_kept};
+        sas_kernel<<<(n + kSasWarps - 1) / kSasWarps, kSasWarps * 32, 0, st>>>(a);
+        step(cudaGetLastError(), "surface points");
+        scan_kernel<<<1, 1024, 0, st>>>(J.n_kept, n, J.offset);
+        step(cudaGetLastError(), "surface points");
+        step(cudaMemcpyAsync(status, err, sizeof(int), cudaMemcpyDeviceToDevice, st), "readback");
+        step(cudaMemcpyAsync(status + 1, J.offset + n, sizeof(int), cudaMemcpyDeviceToDevice, st), "readback");
+    }
+    return e;
+}
+
+// Once the point count is known: the points in (atom, k) order, their sources, and the order in
+// which the feature kernel groups them; the scratch goes back to the pool in stream order.
+cudaError_t surface_finish(cudaStream_t st, const pv_pocket_params* p, SurfaceJob& J, int total, const char** stage) {
+    pv_surface* S = J.S;
+    const int n = J.n, ns = p->n_sphere;
+    S->n_points = total;
+    S->points = S->pool.take<float>(3 * (size_t)(total > 0 ? total : 1));
+    S->src = S->pool.take<int>(total > 0 ? total : 1);
+    S->perm = S->pool.take<int>(total > 0 ? total : 1);
+    *stage = "point allocation";
+    if (S->pool.err != cudaSuccess) return S->pool.err;
+    sas_write_kernel<<<(n + 3) / 4, 128, 0, st>>>(J.atoms, J.arad, J.d_dirs, n, ns, J.kept, J.offset, S->points, S->src);
+    // the point order of the feature kernel: atoms in cell order (slot_elem and key are free again)
+    sorted_counts_kernel<<<(n + 255) / 256, 256, 0, st>>>(J.order, J.n_kept, n, J.slot_elem);
+    scan_kernel<<<1, 1024, 0, st>>>(J.slot_elem, n, J.key);
+    perm_kernel<<<(n + 255) / 256, 256, 0, st>>>(J.order, J.n_kept, J.offset, J.key, n, S->perm);
+    *stage = "point order";
+    cudaError_t e = cudaGetLastError();
+    J.scratch.release();
+    return e;
+}
+
+}  // namespace
+
+extern "C" pv_status pv_surface_create_many(pv_context* ctx, int32_t n_receptors, const pv_receptor* receptors,
+                                            const float* const* radii, const pv_pocket_params* p, pv_surface** out) {
+    int dev = 0;
+    cudaStream_t st = nullptr;
+    if (!pv::context_device_stream(ctx, &dev, &st)) return PV_ERR_STATE;
+    if (!out || n_receptors < 1 || !receptors) return fail(ctx, PV_ERR_ARG, "receptors and out required");
+    for (int j = 0; j < n_receptors; ++j) out[j] = nullptr;
+    if (!valid_params(p)) return fail(ctx, PV_ERR_ARG, "pocket parameters out of range");
+    DeviceGuard guard(dev);
+    std::vector<SurfaceJob> jobs(n_receptors);
+    for (int j = 0; j < n_receptors; ++j) {
+        jobs[j].r = receptors + j;
+        jobs[j].radius = radii ? radii[j] : nullptr;
+        const pv_status s = surface_prepare(ctx, st, jobs[j]);
+        if (s != PV_OK) return s;
+    }
     // lattice directions (spherical Fibonacci lattice, evaluated in double)
     const int ns = p->n_sphere;
     std::vector<float> dirs(3 * (size_t)ns);
@@ -946,104 +1090,53 @@ extern "C" pv_status pv_surface_create(pv_context* ctx, const pv_receptor* r, co
         dirs[3 * k + 1] = (float)(rho * std::sin(golden_angle * k));
         dirs[3 * k + 2] = (float)z;
     }
-    pv_surface* S = new (std::nothrow) pv_surface();
-    if (!S) return fail(ctx, PV_ERR_OOM, "host allocation failed");
-    S->ctx = ctx;
-    S->device = dev;
-    S->pool.init(st, dev);
-    S->n_atoms = n;
-    S->n_sphere = ns;
-    S->G = G;
-    Pool scratch(st, dev);
-    const float* d_xyz = r->xyz;
-    const uint8_t* d_el = r->element;
-    const float* d_rad = radius;
-    if (r->mem == PV_MEM_HOST) {
-        d_xyz = scratch.take<float>(3 * (size_t)n);
-        d_el = r->element ? scratch.take<uint8_t>(n) : nullptr;
-        d_rad = radius ? scratch.take<float>(n) : nullptr;
-    }
-    float4* atoms = scratch.take<float4>(n);
-    float* arad = scratch.take<float>(n);
-    int* key = scratch.take<int>(n + 1);   // n + 1: reused for a scan below
-    int* count = scratch.take<int>(n_cells);
-    int* cursor = scratch.take<int>(n_cells);
-    int* slot_elem = scratch.take<int>(n);
-    int* order = scratch.take<int>(n);
-    int* err = scratch.take<int>(1);
-    float* d_dirs = scratch.take<float>(3 * (size_t)ns);
-    uint32_t* kept = scratch.take<uint32_t>(32 * (size_t)n);
-    int* n_kept = scratch.take<int>(n);
-    int* offset = scratch.take<int>(n + 1);
-    S->sorted = S->pool.take<float4>(n);
-    S->cell_start = S->pool.take<int>(n_cells + 1);
-    cudaError_t e = scratch.err != cudaSuccess ? scratch.err : S->pool.err;
+    // every receptor's work up to its point count, then one readback of all error words and counts
+    Pool batch(st, dev);
+    int* status = batch.take<int>(2 * (size_t)n_receptors);
+    cudaError_t e = batch.err;
     const char* stage = "allocation";
-    auto step = [&](cudaError_t x, const char* what) {
-        if (e == cudaSuccess && x != cudaSuccess) { e = x; stage = what; }
-    };
-    if (e == cudaSuccess && r->mem == PV_MEM_HOST) {
-        step(cudaMemcpyAsync((void*)d_xyz, r->xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st), "receptor upload");
-        if (d_el) step(cudaMemcpyAsync((void*)d_el, r->element, n, cudaMemcpyHostToDevice, st), "receptor upload");
-        if (d_rad) step(cudaMemcpyAsync((void*)d_rad, radius, sizeof(float) * n, cudaMemcpyHostToDevice, st), "radius upload");
-    }
-    int h_err = 0, h_total = 0;
+    for (int j = 0; j < n_receptors && e == cudaSuccess; ++j) e = surface_issue(ctx, st, dev, p, dirs, jobs[j], status + 2 * j, &stage);
+    std::vector<int> h_status(2 * (size_t)n_receptors, 0);
     if (e == cudaSuccess) {
-        step(cudaMemcpyAsync(d_dirs, dirs.data(), sizeof(float) * dirs.size(), cudaMemcpyHostToDevice, st), "lattice upload");
-        step(cudaMemsetAsync(count, 0, sizeof(int) * n_cells, st), "memset");
-        step(cudaMemsetAsync(err, 0, sizeof(int), st), "memset");
+        stage = "readback";
+        e = cudaMemcpyAsync(h_status.data(), status, sizeof(int) * h_status.size(), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
-    if (e == cudaSuccess) {
-        prep_atoms_kernel<<<(n + 255) / 256, 256, 0, st>>>(d_xyz, d_el, d_rad, p->probe, n, G, atoms, arad, key, count, err);
-        step(cudaGetLastError(), "atom preparation");
-        step(bin_keys(key, n, (int)n_cells, count, S->cell_start, cursor, slot_elem, order, st), "atom binning");
-        gather_atoms_kernel<<<(n + 255) / 256, 256, 0, st>>>(order, n, atoms, S->sorted);
-        step(cudaGetLastError(), "atom binning");
+    int bad = 0;
+    for (int j = 0; j < n_receptors && e == cudaSuccess; ++j) bad |= h_status[2 * j];
+    if (e == cudaSuccess && bad) {
+        release_jobs(jobs);
+        batch.release();
+        return fail(ctx, PV_ERR_ARG, (bad & kErrElement) ? "receptor element must be 0..3"
+                                     : (bad & kErrRadius) ? "atom radius must be in (0, 10] A"
+                                                          : "receptor coordinates must be finite");
     }
-    float reach_max = 0.f;
-    if (e == cudaSuccess) {
-        reach_max = r_max + p->probe + 1e-3f;
-        SasArgs a{atoms, S->sorted, arad, S->cell_start, G, d_dirs, n, ns, reach_max, kept, n_kept};
-        sas_kernel<<<(n + kSasWarps - 1) / kSasWarps, kSasWarps * 32, 0, st>>>(a);
-        step(cudaGetLastError(), "surface points");
-        scan_kernel<<<1, 1024, 0, st>>>(n_kept, n, offset);
-        step(cudaGetLastError(), "surface points");
-        step(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st), "readback");
-        step(cudaMemcpyAsync(&h_total, offset + n, sizeof(int), cudaMemcpyDeviceToHost, st), "readback");
-        step(cudaStreamSynchronize(st), "surface points");
-    }
-    if (e == cudaSuccess && h_err) {
-        scratch.release();
-        S->pool.release();
-        delete S;
-        return fail(ctx, PV_ERR_ARG, (h_err & kErrElement) ? "receptor element must be 0..3"
-                                     : (h_err & kErrRadius) ? "atom radius must be in (0, 10] A"
-                                                            : "receptor coordinates must be finite");
-    }
-    if (e == cudaSuccess) {
-        S->n_points = h_total;
-        S->points = S->pool.take<float>(3 * (size_t)(h_total > 0 ? h_total : 1));
-        S->src = S->pool.take<int>(h_total > 0 ? h_total : 1);
-        S->perm = S->pool.take<int>(h_total > 0 ? h_total : 1);
-        step(S->pool.err, "point allocation");
-    }
-    if (e == cudaSuccess) {
-        sas_write_kernel<<<(n + 3) / 4, 128, 0, st>>>(atoms, arad, d_dirs, n, ns, kept, offset, S->points, S->src);
-        step(cudaGetLastError(), "surface points");
-        // the point order of the feature kernel: atoms in cell order (slot_elem is free again)
-        sorted_counts_kernel<<<(n + 255) / 256, 256, 0, st>>>(order, n_kept, n, slot_elem);
-        scan_kernel<<<1, 1024, 0, st>>>(slot_elem, n, key);          // key: n + 1 ints, free again
-        perm_kernel<<<(n + 255) / 256, 256, 0, st>>>(order, n_kept, offset, key, n, S->perm);
-        step(cudaGetLastError(), "point order");
-    }
-    scratch.release();
+    for (int j = 0; j < n_receptors && e == cudaSuccess; ++j) e = surface_finish(st, p, jobs[j], h_status[2 * j + 1], &stage);
+    batch.release();
     if (e != cudaSuccess) {
-        S->pool.release();
-        delete S;
+        release_jobs(jobs);
         return cuda_fail(ctx, e, (std::string("surface: ") + stage).c_str());
     }
-    *out = S;
+    for (int j = 0; j < n_receptors; ++j) out[j] = jobs[j].S;
     return PV_OK;
+}
+
+extern "C" pv_status pv_surface_create(pv_context* ctx, const pv_receptor* r, const float* radius,
+                                       const pv_pocket_params* p, pv_surface** out) {
+    if (!out) {
+        int dev = 0;
+        cudaStream_t st = nullptr;
+        if (!pv::context_device_stream(ctx, &dev, &st)) return PV_ERR_STATE;
+        return fail(ctx, PV_ERR_ARG, "out is null");
+    }
+    *out = nullptr;
+    if (!r) {
+        int dev = 0;
+        cudaStream_t st = nullptr;
+        if (!pv::context_device_stream(ctx, &dev, &st)) return PV_ERR_STATE;
+        return fail(ctx, PV_ERR_ARG, "receptor atom count must be in [1, 200000]");
+    }
+    return pv_surface_create_many(ctx, 1, r, radius ? &radius : nullptr, p, out);
 }
 
 extern "C" pv_status pv_surface_info(const pv_surface* s, int32_t* n_atoms, int32_t* n_points) {
@@ -1139,19 +1232,16 @@ extern "C" void pv_surface_destroy(pv_surface* s) {
     delete s;
 }
 
-extern "C" pv_status pv_cluster_points(pv_context* ctx, int32_t n, const float* dev_xyz, const float* dev_score,
-                                       const pv_pocket_params* p, pv_clusters** out) {
-    int dev = 0;
-    cudaStream_t st = nullptr;
-    if (!pv::context_device_stream(ctx, &dev, &st)) return PV_ERR_STATE;
-    if (!out) return fail(ctx, PV_ERR_ARG, "out is null");
-    *out = nullptr;
-    if (!valid_params(p)) return fail(ctx, PV_ERR_ARG, "pocket parameters out of range");
-    if (n < 0 || n > (1 << 26)) return fail(ctx, PV_ERR_ARG, "point count must be in [0, 2^26]");
-    if (n > 0 && (!dev_xyz || !dev_score)) return fail(ctx, PV_ERR_ARG, "dev_xyz and dev_score required");
-    DeviceGuard guard(dev);
-    pv_clusters* C = new (std::nothrow) pv_clusters();
-    if (!C) return fail(ctx, PV_ERR_OOM, "host allocation failed");
+namespace {
+
+// Steps 4-5 for one point set, issued on the stream; its error word and cluster count are copied
+// to status[0] and status[1] (device memory). C is allocated here (released by the caller on error).
+cudaError_t cluster_issue(pv_context* ctx, cudaStream_t st, int dev, int n, const float* dev_xyz,
+                          const float* dev_score, const pv_pocket_params* p, pv_clusters** Cout, int* status,
+                          const char** stage) {
+    pv_clusters* C = *Cout = new (std::nothrow) pv_clusters();
+    *stage = "allocation";
+    if (!C) return cudaErrorMemoryAllocation;
     C->ctx = ctx;
     C->device = dev;
     C->pool.init(st, dev);
@@ -1162,16 +1252,8 @@ extern "C" pv_status pv_cluster_points(pv_context* ctx, int32_t n, const float* 
     C->center = C->pool.take<float>(3 * m);
     C->size = C->pool.take<int>(m);
     C->first = C->pool.take<int>(m);
-    if (C->pool.err != cudaSuccess) {
-        const cudaError_t e = C->pool.err;
-        C->pool.release();
-        delete C;
-        return cuda_fail(ctx, e, "cluster allocation");
-    }
-    if (n == 0) {
-        *out = C;
-        return PV_OK;
-    }
+    if (C->pool.err != cudaSuccess) return C->pool.err;
+    if (n == 0) return cudaMemsetAsync(status, 0, 2 * sizeof(int), st);
     uint32_t buckets = 1024;
     while (2 * buckets < (uint32_t)n) buckets <<= 1;
     Pool scratch(st, dev);
@@ -1194,11 +1276,9 @@ extern "C" pv_status pv_cluster_points(pv_context* ctx, int32_t n, const float* 
     int* c_first = scratch.take<int>(m);
     int* rank = scratch.take<int>(m);
     cudaError_t e = scratch.err;
-    const char* stage = "allocation";
     auto step = [&](cudaError_t x, const char* what) {
-        if (e == cudaSuccess && x != cudaSuccess) { e = x; stage = what; }
+        if (e == cudaSuccess && x != cudaSuccess) { e = x; *stage = what; }
     };
-    int h_err = 0, h_k = 0;
     if (e == cudaSuccess) {
         step(cudaMemsetAsync(count, 0, sizeof(int) * buckets, st), "memset");
         step(cudaMemsetAsync(err, 0, sizeof(int), st), "memset");
@@ -1242,25 +1322,79 @@ extern "C" pv_status pv_cluster_points(pv_context* ctx, int32_t n, const float* 
         cl_rank_kernel<<<b, 256, 0, st>>>(ra);
         cl_output_kernel<<<b, 256, 0, st>>>(ra);
         step(cudaGetLastError(), "cluster ranking");
-        step(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st), "readback");
-        step(cudaMemcpyAsync(&h_k, n_clusters, sizeof(int), cudaMemcpyDeviceToHost, st), "readback");
-        step(cudaStreamSynchronize(st), "clusters");
+        step(cudaMemcpyAsync(status, err, sizeof(int), cudaMemcpyDeviceToDevice, st), "readback");
+        step(cudaMemcpyAsync(status + 1, n_clusters, sizeof(int), cudaMemcpyDeviceToDevice, st), "readback");
     }
-    scratch.release();
-    if (e == cudaSuccess && h_err) {
-        C->pool.release();
-        delete C;
-        return fail(ctx, PV_ERR_ARG, (h_err & kErrCoord) ? "clustered points need finite coordinates within 2^30 link lengths"
-                                                         : "union-find did not converge");
+    scratch.release();   // stream-ordered: after the kernels above
+    return e;
+}
+
+}  // namespace
+
+extern "C" pv_status pv_cluster_points_many(pv_context* ctx, int32_t n_sets, const int32_t* n_points,
+                                            const float* const* dev_xyz, const float* const* dev_score,
+                                            const pv_pocket_params* p, pv_clusters** out) {
+    int dev = 0;
+    cudaStream_t st = nullptr;
+    if (!pv::context_device_stream(ctx, &dev, &st)) return PV_ERR_STATE;
+    if (!out || n_sets < 1 || !n_points || !dev_xyz || !dev_score) return fail(ctx, PV_ERR_ARG, "point sets and out required");
+    for (int j = 0; j < n_sets; ++j) out[j] = nullptr;
+    if (!valid_params(p)) return fail(ctx, PV_ERR_ARG, "pocket parameters out of range");
+    for (int j = 0; j < n_sets; ++j) {
+        if (n_points[j] < 0 || n_points[j] > (1 << 26)) return fail(ctx, PV_ERR_ARG, "point count must be in [0, 2^26]");
+        if (n_points[j] > 0 && (!dev_xyz[j] || !dev_score[j])) return fail(ctx, PV_ERR_ARG, "dev_xyz and dev_score required");
     }
+    DeviceGuard guard(dev);
+    std::vector<pv_clusters*> cs(n_sets, nullptr);
+    auto release_all = [&]() {
+        for (pv_clusters*& C : cs)
+            if (C) {
+                C->pool.release();
+                delete C;
+                C = nullptr;
+            }
+    };
+    // every set's work, then one readback of all error words and cluster counts
+    Pool batch(st, dev);
+    int* status = batch.take<int>(2 * (size_t)n_sets);
+    cudaError_t e = batch.err;
+    const char* stage = "allocation";
+    for (int j = 0; j < n_sets && e == cudaSuccess; ++j)
+        e = cluster_issue(ctx, st, dev, n_points[j], dev_xyz[j], dev_score[j], p, &cs[j], status + 2 * j, &stage);
+    std::vector<int> h_status(2 * (size_t)n_sets, 0);
+    if (e == cudaSuccess) {
+        stage = "readback";
+        e = cudaMemcpyAsync(h_status.data(), status, sizeof(int) * h_status.size(), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    batch.release();
     if (e != cudaSuccess) {
-        C->pool.release();
-        delete C;
+        release_all();
         return cuda_fail(ctx, e, (std::string("clusters: ") + stage).c_str());
     }
-    C->K = h_k;
-    *out = C;
+    int bad = 0;
+    for (int j = 0; j < n_sets; ++j) bad |= h_status[2 * j];
+    if (bad) {
+        release_all();
+        return fail(ctx, PV_ERR_ARG, (bad & kErrCoord) ? "clustered points need finite coordinates within 2^30 link lengths"
+                                                       : "union-find did not converge");
+    }
+    for (int j = 0; j < n_sets; ++j) {
+        cs[j]->K = h_status[2 * j + 1];
+        out[j] = cs[j];
+    }
     return PV_OK;
+}
+
+extern "C" pv_status pv_cluster_points(pv_context* ctx, int32_t n, const float* dev_xyz, const float* dev_score,
+                                       const pv_pocket_params* p, pv_clusters** out) {
+    if (!out) {
+        int dev = 0;
+        cudaStream_t st = nullptr;
+        if (!pv::context_device_stream(ctx, &dev, &st)) return PV_ERR_STATE;
+        return fail(ctx, PV_ERR_ARG, "out is null");
+    }
+    return pv_cluster_points_many(ctx, 1, &n, &dev_xyz, &dev_score, p, out);
 }
 
 extern "C" pv_status pv_clusters_info(const pv_clusters* c, int32_t* n_points, int32_t* n_clusters) {

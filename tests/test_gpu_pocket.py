@@ -276,6 +276,48 @@ def test_cluster_edge_cases():
         ctx.cluster(pts, sc, _params(link=0.0))
 
 
+# ------------------------------------------------------------------- batched calls --
+
+def test_batched_calls_equal_single_calls():
+    # pv_surface_create_many / pv_cluster_points_many: bit-for-bit the results of one call each,
+    # with host and device receptors, default and given radii, an empty point set, and an error in
+    # one receptor failing the whole call without leaving the context unusable
+    torch = pytest.importorskip("torch")
+    from paper_2506_20043_gb300.api import PVError
+    ctx = G.context()
+    sites = [S.pocket_site(20 + k, n, 2) for k, n in enumerate((900, 1500, 1200))]
+    recs = [_rec32(s.receptor) for s in sites]
+    drec = S.Receptor(torch.tensor(recs[1].xyz, dtype=torch.float32, device="cuda"),
+                      torch.tensor(recs[1].element, device="cuda"), torch.tensor(recs[1].donor, device="cuda"),
+                      torch.tensor(recs[1].acceptor, device="cuda"))
+    rad2 = np.random.default_rng(3).uniform(1.3, 2.2, size=recs[2].n).astype(np.float32)
+    prm = _params(n_sphere=60)
+    many = ctx.surfaces([recs[0], drec, recs[2]], radii=[None, None, rad2], params=prm)
+    single = [ctx.surface(recs[0], params=prm), ctx.surface(recs[1], params=prm),
+              ctx.surface(recs[2], radius=rad2, params=prm)]
+    scores = []
+    for k, (a, b) in enumerate(zip(many, single)):
+        assert a.n_points == b.n_points > 0
+        assert np.array_equal(a.sources(), b.sources())
+        assert torch.equal(a.points(), b.points())
+        props = S.atom_properties(recs[k], k)
+        fa, pa = a.features(props)
+        fb, pb = b.features(props)
+        assert torch.equal(fa, fb) and torch.equal(pa, pb)
+        scores.append(S.ligandability(b.points().cpu().numpy(), sites[k], k, noise=0.0))
+    cm = ctx.cluster_many([(a, sc) for a, sc in zip(many, scores)] + [(np.zeros((0, 3)), np.zeros(0))])
+    assert len(cm) == 4 and cm[3].n_clusters == 0 and cm[3].n_points == 0
+    for c, b, sc in zip(cm, single, scores):
+        r1, r2 = c.read(), ctx.cluster(b.points(), sc).read()
+        assert r1.keys() == r2.keys() and all(np.array_equal(r1[x], r2[x]) for x in r1)
+        assert len(r1["score"]) >= 1
+    bad = S.Receptor(np.zeros((3, 3)), np.array([0, 7, 1], np.uint8), np.zeros(3, np.uint8), np.zeros(3, np.uint8))
+    with pytest.raises(PVError, match="ARG"):
+        ctx.surfaces([recs[0], bad], params=prm)
+    again = ctx.surfaces([recs[0]], params=prm)
+    assert len(again) == 1 and np.array_equal(again[0].sources(), single[0].sources())
+
+
 # ------------------------------------------------------------------ receptor -> boxes --
 
 def test_pocket_pipeline_matches_oracle_and_docks():
