@@ -10,7 +10,9 @@ evaluations per second, the plain one-launch-per-pocket path on a sample, the sc
 microbenchmark (65,536 poses), the search kernel's roofline, and the FP64 CPU oracle.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-Under torchrun (N > 1) each rank docks its own receptor (seed = rank): weak scaling.
+Under torchrun (N > 1) the job is N ligands x the 10 pockets (10 pairs per GPU: weak scaling), split
+into equal pocket-major runs of pairs (shard.plan_pairs) that keep the unsplit job's random streams;
+each rank builds only its pockets' maps, and the ranked poses are gathered and merged on rank 0.
 """
 from __future__ import annotations
 
@@ -38,6 +40,10 @@ UNIT = "pairs/s"
 WORKLOAD = ("multi-pocket: 5,000-atom receptor, 10 pockets (r 6-10 A, 24 A boxes, 0.375 A), "
             "1 ligand 30 atoms / 6 torsions, 1,000 chains x 2,000 MC steps per pocket, top-9 merged")
 CHAINS, STEPS, TOP_K = 1000, 2000, 9
+# FP32 operations of one (grid node, receptor atom within 8 A, ligand type) term evaluation of the
+# map build: surface distance 2, two Gaussians 8 (with their exponentials), repulsion 3,
+# hydrophobic and H-bond ramps 4, accumulation 1
+GRID_FLOPS_PER_TERM = 18
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -155,32 +161,56 @@ def run_ours(args):
     torch.cuda.set_device(local)
     import paper_2506_20043_gb300 as pv
     pv.build()
-    from paper_2506_20043_gb300 import api
+    from paper_2506_20043_gb300 import api, shard
 
     ctx = api.Context(local)
     stream = ctx.stream
-    rec, boxes, lig_src = workload(seed=rank)
-    lig = ctx.ligand(lig_src)
-    types = sorted(set(lig.xs_types.tolist()))
+    rec, boxes, lig_src = workload(seed=0)
+    # the job: `world` ligands x the 10 pockets, split into equal runs of the pocket-major pair list
+    # (shard.plan_pairs), each pair keeping its random stream of the unsplit job; at N = 1 that is
+    # the headline workload (1 ligand x 10 pockets) docked in one call
+    job_ligs = [lig_src] + [S.ligand_centered(S.make_ligand(30, 6, 1000 + i)) for i in range(1, world)]
+    run = shard.plan_pairs(list(range(len(boxes))), len(job_ligs), world)[rank]
+    my_pockets = sorted({p for _, p, _ in run})              # this rank builds only these maps
+    local_pocket = {p: i for i, p in enumerate(my_pockets)}
+    my_ligs = sorted({l for l, _, _ in run})
+    local_lig = {l: i for i, l in enumerate(my_ligs)}
+    ligs = [ctx.ligand(job_ligs[l]) for l in my_ligs]
+    lig = ligs[0]
+    types = sorted(set(int(t) for l in ligs for t in l.xs_types.tolist()))
     dev_rec = S.Receptor(torch.tensor(rec.xyz, dtype=torch.float32, device="cuda"),
                          torch.tensor(rec.element, device="cuda"), torch.tensor(rec.donor, device="cuda"),
                          torch.tensor(rec.acceptor, device="cuda"))
-    pockets = list(range(len(boxes)))
-    params = api.DockParams(chains=CHAINS, steps=STEPS, seed=rank, top_k=TOP_K, host_copy=False, focc=args.focc)
+    my_boxes = [boxes[p] for p in my_pockets]
+    pair_lig = [local_lig[l] for l, _, _ in run]
+    pair_pocket = [local_pocket[p] for _, p, _ in run]
+    params = api.DockParams(chains=CHAINS, steps=STEPS, seed=0, top_k=TOP_K, host_copy=False, focc=args.focc,
+                            pair_keys=[k for _, _, k in run])
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def step(mid=None):
-        gs = ctx.build_grids(dev_rec, boxes, types)
+        gs = ctx.build_grids(dev_rec, my_boxes, types)
         if mid is not None:
             mid.record(stream)
-        r = ctx.dock(gs, [lig], pockets, params)
+        if world == 1:
+            r = ctx.dock(gs, ligs, list(range(len(my_boxes))), params)
+        else:
+            r = ctx.dock_pairs(gs, ligs, pair_lig, pair_pocket, params)
         return gs, r
+
+    def exchange(r):
+        """The job's one exchange step: every rank's ranked kept poses, with global pocket ids,
+        gathered and merged per ligand on rank 0 (host records; no data-path collective)."""
+        recs = shard.records_from_result(r, my_ligs)
+        recs = {l: [(sc, my_pockets[p], c) for sc, p, c in v] for l, v in recs.items()}
+        return shard.gather_merge(recs) if world > 1 else shard.merge_records([recs])
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    times, grid_t, search_s, evals, launches = [], [], 0.0, 0, 0
+    times, grid_t, map_kernel_s, search_s, evals, launches = [], [], 0.0, 0.0, 0, 0
     e0, em, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    merged = None
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.zero_()                                  # L2 flushed between timed steps
@@ -189,10 +219,13 @@ def run_ours(args):
             torch.cuda.synchronize()
             e0.record(stream)
             gs, r = step(em)
+            if world > 1:
+                merged = exchange(r)
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1) * 1e-3)
             grid_t.append(e0.elapsed_time(em) * 1e-3)
+            map_kernel_s += gs.build_seconds()
             ev, _, st = r.stats()
             assert (st == 0).all(), st
             s_s, n_l, _ = r.timing()
@@ -200,6 +233,8 @@ def run_ours(args):
             search_s += s_s
             launches += n_l
             evals += ev
+    if world == 1:
+        merged = exchange(r)
     # search quality of the last timed step: per pocket, the best SF over its chains
     _, chain_best = r.chain_records()
     best_sf = chain_best.min(axis=1)
@@ -208,9 +243,10 @@ def run_ours(args):
         t = torch.tensor(step_t, device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         step_t = t.cpu().numpy()
-    n_pairs = len(pockets)
+    n_pairs = len(run)
     total_t = float(step_t.sum())
-    value = n_pairs * world * args.steps / total_t
+    job_pairs = len(job_ligs) * len(boxes)
+    value = job_pairs * args.steps / total_t
     clocks = clk.summary()
 
     out = None
@@ -224,22 +260,31 @@ def run_ours(args):
         launch_traffic = prof.get("traffic")
         evals_per_launch = evals / max(launches, 1)
         n_rounds = launches // max(args.steps, 1)
-        _, _, gather_gbs = ctx.measure_gather(gs, -1, n_points=1 << 24, reps=10)   # the 10 pockets' map set
+        _, _, gather_gbs = ctx.measure_gather(gs, -1, n_points=1 << 24, reps=10)   # the pockets' map set
         search_gather_gbs = evals * gbytes / search_s / 1e9
+        # the map build (Grid_cache): (node, receptor atom within 8 A, type) term evaluations
+        terms = grid_term_count(torch, rec.xyz, my_boxes, len(types))
+        map_s = map_kernel_s / args.steps
         out = {
             "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_t / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "pairs_per_step_per_gpu": n_pairs, "chains": CHAINS,
-                       "mc_steps": STEPS, "top_k": TOP_K, "ligand_atoms": lig.n_atoms, "ligand_torsions": lig.n_rot,
-                       "intra_pairs": lig.n_pairs, "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+            "config": {"workload": WORKLOAD, "pairs_per_step": job_pairs, "pairs_per_step_per_gpu": n_pairs,
+                       "chains": CHAINS, "mc_steps": STEPS, "top_k": TOP_K, "ligand_atoms": lig.n_atoms,
+                       "ligand_torsions": lig.n_rot, "intra_pairs": lig.n_pairs,
+                       "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "inputs": "receptor, ligand and boxes resident in HBM; grids rebuilt every step",
-                       "parallelism": f"{world} independent receptors, one per GPU",
+                       "parallelism": ("1 GPU" if world == 1 else
+                                       f"{world} GPUs: {world} ligands x 10 pockets split into equal pocket-major "
+                                       "runs of pairs (job-wide pair keys), ranked poses gathered and merged on "
+                                       "rank 0 inside the timed step"),
                        "search_launch": {"variant": shape[0], "warps_per_cta": shape[1], "chains_per_warp": 2 if shape[0] >= 4 else 1},
                        "focc": args.focc},
             "best_sf_per_pocket": {"mean": round(float(best_sf.mean()), 4), "min": round(float(best_sf.min()), 4)},
+            "top_pose": {str(l): list(v[0]) for l, v in sorted(merged.items())} if merged else None,
             "evals_per_s": round(evals / total_t * world, 1),
             "breakdown": {"grid_maps_ms": round(float(np.mean(grid_t)) * 1e3, 3),
+                          "map_kernel_ms": round(map_s * 1e3, 3),
                           "dock_ms": round((total_t / args.steps - float(np.mean(grid_t))) * 1e3, 3),
                           "dock_only_pairs_per_s": round(n_pairs * world / (total_t / args.steps - float(np.mean(grid_t))), 4)},
             "evals_per_step_per_gpu": evals // max(args.steps, 1),
@@ -258,16 +303,25 @@ def run_ours(args):
                                     "frac": round(evals / search_s * prof["inst"] / (n_sm * 4 * max_mhz * 1e6), 4),
                                     "note": "warp instructions issued per second vs 4 per SM per clock"}
                                    if "inst" in prof else None)},
+            "grid_roofline": {"kernel": "grid_kernel", "bound": "alu",
+                              "term_evals_per_launch": terms, "flops_per_term": GRID_FLOPS_PER_TERM,
+                              "achieved": round(terms * GRID_FLOPS_PER_TERM / map_s / 1e12, 3),
+                              "peak": round(peak_tflops, 2), "unit": "TFLOP/s",
+                              "frac": round(terms * GRID_FLOPS_PER_TERM / map_s / 1e12 / peak_tflops, 4),
+                              "term_evals_per_s": round(terms / map_s, 1), "launch_ms": round(map_s * 1e3, 3),
+                              "traffic": None},
             "gpu_launches": args.steps * (6 + 1 + n_rounds + 2),
             "clocks": clocks,
         }
         if not args.no_plain:
-            out["plain"] = run_plain_sample(ctx, api, gs, lig, pockets)
-            out["batched_vs_plain"] = round(value / world / out["plain"]["value"], 2)
+            out["plain"] = run_plain(ctx, api, gs, lig, list(range(len(my_boxes))), shape)
+            out["batched_vs_plain"] = round(value / world / out["plain"]["thread_per_chain"]["value"], 2)
+            out["batched_vs_plain_warp"] = round(value / world / out["plain"]["warp_per_chain"]["value"], 2)
         if not args.no_micro:
             out["score_microbench"] = run_score_microbench(ctx, api, torch)
-        out["rescoring"] = run_rescore_check(ctx, gs, lig, pockets, params)
-        out["e2e"] = run_e2e(ctx, api, torch, rec, boxes, lig_src, types, pockets, args.steps, rank)
+        out["rescoring"] = run_rescore_check(ctx, gs, lig, list(range(len(my_boxes))), params)
+        if world == 1:
+            out["e2e"] = run_e2e(ctx, api, torch, rec, boxes, lig_src, types, list(range(len(boxes))), args.steps, 0)
         if world == 1 and not args.no_cpu:
             out["cpu_baseline"] = run_cpu_baseline(rec, boxes, lig_src, budget_s=args.cpu_budget)
     if world > 1:
@@ -276,19 +330,45 @@ def run_ours(args):
     return out
 
 
-def run_plain_sample(ctx, api, gs, lig, pockets, sample_steps=20):
-    """The paper's organisation (one launch per pair, one thread per chain, host loop) on one
-    pocket for `sample_steps` MC steps; pairs/s extrapolated linearly in MC steps."""
-    r = ctx.dock(gs, [lig], [pockets[0]], chains=CHAINS, steps=sample_steps, seed=0, mode="plain", host_copy=False)
-    ev, _, _ = r.stats()
-    s_s, _, total = r.timing()
-    per_pair = total * STEPS / sample_steps
-    rb = ctx.dock(gs, [lig], [pockets[0]], chains=CHAINS, steps=sample_steps, seed=0, host_copy=False)
-    evb, _, _ = rb.stats()
-    _, _, tb = rb.timing()
-    return {"value": round(1.0 / per_pair, 5), "unit": UNIT, "evals_per_s": round(ev / s_s, 1),
-            "sample": f"1 pocket x {CHAINS} chains x {sample_steps} MC steps, time x {STEPS // sample_steps}",
-            "batched_same_sample_evals_per_s": round(evb / tb, 1)}
+def run_plain(ctx, api, gs, lig, pockets, shape):
+    """The paper's organisation, one launch per pair and a host loop, on one pocket of the
+    workload at its full length (1,000 chains x 2,000 MC steps, not extrapolated), in two forms:
+    thread per chain (as in the paper's engine) and warp per chain (the batched path's own chain
+    kernel and launch shape, one launch per pair with all steps in one block, no queue across pairs,
+    no graph), so that the second ratio isolates what batching itself adds."""
+    out = {"sample": f"1 pocket x {CHAINS} chains x {STEPS} MC steps, one launch per pair, timed in full"}
+    for name, kw in (("thread_per_chain", dict(mode="plain")),
+                     ("warp_per_chain", dict(mode="plain_warp", search_variant=shape[0], warps_per_cta=shape[1]))):
+        r = ctx.dock(gs, [lig], [pockets[0]], chains=CHAINS, steps=STEPS, seed=0, host_copy=False, **kw)
+        ev, _, st = r.stats()
+        assert (st == 0).all(), st
+        s_s, _, total = r.timing()
+        out[name] = {"value": round(1.0 / total, 5), "unit": UNIT, "seconds_per_pair": round(total, 4),
+                     "evals_per_s": round(ev / s_s, 1)}
+    return out
+
+
+def grid_term_count(torch, rec_xyz, boxes, n_types, chunk=4096):
+    """Algorithmic work of the map build: (grid node, receptor atom within 8 A, ligand type)
+    triples over all boxes, counted on the GPU (torch arithmetic, measurement only)."""
+    import math as _m
+    atoms = torch.as_tensor(np.asarray(rec_xyz, np.float32), device="cuda")
+    total = 0
+    for b in boxes:
+        sp = float(np.float32(b.spacing))
+        size = np.asarray(b.size, np.float64)
+        dims = [int(_m.ceil(float(np.float32(size[k])) / sp - 1e-9)) + 1 for k in range(3)]
+        origin = np.asarray(np.float32(np.asarray(b.center, np.float32) - np.float32(size / 2)), np.float64)
+        ax = [torch.tensor(origin[k] + sp * np.arange(dims[k]), dtype=torch.float32, device="cuda") for k in range(3)]
+        near = atoms[((atoms - torch.tensor(origin + 0.5 * sp * (np.array(dims) - 1), dtype=torch.float32,
+                                            device="cuda")).abs() <= torch.tensor(0.5 * sp * (np.array(dims) - 1) + 8.0,
+                                                                                  dtype=torch.float32, device="cuda")).all(1)]
+        zz, yy, xx = torch.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+        nodes = torch.stack([xx.reshape(-1), yy.reshape(-1), zz.reshape(-1)], 1)
+        for i in range(0, nodes.shape[0], chunk):
+            d2 = ((nodes[i:i + chunk, None, :] - near[None, :, :]) ** 2).sum(-1)
+            total += int((d2 < 64.0).sum())
+    return total * n_types
 
 
 def run_rescore_check(ctx, gs, lig, pockets, params):

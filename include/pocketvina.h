@@ -49,11 +49,12 @@ typedef enum {
     PV_ERR_OOM = 3,        /* device allocation failed */
     PV_ERR_TIMEOUT = 4,    /* the search exceeded pv_dock_params.timeout_s (watchdog) */
     PV_ERR_NAN = 5,        /* a non-finite energy was produced */
-    PV_ERR_STATE = 6       /* handle used with a different context, or destroyed */
+    PV_ERR_STATE = 6       /* handle used with a different context, or destroyed; or a step
+                              block of the batched search gave up waiting (block_wait_s) */
 } pv_status;
 
 typedef enum { PV_MEM_HOST = 0, PV_MEM_DEVICE = 1 } pv_mem;
-typedef enum { PV_MODE_BATCHED = 0, PV_MODE_PLAIN = 1 } pv_mode;
+typedef enum { PV_MODE_BATCHED = 0, PV_MODE_PLAIN = 1, PV_MODE_PLAIN_WARP = 2 } pv_mode;
 
 /* Limits of one ligand: atoms and rotatable bonds. */
 #define PV_MAX_ATOMS 64
@@ -105,7 +106,10 @@ typedef struct {
  * Receptor atoms are typed on the device (carbon is polar iff an N/O lies within 1.75 A).
  * `boxes` and `lig_types` are host arrays; lig_types lists distinct XS type ids (0..10).
  * Maps are float32, layout per pocket [type][z][y][x] (x fastest), resident in device memory.
- * Errors: PV_ERR_ARG on empty/oversized input, PV_ERR_OOM, PV_ERR_CUDA. */
+ * A host receptor given in page-locked memory is uploaded before the call returns (the call
+ * then waits for the stream); device receptor arrays are read by the work the call issues.
+ * Errors: PV_ERR_ARG on empty/oversized input, a non-finite box or host receptor coordinate;
+ * PV_ERR_OOM, PV_ERR_CUDA. */
 pv_status pv_build_grids(pv_context* ctx, const pv_receptor* receptor, const pv_box* boxes,
                          int32_t n_pockets, const uint8_t* lig_types, int32_t n_types,
                          pv_grid_set** out);
@@ -118,6 +122,12 @@ void pv_grid_set_destroy(pv_grid_set* set);
 
 /* Number of pockets and total map bytes. */
 pv_status pv_grid_set_info(const pv_grid_set* set, int32_t* n_pockets, int64_t* bytes);
+
+/* Device time of the map-build kernel launches (Grid_cache, "Kernel 1") of the calls that built
+ * this set (pv_build_grids and every pv_grid_set_append), measured with events around each
+ * launch on the context's stream; waits for the last of them. Typing and binning are not
+ * included. PV_ERR_ARG on a null argument. */
+pv_status pv_grid_set_build_seconds(const pv_grid_set* set, double* seconds);
 
 /* Borrowed device view of one map: pointer (valid until the set is destroyed), node counts
  * (x, y, z), origin (first node) and spacing. PV_ERR_ARG if the type has no map. */
@@ -147,7 +157,7 @@ typedef struct {
 /* Builds the torsion tree (rigid fragments, hinge axes), XS types (carbon polar iff bonded to
  * N/O) and the intra-ligand pair list (atoms in different rigid fragments more than three
  * bonds apart, Eq. 3's e_intra), and uploads them. PV_ERR_ARG on a non-bridge rotatable bond
- * or a limit exceeded. */
+ * (one inside a ring), a disconnected ligand, a non-finite coordinate or a limit exceeded. */
 pv_status pv_ligand_create(pv_context* ctx, const pv_ligand_desc* desc, pv_ligand** out);
 void pv_ligand_destroy(pv_ligand* lig);
 
@@ -218,7 +228,10 @@ typedef struct {
     float rmsd_min;            /* A; a pose closer than this to a kept one is dropped */
     int32_t mode;              /* pv_mode: BATCHED = one persistent launch per round over all
                                   pairs, warp per chain; PLAIN = one launch per pair, thread
-                                  per chain, as in the paper's per-ligand loop */
+                                  per chain, as in the paper's per-ligand loop; PLAIN_WARP = one
+                                  launch per pair of BATCHED's warp-per-chain kernel (all steps
+                                  in one block, no queue across pairs, no graph) and a host
+                                  synchronisation per pair: what batching alone adds */
     int32_t bfgs_m;            /* L-BFGS memory (pairs kept), <= 8 */
     int32_t bfgs_max_iter;     /* 0: floor((25 + n_atoms) / 3) */
     int32_t bfgs_max_trials;   /* line-search trials per iteration */
@@ -251,14 +264,32 @@ typedef struct {
                                   no box penalty), then sort each pair's poses and the per-ligand
                                   ranking by that SF; the grid values stay in score_grid and
                                   e_inter_grid */
+    int32_t max_pockets;       /* > 0: dock each ligand only into the first max_pockets of its
+                                  pockets, in the order the caller lists them (pocket_ids of
+                                  pv_dock, or a ligand's pairs in list order for pv_dock_pairs):
+                                  with pockets listed best-ranked first (Methods "Pocket Prediction
+                                  with P2Rank", Eq. 2), the top-ranked pockets only (Results: the
+                                  top five pockets suffice). Pairs are indexed after this cut, as if
+                                  the caller had listed only the kept pockets. 0 = all pockets */
+    double block_wait_s;       /* batched: bound on a step block's wait for the previous block of
+                                  its chains (in practice it never waits); a block that runs out
+                                  is skipped with the chains' later blocks, and the dock returns
+                                  PV_ERR_STATE. <= 0: 30 s */
+    const int32_t* pair_keys;  /* NULL, or one host int32 per pair as the call lists them (pv_dock:
+                                  ligand * n_pockets + position in pocket_ids; pv_dock_pairs: the
+                                  position in its list; both before any max_pockets cut): the
+                                  pair's random stream, Philox counter word 1 in place of its pair
+                                  index. A job split over several calls (one per GPU) passes each
+                                  pair's index in the whole job, so that every chain draws the
+                                  same numbers as in one unsplit call */
 } pv_dock_params;
 
 /* Defaults: chains 64, steps 1000, seed 0, top_k 9, rmsd_min 1.0, BATCHED, m 5, max_iter 0,
  * max_trials 10, eps 1e-3, rho 1e-4, sigma 0.1, temperature 1.2, amplitude 2.0,
  * steps_per_round 0, use_graph 1, warps_per_cta 0, search_variant -1, host_copy 1, timeout_s 0,
- * focc 0, focc_min_delta 1e-4, rescore 0.
+ * focc 0, focc_min_delta 1e-4, rescore 0, max_pockets 0, block_wait_s 30, pair_keys NULL.
  * Autotuning (warps_per_cta 0 or search_variant -1): the first batched dock of a ligand-size
- * bucket on a context times each candidate launch shape on eight MC steps of its own work items
+ * bucket on a context times each candidate launch shape on 32 MC steps of its own work items
  * (results are unaffected: the dock itself restarts every chain) and keeps the fastest. */
 void pv_dock_params_default(pv_dock_params* p);
 
@@ -340,6 +371,29 @@ pv_status pv_dock_result_chains(const pv_dock_result* r, const float** dev_recor
 pv_status pv_dock_result_read_chains(const pv_dock_result* r, float* dst);
 
 void pv_dock_result_destroy(pv_dock_result* r);
+
+/* -------------------------------------------------------------- optimiser check --- */
+
+typedef enum { PV_OBJ_QUADRATIC = 0, PV_OBJ_ROSENBROCK = 1 } pv_objective;
+
+/* Verification of the search's optimiser (RILC-BFGS, Methods "Accelerated Docking", Eq. 6-12):
+ * the same device code that the docking chains run -- the whole-warp form (form 0, one warp per
+ * problem, lane k holding coordinate k) or the thread-per-chain form of the plain path (form 1,
+ * one thread per problem) -- applied to an analytic objective in R^n, so that its iterations can
+ * be compared with a reference implementation decision for decision (the docking score's
+ * trilinear maps and cutoffs make FP32 and FP64 line searches part ways; a smooth function does
+ * not). The retraction is x + step.
+ *   - objective PV_OBJ_QUADRATIC: f = sum_k a_k x_k^2 / 2 with dev_coef [n_problems][n] = a;
+ *     PV_OBJ_ROSENBROCK: f = sum_{k < n-1} 100 (x_{k+1} - x_k^2)^2 + (1 - x_k)^2 (dev_coef unused).
+ *   - dev_x [n_problems][n] float32: start points in, final points out; dev_f [n_problems]: the
+ *     final objective; dev_evals [n_problems] int32: objective evaluations (start point + every
+ *     line-search trial).
+ *   - params: bfgs_m (1..5), bfgs_max_iter (>= 1), bfgs_max_trials, bfgs_eps, rho, sigma.
+ *   - 1 <= n <= 32. Asynchronous on the context stream. PV_ERR_ARG on bad arguments.
+ * The paper has no counterpart of this call: it is a test service of this library. */
+pv_status pv_check_bfgs(pv_context* ctx, int32_t form, int32_t objective, int32_t n, int32_t n_problems,
+                        const float* dev_coef, float* dev_x, const pv_dock_params* params, float* dev_f,
+                        int32_t* dev_evals);
 
 /* ---------------------------------------------- pocket side (Supplementary Algorithm 1) --- */
 

@@ -9,7 +9,8 @@ LIB_PATH = os.path.join(HERE, "_lib", "libpocketvina.so")
 
 PV_OK, PV_ERR_ARG, PV_ERR_CUDA, PV_ERR_OOM, PV_ERR_TIMEOUT, PV_ERR_NAN, PV_ERR_STATE = range(7)
 PV_MEM_HOST, PV_MEM_DEVICE = 0, 1
-PV_MODE_BATCHED, PV_MODE_PLAIN = 0, 1
+PV_MODE_BATCHED, PV_MODE_PLAIN, PV_MODE_PLAIN_WARP = 0, 1, 2
+PV_OBJ_QUADRATIC, PV_OBJ_ROSENBROCK = 0, 1
 STATUS_NAMES = {0: "PV_OK", 1: "PV_ERR_ARG", 2: "PV_ERR_CUDA", 3: "PV_ERR_OOM", 4: "PV_ERR_TIMEOUT",
                 5: "PV_ERR_NAN", 6: "PV_ERR_STATE"}
 
@@ -38,7 +39,8 @@ class pv_dock_params(C.Structure):
                 ("use_graph", C.c_int32), ("warps_per_cta", C.c_int32), ("search_variant", C.c_int32),
                 ("host_copy", C.c_int32),
                 ("timeout_s", C.c_double), ("focc", C.c_int32), ("focc_min_delta", C.c_float),
-                ("rescore", C.c_int32)]
+                ("rescore", C.c_int32), ("max_pockets", C.c_int32), ("block_wait_s", C.c_double),
+                ("pair_keys", C.POINTER(C.c_int32))]
 
 
 class pv_pose(C.Structure):
@@ -72,6 +74,7 @@ SIGNATURES = {
     "pv_grid_set_append": (i32, [vp, vp, C.POINTER(pv_receptor), C.POINTER(pv_box), i32, pi32]),
     "pv_grid_set_destroy": (None, [vp]),
     "pv_grid_set_info": (i32, [vp, pi32, C.POINTER(i64)]),
+    "pv_grid_set_build_seconds": (i32, [vp, C.POINTER(C.c_double)]),
     "pv_grid_set_view": (i32, [vp, i32, i32, C.POINTER(vp), pi32, pf32, pf32]),
     "pv_grid_set_read_map": (i32, [vp, i32, i32, vp]),
     "pv_ligand_create": (i32, [vp, C.POINTER(pv_ligand_desc), C.POINTER(vp)]),
@@ -85,6 +88,7 @@ SIGNATURES = {
     "pv_score_xyz": (i32, [vp, vp, vp, i32, i32, vp, vp, vp, vp]),
     "pv_measure_gather": (i32, [vp, vp, i32, i64, i32, vp]),
     "pv_dock_params_default": (None, [C.POINTER(pv_dock_params)]),
+    "pv_check_bfgs": (i32, [vp, i32, i32, i32, i32, vp, vp, C.POINTER(pv_dock_params), vp, vp]),
     "pv_dock": (i32, [vp, vp, C.POINTER(vp), i32, pi32, i32, C.POINTER(pv_dock_params), C.POINTER(vp)]),
     "pv_dock_pairs": (i32, [vp, vp, C.POINTER(vp), i32, pi32, pi32, i32, C.POINTER(pv_dock_params),
                             C.POINTER(vp)]),

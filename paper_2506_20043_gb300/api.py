@@ -39,7 +39,7 @@ class DockParams:
     seed: int = 0
     top_k: int = 9
     rmsd_min: float = 1.0
-    mode: str = "batched"          # or "plain"
+    mode: str = "batched"          # or "plain" (thread per chain), "plain_warp" (warp per chain), per pair
     bfgs_m: int = 5
     bfgs_max_iter: int = 0
     bfgs_max_trials: int = 10
@@ -57,6 +57,9 @@ class DockParams:
     focc: int = 0                  # first-order consistency check (Eq. 4-5): neighbours kept, 0 = off
     focc_min_delta: float = 1e-4
     rescore: bool = False          # rescore kept poses by direct receptor summation (no grid)
+    max_pockets: int = 0           # > 0: each ligand docked into its first max_pockets pockets only
+    block_wait_s: float = 30.0     # bound on a step block's wait for its predecessor
+    pair_keys: Optional[Sequence[int]] = None   # per pair: its random stream (default: pair index)
 
     def to_c(self) -> A.pv_dock_params:
         p = A.pv_dock_params()
@@ -64,7 +67,11 @@ class DockParams:
         for f in dataclasses.fields(self):
             v = getattr(self, f.name)
             if f.name == "mode":
-                v = {"batched": A.PV_MODE_BATCHED, "plain": A.PV_MODE_PLAIN}[v]
+                v = {"batched": A.PV_MODE_BATCHED, "plain": A.PV_MODE_PLAIN, "plain_warp": A.PV_MODE_PLAIN_WARP}[v]
+            elif f.name == "pair_keys":
+                if v is None:
+                    continue
+                v = (C.c_int32 * len(v))(*[int(k) for k in v])   # kept alive by the struct
             elif isinstance(v, bool):
                 v = int(v)
             setattr(p, f.name, v)
@@ -369,10 +376,11 @@ class Context:
     def dock_top_pockets(self, grids: "GridSet", ligands: Sequence["Ligand"], ranked_pocket_ids: Sequence[int],
                          max_pockets: int = 5, params: Optional[DockParams] = None, **kw) -> "DockResult":
         """Docks into the best-ranked pockets only (pocket ids ordered by the pocket predictor's
-        score, best first): the first max_pockets of them, as the paper suggests five suffice."""
+        score, best first): the first max_pockets of them, as the paper suggests five suffice
+        (the library's max_pockets cut)."""
         if max_pockets < 1:
             raise PVError("max_pockets must be >= 1")
-        return self.dock(grids, ligands, list(ranked_pocket_ids)[:max_pockets], params, **kw)
+        return self.dock(grids, ligands, list(ranked_pocket_ids), params, max_pockets=max_pockets, **kw)
 
     def dock_pairs(self, grids: "GridSet", ligands: Sequence["Ligand"], pair_ligand: Sequence[int],
                    pair_pocket: Sequence[int], params: Optional[DockParams] = None, **kw) -> "DockResult":
@@ -386,7 +394,9 @@ class Context:
         return self._result(st, h, len(ligands), "pv_dock_pairs")
 
     def _result(self, st, h, n_ligs, what):
-        if st not in (A.PV_OK, A.PV_ERR_TIMEOUT, A.PV_ERR_NAN) or not h.value:
+        # a dock that ran and reports a watchdog timeout, a non-finite energy or a step block that
+        # gave up waiting still returns its result handle
+        if st not in (A.PV_OK, A.PV_ERR_TIMEOUT, A.PV_ERR_NAN, A.PV_ERR_STATE) or not h.value:
             self._check(st, what)
         res = DockResult(self, h, n_ligs)
         res.status_code = st
@@ -431,6 +441,12 @@ class GridSet:
         if st != A.PV_OK:
             raise PVError("pv_grid_set_view: no such map")
         return np.array(list(dims)), np.array(list(org), dtype=np.float64), sp.value, p.value
+
+    def build_seconds(self) -> float:
+        """Device time of the map-build kernel launches that built this set."""
+        t = C.c_double()
+        self.ctx._check(self.ctx.lib.pv_grid_set_build_seconds(self.h, C.byref(t)), "pv_grid_set_build_seconds")
+        return t.value
 
     def read_map(self, pocket: int, xs_type: int) -> np.ndarray:
         dims, _, _, _ = self.geometry(pocket, xs_type)

@@ -46,6 +46,7 @@ struct pv_grid_set {
     PvPocket* d_pockets = nullptr;
     std::vector<void*> arenas;
     int64_t bytes = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> map_events;   // around each map-build launch
 };
 
 struct pv_ligand {
@@ -76,6 +77,7 @@ struct pv_dock_result {
     double search_seconds = 0.0;    // the search kernel launches alone (events around them)
     int search_launches = 0;
     int search_variant = 0, warps_per_cta = 0;   // launch shape used (batched)
+    int mode = PV_MODE_BATCHED;
 };
 
 // ---------------------------------------------------------------------------- helpers ---
@@ -155,6 +157,15 @@ void pv::context_set_error(pv_context* ctx, const char* msg) {
     if (ctx && ctx->magic == kCtxMagic) ctx->err = msg;
 }
 
+bool pv::host_pinned(const void* a, const void* b, const void* c, const void* d) {
+    for (const void* p : {a, b, c, d}) {
+        cudaPointerAttributes at;
+        if (p && cudaPointerGetAttributes(&at, p) == cudaSuccess && at.type == cudaMemoryTypeHost) return true;
+        cudaGetLastError();
+    }
+    return false;
+}
+
 extern "C" pv_status pv_context_create(int device, void* cuda_stream, pv_context** out) {
     if (!out) return PV_ERR_ARG;
     *out = nullptr;
@@ -216,6 +227,13 @@ static pv_status add_receptor(pv_context* ctx, pv_grid_set* set, const pv_recept
     if (!r->xyz || !r->element || !r->donor || !r->acceptor) return fail(ctx, PV_ERR_ARG, "receptor arrays required");
     if (r->mem != PV_MEM_HOST && r->mem != PV_MEM_DEVICE) return fail(ctx, PV_ERR_ARG, "receptor mem kind");
     const int n = r->n_atoms;
+    if (r->mem == PV_MEM_HOST)
+        for (int i = 0; i < 3 * n; ++i)
+            if (!std::isfinite(r->xyz[i])) return fail(ctx, PV_ERR_ARG, "receptor coordinate is not finite");
+    for (int p = 0; p < n_pockets; ++p)
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(boxes[p].center[k]) || !std::isfinite(boxes[p].size[k]))
+                return fail(ctx, PV_ERR_ARG, "box center and size must be finite");
     std::vector<PvPocket> pk(n_pockets);
     double lo[3] = {1e30, 1e30, 1e30}, hi[3] = {-1e30, -1e30, -1e30};
     size_t map_floats = 0;
@@ -294,6 +312,10 @@ static pv_status add_receptor(pv_context* ctx, pv_grid_set* set, const pv_recept
         if (e == cudaSuccess) e = cudaMemcpyAsync(w + o_el, r->element, n, cudaMemcpyHostToDevice, ctx->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(w + o_don, r->donor, n, cudaMemcpyHostToDevice, ctx->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(w + o_acc, r->acceptor, n, cudaMemcpyHostToDevice, ctx->stream);
+        // copies from page-locked memory are still in flight on return (pageable sources have been
+        // staged): wait for them, so the caller may reuse its arrays once the call returns
+        if (e == cudaSuccess && host_pinned(r->xyz, r->element, r->donor, r->acceptor))
+            e = cudaStreamSynchronize(ctx->stream);
         xyz = (const float*)(w + o_xyz);
         el = (const uint8_t*)(w + o_el);
         don = (const uint8_t*)(w + o_don);
@@ -315,9 +337,16 @@ static pv_status add_receptor(pv_context* ctx, pv_grid_set* set, const pv_recept
     }
     if (e == cudaSuccess) {
         stage = "map build";
-        e = launch_grid_tiles((const float4*)(w + o_sorted), (const int*)(w + o_start), flo, kCellEdge, cd, d_p,
-                              (const int2*)(w + o_tiles), (int)tiles.size(), pack_slots(set->slot, 0),
-                              pack_slots(set->slot, 1), set->type_mask, ctx->stream);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        if (e == cudaSuccess) set->map_events.push_back({e0, e1});
+        if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+        if (e == cudaSuccess)
+            e = launch_grid_tiles((const float4*)(w + o_sorted), (const int*)(w + o_start), flo, kCellEdge, cd, d_p,
+                                  (const int2*)(w + o_tiles), (int)tiles.size(), pack_slots(set->slot, 0),
+                                  pack_slots(set->slot, 1), set->type_mask, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
     }
     if (e != cudaSuccess) {
         dfree(ctx, w);
@@ -379,8 +408,27 @@ extern "C" void pv_grid_set_destroy(pv_grid_set* set) {
         DeviceGuard g(ctx->device);
         for (void* a : set->arenas) dfree(ctx, a);
         dfree(ctx, set->d_pockets);
+        for (auto& ev : set->map_events) {
+            cudaEventDestroy(ev.first);
+            cudaEventDestroy(ev.second);
+        }
     }
     delete set;
+}
+
+extern "C" pv_status pv_grid_set_build_seconds(const pv_grid_set* set, double* seconds) {
+    if (!set || !seconds) return PV_ERR_ARG;
+    DeviceGuard g(set->ctx->device);
+    double total = 0.0;
+    for (const auto& ev : set->map_events) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(ev.second);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev.first, ev.second);
+        if (e != cudaSuccess) return cuda_fail(set->ctx, e, "map build timing");
+        total += ms * 1e-3;
+    }
+    *seconds = total;
+    return PV_OK;
 }
 
 extern "C" pv_status pv_grid_set_info(const pv_grid_set* set, int32_t* n_pockets, int64_t* bytes) {
@@ -627,6 +675,9 @@ extern "C" void pv_dock_params_default(pv_dock_params* p) {
     p->rescore = 0;
     p->host_copy = 1;
     p->timeout_s = 0.0;
+    p->max_pockets = 0;
+    p->block_wait_s = 30.0;
+    p->pair_keys = nullptr;
 }
 
 static void result_free(pv_dock_result* r) {
@@ -642,16 +693,18 @@ extern "C" void pv_dock_result_destroy(pv_dock_result* r) { result_free(r); }
 
 static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* const* ligs, int n_ligs,
                            const std::vector<int>& pair_lig, const std::vector<int>& pair_pocket,
-                           const pv_dock_params* prm, pv_dock_result** out) {
+                           const std::vector<int>& pair_key, const pv_dock_params* prm, pv_dock_result** out) {
     const int n_pairs = (int)pair_lig.size();
     const pv_dock_params& p = *prm;
+    if (!(std::isfinite(p.block_wait_s))) return fail(ctx, PV_ERR_ARG, "block_wait_s must be finite");
     if (p.chains < 1 || p.chains > 16384) return fail(ctx, PV_ERR_ARG, "chains must be in [1, 16384]");
     if (p.steps < 0) return fail(ctx, PV_ERR_ARG, "steps < 0");
     if (p.top_k < 1 || p.top_k > kMaxTopK) return fail(ctx, PV_ERR_ARG, "top_k must be in [1, 32]");
     if (!(p.rmsd_min >= 0.f)) return fail(ctx, PV_ERR_ARG, "rmsd_min < 0");
     if (p.bfgs_m < 1 || p.bfgs_m > 5) return fail(ctx, PV_ERR_ARG, "bfgs_m must be in [1, 5] on this path");
     if (p.bfgs_max_trials < 1 || p.bfgs_max_iter < 0) return fail(ctx, PV_ERR_ARG, "bad BFGS limits");
-    if (p.mode != PV_MODE_BATCHED && p.mode != PV_MODE_PLAIN) return fail(ctx, PV_ERR_ARG, "unknown mode");
+    if (p.mode != PV_MODE_BATCHED && p.mode != PV_MODE_PLAIN && p.mode != PV_MODE_PLAIN_WARP)
+        return fail(ctx, PV_ERR_ARG, "unknown mode");
     if (p.warps_per_cta < 0 || p.warps_per_cta > 16) return fail(ctx, PV_ERR_ARG, "warps_per_cta must be 0..16");
     if (p.focc < 0 || p.focc > PV_FOCC_MAX || !(p.focc_min_delta >= 0.f))
         return fail(ctx, PV_ERR_ARG, "focc must be 0..4 and focc_min_delta >= 0");
@@ -728,7 +781,8 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     const int auto_lanes = (all_team16 && max_atoms <= 16) ? 16 : 32;
     int variant = p.search_variant >= 0 ? p.search_variant : (auto_lanes == 16 ? 4 : 0);
     int W = p.warps_per_cta > 0 ? p.warps_per_cta : 4;
-    const bool autotune = p.mode == PV_MODE_BATCHED && (p.search_variant < 0 || p.warps_per_cta == 0);
+    const bool warp_chains = p.mode != PV_MODE_PLAIN;   // batched, or one warp-per-chain launch per pair
+    const bool autotune = warp_chains && (p.search_variant < 0 || p.warps_per_cta == 0);
     int max_rounds = 0;
     for (int i = 0; i < n_ligs; ++i) max_rounds = std::max(max_rounds, ligs[i]->rec.n_rounds);
     // the parameters the caller fixed (a variant or a CTA size) are part of the key: a shape tuned
@@ -751,7 +805,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     const size_t items_cap = make_items(W_min).size();
     std::vector<PvPairDesc> pdesc(n_pairs);
     for (int q = 0; q < n_pairs; ++q)
-        pdesc[q] = PvPairDesc{pair_lig[q], pair_pocket[q], ligs[pair_lig[q]]->rec.n_rounds, 0};
+        pdesc[q] = PvPairDesc{pair_lig[q], pair_pocket[q], ligs[pair_lig[q]]->rec.n_rounds, pair_key[q]};
     std::vector<const void*> ligptr(n_ligs);
     for (int i = 0; i < n_ligs; ++i) ligptr[i] = ligs[i]->d_blob;
     // one launch (round) covers all MC steps unless steps_per_round asks for more; a launch's steps
@@ -843,6 +897,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     A.lig_smem_bytes = max_blob;
     A.t0 = evals + 1;
     A.timeout_ns = p.timeout_s > 0 ? (unsigned long long)(p.timeout_s * 1e9) : 0ull;
+    A.wait_ns = p.block_wait_s > 0 ? (unsigned long long)(std::min(p.block_wait_s, 1e9) * 1e9) : 30000000000ull;
     A.err = ctr;
     A.evals = evals;
     TopkArgs T;
@@ -950,6 +1005,12 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
         }
     }
     A.items_per_block = (int)items.size();
+    // each pair's run of work items (items are grouped by pair) for the per-pair launches
+    std::vector<int> item_start(n_pairs, 0), item_count(n_pairs, 0);
+    for (int i = (int)items.size() - 1; i >= 0; --i) {
+        item_start[items[i].pair] = i;
+        item_count[items[i].pair]++;
+    }
     // grid of the persistent rounds: every SM filled to its occupancy
     int occ = 0;
     const int smem = search_smem_bytes(max_blob, W, search_variant_lanes(variant));
@@ -996,6 +1057,28 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
             }
             if (x == cudaSuccess) x = cudaEventRecordWithFlags(evs1, s, ev_flags);
             if (x == cudaSuccess) x = launch_topk(T, n_pairs, s);
+        } else if (p.mode == PV_MODE_PLAIN_WARP) {
+            // the paper's per-pair host loop over the batched path's own chain kernel: one launch
+            // per pair covering its chain blocks and all MC steps as a single step block, the
+            // pair's selection, and a host synchronisation before the next pair
+            for (int q = 0; q < n_pairs && x == cudaSuccess; ++q) {
+                SearchArgs a = A;
+                a.items = A.items + item_start[q];
+                a.items_per_block = item_count[q];
+                a.n_items = item_count[q];
+                a.queue = ctr + 2;
+                a.step0 = 0;
+                a.step1 = p.steps;
+                a.block_steps = std::max(1, p.steps);
+                x = cudaMemsetAsync(ctr + 2, 0, sizeof(int), s);
+                if (x == cudaSuccess)
+                    x = launch_search_round(a, variant, std::max(1, std::min(item_count[q], ctx->sms * occ)), W, s);
+                TopkArgs t = T;
+                t.pair0 = q;
+                if (x == cudaSuccess) x = launch_topk(t, 1, s);
+                if (x == cudaSuccess) x = cudaStreamSynchronize(s);
+            }
+            if (x == cudaSuccess) x = cudaEventRecordWithFlags(evs1, s, ev_flags);
         } else {
             for (int q = 0; q < n_pairs && x == cudaSuccess; ++q) {
                 SearchArgs a = A;
@@ -1053,6 +1136,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     R->seconds = ms * 1e-3;
     R->search_seconds = ms_search * 1e-3;
     R->search_launches = p.mode == PV_MODE_BATCHED ? n_rounds : n_pairs;
+    R->mode = p.mode;
     int err_bits = 0;
     unsigned long long ev = 0;
     e = cudaMemcpy(&err_bits, ctr, sizeof(int), cudaMemcpyDeviceToHost);
@@ -1083,7 +1167,9 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     *out = R;
     if (err_bits & PV_EBIT_TIMEOUT) return fail(ctx, PV_ERR_TIMEOUT, "search exceeded timeout_s");
     if (err_bits & PV_EBIT_NAN) return fail(ctx, PV_ERR_NAN, "non-finite energy in a chain");
-    if (err_bits & PV_EBIT_WAIT) return fail(ctx, PV_ERR_STATE, "a step block waited 30 s for its predecessor");
+    if (err_bits & PV_EBIT_WAIT)
+        return fail(ctx, PV_ERR_STATE, "a step block gave up waiting for its predecessor (block_wait_s); its chains "
+                                       "stopped there");
     return PV_OK;
 }
 
@@ -1095,10 +1181,17 @@ extern "C" pv_status pv_dock(pv_context* ctx, const pv_grid_set* set, pv_ligand*
     *out = nullptr;
     if (!set || set->ctx != ctx) return fail(ctx, PV_ERR_STATE, "grid set of another context");
     if (!ligs || n_ligs < 1 || !pocket_ids || n_pockets < 1 || !params) return fail(ctx, PV_ERR_ARG, "bad arguments");
-    std::vector<int> pl, pp;
+    if (params->max_pockets < 0) return fail(ctx, PV_ERR_ARG, "max_pockets must be >= 0");
+    // the top-ranked pockets only: the first max_pockets of the caller's order
+    const int kp = params->max_pockets > 0 ? std::min<int>(n_pockets, params->max_pockets) : n_pockets;
+    std::vector<int> pl, pp, key;
     for (int i = 0; i < n_ligs; ++i)
-        for (int k = 0; k < n_pockets; ++k) { pl.push_back(i); pp.push_back(pocket_ids[k]); }
-    return dock_impl(ctx, set, ligs, n_ligs, pl, pp, params, out);
+        for (int k = 0; k < kp; ++k) {
+            key.push_back(params->pair_keys ? params->pair_keys[(size_t)i * n_pockets + k] : (int)pl.size());
+            pl.push_back(i);
+            pp.push_back(pocket_ids[k]);
+        }
+    return dock_impl(ctx, set, ligs, n_ligs, pl, pp, key, params, out);
 }
 
 extern "C" pv_status pv_dock_pairs(pv_context* ctx, const pv_grid_set* set, pv_ligand* const* ligs, int32_t n_ligs,
@@ -1110,8 +1203,22 @@ extern "C" pv_status pv_dock_pairs(pv_context* ctx, const pv_grid_set* set, pv_l
     if (!set || set->ctx != ctx) return fail(ctx, PV_ERR_STATE, "grid set of another context");
     if (!ligs || n_ligs < 1 || !pair_ligand || !pair_pocket || n_pairs < 1 || !params)
         return fail(ctx, PV_ERR_ARG, "bad arguments");
-    std::vector<int> pl(pair_ligand, pair_ligand + n_pairs), pp(pair_pocket, pair_pocket + n_pairs);
-    return dock_impl(ctx, set, ligs, n_ligs, pl, pp, params, out);
+    if (params->max_pockets < 0) return fail(ctx, PV_ERR_ARG, "max_pockets must be >= 0");
+    std::vector<int> pl, pp, key;
+    std::map<int, std::vector<int>> kept;   // per ligand: its first max_pockets distinct pockets
+    for (int q = 0; q < n_pairs; ++q) {
+        if (params->max_pockets > 0) {
+            std::vector<int>& mine = kept[pair_ligand[q]];
+            if (std::find(mine.begin(), mine.end(), pair_pocket[q]) == mine.end()) {
+                if ((int)mine.size() >= params->max_pockets) continue;
+                mine.push_back(pair_pocket[q]);
+            }
+        }
+        key.push_back(params->pair_keys ? params->pair_keys[q] : (int)pl.size());
+        pl.push_back(pair_ligand[q]);
+        pp.push_back(pair_pocket[q]);
+    }
+    return dock_impl(ctx, set, ligs, n_ligs, pl, pp, key, params, out);
 }
 
 extern "C" pv_status pv_dock_result_info(const pv_dock_result* r, int32_t* n_pairs, int32_t* top_k,
@@ -1183,7 +1290,10 @@ extern "C" pv_status pv_dock_result_stats(const pv_dock_result* r, uint64_t* n_e
         if (st != PV_OK) return st;
         for (int q = 0; q < r->n_pairs; ++q) {
             const int b = r->status[q];
-            status[q] = (b & PV_EBIT_TIMEOUT) ? PV_ERR_TIMEOUT : ((b & PV_EBIT_NAN) ? PV_ERR_NAN : PV_OK);
+            status[q] = (b & PV_EBIT_TIMEOUT) ? PV_ERR_TIMEOUT
+                        : (b & PV_EBIT_NAN)   ? PV_ERR_NAN
+                        : (b & PV_EBIT_WAIT)  ? PV_ERR_STATE
+                                              : PV_OK;
         }
     }
     return PV_OK;

@@ -17,8 +17,8 @@ namespace pv {
 // chain (have == false) only take part in the loop's warp vote.
 template <int LANES, bool FOCC>
 __device__ __forceinline__ void run_chain(const SearchArgs& A, const PvLigBlob& L, WarpScratch& S, const Site& site,
-                                          int pair, int chain, bool have, int step0, int step1, uint32_t& evals_out,
-                                          int& flags_out) {
+                                          int pair, uint32_t key, int chain, bool have, int step0, int step1,
+                                          uint32_t& evals_out, int& flags_out) {
     using Tm = Team<LANES>;
     const int tl = Tm::lane();
     const PvSearchConst& C = A.C;
@@ -42,7 +42,7 @@ __device__ __forceinline__ void run_chain(const SearchArgs& A, const PvLigBlob& 
     int it = 0, tr = 0, stored = 0, head = 0, iters = 0;
     bool have_lo = false, bstart = true;
     if (stage == kStart) {
-        xt = random_pose<LANES>(L, *site.P, (uint32_t)chain, (uint32_t)pair, C);
+        xt = random_pose<LANES>(L, *site.P, (uint32_t)chain, key, C);
         iters = 0;
     } else if (stage == kOptimise) {
         for (int i = tl; i < 7 + n_rot; i += LANES) curs[i] = __ldcg(rec + PV_CH_CUR + i);
@@ -56,7 +56,7 @@ __device__ __forceinline__ void run_chain(const SearchArgs& A, const PvLigBlob& 
         Tm::sync();
         if (s < step1) {
             xt = load_pose<LANES>(curs, n_rot);
-            u = mutate<LANES>(L, xt, (uint32_t)chain, (uint32_t)pair, s, C);
+            u = mutate<LANES>(L, xt, (uint32_t)chain, key, s, C);
             iters = max_iter;
         } else {
             stage = kDone;
@@ -186,7 +186,7 @@ __device__ __forceinline__ void run_chain(const SearchArgs& A, const PvLigBlob& 
         }
         if (s < step1) {                                        // the next MC step
             xt = load_pose<LANES>(curs, n_rot);
-            u = mutate<LANES>(L, xt, (uint32_t)chain, (uint32_t)pair, s, C);
+            u = mutate<LANES>(L, xt, (uint32_t)chain, key, s, C);
             bstart = true;
             iters = max_iter;
         } else {
@@ -205,25 +205,44 @@ __device__ __forceinline__ void run_chain(const SearchArgs& A, const PvLigBlob& 
             rec[PV_CH_ECUR] = e_cur;
             rec[PV_CH_EBEST] = e_best;
             rec[PV_CH_EVALS] = __uint_as_float(evals_before + evals);
-            const int old = step0 == 0 ? 0 : __float_as_int(__ldcg(rec + PV_CH_FLAGS));
-            rec[PV_CH_FLAGS] = __int_as_float(old | flags);
+            if (flags) atomicOr(reinterpret_cast<int*>(rec + PV_CH_FLAGS), flags);   // zeroed at the dock's start
         }
     }
     evals_out = evals;
     flags_out = flags;
 }
 
-// RILC-BFGS (Eq. 6-12) of one whole-warp chain from x (updated in place); returns SF(x) and, in
-// g_out, the lane's component of its gradient. One evaluation call site: the start point, then
-// every line-search trial. With a neighbour ring (n_nb >= 0), the start point is first put to the
-// consistency check (Eq. 4-5); a candidate that fails it is returned as it is.
-template <bool FOCC>
-__device__ __forceinline__ float warp_local_search(const PvLigBlob& L, WarpScratch& S, const Site& site, Pose& x,
-                                                   const PvSearchConst& C, int max_iter, uint32_t& evals,
-                                                   float& g_out, const float* ring) {
+// The docking objective of a whole-warp chain: SF (Eq. 3) at a pose with its tangent gradient (lane
+// k holds component k), and the retraction of a tangent step (translation, world-frame rotation
+// vector, torsions). warp_rilc_bfgs is written against this interface so that the same optimiser
+// code also runs on analytic objectives (pv_check.cu).
+struct WarpDockObjective {
+    using State = Pose;
+    const PvLigBlob& L;
+    WarpScratch& S;
+    const Site& site;
+    int n_tan;
+    __device__ __forceinline__ float eval(const Pose& x, float& g) const {
+        return team_eval<32>(L, S, site, x, g, true);
+    }
+    __device__ __forceinline__ Pose retract(const Pose& x, float step) const {
+        return team_retract<32>(x, step, n_tan);
+    }
+};
+
+// RILC-BFGS (Eq. 6-12) of one whole-warp team from x (updated in place); returns the objective at
+// x and, in g_out, the lane's component of its gradient. One evaluation call site: the start
+// point, then every line-search trial. With a neighbour ring (FOCC, dock objective only), the start
+// point is first put to the consistency check (Eq. 4-5); a candidate that fails it is returned as
+// it is.
+template <bool FOCC, class Obj>
+__device__ __forceinline__ float warp_rilc_bfgs(const Obj& obj, WarpScratch& S, typename Obj::State& x,
+                                                const PvSearchConst& C, int max_iter, uint32_t& evals, float& g_out,
+                                                const float* ring, int n_rot) {
     using Tm = Team<32>;
+    using State = typename Obj::State;
     const int tl = Tm::lane();
-    const int n_tan = 6 + L.h.n_rot, m = C.bfgs_m;
+    const int m = C.bfgs_m;
     float* Hs = &S.hs[0][0];
     float* Hy = &S.hy[0][0];
     // The line search's uniform scalars live in S.cs between evaluations: each iteration loads them
@@ -232,10 +251,10 @@ __device__ __forceinline__ float warp_local_search(const PvLigBlob& L, WarpScrat
     ChainScalars& Q = S.cs;
     float rh = 0.f, al = 0.f, g = 0.f, d = 0.f;
     bool start = true;
-    Pose xt = x;
+    State xt = x;
     for (;;) {
         float ge;
-        const float fe = team_eval<32>(L, S, site, xt, ge, true);
+        const float fe = obj.eval(xt, ge);
         ++evals;
         float f = Q.f, gd = Q.gd, lam = Q.lam, lo = Q.lo, hi = Q.hi, flo = Q.flo;
         int it = Q.it, tr = Q.tr, stored = Q.stored, head = Q.head, have_lo = Q.have_lo;
@@ -243,7 +262,9 @@ __device__ __forceinline__ float warp_local_search(const PvLigBlob& L, WarpScrat
         if (start) {
             start = false;
             f = fe; g = ge; it = 0; stored = 0; head = 0;
-            if (FOCC && ring && !focc_pass<32>(x, fe, g, ring, Q.nb_n, L.h.n_rot, C.focc_min_delta)) stop = true;
+            bool skip = false;
+            if constexpr (FOCC) skip = ring && !focc_pass<32>(x, fe, g, ring, Q.nb_n, n_rot, C.focc_min_delta);
+            if (skip) stop = true;
             else next_iter = true;
         } else {
             const float gtd = Tm::sum(ge * d);
@@ -261,13 +282,13 @@ __device__ __forceinline__ float warp_local_search(const PvLigBlob& L, WarpScrat
                 ++tr;
                 if (tr < C.bfgs_max_trials) {
                     lam = hi < 0.f ? 2.f * lam : 0.5f * (lo + hi);
-                    xt = team_retract<32>(x, lam * d, n_tan);
+                    xt = obj.retract(x, lam * d);
                     retry = true;
                 } else if (!have_lo) {
                     stop = true;                                // no acceptable step: stop at x
                 } else {
                     lam = lo; ft = flo; gt = S.glo[tl];
-                    xt = team_retract<32>(x, lam * d, n_tan);   // the same arithmetic as that trial
+                    xt = obj.retract(x, lam * d);               // the same arithmetic as that trial
                     take = true;
                 }
             }
@@ -297,7 +318,7 @@ __device__ __forceinline__ float warp_local_search(const PvLigBlob& L, WarpScrat
                     stop = true;
                 } else {
                     lam = 1.f; lo = 0.f; hi = -1.f; have_lo = 0; tr = 0;
-                    xt = team_retract<32>(x, lam * d, n_tan);
+                    xt = obj.retract(x, lam * d);
                 }
             }
         }
@@ -314,8 +335,8 @@ __device__ __forceinline__ float warp_local_search(const PvLigBlob& L, WarpScrat
 }
 template <bool FOCC>
 __device__ __forceinline__ void run_chain_warp(const SearchArgs& A, const PvLigBlob& L, WarpScratch& S,
-                                               const Site& site, int pair, int chain, int step0, int step1,
-                                               uint32_t& evals_out, int& flags_out) {
+                                               const Site& site, int pair, uint32_t key, int chain, int step0,
+                                               int step1, uint32_t& evals_out, int& flags_out) {
     using Tm = Team<32>;
     const int tl = Tm::lane();
     const PvSearchConst& C = A.C;
@@ -349,18 +370,19 @@ __device__ __forceinline__ void run_chain_warp(const SearchArgs& A, const PvLigB
         Tm::sync();
     }
     Pose cand;
-    if (step0 == 0) cand = random_pose<32>(L, *site.P, (uint32_t)chain, (uint32_t)pair, C);
+    if (step0 == 0) cand = random_pose<32>(L, *site.P, (uint32_t)chain, key, C);
     for (;;) {
         const int stage0 = Q.stage, s0 = Q.s;                   // 0 start, 1 MC step, 2 refine
         if (!(stage0 == 0 || s0 < step1)) break;
         if (stage0 == 1) {
             cand = load_pose<32>(curs, n_rot);
-            const float u = mutate<32>(L, cand, (uint32_t)chain, (uint32_t)pair, s0, C);
+            const float u = mutate<32>(L, cand, (uint32_t)chain, key, s0, C);
             Tm::sync();
             Q.u = u;
         }
-        const float e_new = warp_local_search<FOCC>(L, S, site, cand, C, stage0 == 0 ? 0 : max_iter, evals, g_new,
-                                                    FOCC && stage0 == 1 ? ring : nullptr);
+        const WarpDockObjective obj{L, S, site, 6 + n_rot};
+        const float e_new = warp_rilc_bfgs<FOCC>(obj, S, cand, C, stage0 == 0 ? 0 : max_iter, evals, g_new,
+                                                 FOCC && stage0 == 1 ? ring : nullptr, n_rot);
         float e_cur = Q.e_cur, e_best = Q.e_best;
         const float u = Q.u;
         int s = Q.s, stage = Q.stage, flags = Q.flags, nb_n = Q.nb_n, nb_head = Q.nb_head;
@@ -418,8 +440,7 @@ __device__ __forceinline__ void run_chain_warp(const SearchArgs& A, const PvLigB
         rec[PV_CH_ECUR] = e_cur;
         rec[PV_CH_EBEST] = e_best;
         rec[PV_CH_EVALS] = __uint_as_float(Q.evals_before + evals);
-        const int old = step0 == 0 ? 0 : __float_as_int(__ldcg(rec + PV_CH_FLAGS));
-        rec[PV_CH_FLAGS] = __int_as_float(old | flags);
+        if (flags) atomicOr(reinterpret_cast<int*>(rec + PV_CH_FLAGS), flags);   // zeroed at the dock's start
     }
     Tm::sync();
     evals_out = evals;
@@ -431,24 +452,25 @@ __device__ __forceinline__ int load_acquire(const int* p) {
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void store_release(int* p, int v) {
-    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 // Waits until the chain block's previous step block is published (`*progress >= blk`). Every CTA
 // of the launch is resident and a block is taken from the queue only after all blocks before it,
-// by CTAs that are running, so the wait ends; it is still bounded (30 s), after which the block
-// runs anyway and the launch reports PV_EBIT_WAIT.
-__device__ __forceinline__ bool wait_block(const int* progress, int blk) {
-    if (load_acquire(progress) >= blk) return true;
+// by CTAs that are running, so the wait ends; it is still bounded by limit_ns. Returns 1 when the
+// predecessor is published, 0 when the bound ran out, -1 when the work item was given up
+// (poisoned) by an earlier block.
+__device__ __forceinline__ int wait_block(const int* progress, int blk, unsigned long long limit_ns) {
+    int v = load_acquire(progress);
+    if (v >= PV_PROGRESS_POISON) return -1;
+    if (v >= blk) return 1;
     const unsigned long long t0 = globaltimer();
     unsigned ns = 64;
-    while (load_acquire(progress) < blk) {
-        if (globaltimer() - t0 > 30000000000ull) return false;
+    for (;;) {
+        if (globaltimer() - t0 >= limit_ns) return 0;
         __nanosleep(ns);
         if (ns < 4096) ns <<= 1;
+        v = load_acquire(progress);
+        if (v >= PV_PROGRESS_POISON) return -1;
+        if (v >= blk) return 1;
     }
-    return true;
 }
 
 // One launch of the batched search: MC steps [step0, step1) of every chain of every pair, cut into
@@ -462,7 +484,7 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) search_round_kernel(SearchA
     extern __shared__ __align__(16) unsigned char smem[];
     PvLigBlob& L = *reinterpret_cast<PvLigBlob*>(smem);
     WarpScratch* scratch = reinterpret_cast<WarpScratch*>(smem + ((A.lig_smem_bytes + 127) & ~127));
-    __shared__ int s_item, s_lig;
+    __shared__ int s_item, s_lig, s_skip;
     __shared__ PvPocket s_pocket;
     constexpr int TPW = 32 / LANES;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -489,9 +511,26 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) search_round_kernel(SearchA
             stage_ligand(&L, A.ligs[pd.ligand], A.slots_lo, A.slots_hi);
             if (threadIdx.x == 0) s_lig = pd.ligand;
         }
-        if (blk > 0 && threadIdx.x == 0 && !wait_block(A.progress + j, blk)) atomicOr(A.err, PV_EBIT_WAIT);
+        if (threadIdx.x == 0) {
+            // a block whose predecessor is not published within the bound is skipped, not run on
+            // chain records that are still being written; the work item's later blocks are
+            // skipped too (poisoned progress) and the launch reports PV_EBIT_WAIT
+            const int w = blk > 0 ? wait_block(A.progress + j, blk, A.wait_ns) : 1;
+            if (w == 0) {
+                atomicOr(A.err, PV_EBIT_WAIT);
+                atomicMax(A.progress + j, PV_PROGRESS_POISON);
+            }
+            s_skip = w != 1;
+        }
         __syncthreads();
         const int chain = item.chain0 + team;
+        if (s_skip) {
+            if (Team<LANES>::lane() == 0 && chain < A.C.chains) {
+                float* rec = A.chains + ((size_t)item.pair * A.C.chains + chain) * PV_CHAIN_STRIDE;
+                atomicOr(reinterpret_cast<int*>(rec + PV_CH_FLAGS), PV_EBIT_WAIT);
+            }
+            continue;
+        }
         Site site;
         site.maps = s_pocket.maps;
         site.P = &s_pocket;
@@ -499,10 +538,11 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) search_round_kernel(SearchA
         int flags = 0;
         if constexpr (LANES == 32) {
             if (chain < A.C.chains)
-                run_chain_warp<FOCC>(A, L, scratch[team], site, item.pair, chain, step0, step1, evals, flags);
+                run_chain_warp<FOCC>(A, L, scratch[team], site, item.pair, (uint32_t)pd.key, chain, step0, step1,
+                                     evals, flags);
         } else {
-            run_chain<LANES, FOCC>(A, L, scratch[team], site, item.pair, chain, chain < A.C.chains, step0, step1,
-                                   evals, flags);
+            run_chain<LANES, FOCC>(A, L, scratch[team], site, item.pair, (uint32_t)pd.key, chain, chain < A.C.chains,
+                                   step0, step1, evals, flags);
         }
         if (Team<LANES>::lane() == 0 && evals) {
             atomicAdd(A.evals, (unsigned long long)evals);
@@ -510,11 +550,12 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) search_round_kernel(SearchA
         }
         __syncwarp();
         (void)lane;
-        // the chain records of this block are written: publish it to the next block's item
+        // the chain records of this block are written: publish it to the next block's item (a
+        // maximum, so that a poisoned item stays poisoned)
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            store_release(A.progress + j, blk + 1);
+            atomicMax(A.progress + j, blk + 1);
         }
     }
 }

@@ -11,6 +11,9 @@ namespace pv {
 // Context access for entry points defined outside pv_api.cu (false on a bad handle).
 bool context_device_stream(pv_context* ctx, int* device, cudaStream_t* stream);
 void context_set_error(pv_context* ctx, const char* msg);
+// Whether any of the host arrays is page-locked (cudaMallocHost or registered): copies from them
+// run asynchronously, so a call that must not retain them waits for those copies.
+bool host_pinned(const void* a, const void* b, const void* c, const void* d);
 
 constexpr int kSearchThreadsMax = 512;
 constexpr int kTopkThreads = 256;
@@ -73,6 +76,7 @@ struct SearchArgs {
     int lig_smem_bytes;            // staging capacity for one ligand
     const unsigned long long* t0;  // start time of the dock (globaltimer)
     unsigned long long timeout_ns; // 0 = none
+    unsigned long long wait_ns;    // batched: bound on a step block's wait for its predecessor
     int* err;
     unsigned long long* evals;
 };

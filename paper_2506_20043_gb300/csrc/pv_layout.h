@@ -104,11 +104,14 @@ struct PvPairDesc {
     int32_t ligand;        // index into the ligand pointer table
     int32_t pocket;        // pocket id
     int32_t lig_rounds;    // pair rounds of that ligand
-    int32_t pad;
+    int32_t key;           // the pair's random stream: Philox counter word 1 (default: pair index)
 };
 
 // Device-side error bits
 enum { PV_EBIT_TIMEOUT = 1, PV_EBIT_NAN = 2, PV_EBIT_ARG = 4, PV_EBIT_WAIT = 8 };
+// Progress value of a work item whose step block gave up waiting for its predecessor: its later
+// blocks are skipped too (above any real block count).
+#define PV_PROGRESS_POISON (1 << 30)
 
 // Output record of a kept pose (matches pv_pose in the public header).
 struct PvPoseRec {

@@ -135,6 +135,8 @@ bool build_ligand(const LigandInput& in, LigandRecord& out, std::string& err) {
     }
     for (int i = 0; i < n; ++i)
         if (in.element[i] > 3) { err = "element must be 0..3 (C, N, O, S)"; return false; }
+    for (int i = 0; i < 3 * n; ++i)
+        if (!std::isfinite(in.xyz[i])) { err = "ligand coordinate is not finite"; return false; }
     // XS types: carbon is polar iff bonded to N or O
     out.xs.assign(n, 0);
     int type_mask = 0;

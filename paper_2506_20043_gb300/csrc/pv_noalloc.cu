@@ -89,6 +89,12 @@ extern "C" pv_status pv_build_grid_noalloc(pv_context* ctx, const pv_receptor* r
     }
     for (int t = 0; t < PV_N_XS; ++t)
         if (mask & (1 << t)) slot[t] = (int8_t)n_maps++;
+    if (r->mem == PV_MEM_HOST)
+        for (int i = 0; i < 3 * r->n_atoms; ++i)
+            if (!std::isfinite(r->xyz[i])) return fail(ctx, PV_ERR_ARG, "receptor coordinate is not finite");
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(box->center[k]) || !std::isfinite(box->size[k]))
+            return fail(ctx, PV_ERR_ARG, "box center and size must be finite");
     PvPocket P;
     std::memset(&P, 0, sizeof(P));
     double lo[3], hi[3];
@@ -121,6 +127,8 @@ extern "C" pv_status pv_build_grid_noalloc(pv_context* ctx, const pv_receptor* r
                                          std::to_string(kMaxCells) + " binning cells and " +
                                          std::to_string(kMaxTiles) + " node tiles)");
     int prev = -1;
+    // like every entry point of the library: an error the calling thread left pending is cleared
+    // here, so that the launch checks below report only this call's own launches
     cudaGetLastError();
     if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
     if (prev != device && cudaSetDevice(device) != cudaSuccess) return fail(ctx, PV_ERR_CUDA, "cudaSetDevice failed");
@@ -158,6 +166,11 @@ extern "C" pv_status pv_build_grid_noalloc(pv_context* ctx, const pv_receptor* r
             acc = (const uint8_t*)(scratch + kOffAcc);
         }
         if (e == cudaSuccess) e = cudaMemcpyAsync(scratch + kOffPocket, &P, sizeof(P), cudaMemcpyHostToDevice, stream);
+        // a copy from page-locked host memory is still in flight when cudaMemcpyAsync returns (from
+        // pageable memory, which includes P, it has been staged): wait for it, so that the caller
+        // may free or reuse its arrays once this call returns
+        if (e == cudaSuccess && r->mem == PV_MEM_HOST && host_pinned(r->xyz, r->element, r->donor, r->acceptor))
+            e = cudaStreamSynchronize(stream);
         if (e == cudaSuccess) {
             fill_tiles_kernel<<<(int)((n_tiles + 255) / 256), 256, 0, stream>>>((int2*)(scratch + kOffTiles), (int)n_tiles);
             e = cudaGetLastError();

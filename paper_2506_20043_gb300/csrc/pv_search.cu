@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(128) plain_search_kernel(SearchArgs A, int pai
     tc.slots_hi = A.slots_hi;
     tc.evals = 0;
     float* rec = A.chains + ((size_t)pair * A.C.chains + chain) * PV_CHAIN_STRIDE;
-    thread_run_chain(tc, A.C, (uint32_t)chain, (uint32_t)pair, A.step0, A.step1, rec, A.t0,
+    thread_run_chain(tc, A.C, (uint32_t)chain, (uint32_t)pd.key, A.step0, A.step1, rec, A.t0,
                      A.timeout_ns, A.err);
     atomicAdd(A.evals, (unsigned long long)tc.evals);
 }

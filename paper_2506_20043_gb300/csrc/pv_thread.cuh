@@ -101,16 +101,29 @@ __device__ __forceinline__ void thread_retract(const float* x, const float* s, i
     for (int k = 0; k < n_rot; ++k) y[7 + k] = x[7 + k] + s[6 + k];
 }
 
-// RILC-BFGS on one thread; the same steps as warp_bfgs (Eq. 6-12).
-static __device__ float thread_bfgs(ThreadChain& c, ThreadWork& w, float* x, const PvSearchConst& C,
-                             int max_iter) {
-    const int n_rot = c.L->h.n_rot, nt = 6 + n_rot, np = 7 + n_rot;
+// The docking objective of a thread-per-chain chain: SF (Eq. 3) of a POT with its tangent
+// gradient, and the retraction of a tangent step. thread_rilc_bfgs is written against this
+// interface so that the same optimiser code also runs on analytic objectives (pv_check.cu).
+struct ThreadDockObjective {
+    ThreadChain& c;
+    ThreadWork& w;
+    int n_rot, nt, np;             // torsions, tangent and state dimensions
+    __device__ __forceinline__ float eval(const float* x, float* g) const { return thread_eval(c, w, x, g); }
+    __device__ __forceinline__ void retract(const float* x, const float* s, float* y) const {
+        thread_retract(x, s, n_rot, y);
+    }
+};
+
+// RILC-BFGS on one thread; the same steps as warp_rilc_bfgs (Eq. 6-12).
+template <class Obj>
+static __device__ float thread_rilc_bfgs(const Obj& obj, float* x, const PvSearchConst& C, int max_iter) {
+    const int nt = obj.nt, np = obj.np;
     const int m = C.bfgs_m;
     float g[PV_MAX_TAN], d[PV_MAX_TAN], q[PV_MAX_TAN], gt[PV_MAX_TAN], glo[PV_MAX_TAN];
     float xt[PV_MAX_POT], xlo[PV_MAX_POT], st[PV_MAX_TAN];
     float Sh[PV_MAX_M][PV_MAX_TAN], Yh[PV_MAX_M][PV_MAX_TAN], rh[PV_MAX_M], al[PV_MAX_M];
     int stored = 0;
-    float f = thread_eval(c, w, x, g);
+    float f = obj.eval(x, g);
     for (int it = 0; it < max_iter; ++it) {
         for (int k = 0; k < nt; ++k) q[k] = g[k];
         for (int a = 0; a < stored; ++a) {
@@ -137,8 +150,8 @@ static __device__ float thread_bfgs(ThreadChain& c, ThreadWork& w, float* x, con
         bool accepted = false, have_lo = false;
         for (int tr = 0; tr < C.bfgs_max_trials; ++tr) {
             for (int k = 0; k < nt; ++k) st[k] = lam * d[k];
-            thread_retract(x, st, n_rot, xt);
-            ft = thread_eval(c, w, xt, gt);
+            obj.retract(x, st, xt);
+            ft = obj.eval(xt, gt);
             float gtd = 0.f;
             for (int k = 0; k < nt; ++k) gtd += gt[k] * d[k];
             if (!(ft <= f + lam * C.rho * gd)) {
@@ -241,12 +254,13 @@ static __device__ void thread_run_chain(ThreadChain& c, const PvSearchConst& C, 
             cand[7 + entity - 2] = -PV_PI + 2.f * PV_PI * u01(b1.x);
         }
         const float u = u01(b1.y);
-        const float e_new = thread_bfgs(c, w, cand, C, max_iter);
+        const ThreadDockObjective obj{c, w, n_rot, 6 + n_rot, 7 + n_rot};
+        const float e_new = thread_rilc_bfgs(obj, cand, C, max_iter);
         if (e_new < e_cur || u < expf((e_cur - e_new) / C.temperature)) {
             for (int k = 0; k < np; ++k) cur[k] = cand[k];
             e_cur = e_new;
             if (e_cur < e_best) {
-                e_cur = thread_bfgs(c, w, cur, C, max_iter);
+                e_cur = thread_rilc_bfgs(obj, cur, C, max_iter);
                 for (int k = 0; k < np; ++k) best[k] = cur[k];
                 e_best = e_cur;
             }

@@ -2,7 +2,10 @@
 
 Units of the search are independent (ligand, pocket, chain), so ranks work on disjoint shards with no
 data-path collective. Shards are cut by pocket first, so that each GPU builds and holds only the maps
-of its own pockets, then by ligand when there are fewer pocket groups than ranks. The only exchange
+of its own pockets, then by ligand when there are fewer pocket groups than ranks (plan_shards), or as
+equal contiguous runs of the pocket-major pair list (plan_pairs: balanced to one pair, a pocket's maps
+built on at most the two ranks whose runs meet inside it). Each pair keeps its random stream from the
+unsplit job (its pair key), so the split does not change any chain. The only exchange
 is the final one: each rank's kept poses (a few records per pair) are gathered on the host and merged
 per ligand by score, ties by (pocket, chain) -- the same order the GPU merge uses within a rank.
 
@@ -38,6 +41,26 @@ def plan_shards(pocket_ids: Sequence[int], n_ligands: int, world: int) -> List[T
     return out
 
 
+def plan_pairs(pocket_ids: Sequence[int], n_ligands: int, world: int) -> List[List[Tuple[int, int, int]]]:
+    """Per rank: its pairs as (ligand, pocket id, key), with key = ligand * len(pocket_ids) + the
+    pocket's position (the pair's index, hence its random stream, in one unsplit pv_dock call). The
+    job's pairs are taken pocket-major (all ligands of the first pocket, then of the next) and cut
+    into `world` contiguous runs whose sizes differ by at most one, so every rank gets the same
+    work to within one pair and builds the maps of only the few pockets its run touches."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    pockets = list(pocket_ids)
+    n_p = len(pockets)
+    order = [(li, pockets[k], li * n_p + k) for k in range(n_p) for li in range(max(n_ligands, 0))]
+    base, extra = divmod(len(order), world)
+    out, start = [], 0
+    for r in range(world):
+        size = base + (1 if r < extra else 0)
+        out.append(order[start:start + size])
+        start += size
+    return out
+
+
 def merge_records(per_rank: Sequence[Dict[int, List[Record]]]) -> Dict[int, List[Record]]:
     """Merges {ligand: [(SF, pocket, chain), ...]} from every rank into one ranking per ligand."""
     merged: Dict[int, List[Record]] = {}
@@ -49,7 +72,9 @@ def merge_records(per_rank: Sequence[Dict[int, List[Record]]]) -> Dict[int, List
 
 def records_from_result(result, ligand_ids: Sequence[int]) -> Dict[int, List[Record]]:
     """{global ligand id: records} from a DockResult of this rank (ligand_ids maps the rank's local
-    ligand index to the job's ligand id)."""
+    ligand index to the job's ligand id). Ranks that dock their pairs with the job-wide pair keys
+    (pv_dock_params.pair_keys) and the same search team width reproduce, after merge_records, the
+    ranking of one unsplit dock bit for bit."""
     poses = result.poses.reshape(-1)
     out: Dict[int, List[Record]] = {}
     for local, lig in enumerate(ligand_ids):

@@ -1,4 +1,5 @@
-"""Seeded synthetic docking inputs: receptors with carved pockets, torsion-tree ligands, poses.
+"""Seeded synthetic docking inputs: receptors with carved pockets, torsion-tree ligands (acyclic, or
+built around rigid six-membered rings), poses.
 
 This module only *generates inputs*. It holds none of the docking arithmetic: no atom typing,
 no scoring terms, no kinematics, no search. Both the FP64 oracle (``oracle/``) and the CUDA
@@ -219,6 +220,116 @@ def make_ligand(n_atoms: int, n_rot: int, seed: int) -> Ligand:
         donor, acceptor = _hbond_flags(rng, element)
         return Ligand(xyz, element, donor, acceptor, bonds_a, rot)
     raise RuntimeError("ligand growth failed")
+
+
+RING_BOND = 1.40                                # aromatic six-membered ring: side = circumradius
+
+
+def make_ring_ligand(n_atoms: int, n_rot: int, seed: int, rings: str = "single") -> Ligand:
+    """Heavy-atom ligand built around rigid six-membered rings (planar hexagons, 1.40 A bonds):
+    ``rings`` = "single" (one ring), "fused" (two rings sharing a bond, naphthalene-like) or
+    "linked" (two rings joined by a 1.5 A single bond, biphenyl-like). Ring atoms are C, or N with
+    probability 0.15, and take at most one substituent, placed on the outward bisector in the ring
+    plane; the remaining atoms grow as trees (as in ``make_ligand``: 1.5 A bonds, 109.5 degree angles,
+    random dihedrals, the same clash rejection). Ring bonds are never rotatable (they are not
+    bridges); ``n_rot`` rotatable bonds are drawn among the bridges whose two atoms both have degree
+    >= 2 (the ring-ring link included) and capped at their number."""
+    if rings not in ("single", "fused", "linked"):
+        raise ValueError("rings must be single, fused or linked")
+    rng = np.random.default_rng([seed, 0x21C])
+    n_ring = 6 if rings == "single" else (10 if rings == "fused" else 12)
+    if n_atoms < n_ring:
+        raise ValueError(f"a {rings} ring scaffold needs at least {n_ring} atoms")
+    for _attempt in range(1000):
+        u = _unit(rng.normal(size=3))
+        v = _perp(u)
+        ang = np.arange(6) * (math.pi / 3.0)
+        hexagon = lambda c, a0: c + RING_BOND * (np.cos(ang + a0)[:, None] * u + np.sin(ang + a0)[:, None] * v)  # noqa: E731
+        xyz = [*hexagon(np.zeros(3), 0.0)]
+        bonds: List[Tuple[int, int]] = [(k, (k + 1) % 6) for k in range(6)]
+        ring_bonds = set(range(6))
+        if rings == "fused":
+            # the second hexagon shares atoms 0 and 1; its centre is the first's reflected across them
+            c2 = xyz[0] + xyz[1]
+            second = hexagon(c2, math.pi)            # vertex k = c2 - (vertex k of the first ring)
+            # so second[0] is atom 1 and second[1] is atom 0; add the four others
+            idx = {0: 1, 1: 0}
+            for k in (2, 3, 4, 5):
+                idx[k] = len(xyz)
+                xyz.append(second[k])
+            for k in range(6):
+                a, b = idx[k], idx[(k + 1) % 6]
+                if {a, b} != {0, 1}:
+                    ring_bonds.add(len(bonds))
+                    bonds.append((a, b))
+        elif rings == "linked":
+            out = _unit(xyz[3])                        # radial direction of atom 3
+            c2 = xyz[3] + (BOND_LENGTH + RING_BOND) * out
+            second = hexagon(c2, 0.0)                  # its vertex 0 faces atom 3
+            base = len(xyz)
+            xyz.extend(second)
+            for k in range(6):
+                ring_bonds.add(len(bonds))
+                bonds.append((base + k, base + (k + 1) % 6))
+            bonds.append((3, base))                    # the link: a bridge
+        xyz = np.array(xyz)
+        n0 = len(xyz)
+        element = np.zeros(n_atoms, np.uint8)
+        element[:n0] = np.where(rng.random(n0) < 0.15, ELEM_N, ELEM_C)
+        element[0] = ELEM_C
+        element[n0:] = rng.choice(3, size=n_atoms - n0, p=LIGAND_ELEMENT_P)
+        nbrs: List[List[int]] = [[] for _ in range(n_atoms)]
+        for a, b in bonds:
+            nbrs[a].append(b)
+            nbrs[b].append(a)
+        in_ring = np.zeros(n_atoms, bool)
+        for bi in ring_bonds:
+            in_ring[list(bonds[bi])] = True
+        xyz = np.concatenate([xyz, np.zeros((n_atoms - n0, 3))])
+        ok = True
+        for k in range(n0, n_atoms):
+            placed = False
+            for _try in range(200):
+                free = [a for a in range(k) if len(nbrs[a]) < (3 if in_ring[a] else MAX_VALENCE[int(element[a])])]
+                if not free:
+                    break
+                p = int(rng.choice(free))
+                if in_ring[p]:
+                    w = -sum(_unit(xyz[q] - xyz[p]) for q in nbrs[p] if in_ring[q])
+                    pos = xyz[p] + BOND_LENGTH * _unit(w)
+                elif not nbrs[p]:
+                    pos = xyz[p] + BOND_LENGTH * _unit(rng.normal(size=3))
+                else:
+                    g = nbrs[p][0]
+                    uu = _unit(xyz[g] - xyz[p])
+                    ww = _perp(uu)
+                    phi = rng.uniform(-math.pi, math.pi)
+                    ww = ww * math.cos(phi) + np.cross(uu, ww) * math.sin(phi)
+                    pos = xyz[p] + BOND_LENGTH * (math.cos(BOND_ANGLE) * uu + math.sin(BOND_ANGLE) * ww)
+                dist_p = _graph_dist(nbrs[:k] + [[]], p)[:k]
+                d = np.linalg.norm(xyz[:k] - pos, axis=1)
+                if (d[dist_p == 1] < 2.3).any() or (d[dist_p >= 2] < 2.5).any():
+                    continue
+                xyz[k] = pos
+                nbrs[p].append(k)
+                nbrs[k].append(p)
+                bonds.append((p, k))
+                placed = True
+                break
+            if not placed:
+                ok = False
+                break
+        if not ok:
+            continue
+        deg = np.array([len(x) for x in nbrs])
+        cand = [i for i, (a, b) in enumerate(bonds) if i not in ring_bonds and deg[a] >= 2 and deg[b] >= 2]
+        k_rot = min(n_rot, len(cand))
+        rot = np.zeros(len(bonds), dtype=np.uint8)
+        if k_rot:
+            rot[rng.choice(cand, size=k_rot, replace=False)] = 1
+        donor, acceptor = _hbond_flags(rng, element)
+        return Ligand(xyz, element, donor, acceptor, np.array(bonds, dtype=np.int32).reshape(-1, 2), rot)
+    raise RuntimeError("ring ligand growth failed")
 
 
 def ligand_centered(lig: Ligand) -> Ligand:

@@ -156,3 +156,41 @@ def check_rescored(r, q, L, rec, rec_types, base=None):
         for p in poses[:n]:
             b = by_chain[int(p["chain"])]
             assert p["score_grid"] == b["score"] and p["e_inter_grid"] == b["e_inter"]
+
+
+def oracle_chains_perturbed(L, grid, box, params, unit, n_chains, noise, seed):
+    """The oracle's Monte-Carlo chains (its random start, mutation, RILC-BFGS, Metropolis test and
+    refinement, step for step as oracle.mc_chains runs them) with every score evaluation's energy
+    and gradient multiplied by (1 + noise * N(0, 1)) draws: how far FP64 runs part ways with the
+    oracle under perturbations of the size of FP32 rounding. With noise = 0 it reproduces
+    mc_chains exactly. Returns the chains' best SF and their score evaluation counts."""
+    rng = np.random.default_rng(seed)
+
+    def fg(x):
+        e, g, _ = L.score(grid, x, True)
+        return e * (1 + noise * rng.standard_normal()), g * (1 + noise * rng.standard_normal(g.shape))
+
+    def bfgs(x):
+        xo, f, _, ev = O.bfgs_generic(fg, L.retract, x, 6 + L.n_rot, params)
+        return xo, f, ev
+
+    out = np.zeros(n_chains)
+    evals = np.zeros(n_chains, np.int64)
+    for c in range(n_chains):
+        cur = O.random_conformation(L, box, params.seed, unit, c)
+        e_cur = fg(cur)[0]
+        e_best = e_cur
+        n_ev = 1
+        for st in range(params.steps):
+            cand, e_new, k = bfgs(O.mutate(L, cur, params.amplitude, params.seed, unit, c, st))
+            n_ev += k
+            u = O.metropolis_uniform(params.seed, unit, c, st)
+            if O.metropolis_accept(e_cur, e_new, params.temperature, u):
+                cur, e_cur = cand, e_new
+                if e_cur < e_best:
+                    cur, e_cur, k = bfgs(cur)
+                    n_ev += k
+                    e_best = e_cur
+        out[c] = e_best
+        evals[c] = n_ev
+    return out, evals

@@ -52,3 +52,38 @@ def test_pocket_parameter_defaults_agree():
     for f in dataclasses.fields(q):
         assert getattr(p, f.name) == pytest.approx(getattr(q, f.name)), f.name
     assert lib.pv_pocket_params_default(None) == _capi.PV_ERR_ARG
+
+
+def test_dock_params_layout_and_defaults_agree(tmp_path):
+    """The binding's pv_dock_params has the C struct's size and field offsets (compiled with the
+    host compiler from the header), and its defaults are the library's (host-only call)."""
+    import dataclasses
+    import shutil
+    import subprocess
+    from paper_2506_20043_gb300 import _capi, api
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    fields = [f[0] for f in _capi.pv_dock_params._fields_]
+    prog = tmp_path / "layout.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "pocketvina.h"\nint main(void) {\n'
+                    '  printf("%zu\\n", sizeof(pv_dock_params));\n' +
+                    "".join(f'  printf("%zu\\n", offsetof(pv_dock_params, {f}));\n' for f in fields) +
+                    "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got[0] == ctypes.sizeof(_capi.pv_dock_params)
+    assert got[1:] == [getattr(_capi.pv_dock_params, f).offset for f in fields]
+    lib = _capi.load()
+    p = _capi.pv_dock_params()
+    lib.pv_dock_params_default(ctypes.byref(p))
+    q = api.DockParams()
+    for f in dataclasses.fields(q):
+        if f.name == "pair_keys":
+            assert not p.pair_keys and q.pair_keys is None
+            continue
+        v = getattr(q, f.name)
+        if f.name == "mode":
+            v = _capi.PV_MODE_BATCHED
+        assert getattr(p, f.name) == pytest.approx(float(v)), f.name

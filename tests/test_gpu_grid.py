@@ -104,3 +104,22 @@ def test_grid_argument_errors():
     gs = ctx.build_grids(w.receptors[0], [S.Box(np.zeros(3), np.array([4.0, 4.0, 4.0]), 0.375)], [0])
     with pytest.raises(PVError):
         gs.read_map(0, 3)
+
+
+def test_pinned_host_receptor_is_uploaded_before_return():
+    """A receptor in page-locked host memory: the call returns only after its upload, so the caller
+    may overwrite the arrays at once (here before any synchronisation) without changing the maps."""
+    torch = pytest.importorskip("torch")
+    ctx = G.context()
+    rec = G.receptor32(S.tiny().receptors[0])
+    box = [S.Box(np.array([1.0, -2.0, 0.5]), np.array([9.0, 9.0, 9.0]), 0.375)]
+    ref = ctx.build_grids(rec, box, [0, 6, 9])
+    pin = [torch.tensor(np.asarray(rec.xyz, np.float32)).pin_memory()] + \
+          [torch.tensor(np.asarray(a, np.uint8)).pin_memory() for a in (rec.element, rec.donor, rec.acceptor)]
+    for _ in range(3):
+        fresh = [t.clone().pin_memory() for t in pin]
+        gs = ctx.build_grids(S.Receptor(*fresh), box, [0, 6, 9])
+        fresh[0].fill_(0.0)
+        fresh[1].fill_(3)
+        for t in (0, 6, 9):
+            np.testing.assert_array_equal(gs.read_map(0, t), ref.read_map(0, t))

@@ -284,3 +284,19 @@ def test_autograd_over_coordinates_vs_fd():
         assert (np.abs(got[i] - fd) <= G.GRAD_TOL * np.maximum(np.abs(fd), 1.0)).all(), (i, np.abs(got[i] - fd).max())
         checked += 1
     assert checked >= 16
+
+
+@pytest.mark.parametrize("rings", ["single", "fused", "linked"])
+def test_ring_ligands_score_and_gradient_match_oracle(rings):
+    """Ligands with rigid six-membered rings (one, two fused, two linked by a rotatable bond): SF,
+    parts and tangent gradient of 1,000 random poses against the oracle."""
+    ctx = G.context()
+    rec, box, _ = _site(n_rec=4000, box_size=12.0)
+    lig = G.ligand32(S.ligand_centered(S.make_ring_ligand(28, 6, 7, rings)))
+    poses = S.random_poses(1000, box, int(lig.rotatable.sum()), seed=2)
+    e, g, parts, er, gr, pr, xyz, *_ = _run(ctx, rec, box, lig, poses, lazy=False)
+    assert G.close(e, er).all(), np.abs(e - er).max()
+    assert G.close(parts, pr).all()
+    ok = np.abs(g - gr) <= G.GRAD_TOL * np.maximum(np.abs(gr), 1.0)
+    bad = ~ok.all(axis=1) & ~_near_face(xyz, box)
+    assert bad.sum() == 0, (np.argwhere(bad)[:5], np.abs(g - gr).max())

@@ -73,7 +73,22 @@ CASES = [(n, r, s) for s, (n, r) in enumerate([(5, 0), (8, 2), (12, 3), (16, 4),
 @pytest.mark.parametrize("n_atoms,n_rot,seed", CASES + [(int(n), int(r), 100 + i) for i, (n, r) in enumerate(
     zip(np.random.default_rng(4).integers(6, 33, 24), np.random.default_rng(5).integers(0, 11, 24)))])
 def test_schedules_hold_every_oracle_pair_once(lib, n_atoms, n_rot, seed):
-    lig = S.ligand_centered(S.make_ligand(n_atoms, n_rot, seed))
+    _check_schedules(lib, S.ligand_centered(S.make_ligand(n_atoms, n_rot, seed)), n_atoms)
+
+
+RING_CASES = [(n, r, s, k) for s, (n, r, k) in enumerate([(8, 1, "single"), (16, 3, "single"), (30, 6, "single"),
+                                                          (12, 1, "fused"), (24, 4, "fused"), (40, 8, "fused"),
+                                                          (14, 2, "linked"), (30, 6, "linked"), (60, 12, "linked")])]
+
+
+@pytest.mark.parametrize("n_atoms,n_rot,seed,rings", RING_CASES)
+def test_schedules_of_ring_ligands(lib, n_atoms, n_rot, seed, rings):
+    """Ligands with rigid rings: pairs inside a ring are excluded (one rigid fragment), and the
+    'more than three bonds apart' rule counts bonds along the shorter way round a ring."""
+    _check_schedules(lib, S.ligand_centered(S.make_ring_ligand(n_atoms, n_rot, seed, rings)), n_atoms)
+
+
+def _check_schedules(lib, lig, n_atoms):
     L = O.OracleLigand(lig)
     ref = {(min(int(a), int(b)), max(int(a), int(b))) for a, b in L.pairs}
     assert len(ref) == L.n_pairs

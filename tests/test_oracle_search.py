@@ -186,3 +186,19 @@ def test_merge_orders_by_score_then_pocket_then_chain():
     r0 = O.PairResult(0, 0, None, None, 0, np.array([4, 1]), np.array([-7.0, -5.0]), None, None, None)
     r1 = O.PairResult(0, 1, None, None, 0, np.array([0, 2]), np.array([-7.0, -8.0]), None, None, None)
     assert O.merge_pockets([r1, r0]) == [(-8.0, 1, 2), (-7.0, 0, 4), (-7.0, 1, 0), (-5.0, 0, 1)]
+
+
+def test_perturbed_chain_replay_reproduces_the_oracle_without_noise():
+    """The GPU tests' perturbed replay of the oracle's chains (tests/_gpu.py) follows mc_chains step
+    for step: with no noise it gives the same best SF on every chain (an empty box: zero maps)."""
+    from tests import _gpu as G
+    lig = S.ligand_centered(S.make_ligand(14, 3, 5))
+    L = O.OracleLigand(lig)
+    box = S.Box(np.array([100.0, 0.0, 0.0]), np.array([16.0, 16.0, 16.0]), 0.375)
+    types = sorted(set(L.xs.tolist()))
+    og = O.OracleGrid(None, box, types, maps=np.zeros((len(types), int(np.prod(O.grid_geometry(box)[1])))))
+    p = O.SearchParams(seed=4, steps=3, max_iter=6)
+    _, ref, ref_ev = O.mc_chains(L, og, box, p, unit=2, n_chains=12)
+    got, ev = G.oracle_chains_perturbed(L, og, box, p, 2, 12, 0.0, 1)
+    np.testing.assert_array_equal(got, ref)
+    np.testing.assert_array_equal(ev, ref_ev)

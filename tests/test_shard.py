@@ -29,6 +29,26 @@ def test_plan_covers_every_pair_once(world, n_pockets, n_ligs):
         assert all(len(v) == 1 for v in owners.values())
 
 
+@pytest.mark.parametrize("world,n_pockets,n_ligs", [(1, 10, 1), (2, 10, 1), (4, 10, 4), (8, 10, 8), (3, 5, 3),
+                                                    (8, 2, 3)])
+def test_pair_plan_is_balanced_and_keeps_pair_keys(world, n_pockets, n_ligs):
+    pockets = list(range(50, 50 + n_pockets))
+    plan = shard.plan_pairs(pockets, n_ligs, world)
+    assert len(plan) == world
+    flat = [p for part in plan for p in part]
+    # every pair once, with the key it has in one unsplit dock (ligand * n_pockets + position)
+    assert sorted(flat) == sorted((l, pockets[k], l * n_pockets + k) for l in range(n_ligs) for k in range(n_pockets))
+    sizes = [len(part) for part in plan]
+    assert max(sizes) - min(sizes) <= 1
+    # runs are contiguous in pocket-major order, so a pocket spans consecutive ranks only
+    owners = {}
+    for r, part in enumerate(plan):
+        for _, p, _ in part:
+            owners.setdefault(p, set()).add(r)
+    for rs in owners.values():
+        assert sorted(rs) == list(range(min(rs), max(rs) + 1))
+
+
 def test_merge_orders_by_score_pocket_chain():
     a = {0: [(-7.0, 3, 1), (-5.0, 3, 4)], 1: [(-2.0, 0, 0)]}
     b = {0: [(-7.0, 1, 9), (-8.0, 2, 2)]}

@@ -3,7 +3,8 @@
 It serves callers that cannot allocate device memory when they need a grid. Its maps must equal
 those of the allocating pv_build_grids within the grid tolerance, on two calls in a row (the
 second with a different receptor, box and type set, so anything the first call left in the
-shared scratch array would show). Named to be collected last.
+shared scratch array would show), and the FP64 oracle's direct sums at sampled nodes; the
+receptor may be host or device memory. Named to be collected last.
 """
 import ctypes as C
 
@@ -50,6 +51,37 @@ def test_noalloc_maps_match_pv_build_grids_on_two_calls():
         for m, t in enumerate(sorted(types)):
             ref = ref_set.read_map(0, t)
             assert G.close(got[m], ref).all(), (t, np.abs(got[m] - ref).max())
+        # the oracle's direct sum over every receptor atom at sampled nodes of every map
+        rt = O.xs_type_receptor(rec)
+        idx = np.random.default_rng(5).integers(0, dims, size=(60, 3))
+        for m, t in enumerate(sorted(types)):
+            ref = np.array([O.grid_node_value(rec, rt, box, t, *i) for i in idx])
+            assert G.close(got[m][idx[:, 2], idx[:, 1], idx[:, 0]], ref).all(), t
+
+
+def test_noalloc_device_resident_receptor():
+    """The receptor given as device arrays (PV_MEM_DEVICE: read in place, nothing uploaded into
+    the scratch array): the same maps as from host arrays, twice in a row."""
+    torch = pytest.importorskip("torch")
+    from paper_2506_20043_gb300 import _capi as A
+    ctx = G.context()
+    rec = G.receptor32(S.make_receptor(2500, 11, [(np.array([1.0, 2.0, -1.0]), 7.0)]))
+    box = G.box32(S.Box(np.array([1.0, 2.0, -1.0]), np.array([16.0, 16.0, 16.0]), 0.375))
+    types = [0, 2, 6, 9]
+    drec = S.Receptor(torch.tensor(rec.xyz, dtype=torch.float32, device="cuda"),
+                      torch.tensor(rec.element, device="cuda"), torch.tensor(rec.donor, device="cuda"),
+                      torch.tensor(rec.acceptor, device="cuda"))
+    _, dims = O.grid_geometry(box)
+    nxyz = int(np.prod(dims))
+    outs = []
+    for r in (rec, drec, rec):
+        out = torch.full((len(types), nxyz), float("nan"), dtype=torch.float32, device="cuda")
+        st, msg = _call_noalloc(ctx, r, box, types, out)
+        assert st == A.PV_OK, msg
+        torch.cuda.synchronize()
+        outs.append(out.cpu().numpy())
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
@@ -63,3 +95,7 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     rec = S.make_receptor(1000, 4)
     st, msg = _call_noalloc(ctx, rec, S.Box(np.zeros(3), np.array([120.0] * 3), 1.0), [0], out)
     assert st == A.PV_ERR_ARG and "scratch" in msg
+    # a non-finite centre or size is refused before any size is derived from it
+    for c, sz in (((np.nan, 0.0, 0.0), 10.0), ((0.0, np.inf, 0.0), 10.0), ((0.0, 0.0, 0.0), np.nan)):
+        st, msg = _call_noalloc(ctx, rec, S.Box(np.array(c), np.array([sz] * 3), 0.375), [0], out)
+        assert st == A.PV_ERR_ARG and "finite" in msg
