@@ -114,8 +114,8 @@ def workload(seed: int):
 # Sources of what the multi-pocket bench launches (grid build, search, top-k, merge) and of the
 # host code that shapes those launches; the stored profiles are valid while these are unchanged.
 DOCK_SOURCES = ("pv_api.cu", "pv_chain.cuh", "pv_device.cuh", "pv_grid.cu", "pv_internal.h",
-                "pv_layout.h", "pv_ligand.cpp", "pv_ligand.h", "pv_search.cu", "pv_stage.cuh",
-                "pv_thread.cuh", "pv_warp.cuh")
+                "pv_layout.h", "pv_ligand.cpp", "pv_ligand.h", "pv_search.cu", "pv_search_packed.cu",
+                "pv_stage.cuh", "pv_terms.h", "pv_thread.cuh", "pv_warp.cuh")
 
 
 def kernel_source_hash() -> str:
@@ -189,7 +189,8 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def step(mid=None):
-        gs = ctx.build_grids(dev_rec, my_boxes, types)
+        # the maps in both layouts: the autotuner picks the one the search reads
+        gs = ctx.build_grids(dev_rec, my_boxes, types).pack()
         if mid is not None:
             mid.record(stream)
         if world == 1:
@@ -230,6 +231,7 @@ def run_ours(args):
             assert (st == 0).all(), st
             s_s, n_l, _ = r.timing()
             shape = r.launch_shape()
+            layout = r.map_layout()
             search_s += s_s
             launches += n_l
             evals += ev
@@ -260,7 +262,10 @@ def run_ours(args):
         launch_traffic = prof.get("traffic")
         evals_per_launch = evals / max(launches, 1)
         n_rounds = launches // max(args.steps, 1)
-        _, _, gather_gbs = ctx.measure_gather(gs, -1, n_points=1 << 24, reps=10)   # the pockets' map set
+        # the gather alone over the pockets' map set, in both layouts; the search's gathers are
+        # compared with the higher of the two ceilings
+        gather = {lay: ctx.measure_gather(gs, -1, n_points=1 << 24, reps=10, layout=lay)[2] for lay in (0, 1)}
+        gather_gbs = max(gather.values())
         search_gather_gbs = evals * gbytes / search_s / 1e9
         # the map build (Grid_cache): (node, receptor atom within 8 A, type) term evaluations
         terms = grid_term_count(torch, rec.xyz, my_boxes, len(types))
@@ -278,7 +283,8 @@ def run_ours(args):
                                        f"{world} GPUs: {world} ligands x 10 pockets split into equal pocket-major "
                                        "runs of pairs (job-wide pair keys), ranked poses gathered and merged on "
                                        "rank 0 inside the timed step"),
-                       "search_launch": {"variant": shape[0], "warps_per_cta": shape[1], "chains_per_warp": 2 if shape[0] >= 4 else 1},
+                       "search_launch": {"variant": shape[0], "warps_per_cta": shape[1], "chains_per_warp": 2 if shape[0] >= 4 else 1,
+                                         "map_layout": "cell-packed" if layout == 1 else "plain"},
                        "focc": args.focc},
             "best_sf_per_pocket": {"mean": round(float(best_sf.mean()), 4), "min": round(float(best_sf.min()), 4)},
             "top_pose": {str(l): list(v[0]) for l, v in sorted(merged.items())} if merged else None,
@@ -296,6 +302,7 @@ def run_ours(args):
                          "launch_ms": round(search_s / max(launches, 1) * 1e3, 3),
                          "l2_gather_gbs": round(search_gather_gbs, 1),
                          "gather_ceiling_gbs": round(gather_gbs, 1),
+                         "gather_ceiling_by_layout_gbs": {"plain": round(gather[0], 1), "cell_packed": round(gather[1], 1)},
                          "gather_frac": round(search_gather_gbs / gather_gbs, 4),
                          "issue": ({"warp_inst_per_eval": prof["inst"],
                                     "achieved_ginst_s": round(evals / search_s * prof["inst"] / 1e9, 1),
@@ -314,7 +321,7 @@ def run_ours(args):
             "clocks": clocks,
         }
         if not args.no_plain:
-            out["plain"] = run_plain(ctx, api, gs, lig, list(range(len(my_boxes))), shape)
+            out["plain"] = run_plain(ctx, api, gs, lig, list(range(len(my_boxes))), (shape[0], shape[1], layout))
             out["batched_vs_plain"] = round(value / world / out["plain"]["thread_per_chain"]["value"], 2)
             out["batched_vs_plain_warp"] = round(value / world / out["plain"]["warp_per_chain"]["value"], 2)
         if not args.no_micro:
@@ -338,7 +345,8 @@ def run_plain(ctx, api, gs, lig, pockets, shape):
     no graph), so that the second ratio isolates what batching itself adds."""
     out = {"sample": f"1 pocket x {CHAINS} chains x {STEPS} MC steps, one launch per pair, timed in full"}
     for name, kw in (("thread_per_chain", dict(mode="plain")),
-                     ("warp_per_chain", dict(mode="plain_warp", search_variant=shape[0], warps_per_cta=shape[1]))):
+                     ("warp_per_chain", dict(mode="plain_warp", search_variant=shape[0], warps_per_cta=shape[1],
+                                             map_layout=shape[2]))):
         r = ctx.dock(gs, [lig], [pockets[0]], chains=CHAINS, steps=STEPS, seed=0, host_copy=False, **kw)
         ev, _, st = r.stats()
         assert (st == 0).all(), st
@@ -426,7 +434,7 @@ def run_e2e(ctx, api, torch, rec, boxes, lig_src, types, pockets, steps, seed):
     d2h = 0
     t0 = time.perf_counter()
     for _ in range(steps):
-        gs = ctx.build_grids(host_rec, boxes, types)
+        gs = ctx.build_grids(host_rec, boxes, types).pack()
         lig = ctx.ligand(lig_src)
         r = ctx.dock(gs, [lig], pockets, chains=CHAINS, steps=STEPS, seed=seed, top_k=TOP_K, host_copy=True)
         poses, kept, pots, xyz = r.fetch()
@@ -841,15 +849,20 @@ def run_small_case(args):
     rec, boxes, lig_src = workload(seed=0)
     lig = ctx.ligand(lig_src)
     gs = ctx.build_grids(rec, boxes, sorted(set(lig.xs_types.tolist())))
+    if args.layout == 1:
+        gs.pack()
     r = ctx.dock(gs, [lig], list(range(len(boxes))), chains=CHAINS, steps=args.small_steps, seed=0, host_copy=False,
-                 search_variant=args.variant, warps_per_cta=args.warps, steps_per_round=args.small_steps)
+                 search_variant=args.variant, warps_per_cta=args.warps, steps_per_round=args.small_steps,
+                 map_layout=args.layout)
     ev, sec, st = r.stats()
     mrec, mbox, mlig_src, mposes = S.score_microbench()
     mlig = ctx.ligand(mlig_src)
     mgs = ctx.build_grids(mrec, [mbox], sorted(set(mlig.xs_types.tolist())))
     ctx.score(mgs, mlig, 0, torch.tensor(mposes, dtype=torch.float32, device="cuda"))
     torch.cuda.synchronize()
-    return {"case": "small", "evals": int(ev), "seconds": round(sec, 4), "launch": r.launch_shape(),
+    s_s, _, _ = r.timing()
+    return {"case": "small", "evals": int(ev), "seconds": round(sec, 4), "search_seconds": round(s_s, 5),
+            "evals_per_s": round(ev / s_s, 1), "launch": r.launch_shape(), "layout": r.map_layout(),
             "status_ok": bool((st == 0).all())}
 
 
@@ -874,6 +887,7 @@ def main():
     ap.add_argument("--variant", type=int, default=0, help="search kernel variant of --case small")
     ap.add_argument("--warps", type=int, default=2, help="warps per CTA of --case small")
     ap.add_argument("--small-steps", type=int, default=20, help="MC steps of --case small (one launch)")
+    ap.add_argument("--layout", type=int, default=0, choices=[0, 1], help="map layout of --case small (1: cell-packed)")
     args = ap.parse_args()
     if args.case == "small":
         out = run_small_case(args)

@@ -123,6 +123,13 @@ void pv_grid_set_destroy(pv_grid_set* set);
 /* Number of pockets and total map bytes. */
 pv_status pv_grid_set_info(const pv_grid_set* set, int32_t* n_pockets, int64_t* bytes);
 
+/* Adds a cell-packed copy of every map of the set (and of every pocket appended later): each grid
+ * cell's eight corner values stored together (32 bytes, two 16-byte loads from one memory sector)
+ * instead of eight scalar loads from at least four sectors, for 8x the map memory. Lookups in
+ * either layout interpolate the same values with the same arithmetic, so results do not depend on
+ * which one a dock reads (pv_dock_params.map_layout). Asynchronous. PV_ERR_OOM, PV_ERR_CUDA. */
+pv_status pv_grid_set_pack(pv_context* ctx, pv_grid_set* set);
+
 /* Device time of the map-build kernel launches (Grid_cache, "Kernel 1") of the calls that built
  * this set (pv_build_grids and every pv_grid_set_append), measured with events around each
  * launch on the context's stream; waits for the last of them. Typing and binning are not
@@ -217,6 +224,10 @@ pv_status pv_pose_coords(pv_context* ctx, const pv_ligand* lig, int32_t n_poses,
  * PV_ERR_ARG for a bad pocket, n_points < 1, reps < 1 or a null output. Synchronous. */
 pv_status pv_measure_gather(pv_context* ctx, const pv_grid_set* set, int32_t pocket, int64_t n_points,
                             int32_t reps, float* ms_per_launch);
+/* The same in a given map layout: 0 plain, 1 cell-packed (PV_ERR_ARG if the set holds no packed
+ * copy, see pv_grid_set_pack). pv_measure_gather measures layout 0. */
+pv_status pv_measure_gather_layout(pv_context* ctx, const pv_grid_set* set, int32_t pocket, int64_t n_points,
+                                   int32_t reps, int32_t layout, float* ms_per_launch);
 
 /* ------------------------------------------------------------------------- docking --- */
 
@@ -282,15 +293,22 @@ typedef struct {
                                   index. A job split over several calls (one per GPU) passes each
                                   pair's index in the whole job, so that every chain draws the
                                   same numbers as in one unsplit call */
+    int32_t map_layout;        /* maps the search reads: 0 plain, 1 cell-packed (the set must hold
+                                  them, pv_grid_set_pack), -1 = the autotuner picks between them
+                                  when the set holds both, else plain. Results are the same */
 } pv_dock_params;
 
 /* Defaults: chains 64, steps 1000, seed 0, top_k 9, rmsd_min 1.0, BATCHED, m 5, max_iter 0,
  * max_trials 10, eps 1e-3, rho 1e-4, sigma 0.1, temperature 1.2, amplitude 2.0,
  * steps_per_round 0, use_graph 1, warps_per_cta 0, search_variant -1, host_copy 1, timeout_s 0,
- * focc 0, focc_min_delta 1e-4, rescore 0, max_pockets 0, block_wait_s 30, pair_keys NULL.
- * Autotuning (warps_per_cta 0 or search_variant -1): the first batched dock of a ligand-size
- * bucket on a context times each candidate launch shape on 32 MC steps of its own work items
- * (results are unaffected: the dock itself restarts every chain) and keeps the fastest. */
+ * focc 0, focc_min_delta 1e-4, rescore 0, max_pockets 0, block_wait_s 30, pair_keys NULL,
+ * map_layout -1.
+ * Autotuning (warps_per_cta 0, search_variant -1, or map_layout -1 on a set holding both layouts):
+ * the first batched dock of a ligand-size bucket on a context times each candidate launch shape on
+ * 32 MC steps of its own work items, the fastest of three runs (results are unaffected: the dock
+ * itself restarts every chain); a candidate displaces the first one tried only when it is faster
+ * by more than 2 %, so that shapes within the trials' noise do not alternate between runs. The
+ * chosen shape is then timed on the cell-packed maps too, with the same margin. */
 void pv_dock_params_default(pv_dock_params* p);
 
 /* Docks every ligand into every listed pocket (Supplementary Algorithms 2 and 3). Pair
@@ -350,6 +368,9 @@ pv_status pv_dock_result_stats(const pv_dock_result* r, uint64_t* n_evals, doubl
  * kernels), their count, and the whole launch sequence (search + selection + merge). */
 pv_status pv_dock_result_timing(const pv_dock_result* r, double* search_seconds,
                                 int32_t* search_launches, double* total_seconds);
+
+/* Map layout the search read (0 plain, 1 cell-packed). */
+pv_status pv_dock_result_map_layout(const pv_dock_result* r, int32_t* map_layout);
 
 /* Launch shape the batched search used (after autotuning): register variant and chains per CTA. */
 pv_status pv_dock_result_launch(const pv_dock_result* r, int32_t* search_variant, int32_t* warps_per_cta);

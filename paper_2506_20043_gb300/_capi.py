@@ -40,7 +40,7 @@ class pv_dock_params(C.Structure):
                 ("host_copy", C.c_int32),
                 ("timeout_s", C.c_double), ("focc", C.c_int32), ("focc_min_delta", C.c_float),
                 ("rescore", C.c_int32), ("max_pockets", C.c_int32), ("block_wait_s", C.c_double),
-                ("pair_keys", C.POINTER(C.c_int32))]
+                ("pair_keys", C.POINTER(C.c_int32)), ("map_layout", C.c_int32)]
 
 
 class pv_pose(C.Structure):
@@ -75,6 +75,7 @@ SIGNATURES = {
     "pv_grid_set_destroy": (None, [vp]),
     "pv_grid_set_info": (i32, [vp, pi32, C.POINTER(i64)]),
     "pv_grid_set_build_seconds": (i32, [vp, C.POINTER(C.c_double)]),
+    "pv_grid_set_pack": (i32, [vp, vp]),
     "pv_grid_set_view": (i32, [vp, i32, i32, C.POINTER(vp), pi32, pf32, pf32]),
     "pv_grid_set_read_map": (i32, [vp, i32, i32, vp]),
     "pv_ligand_create": (i32, [vp, C.POINTER(pv_ligand_desc), C.POINTER(vp)]),
@@ -87,6 +88,7 @@ SIGNATURES = {
     "pv_pose_coords": (i32, [vp, vp, i32, vp, vp]),
     "pv_score_xyz": (i32, [vp, vp, vp, i32, i32, vp, vp, vp, vp]),
     "pv_measure_gather": (i32, [vp, vp, i32, i64, i32, vp]),
+    "pv_measure_gather_layout": (i32, [vp, vp, i32, i64, i32, i32, vp]),
     "pv_dock_params_default": (None, [C.POINTER(pv_dock_params)]),
     "pv_check_bfgs": (i32, [vp, i32, i32, i32, i32, vp, vp, C.POINTER(pv_dock_params), vp, vp]),
     "pv_dock": (i32, [vp, vp, C.POINTER(vp), i32, pi32, i32, C.POINTER(pv_dock_params), C.POINTER(vp)]),
@@ -98,6 +100,7 @@ SIGNATURES = {
     "pv_dock_result_stats": (i32, [vp, C.POINTER(u64), C.POINTER(C.c_double), pi32]),
     "pv_dock_result_timing": (i32, [vp, C.POINTER(C.c_double), pi32, C.POINTER(C.c_double)]),
     "pv_dock_result_launch": (i32, [vp, pi32, pi32]),
+    "pv_dock_result_map_layout": (i32, [vp, pi32]),
     "pv_dock_result_device": (i32, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),
     "pv_dock_result_chains": (i32, [vp, C.POINTER(vp), pi32, pi32, pi32, pi32]),
     "pv_dock_result_read_chains": (i32, [vp, vp]),

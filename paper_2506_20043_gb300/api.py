@@ -60,6 +60,7 @@ class DockParams:
     max_pockets: int = 0           # > 0: each ligand docked into its first max_pockets pockets only
     block_wait_s: float = 30.0     # bound on a step block's wait for its predecessor
     pair_keys: Optional[Sequence[int]] = None   # per pair: its random stream (default: pair index)
+    map_layout: int = -1           # 0 plain, 1 cell-packed, -1 autotuned when the set holds both
 
     def to_c(self) -> A.pv_dock_params:
         p = A.pv_dock_params()
@@ -352,13 +353,14 @@ class Context:
                     "pv_pose_coords")
         return out
 
-    def measure_gather(self, grids: "GridSet", pocket: int = 0, n_points: int = 1 << 24, reps: int = 10):
+    def measure_gather(self, grids: "GridSet", pocket: int = 0, n_points: int = 1 << 24, reps: int = 10,
+                       layout: int = 0):
         """The trilinear gather alone (value + gradient at hashed positions in the pocket's box;
-        pocket -1: over every pocket of the set): returns (milliseconds per launch, points per
-        second, algorithmic GB/s at 32 B per point)."""
+        pocket -1: over every pocket of the set) in a map layout (0 plain, 1 cell-packed): returns
+        (milliseconds per launch, points per second, algorithmic GB/s at 32 B per point)."""
         ms = C.c_float()
-        self._check(self.lib.pv_measure_gather(self.h, grids.h, int(pocket), int(n_points), int(reps), C.byref(ms)),
-                    "pv_measure_gather")
+        self._check(self.lib.pv_measure_gather_layout(self.h, grids.h, int(pocket), int(n_points), int(reps),
+                                                      int(layout), C.byref(ms)), "pv_measure_gather_layout")
         t = ms.value * 1e-3
         return ms.value, n_points / t, 32.0 * n_points / t / 1e9
 
@@ -441,6 +443,11 @@ class GridSet:
         if st != A.PV_OK:
             raise PVError("pv_grid_set_view: no such map")
         return np.array(list(dims)), np.array(list(org), dtype=np.float64), sp.value, p.value
+
+    def pack(self) -> "GridSet":
+        """Adds the cell-packed copy of every map (pv_grid_set_pack)."""
+        self.ctx._check(self.ctx.lib.pv_grid_set_pack(self.ctx.h, self.h), "pv_grid_set_pack")
+        return self
 
     def build_seconds(self) -> float:
         """Device time of the map-build kernel launches that built this set."""
@@ -556,6 +563,12 @@ class DockResult:
         self.ctx._check(self.ctx.lib.pv_dock_result_timing(self.h, C.byref(s), C.byref(n), C.byref(t)),
                         "pv_dock_result_timing")
         return s.value, n.value, t.value
+
+    def map_layout(self) -> int:
+        """Map layout the search read: 0 plain, 1 cell-packed."""
+        v = C.c_int32()
+        self.ctx._check(self.ctx.lib.pv_dock_result_map_layout(self.h, C.byref(v)), "pv_dock_result_map_layout")
+        return v.value
 
     def launch_shape(self):
         """(search kernel variant, warps per CTA) used by the batched search."""

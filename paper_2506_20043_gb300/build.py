@@ -13,8 +13,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libpocketvina.so")
-SOURCES = ["pv_api.cu", "pv_grid.cu", "pv_score.cu", "pv_search.cu", "pv_search_focc.cu", "pv_ligand.cpp", "pv_noalloc.cu", "pv_probe.cu", "pv_pocket.cu",
-           "pv_check.cu"]
+SOURCES = ["pv_api.cu", "pv_grid.cu", "pv_score.cu", "pv_search.cu", "pv_search_focc.cu", "pv_search_packed.cu",
+           "pv_search_focc_packed.cu", "pv_ligand.cpp", "pv_noalloc.cu", "pv_probe.cu", "pv_pocket.cu", "pv_check.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

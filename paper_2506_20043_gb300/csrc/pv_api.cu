@@ -34,7 +34,7 @@ struct pv_context {
                                              // be the legacy default stream, which cannot capture)
     // autotuned (search variant, warps per CTA) per (ligand atoms / 8, check on/off and team width;
     // pair rounds / 4 and the caller's fixed variant or CTA size)
-    std::map<std::pair<int, int>, std::pair<int, int>> tuned;
+    std::map<std::pair<int, int>, std::tuple<int, int, int>> tuned;   // -> (variant, warps, layout)
 };
 
 struct pv_grid_set {
@@ -47,6 +47,7 @@ struct pv_grid_set {
     std::vector<void*> arenas;
     int64_t bytes = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> map_events;   // around each map-build launch
+    bool packed = false;            // every pocket also holds its maps cell-packed (P.cells)
 };
 
 struct pv_ligand {
@@ -77,6 +78,7 @@ struct pv_dock_result {
     double search_seconds = 0.0;    // the search kernel launches alone (events around them)
     int search_launches = 0;
     int search_variant = 0, warps_per_cta = 0;   // launch shape used (batched)
+    int map_layout = 0;                          // map layout the search read
     int mode = PV_MODE_BATCHED;
 };
 
@@ -257,6 +259,7 @@ static pv_status add_receptor(pv_context* ctx, pv_grid_set* set, const pv_recept
         P.inv_spacing = 1.0f / b.spacing;
         P.nxy = P.dims[0] * P.dims[1];
         P.nxyz = P.nxy * P.dims[2];
+        P.ncells = (P.dims[0] - 1) * (P.dims[1] - 1) * (P.dims[2] - 1);
         map_floats += (size_t)P.nxyz * set->n_maps;
     }
     int cd[3];
@@ -288,6 +291,19 @@ static pv_status add_receptor(pv_context* ctx, pv_grid_set* set, const pv_recept
         off += (size_t)pk[p].nxyz * set->n_maps;
         pk[p].rec_atoms = typed;
         pk[p].rec_n = n;
+    }
+    if (set->packed) {   // the set keeps the cell-packed layout too: pack the new pockets as well
+        size_t cells = 0;
+        for (int p = 0; p < n_pockets; ++p) cells += (size_t)pk[p].ncells * set->n_maps;
+        float4* carena = (float4*)dalloc(ctx, cells * 2 * sizeof(float4));
+        if (!carena) return fail(ctx, PV_ERR_OOM, "packed map allocation failed");
+        set->arenas.push_back(carena);
+        set->bytes += (int64_t)(cells * 2 * sizeof(float4));
+        size_t co = 0;
+        for (int p = 0; p < n_pockets; ++p) {
+            pk[p].cells = carena + co;
+            co += (size_t)pk[p].ncells * set->n_maps * 2;
+        }
     }
     // pocket table (all pockets of the set)
     set->pockets.insert(set->pockets.end(), pk.begin(), pk.end());
@@ -347,6 +363,10 @@ static pv_status add_receptor(pv_context* ctx, pv_grid_set* set, const pv_recept
                                   (const int2*)(w + o_tiles), (int)tiles.size(), pack_slots(set->slot, 0),
                                   pack_slots(set->slot, 1), set->type_mask, ctx->stream);
         if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+    }
+    if (e == cudaSuccess && set->packed) {
+        stage = "map packing";
+        e = launch_pack_cells(d_p, set->pockets.data(), first, n_pockets, set->n_maps, ctx->stream);
     }
     if (e != cudaSuccess) {
         dfree(ctx, w);
@@ -428,6 +448,43 @@ extern "C" pv_status pv_grid_set_build_seconds(const pv_grid_set* set, double* s
         total += ms * 1e-3;
     }
     *seconds = total;
+    return PV_OK;
+}
+
+extern "C" pv_status pv_grid_set_pack(pv_context* ctx, pv_grid_set* set) {
+    if (!ctx || ctx->magic != kCtxMagic) return PV_ERR_STATE;
+    if (!set || set->ctx != ctx) return fail(ctx, PV_ERR_STATE, "grid set of another context");
+    if (set->packed) return PV_OK;
+    DeviceGuard g(ctx->device);
+    const int np = (int)set->pockets.size();
+    size_t cells = 0;
+    for (const PvPocket& P : set->pockets) cells += (size_t)P.ncells * set->n_maps;
+    float4* carena = (float4*)dalloc(ctx, cells * 2 * sizeof(float4));
+    if (!carena) return fail(ctx, PV_ERR_OOM, "packed map allocation failed");
+    std::vector<PvPocket> pk = set->pockets;
+    size_t co = 0;
+    for (PvPocket& P : pk) {
+        P.cells = carena + co;
+        co += (size_t)P.ncells * set->n_maps * 2;
+    }
+    PvPocket* d_p = (PvPocket*)dalloc(ctx, sizeof(PvPocket) * np);
+    if (!d_p) {
+        dfree(ctx, carena);
+        return fail(ctx, PV_ERR_OOM, "pocket table allocation failed");
+    }
+    cudaError_t e = cudaMemcpyAsync(d_p, pk.data(), sizeof(PvPocket) * np, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = launch_pack_cells(d_p, pk.data(), 0, np, set->n_maps, ctx->stream);
+    if (e != cudaSuccess) {
+        dfree(ctx, d_p);
+        dfree(ctx, carena);
+        return cuda_fail(ctx, e, "map packing");
+    }
+    set->arenas.push_back(carena);
+    set->bytes += (int64_t)(cells * 2 * sizeof(float4));
+    dfree(ctx, set->d_pockets);
+    set->d_pockets = d_p;
+    set->pockets = pk;
+    set->packed = true;
     return PV_OK;
 }
 
@@ -617,10 +674,17 @@ extern "C" pv_status pv_pose_coords(pv_context* ctx, const pv_ligand* lig, int32
 
 extern "C" pv_status pv_measure_gather(pv_context* ctx, const pv_grid_set* set, int32_t pocket, int64_t n_points,
                                        int32_t reps, float* ms_per_launch) {
+    return pv_measure_gather_layout(ctx, set, pocket, n_points, reps, 0, ms_per_launch);
+}
+
+extern "C" pv_status pv_measure_gather_layout(pv_context* ctx, const pv_grid_set* set, int32_t pocket,
+                                              int64_t n_points, int32_t reps, int32_t layout, float* ms_per_launch) {
     if (!ctx || ctx->magic != kCtxMagic) return PV_ERR_STATE;
     if (!set || set->ctx != ctx) return fail(ctx, PV_ERR_STATE, "grid set of another context");
     if (pocket < -1 || pocket >= (int)set->pockets.size() || n_points < 1 || reps < 1 || !ms_per_launch)
         return fail(ctx, PV_ERR_ARG, "bad arguments");
+    if (layout != 0 && layout != 1) return fail(ctx, PV_ERR_ARG, "layout must be 0 (plain) or 1 (cell-packed)");
+    if (layout == 1 && !set->packed) return fail(ctx, PV_ERR_ARG, "the grid set holds no cell-packed maps (pv_grid_set_pack)");
     DeviceGuard g(ctx->device);
     const PvPocket* table = pocket < 0 ? set->d_pockets : set->d_pockets + pocket;
     const int n_table = pocket < 0 ? (int)set->pockets.size() : 1;
@@ -630,10 +694,12 @@ extern "C" pv_status pv_measure_gather(pv_context* ctx, const pv_grid_set* set, 
     if (!sink) return fail(ctx, PV_ERR_OOM, "device allocation failed");
     cudaError_t e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
-    if (e == cudaSuccess) e = launch_gather_probe(table, n_table, set->n_maps, n_points, 1u, sink, ctx->sms, ctx->stream);
+    if (e == cudaSuccess)
+        e = launch_gather_probe(table, n_table, set->n_maps, n_points, 1u, sink, ctx->sms, layout, ctx->stream);
     if (e == cudaSuccess) e = cudaEventRecord(t0, ctx->stream);
     for (int r = 0; r < reps && e == cudaSuccess; ++r)
-        e = launch_gather_probe(table, n_table, set->n_maps, n_points, 2u + (uint32_t)r * 977u, sink, ctx->sms, ctx->stream);
+        e = launch_gather_probe(table, n_table, set->n_maps, n_points, 2u + (uint32_t)r * 977u, sink, ctx->sms, layout,
+                                ctx->stream);
     if (e == cudaSuccess) e = cudaEventRecord(t1, ctx->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(t1);
     float ms = 0.f;
@@ -678,6 +744,7 @@ extern "C" void pv_dock_params_default(pv_dock_params* p) {
     p->max_pockets = 0;
     p->block_wait_s = 30.0;
     p->pair_keys = nullptr;
+    p->map_layout = -1;
 }
 
 static void result_free(pv_dock_result* r) {
@@ -706,6 +773,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     if (p.mode != PV_MODE_BATCHED && p.mode != PV_MODE_PLAIN && p.mode != PV_MODE_PLAIN_WARP)
         return fail(ctx, PV_ERR_ARG, "unknown mode");
     if (p.warps_per_cta < 0 || p.warps_per_cta > 16) return fail(ctx, PV_ERR_ARG, "warps_per_cta must be 0..16");
+    if (p.map_layout < -1 || p.map_layout > 1) return fail(ctx, PV_ERR_ARG, "map_layout must be -1, 0 or 1");
     if (p.focc < 0 || p.focc > PV_FOCC_MAX || !(p.focc_min_delta >= 0.f))
         return fail(ctx, PV_ERR_ARG, "focc must be 0..4 and focc_min_delta >= 0");
     if (p.focc > 0 && p.mode != PV_MODE_BATCHED)
@@ -782,19 +850,27 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     int variant = p.search_variant >= 0 ? p.search_variant : (auto_lanes == 16 ? 4 : 0);
     int W = p.warps_per_cta > 0 ? p.warps_per_cta : 4;
     const bool warp_chains = p.mode != PV_MODE_PLAIN;   // batched, or one warp-per-chain launch per pair
-    const bool autotune = warp_chains && (p.search_variant < 0 || p.warps_per_cta == 0);
+    // map layout: the caller's, or (map_layout -1) the cell-packed one is a candidate when the set
+    // holds it; the layout never changes results (the same corners, the same arithmetic)
+    if (p.map_layout == 1 && !set->packed)
+        return fail(ctx, PV_ERR_ARG, "map_layout 1 needs a grid set with cell-packed maps (pv_grid_set_pack)");
+    const bool tune_layout = warp_chains && p.map_layout < 0 && set->packed;
+    int layout = p.map_layout == 1 ? 1 : 0;
+    const bool autotune = warp_chains && (p.search_variant < 0 || p.warps_per_cta == 0 || tune_layout);
     int max_rounds = 0;
     for (int i = 0; i < n_ligs; ++i) max_rounds = std::max(max_rounds, ligs[i]->rec.n_rounds);
-    // the parameters the caller fixed (a variant or a CTA size) are part of the key: a shape tuned
-    // with one of them free may not suit the other fixed
+    // the parameters the caller fixed (a variant, a CTA size, a layout) are part of the key: a shape
+    // tuned with one of them free may not suit the other fixed
     const std::pair<int, int> tune_key{4 * ((max_atoms + 7) / 8) + 2 * (p.focc > 0 ? 1 : 0) + (auto_lanes == 16 ? 1 : 0),
-                                       ((max_rounds + 3) / 4) * 1024 + p.warps_per_cta * 16 + (p.search_variant + 1)};
+                                       ((max_rounds + 3) / 4) * 1024 + p.warps_per_cta * 16 + (p.search_variant + 1) +
+                                           (tune_layout ? 1 << 20 : 0) + ((p.map_layout + 1) << 21)};
     bool need_tune = false;
     if (autotune) {
         auto it = ctx->tuned.find(tune_key);
         if (it != ctx->tuned.end()) {
-            if (p.search_variant < 0) variant = it->second.first;
-            if (p.warps_per_cta == 0) W = it->second.second;
+            if (p.search_variant < 0) variant = std::get<0>(it->second);
+            if (p.warps_per_cta == 0) W = std::get<1>(it->second);
+            if (tune_layout) layout = std::get<2>(it->second);
         } else {
             need_tune = true;
         }
@@ -924,36 +1000,37 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     M.rank_stride = R->rank_stride;
     M.ranking = R->d_ranking;
     // autotuning: time each candidate launch shape on kTuneSteps MC steps of its own first work
-    // items (long enough that chains which share a CTA even out, as over a real step block)
+    // items (long enough that chains which share a CTA even out, as over a real step block), the
+    // faster of three runs; then, if the set holds cell-packed maps too, the chosen shape on them.
+    // A candidate replaces the incumbent (the first candidate, a fixed preference order) only when
+    // it is faster by more than kTuneMargin, so that shapes within the trials' noise do not flip
+    // between runs.
     if (need_tune) {
         constexpr int kTuneSteps = 32;
-        static const int cand[][2] = {{0, 1}, {0, 2}, {0, 4}, {0, 8}, {1, 4}, {2, 4}, {3, 4},
-                                      {4, 1}, {4, 2}, {4, 4}, {5, 4}, {6, 4}, {7, 4}};
+        constexpr float kTuneMargin = 0.02f;
+        static const int cand[][2] = {{0, 2}, {0, 1}, {0, 4}, {0, 8}, {1, 4}, {2, 4}, {3, 4},
+                                      {4, 2}, {4, 1}, {4, 4}, {5, 4}, {6, 4}, {7, 4}};
         cudaEvent_t t0, t1;
         cudaEventCreate(&t0);
         cudaEventCreate(&t1);
-        float best_ms = 1e30f;
-        int best_v = variant, best_w = W;
-        for (const auto& cw : cand) {
-            const int v = p.search_variant >= 0 ? p.search_variant : cw[0];
-            const int wc = p.warps_per_cta > 0 ? p.warps_per_cta : cw[1];
-            if (wc > search_variant_max_warps(v)) continue;
+        // per-chain time of one shape and layout; < 0 when the shape does not fit
+        auto trial = [&](int v, int wc, int lay, float& per_chain) -> cudaError_t {
+            per_chain = -1.f;
             const int lanes_c = search_variant_lanes(v);
-            if (lanes_c == 16 && !all_team16) continue;
-            if (p.search_variant < 0 && lanes_c != auto_lanes) continue;
             int occ_c = 0;
-            if (search_max_ctas_per_sm(v, p.focc > 0, wc, search_smem_bytes(max_blob, wc, lanes_c), &occ_c) != cudaSuccess ||
+            if (search_max_ctas_per_sm(v, p.focc > 0, lay, wc, search_smem_bytes(max_blob, wc, lanes_c), &occ_c) !=
+                    cudaSuccess ||
                 occ_c < 1) {
                 cudaGetLastError();
-                continue;
+                return cudaSuccess;
             }
             // whole waves of the shape's resident CTAs (up to four) when the work allows, so that a
             // partly filled last wave, which the chained step blocks of a real launch do not have,
             // does not weigh on the shapes with fewer, larger CTAs
-            std::vector<PvItem> trial = make_items(wc * (32 / lanes_c));
+            std::vector<PvItem> trial_items = make_items(wc * (32 / lanes_c));
             const size_t slots = (size_t)ctx->sms * occ_c;
-            size_t n_waves = std::min<size_t>(4, trial.size() / slots);
-            const int n_trial = (int)(n_waves > 0 ? n_waves * slots : trial.size());
+            const size_t n_waves = std::min<size_t>(4, trial_items.size() / slots);
+            const int n_trial = (int)(n_waves > 0 ? n_waves * slots : trial_items.size());
             SearchArgs a = A;
             a.items = (const PvItem*)((char*)R->d_work + o_items);
             a.n_items = 0;                       // an empty launch first: loads the variant's code
@@ -962,13 +1039,14 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
             a.step1 = std::min(p.steps, kTuneSteps);
             a.items_per_block = n_trial;         // one step block
             a.block_steps = kTuneSteps;
-            cudaError_t x = cudaMemcpyAsync((char*)R->d_work + o_items, trial.data(), sizeof(PvItem) * n_trial,
+            a.layout = lay;
+            cudaError_t x = cudaMemcpyAsync((char*)R->d_work + o_items, trial_items.data(), sizeof(PvItem) * n_trial,
                                             cudaMemcpyHostToDevice, ctx->stream);
             if (x == cudaSuccess) x = cudaMemsetAsync(ctr, 0, sizeof(int) * 2, ctx->stream);
             if (x == cudaSuccess) x = launch_search_round(a, v, 1, wc, ctx->stream);
             a.n_items = n_trial;
             float ms = 1e30f;
-            for (int rep = 0; rep < 2 && x == cudaSuccess; ++rep) {   // the faster of two runs
+            for (int rep = 0; rep < 3 && x == cudaSuccess; ++rep) {   // the fastest of three runs
                 x = cudaMemsetAsync(ctr, 0, sizeof(int) * 2, ctx->stream);
                 if (x == cudaSuccess) x = launch_mark_t0(evals + 1, ctx->stream);
                 if (x == cudaSuccess) x = cudaEventRecord(t0, ctx->stream);
@@ -980,22 +1058,46 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
                 if (x == cudaSuccess) x = cudaEventElapsedTime(&t, t0, t1);
                 if (x == cudaSuccess) ms = std::min(ms, t);
             }
-            if (x != cudaSuccess) {
-                cudaEventDestroy(t0);
-                cudaEventDestroy(t1);
-                result_free(R);
-                return cuda_fail(ctx, x, "autotune");
-            }
             // per unit of work: the trials cover different numbers of chains
-            const float per_chain = ms / (float)std::min<long long>((long long)n_trial * wc * (32 / lanes_c),
-                                                                     (long long)n_pairs * p.chains);
-            if (per_chain < best_ms) { best_ms = per_chain; best_v = v; best_w = wc; }
+            if (x == cudaSuccess)
+                per_chain = ms / (float)std::min<long long>((long long)n_trial * wc * (32 / lanes_c),
+                                                           (long long)n_pairs * p.chains);
+            return x;
+        };
+        float best_ms = -1.f;
+        int best_v = variant, best_w = W;
+        cudaError_t x = cudaSuccess;
+        const bool tune_shape = p.search_variant < 0 || p.warps_per_cta == 0;
+        for (const auto& cw : cand) {
+            if (!tune_shape) break;
+            const int v = p.search_variant >= 0 ? p.search_variant : cw[0];
+            const int wc = p.warps_per_cta > 0 ? p.warps_per_cta : cw[1];
+            if (wc > search_variant_max_warps(v)) continue;
+            const int lanes_c = search_variant_lanes(v);
+            if (lanes_c == 16 && !all_team16) continue;
+            if (p.search_variant < 0 && lanes_c != auto_lanes) continue;
+            float pc = 0.f;
+            x = trial(v, wc, layout, pc);
+            if (x != cudaSuccess) break;
+            if (pc < 0.f) continue;
+            if (best_ms < 0.f || pc < best_ms * (1.f - kTuneMargin)) { best_ms = pc; best_v = v; best_w = wc; }
+        }
+        if (x == cudaSuccess && tune_layout) {
+            float plain_ms = best_ms, packed_ms = -1.f;
+            if (plain_ms < 0.f) x = trial(best_v, best_w, 0, plain_ms);
+            if (x == cudaSuccess) x = trial(best_v, best_w, 1, packed_ms);
+            if (x == cudaSuccess && packed_ms > 0.f && plain_ms > 0.f && packed_ms < plain_ms * (1.f - kTuneMargin))
+                layout = 1;
         }
         cudaEventDestroy(t0);
         cudaEventDestroy(t1);
+        if (x != cudaSuccess) {
+            result_free(R);
+            return cuda_fail(ctx, x, "autotune");
+        }
         variant = best_v;
         W = best_w;
-        ctx->tuned[tune_key] = {variant, W};
+        ctx->tuned[tune_key] = std::make_tuple(variant, W, layout);
         items = make_items(W * (32 / search_variant_lanes(variant)));
         e = cudaMemcpyAsync((char*)R->d_work + o_items, items.data(), sizeof(PvItem) * items.size(),
                             cudaMemcpyHostToDevice, ctx->stream);
@@ -1004,6 +1106,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
             return cuda_fail(ctx, e, "item upload");
         }
     }
+    A.layout = layout;
     A.items_per_block = (int)items.size();
     // each pair's run of work items (items are grouped by pair) for the per-pair launches
     std::vector<int> item_start(n_pairs, 0), item_count(n_pairs, 0);
@@ -1014,7 +1117,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     // grid of the persistent rounds: every SM filled to its occupancy
     int occ = 0;
     const int smem = search_smem_bytes(max_blob, W, search_variant_lanes(variant));
-    e = search_max_ctas_per_sm(variant, p.focc > 0, W, smem, &occ);
+    e = search_max_ctas_per_sm(variant, p.focc > 0, layout, W, smem, &occ);
     if (e != cudaSuccess || occ < 1) {
         result_free(R);
         return e != cudaSuccess ? cuda_fail(ctx, e, "occupancy") : fail(ctx, PV_ERR_ARG, "search kernel does not fit");
@@ -1023,6 +1126,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     const int grid = std::max(1, std::min((int)items.size(), ctx->sms * occ));
     R->search_variant = variant;
     R->warps_per_cta = W;
+    R->map_layout = layout;
     e = prepare_topk(T);
     if (e == cudaSuccess) e = prepare_merge(R->rank_stride);
     if (e != cudaSuccess) {
@@ -1337,6 +1441,12 @@ extern "C" pv_status pv_dock_result_timing(const pv_dock_result* r, double* sear
     if (search_seconds) *search_seconds = r->search_seconds;
     if (search_launches) *search_launches = r->search_launches;
     if (total_seconds) *total_seconds = r->seconds;
+    return PV_OK;
+}
+
+extern "C" pv_status pv_dock_result_map_layout(const pv_dock_result* r, int32_t* map_layout) {
+    if (!r || !map_layout) return PV_ERR_ARG;
+    *map_layout = r->map_layout;
     return PV_OK;
 }
 

@@ -15,7 +15,7 @@ namespace pv {
 // (Eq. 6-12), the Metropolis test (Eq. 13 read as exp((e_cur - e_new) / T)), and for a new best a
 // second RILC-BFGS run whose result becomes both current and best. Lanes of a team without a
 // chain (have == false) only take part in the loop's warp vote.
-template <int LANES, bool FOCC>
+template <int LANES, bool FOCC, int LAYOUT>
 __device__ __forceinline__ void run_chain(const SearchArgs& A, const PvLigBlob& L, WarpScratch& S, const Site& site,
                                           int pair, uint32_t key, int chain, bool have, int step0, int step1,
                                           uint32_t& evals_out, int& flags_out) {
@@ -67,7 +67,7 @@ __device__ __forceinline__ void run_chain(const SearchArgs& A, const PvLigBlob& 
         if (!__any_sync(PV_FULL, active)) break;
         if (!active) continue;
         float ge;
-        const float fe = team_eval<LANES>(L, S, site, xt, ge, true);
+        const float fe = team_eval<LANES, true, LAYOUT>(L, S, site, xt, ge, true);
         ++evals;
         bool bdone = false, next_iter = false;
         if (bstart) {                                   // the start point of a local search
@@ -216,6 +216,7 @@ __device__ __forceinline__ void run_chain(const SearchArgs& A, const PvLigBlob& 
 // k holds component k), and the retraction of a tangent step (translation, world-frame rotation
 // vector, torsions). warp_rilc_bfgs is written against this interface so that the same optimiser
 // code also runs on analytic objectives (pv_check.cu).
+template <int LAYOUT>
 struct WarpDockObjective {
     using State = Pose;
     const PvLigBlob& L;
@@ -223,7 +224,7 @@ struct WarpDockObjective {
     const Site& site;
     int n_tan;
     __device__ __forceinline__ float eval(const Pose& x, float& g) const {
-        return team_eval<32>(L, S, site, x, g, true);
+        return team_eval<32, true, LAYOUT>(L, S, site, x, g, true);
     }
     __device__ __forceinline__ Pose retract(const Pose& x, float step) const {
         return team_retract<32>(x, step, n_tan);
@@ -333,7 +334,7 @@ __device__ __forceinline__ float warp_rilc_bfgs(const Obj& obj, WarpScratch& S, 
         Q.it = it; Q.tr = tr; Q.stored = stored; Q.head = head; Q.have_lo = have_lo;
     }
 }
-template <bool FOCC>
+template <bool FOCC, int LAYOUT>
 __device__ __forceinline__ void run_chain_warp(const SearchArgs& A, const PvLigBlob& L, WarpScratch& S,
                                                const Site& site, int pair, uint32_t key, int chain, int step0,
                                                int step1, uint32_t& evals_out, int& flags_out) {
@@ -380,7 +381,7 @@ __device__ __forceinline__ void run_chain_warp(const SearchArgs& A, const PvLigB
             Tm::sync();
             Q.u = u;
         }
-        const WarpDockObjective obj{L, S, site, 6 + n_rot};
+        const WarpDockObjective<LAYOUT> obj{L, S, site, 6 + n_rot};
         const float e_new = warp_rilc_bfgs<FOCC>(obj, S, cand, C, stage0 == 0 ? 0 : max_iter, evals, g_new,
                                                  FOCC && stage0 == 1 ? ring : nullptr, n_rot);
         float e_cur = Q.e_cur, e_best = Q.e_best;
@@ -478,8 +479,9 @@ __device__ __forceinline__ int wait_block(const int* progress, int blk, unsigned
 // 0, then of block 1, and so on, so no SM idles at a block boundary while the chains of the last
 // wave finish (the blocks of one chain block run in order through `progress`). Compiled for
 // several (threads per CTA, minimum CTAs per SM) bounds, i.e. register budgets, and team widths (a
-// chain per warp, or per half warp); the runtime picks one (search variant).
-template <int THREADS, int MIN_CTAS, int LANES, bool FOCC>
+// chain per warp, or per half warp), and for both map layouts (plain, cell-packed); the runtime
+// picks one (search variant, layout).
+template <int THREADS, int MIN_CTAS, int LANES, bool FOCC, int LAYOUT>
 __global__ void __launch_bounds__(THREADS, MIN_CTAS) search_round_kernel(SearchArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     PvLigBlob& L = *reinterpret_cast<PvLigBlob*>(smem);
@@ -489,6 +491,7 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) search_round_kernel(SearchA
     constexpr int TPW = 32 / LANES;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int team = warp * TPW + Team<LANES>::index();
+    init_scratch<LANES>(scratch[team]);
     if (threadIdx.x == 0) s_lig = -1;
     for (;;) {
         __syncthreads();
@@ -538,11 +541,11 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) search_round_kernel(SearchA
         int flags = 0;
         if constexpr (LANES == 32) {
             if (chain < A.C.chains)
-                run_chain_warp<FOCC>(A, L, scratch[team], site, item.pair, (uint32_t)pd.key, chain, step0, step1,
-                                     evals, flags);
+                run_chain_warp<FOCC, LAYOUT>(A, L, scratch[team], site, item.pair, (uint32_t)pd.key, chain, step0,
+                                             step1, evals, flags);
         } else {
-            run_chain<LANES, FOCC>(A, L, scratch[team], site, item.pair, (uint32_t)pd.key, chain, chain < A.C.chains,
-                                   step0, step1, evals, flags);
+            run_chain<LANES, FOCC, LAYOUT>(A, L, scratch[team], site, item.pair, (uint32_t)pd.key, chain,
+                                           chain < A.C.chains, step0, step1, evals, flags);
         }
         if (Team<LANES>::lane() == 0 && evals) {
             atomicAdd(A.evals, (unsigned long long)evals);

@@ -4,6 +4,7 @@
 #include <stdint.h>
 #include <cuda_runtime.h>
 #include "pv_layout.h"
+#include "pv_terms.h"
 
 #define PV_FULL 0xffffffffu
 #define PV_PI 3.14159265358979323846f
@@ -14,14 +15,7 @@ namespace pv {
 // AutoDock Vina scoring terms (Trott & Olson 2010; the scoring function the paper's engine
 // evaluates, Eq. 3). Surface distance d = r - R_i - R_j, cutoff r < 8 A.
 // ------------------------------------------------------------------------------------------
-constexpr float kWGauss1 = -0.0356f;
-constexpr float kWGauss2 = -0.00516f;
-constexpr float kWRepulsion = 0.840f;
-constexpr float kWHydrophobic = -0.0351f;
-constexpr float kWHBond = -0.587f;
-constexpr float kWRot = 0.0585f;
-constexpr float kCutoff = 8.0f;
-constexpr float kCutoff2 = 64.0f;
+// (weights, cutoff and ramp ends in pv_terms.h)
 constexpr float kOutSlope = 10.0f;       // kcal/mol/A beyond the grid
 
 // XS type properties, indexed by type id (C_H, C_P, N_P, N_D, N_A, N_DA, O_P, O_D, O_A, O_DA, S_P)
@@ -63,6 +57,27 @@ __device__ __forceinline__ float vina_pair_r2(float r2, float rsum, bool hyd, bo
     const float e = kWGauss1 * g1 + kWGauss2 * g2 + kWRepulsion * rep * rep + w * v;
     const float de = (-8.0f * kWGauss1) * d * g1 + (-0.5f * kWGauss2) * b * g2 + (2.0f * kWRepulsion) * rep + w * dv;
     dedr_over_r = r2 > 1e-12f ? de * rinv : 0.0f;
+    return e;
+}
+
+// The same pair energy with the ramp of the hydrophobic or H-bond term given by its constants,
+// w sat(c0 + c1 d) (c0 = c1 = w = 0 for neither; the values of the ramps above), as the intra-pair
+// records of a ligand carry them: no per-pair flag decoding. r2 > 0 (a pair of distinct atoms).
+__device__ __forceinline__ float vina_pair_ramp(float r2, float rsum, float c0, float c1, float w,
+                                                float& dedr_over_r) {
+    const float rinv = rsqrtf(fmaxf(r2, 1e-12f));
+    const float r = r2 * rinv;
+    const float d = r - rsum;
+    const float g1 = exp2_approx(d * d * (-4.0f * kLog2e));     // exp(-(d / 0.5)^2)
+    const float b = d - 3.0f;
+    const float g2 = exp2_approx(b * b * (-0.25f * kLog2e));    // exp(-((d - 3) / 2)^2)
+    const float rep = fminf(d, 0.0f);
+    const float t = fmaf(c1, d, c0);
+    const float v = __saturatef(t);
+    const float dv = (t > 0.0f && t <= 1.0f) ? c1 : 0.0f;
+    const float e = kWGauss1 * g1 + kWGauss2 * g2 + kWRepulsion * rep * rep + w * v;
+    const float de = (-8.0f * kWGauss1) * d * g1 + (-0.5f * kWGauss2) * b * g2 + (2.0f * kWRepulsion) * rep + w * dv;
+    dedr_over_r = de * rinv;
     return e;
 }
 
@@ -208,51 +223,89 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
 
 // ------------------------------------------------------------------------------------------
 // Trilinear interpolation of one map (Eq. 3: e_inter from the grid cache) with its gradient.
-// Outside the grid the point is clamped to it and kOutSlope * distance is added.
+// Outside the grid the point is clamped to it and kOutSlope * distance is added. Two layouts hold
+// the same node values: plain maps [z][y][x], whose eight corners take eight scalar loads from at
+// least four 32-byte sectors, and cell-packed maps (each cell's eight corners contiguous, 32 bytes:
+// two 16-byte loads from one sector). Both interpolate the same eight values with the same
+// arithmetic, so they give the same bits.
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ float grid_eval(const float* __restrict__ map, const PvPocket& P,
-                                           float3 p, float3& dEdx) {
-    float g[3] = {(p.x - P.origin[0]) * P.inv_spacing, (p.y - P.origin[1]) * P.inv_spacing,
-                  (p.z - P.origin[2]) * P.inv_spacing};
-    float f[3], out[3];
-    int i[3];
-    bool cl[3];
+struct GridCell {
+    int i[3];          // the cell's lowest node
+    float f[3];        // position inside the cell, [0, 1]
+    float out[3];      // distance outside the grid per axis (A), 0 inside
+    bool cl[3];        // clamped per axis
+};
+
+__device__ __forceinline__ GridCell grid_locate(const PvPocket& P, float3 p) {
+    const float g[3] = {(p.x - P.origin[0]) * P.inv_spacing, (p.y - P.origin[1]) * P.inv_spacing,
+                        (p.z - P.origin[2]) * P.inv_spacing};
+    GridCell c;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        float hi = (float)(P.dims[k] - 1);
-        cl[k] = (g[k] < 0.0f) || (g[k] > hi);
-        float gc = fminf(fmaxf(g[k], 0.0f), hi);
+        const float hi = (float)(P.dims[k] - 1);
+        c.cl[k] = (g[k] < 0.0f) || (g[k] > hi);
+        const float gc = fminf(fmaxf(g[k], 0.0f), hi);
         int ii = (int)floorf(gc);
         ii = min(ii, P.dims[k] - 2);
-        i[k] = ii;
-        f[k] = gc - (float)ii;
-        out[k] = cl[k] ? (g[k] - gc) * P.spacing : 0.0f;
+        c.i[k] = ii;
+        c.f[k] = gc - (float)ii;
+        c.out[k] = c.cl[k] ? (g[k] - gc) * P.spacing : 0.0f;
     }
-    const float* base = map + ((long long)i[2] * P.nxy + (long long)i[1] * P.dims[0] + i[0]);
-    float v000 = __ldg(base), v100 = __ldg(base + 1);
-    float v010 = __ldg(base + P.dims[0]), v110 = __ldg(base + P.dims[0] + 1);
-    float v001 = __ldg(base + P.nxy), v101 = __ldg(base + P.nxy + 1);
-    float v011 = __ldg(base + P.nxy + P.dims[0]), v111 = __ldg(base + P.nxy + P.dims[0] + 1);
-    float fx = f[0], fy = f[1], fz = f[2];
-    float gx = 1.f - fx, gy = 1.f - fy, gz = 1.f - fz;
+    return c;
+}
+
+// v = the corners (x fastest): v000, v100, v010, v110, v001, v101, v011, v111
+__device__ __forceinline__ float grid_interpolate(const PvPocket& P, const GridCell& c, const float4 lo,
+                                                  const float4 hi, float3& dEdx) {
+    const float v000 = lo.x, v100 = lo.y, v010 = lo.z, v110 = lo.w;
+    const float v001 = hi.x, v101 = hi.y, v011 = hi.z, v111 = hi.w;
+    const float fx = c.f[0], fy = c.f[1], fz = c.f[2];
+    const float gx = 1.f - fx, gy = 1.f - fy, gz = 1.f - fz;
     // along x
-    float a00 = gx * v000 + fx * v100, a10 = gx * v010 + fx * v110;
-    float a01 = gx * v001 + fx * v101, a11 = gx * v011 + fx * v111;
-    float b0 = gy * a00 + fy * a10, b1 = gy * a01 + fy * a11;
+    const float a00 = gx * v000 + fx * v100, a10 = gx * v010 + fx * v110;
+    const float a01 = gx * v001 + fx * v101, a11 = gx * v011 + fx * v111;
+    const float b0 = gy * a00 + fy * a10, b1 = gy * a01 + fy * a11;
     float val = gz * b0 + fz * b1;
-    float dx = gz * (gy * (v100 - v000) + fy * (v110 - v010)) + fz * (gy * (v101 - v001) + fy * (v111 - v011));
-    float dy = gz * (a10 - a00) + fz * (a11 - a01);
-    float dz = b1 - b0;
-    dEdx = make_float3(cl[0] ? 0.f : dx * P.inv_spacing, cl[1] ? 0.f : dy * P.inv_spacing,
-                       cl[2] ? 0.f : dz * P.inv_spacing);
-    float d2 = out[0] * out[0] + out[1] * out[1] + out[2] * out[2];
+    const float dx = gz * (gy * (v100 - v000) + fy * (v110 - v010)) + fz * (gy * (v101 - v001) + fy * (v111 - v011));
+    const float dy = gz * (a10 - a00) + fz * (a11 - a01);
+    const float dz = b1 - b0;
+    dEdx = make_float3(c.cl[0] ? 0.f : dx * P.inv_spacing, c.cl[1] ? 0.f : dy * P.inv_spacing,
+                       c.cl[2] ? 0.f : dz * P.inv_spacing);
+    const float d2 = c.out[0] * c.out[0] + c.out[1] * c.out[1] + c.out[2] * c.out[2];
     if (d2 > 0.0f) {
-        float dist = sqrtf(d2);
+        const float dist = sqrtf(d2);
         val += kOutSlope * dist;
-        float s = kOutSlope / dist;
-        dEdx.x += s * out[0]; dEdx.y += s * out[1]; dEdx.z += s * out[2];
+        const float sl = kOutSlope / dist;
+        dEdx.x += sl * c.out[0]; dEdx.y += sl * c.out[1]; dEdx.z += sl * c.out[2];
     }
     return val;
+}
+
+// Plain layout: `map` is one map [z][y][x].
+__device__ __forceinline__ float grid_eval(const float* __restrict__ map, const PvPocket& P,
+                                           float3 p, float3& dEdx) {
+    const GridCell c = grid_locate(P, p);
+    const float* base = map + ((long long)c.i[2] * P.nxy + (long long)c.i[1] * P.dims[0] + c.i[0]);
+    const float4 lo = make_float4(__ldg(base), __ldg(base + 1), __ldg(base + P.dims[0]), __ldg(base + P.dims[0] + 1));
+    const float4 hi = make_float4(__ldg(base + P.nxy), __ldg(base + P.nxy + 1), __ldg(base + P.nxy + P.dims[0]),
+                                  __ldg(base + P.nxy + P.dims[0] + 1));
+    return grid_interpolate(P, c, lo, hi, dEdx);
+}
+
+// Cell-packed layout: `cells` holds one map's cells [z][y][x] over (dims - 1) per axis, two float4
+// per cell (the corners in grid_interpolate's order).
+__device__ __forceinline__ float grid_eval_cells(const float4* __restrict__ cells, const PvPocket& P,
+                                                 float3 p, float3& dEdx) {
+    const GridCell c = grid_locate(P, p);
+    const float4* cp = cells + 2 * (((long long)c.i[2] * (P.dims[1] - 1) + c.i[1]) * (P.dims[0] - 1) + c.i[0]);
+    return grid_interpolate(P, c, __ldg(cp), __ldg(cp + 1), dEdx);
+}
+
+// The lookup of map slot `slot` of a pocket in the layout LAYOUT (0 plain, 1 cell-packed).
+template <int LAYOUT>
+__device__ __forceinline__ float grid_eval_slot(const PvPocket& P, int slot, float3 p, float3& dEdx) {
+    if constexpr (LAYOUT == 0) return grid_eval(P.maps + (long long)slot * P.nxyz, P, p, dEdx);
+    else return grid_eval_cells(P.cells + 2LL * slot * P.ncells, P, p, dEdx);
 }
 
 // ------------------------------------------------------------------------------------------

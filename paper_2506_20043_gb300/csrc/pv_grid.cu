@@ -276,6 +276,33 @@ __global__ void __launch_bounds__(kGridThreads) grid_kernel(GridArgs A) {
     }
 }
 
+// Cell-packed copy of one pocket's maps: thread per (map slot, cell), the cell's eight corners
+// (x fastest) read from the plain map and written as two float4.
+__global__ void __launch_bounds__(256) pack_cells_kernel(const PvPocket* __restrict__ pockets, int pocket, int n_maps) {
+    const PvPocket& P = pockets[pocket];
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long long)n_maps * P.ncells) return;
+    const int slot = (int)(k / P.ncells), cell = (int)(k - (long long)slot * P.ncells);
+    const int cx = P.dims[0] - 1, cy = P.dims[1] - 1;
+    const int ix = cell % cx, iy = (cell / cx) % cy, iz = cell / (cx * cy);
+    const float* m = P.maps + (long long)slot * P.nxyz + ((long long)iz * P.nxy + (long long)iy * P.dims[0] + ix);
+    float4* out = const_cast<float4*>(P.cells) + 2 * k;
+    out[0] = make_float4(m[0], m[1], m[P.dims[0]], m[P.dims[0] + 1]);
+    out[1] = make_float4(m[P.nxy], m[P.nxy + 1], m[P.nxy + P.dims[0]], m[P.nxy + P.dims[0] + 1]);
+}
+
+cudaError_t launch_pack_cells(const PvPocket* pockets_dev, const PvPocket* pockets_host, int first, int n,
+                              int n_maps, cudaStream_t s) {
+    for (int p = first; p < first + n; ++p) {
+        const long long work = (long long)n_maps * pockets_host[p].ncells;
+        if (work <= 0) continue;
+        pack_cells_kernel<<<(unsigned)((work + 255) / 256), 256, 0, s>>>(pockets_dev, p, n_maps);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_grid_tiles(const float4* sorted, const int* cell_start, const float lo[3],
                               float cell, const int cdims[3], const PvPocket* pockets_dev,
                               const int2* tiles_dev, int n_tiles, uint64_t slots_lo, uint64_t slots_hi,

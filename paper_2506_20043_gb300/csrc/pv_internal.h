@@ -35,6 +35,11 @@ cudaError_t launch_grid_tiles(const float4* sorted, const int* cell_start, const
                               const int2* tiles_dev, int n_tiles, uint64_t slots_lo, uint64_t slots_hi,
                               int type_mask, cudaStream_t s);
 
+// Cell-packed copies of the maps of pockets [first, first + n) of a device pocket table: for every
+// map slot and cell, its eight corner values as two float4 at P.cells.
+cudaError_t launch_pack_cells(const PvPocket* pockets_dev, const PvPocket* pockets_host, int first, int n,
+                              int n_maps, cudaStream_t s);
+
 // ---- scoring (pv_score.cu) ----
 // pocket: device pointer to the pocket record (its maps pointer included)
 cudaError_t launch_score(const PvLigBlob* lig, int lig_bytes, const PvPocket* pocket,
@@ -55,7 +60,7 @@ cudaError_t launch_pose_coords(const PvLigBlob* lig, int lig_bytes, int n_poses,
 // pocket of the device table, on hashed map slots in [0, n_slots); sink is written only in a case
 // that does not occur.
 cudaError_t launch_gather_probe(const PvPocket* pockets_dev, int n_pockets, int n_slots, long long n_points,
-                                uint32_t seed, float* sink, int n_sm, cudaStream_t s);
+                                uint32_t seed, float* sink, int n_sm, int layout, cudaStream_t s);
 
 // ---- search (pv_search.cu) ----
 struct SearchArgs {
@@ -79,6 +84,7 @@ struct SearchArgs {
     unsigned long long wait_ns;    // batched: bound on a step block's wait for its predecessor
     int* err;
     unsigned long long* evals;
+    int layout;                    // map layout the kernel reads: 0 plain, 1 cell-packed
 };
 int search_smem_bytes(int lig_bytes, int warps, int lanes);
 // Variants of the round kernel: 0-3 run a chain per warp, 4-7 a chain per half warp (ligands of
@@ -87,9 +93,13 @@ int search_smem_bytes(int lig_bytes, int warps, int lanes);
 constexpr int kSearchVariants = 8;
 int search_variant_max_warps(int variant);
 int search_variant_lanes(int variant);
-cudaError_t search_max_ctas_per_sm(int variant, bool focc, int warps, int smem, int* out);
-// The round kernel of a variant with the consistency check (Eq. 4-5) compiled in (pv_search_focc.cu).
+cudaError_t search_max_ctas_per_sm(int variant, bool focc, int layout, int warps, int smem, int* out);
+// The round kernel of a variant with the consistency check (Eq. 4-5) compiled in (pv_search_focc.cu),
+// and the variants reading cell-packed maps without and with the check (pv_search_packed.cu,
+// pv_search_focc_packed.cu).
 const void* search_focc_kernel(int variant);
+const void* search_packed_kernel(int variant);
+const void* search_focc_packed_kernel(int variant);
 cudaError_t launch_search_round(const SearchArgs& a, int variant, int grid, int warps, cudaStream_t s);
 cudaError_t launch_plain_search(const SearchArgs& a, int pair, const PvLigBlob* lig_dev,
                                 cudaStream_t s);

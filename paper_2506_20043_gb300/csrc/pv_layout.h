@@ -25,6 +25,18 @@ struct PvLigHeader {
     int32_t pad[3];
 };
 
+// One lane's share of one intra-pair round (16 bytes). meta bits: 0-6 the partner atom of the pair
+// the lane sends (device order; 64 = the far dummy atom of an empty slot, whose pair lies beyond
+// the cutoff), 7 the pair's own atom is the lane's second (lane + LANES), 8-12 the lane whose pair
+// this lane receives, 13 a pair is received, 14 the received pair's atom is the lane's second, 16
+// hydrophobic, 17 H-bond, 31 a pair is sent. The ramp of the hydrophobic or H-bond term is
+// w * sat(c0 + c1 d) on the surface distance d (c0 = c1 = w = 0 without one).
+struct PvPairSlot {
+    int32_t meta;
+    float c0, c1, w;
+};
+#define PV_DUMMY_ATOM 64
+
 struct PvLigBlob {
     PvLigHeader h;
     float4 atom[64];            // xyz: input coordinates minus the fragment anchor; w: int bits
@@ -36,12 +48,8 @@ struct PvLigBlob {
     int32_t frag_tor[PV_MAX_FRAGS];  // torsion index of the fragment's hinge (root: -1)
     int32_t tor_frag[PV_MAX_FRAGS];  // fragment of torsion k
     int32_t atom_src[64];            // input index of device atom i
-    uint32_t pairs[1];               // n_rounds * 32 words (warp schedule), then n_rounds16 * 16
-                                     // words (half-warp schedule); word l of a round is lane l's:
-                                     // pair sent: target atom (bits 0-5), source atom l + LANES *
-                                     // bit 6, hydrophobic (bit 16), H-bond (bit 17), valid (bit 31);
-                                     // pair received: source lane (bits 8-12), valid (bit 13),
-                                     // receiving atom l + LANES * bit 14
+    PvPairSlot pairs[1];             // n_rounds * 32 slots (warp schedule), then n_rounds16 * 16
+                                     // slots (half-warp schedule); slot l of a round is lane l's
 };
 #define PV_LIG_FIXED_BYTES ((int)offsetof(PvLigBlob, pairs))
 
@@ -55,10 +63,11 @@ struct PvPocket {
     float size[3];
     float* maps;                // this pocket's maps, slot-major, each [z][y][x]
     int32_t nxy, nxyz;
-    int32_t pad[2];
+    const float4* cells;        // the same maps cell-packed (slot-major, each cell's 8 corners as two
+                                // float4), or null when the grid set holds the plain layout only
     const float4* rec_atoms;    // the pocket's receptor: xyz and XS type (int bits), for rescoring
     int32_t rec_n;
-    int32_t pad2;
+    int32_t ncells;             // cells per map: (dims - 1) per axis
 };
 
 // XS type -> map slot of a grid set (-1: no map)

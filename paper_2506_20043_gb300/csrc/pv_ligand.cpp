@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "pv_ligand.h"
+#include "pv_terms.h"
 
 namespace pv {
 
@@ -255,26 +256,37 @@ bool build_ligand(const LigandInput& in, LigandRecord& out, std::string& err) {
     // most one pair to send and one to receive, so a round needs neither atomics nor shared memory.
     // A warp schedule (32 lanes) always; a half-warp schedule (16 lanes) when the ligand fits a
     // half-warp team (at most 32 atoms, 16 fragments, 6 + n_rot <= 16 tangent coordinates).
-    auto schedule = [&](int lanes, std::vector<std::vector<uint32_t>>& rounds) {
+    auto schedule = [&](int lanes, std::vector<std::vector<PvPairSlot>>& rounds) {
         std::vector<std::pair<int, int>> edges;   // (source, target), device atom indices
         for (auto& p : pairs) edges.push_back({dev_of[p.first], dev_of[p.second]});
         orient_pairs(n, edges, lanes);
         std::vector<int> colour;
         const int nr = colour_rounds(edges, colour, lanes);
-        rounds.assign(nr, std::vector<uint32_t>(lanes, 0u));
+        // an empty slot sends its "pair" to the far dummy atom: beyond the cutoff, no energy, no force
+        rounds.assign(nr, std::vector<PvPairSlot>(lanes, PvPairSlot{PV_DUMMY_ATOM, 0.f, 0.f, 0.f}));
         for (size_t e = 0; e < edges.size(); ++e) {
             const int src = edges[e].first, tgt = edges[e].second;
             const int ti = out.xs[src_of_dev(src)], tj = out.xs[src_of_dev(tgt)];
             const uint32_t hyd = (is_hyd(ti) && is_hyd(tj)) ? 1u : 0u;
             const uint32_t hb = ((is_don(ti) && is_acc(tj)) || (is_acc(ti) && is_don(tj))) ? 1u : 0u;
             const uint32_t half = (uint32_t)(src / lanes);
-            rounds[colour[e]][src % lanes] |= (uint32_t)tgt | (half << 6) | (hyd << 16) | (hb << 17) | (1u << 31);
+            PvPairSlot& s = rounds[colour[e]][src % lanes];
+            s.meta = (int32_t)(((uint32_t)s.meta & ~127u) | (uint32_t)tgt | (half << 7) | (hyd << 16) | (hb << 17) |
+                               (1u << 31));
+            // the ramp w sat(c0 + c1 d): hydrophobic 1 below d = 0.5 to 0 at 1.5, H-bond 1 below
+            // d = -0.7 to 0 at 0 (the two never meet in one pair)
+            const float good = hyd ? kHydGood : kHBondGood, bad = hyd ? kHydBad : kHBondBad;
+            s.c1 = (hyd || hb) ? -1.0f / (bad - good) : 0.0f;    // sat((bad - d) / (bad - good))
+            s.c0 = (hyd || hb) ? bad / (bad - good) : 0.0f;
+            s.w = hyd ? kWHydrophobic : (hb ? kWHBond : 0.0f);
             // the target's lane: which lane sends to it this round, and which of its atoms
-            rounds[colour[e]][tgt % lanes] |= ((uint32_t)(src % lanes) << 8) | (1u << 13) | ((uint32_t)(tgt / lanes) << 14);
+            PvPairSlot& t = rounds[colour[e]][tgt % lanes];
+            t.meta = (int32_t)((uint32_t)t.meta | ((uint32_t)(src % lanes) << 8) | (1u << 13) |
+                               ((uint32_t)(tgt / lanes) << 14));
         }
         return nr;
     };
-    std::vector<std::vector<uint32_t>> rounds, rounds16;
+    std::vector<std::vector<PvPairSlot>> rounds, rounds16;
     const int n_rounds_sched = schedule(32, rounds);
     const bool team16 = n <= 32 && nfrag <= 16 && 6 + n_rot <= 16;
     const int n_rounds16 = team16 ? schedule(16, rounds16) : 0;
@@ -284,7 +296,7 @@ bool build_ligand(const LigandInput& in, LigandRecord& out, std::string& err) {
     }
     // record
     const int n_rounds = n_rounds_sched;
-    const int bytes = PV_LIG_FIXED_BYTES + (n_rounds * 32 + n_rounds16 * 16) * 4;
+    const int bytes = PV_LIG_FIXED_BYTES + (n_rounds * 32 + n_rounds16 * 16) * (int)sizeof(PvPairSlot);
     out.blob.assign((size_t)((bytes + 15) / 16) * 16, 0);
     PvLigBlob* L = reinterpret_cast<PvLigBlob*>(out.blob.data());
     L->h.n_atoms = n;

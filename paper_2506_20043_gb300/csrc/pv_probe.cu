@@ -20,6 +20,7 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
     return x;
 }
 
+template <int LAYOUT>
 __global__ void __launch_bounds__(256) gather_probe_kernel(const PvPocket* __restrict__ pockets, int n_pockets,
                                                            int n_slots, long long n_points, uint32_t seed,
                                                            float* sink) {
@@ -34,7 +35,7 @@ __global__ void __launch_bounds__(256) gather_probe_kernel(const PvPocket* __res
                                      P.center[2] + (u01(h2) - 0.5f) * P.size[2]);
         const int slot = (int)__umulhi(h3, (uint32_t)n_slots);
         float3 g;
-        acc += grid_eval(P.maps + (long long)slot * P.nxyz, P, p, g);
+        acc += grid_eval_slot<LAYOUT>(P, slot, p, g);
         acc += g.x + g.y + g.z;
     }
     // keeps the loads live without a store per thread: written only if the sum is this exact value
@@ -42,11 +43,14 @@ __global__ void __launch_bounds__(256) gather_probe_kernel(const PvPocket* __res
 }
 
 cudaError_t launch_gather_probe(const PvPocket* pockets_dev, int n_pockets, int n_slots, long long n_points,
-                                uint32_t seed, float* sink, int n_sm, cudaStream_t s) {
+                                uint32_t seed, float* sink, int n_sm, int layout, cudaStream_t s) {
     const int threads = 256;
     const long long blocks_needed = (n_points + threads - 1) / threads;
-    const int grid = (int)std::min<long long>(blocks_needed, (long long)n_sm * 8);
-    gather_probe_kernel<<<std::max(grid, 1), threads, 0, s>>>(pockets_dev, n_pockets, n_slots, n_points, seed, sink);
+    const int grid = std::max(1, (int)std::min<long long>(blocks_needed, (long long)n_sm * 8));
+    if (layout == 1)
+        gather_probe_kernel<1><<<grid, threads, 0, s>>>(pockets_dev, n_pockets, n_slots, n_points, seed, sink);
+    else
+        gather_probe_kernel<0><<<grid, threads, 0, s>>>(pockets_dev, n_pockets, n_slots, n_points, seed, sink);
     return cudaGetLastError();
 }
 

@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(kScoreWarps * 32) score_kernel(ScoreArgs A) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_rot = L.h.n_rot, n = L.h.n_atoms, nt = 6 + n_rot;
     WarpScratch& S = scratch[warp];
+    init_scratch<32>(S);
     Site site;
     site.maps = s_pocket.maps;
     site.P = &s_pocket;
@@ -171,6 +172,7 @@ __global__ void __launch_bounds__(kScoreWarps * 32) score_xyz_kernel(ScoreXyzArg
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = L.h.n_atoms;
     WarpScratch& S = scratch[warp];
+    init_scratch<32>(S);
     Site site;
     site.maps = s_pocket.maps;
     site.P = &s_pocket;

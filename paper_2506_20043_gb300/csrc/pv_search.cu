@@ -43,19 +43,20 @@ struct VariantEntry {
     int lanes;
 };
 static const VariantEntry kVariants[kSearchVariants] = {
-    {(const void*)search_round_kernel<512, 1, 32, false>, 512, 32},   // widest register budget
-    {(const void*)search_round_kernel<128, 5, 32, false>, 128, 32},
-    {(const void*)search_round_kernel<128, 6, 32, false>, 128, 32},
-    {(const void*)search_round_kernel<128, 8, 32, false>, 128, 32},   // 64 registers
-    {(const void*)search_round_kernel<512, 1, 16, false>, 512, 16},   // two chains per warp
-    {(const void*)search_round_kernel<128, 5, 16, false>, 128, 16},
-    {(const void*)search_round_kernel<128, 6, 16, false>, 128, 16},
-    {(const void*)search_round_kernel<128, 8, 16, false>, 128, 16},
+    {(const void*)search_round_kernel<512, 1, 32, false, 0>, 512, 32},   // widest register budget
+    {(const void*)search_round_kernel<128, 5, 32, false, 0>, 128, 32},
+    {(const void*)search_round_kernel<128, 6, 32, false, 0>, 128, 32},
+    {(const void*)search_round_kernel<128, 8, 32, false, 0>, 128, 32},   // 64 registers
+    {(const void*)search_round_kernel<512, 1, 16, false, 0>, 512, 16},   // two chains per warp
+    {(const void*)search_round_kernel<128, 5, 16, false, 0>, 128, 16},
+    {(const void*)search_round_kernel<128, 6, 16, false, 0>, 128, 16},
+    {(const void*)search_round_kernel<128, 8, 16, false, 0>, 128, 16},
 };
-static int g_variant_smem[2][kSearchVariants][64];
+static int g_variant_smem[4][kSearchVariants][64];
 
-// The kernel of a variant, with or without the consistency check.
-static const void* variant_fn(int variant, bool focc) {
+// The kernel of a variant, with or without the consistency check, for a map layout.
+static const void* variant_fn(int variant, bool focc, int layout) {
+    if (layout == 1) return focc ? search_focc_packed_kernel(variant) : search_packed_kernel(variant);
     return focc ? search_focc_kernel(variant) : kVariants[variant].fn;
 }
 
@@ -69,11 +70,12 @@ int search_variant_lanes(int variant) {
     return kVariants[variant].lanes;
 }
 
-cudaError_t search_max_ctas_per_sm(int variant, bool focc, int warps, int smem, int* out) {
-    if (variant < 0 || variant >= kSearchVariants || warps * 32 > kVariants[variant].max_threads)
+cudaError_t search_max_ctas_per_sm(int variant, bool focc, int layout, int warps, int smem, int* out) {
+    if (variant < 0 || variant >= kSearchVariants || warps * 32 > kVariants[variant].max_threads ||
+        (layout != 0 && layout != 1))
         return cudaErrorInvalidValue;
-    const void* fn = variant_fn(variant, focc);
-    cudaError_t e = ensure_smem(fn, smem, g_variant_smem[focc ? 1 : 0][variant]);
+    const void* fn = variant_fn(variant, focc, layout);
+    cudaError_t e = ensure_smem(fn, smem, g_variant_smem[2 * layout + (focc ? 1 : 0)][variant]);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fn, warps * 32, smem);
 }
@@ -82,10 +84,10 @@ cudaError_t launch_search_round(const SearchArgs& a, int variant, int grid, int 
     if (variant < 0 || variant >= kSearchVariants || warps * 32 > kVariants[variant].max_threads)
         return cudaErrorInvalidValue;
     const bool focc = a.C.focc > 0;
-    if (focc && !a.ring) return cudaErrorInvalidValue;
-    const void* fn = variant_fn(variant, focc);
+    if ((focc && !a.ring) || (a.layout != 0 && a.layout != 1)) return cudaErrorInvalidValue;
+    const void* fn = variant_fn(variant, focc, a.layout);
     const int smem = search_smem_bytes(a.lig_smem_bytes, warps, kVariants[variant].lanes);
-    cudaError_t e = ensure_smem(fn, smem, g_variant_smem[focc ? 1 : 0][variant]);
+    cudaError_t e = ensure_smem(fn, smem, g_variant_smem[2 * a.layout + (focc ? 1 : 0)][variant]);
     if (e != cudaSuccess) return e;
     void* args[] = {(void*)&a};
     return cudaLaunchKernel(fn, dim3(grid), dim3(warps * 32), args, (size_t)smem, s);
@@ -192,6 +194,7 @@ __global__ void __launch_bounds__(kTopkThreads) topk_kernel(TopkArgs A) {
     __shared__ int s_nkept, s_status;
     __shared__ PvPocket s_pocket;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    init_scratch<32>(scratch[warp]);
     const PvPairDesc pd = A.pairs[pair];
     if (threadIdx.x < (int)(sizeof(PvPocket) / 4))
         reinterpret_cast<int*>(&s_pocket)[threadIdx.x] =
@@ -365,7 +368,6 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs A) {
     int* vals = reinterpret_cast<int*>(keys + n_sort);
     for (int i = threadIdx.x; i < n_sort; i += blockDim.x) {
         unsigned long long k = ~0ull;
-        int v = -1;
         if (i < n_ent) {
             const int pair = A.lig_pairs[p0 + i / A.top_k];
             const int slot = i % A.top_k;
@@ -373,12 +375,10 @@ __global__ void __launch_bounds__(256) merge_kernel(MergeArgs A) {
                 const PvPoseRec r = A.poses[(size_t)pair * A.top_k + slot];
                 k = ((unsigned long long)order_key(r.score) << 32) |
                     ((unsigned long long)(r.pocket & 0xffff) << 16) | (unsigned)(r.chain & 0xffff);
-                v = pair * A.top_k + slot;
             }
         }
         keys[i] = k;
         vals[i] = i;   // position, resolved to the pose index after sorting
-        (void)v;
     }
     __syncthreads();
     // sort (key, position) pairs: fold the position into the low bits of a second pass-free key

@@ -14,8 +14,8 @@ __device__ __forceinline__ int slot_of(uint64_t lo, uint64_t hi, int xs) {
 // each atom's map slot into bits 16-23 of its packed word. Ends with __syncthreads().
 __device__ __forceinline__ void stage_ligand(PvLigBlob* dst, const PvLigBlob* __restrict__ src,
                                              uint64_t slots_lo, uint64_t slots_hi) {
-    const int pair_words = src->h.n_rounds * 32 + src->h.n_rounds16 * 16;
-    const int words = (PV_LIG_FIXED_BYTES + pair_words * 4 + 15) / 16;
+    const int pair_slots = src->h.n_rounds * 32 + src->h.n_rounds16 * 16;
+    const int words = (PV_LIG_FIXED_BYTES + pair_slots * (int)sizeof(PvPairSlot) + 15) / 16;
     const int4* s = reinterpret_cast<const int4*>(src);
     int4* d = reinterpret_cast<int4*>(dst);
     for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = __ldg(s + i);

@@ -53,9 +53,9 @@ static __device__ __noinline__ float thread_eval(ThreadChain& c, ThreadWork& w, 
     }
     const int slots = L->h.n_rounds * 32;
     for (int k = 0; k < slots; ++k) {
-        const uint32_t pw = L->pairs[k];
+        const uint32_t pw = (uint32_t)L->pairs[k].meta;
         if (!(pw >> 31)) continue;
-        const int i = (k & 31) + 32 * ((pw >> 6) & 1), j = pw & 63;
+        const int i = (k & 31) + 32 * ((pw >> 7) & 1), j = pw & 127;
         const float dx = w.x[i][0] - w.x[j][0], dy = w.x[i][1] - w.x[j][1], dz = w.x[i][2] - w.x[j][2];
         const float r2 = dx * dx + dy * dy + dz * dz;
         if (r2 >= kCutoff2) continue;

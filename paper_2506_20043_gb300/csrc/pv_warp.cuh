@@ -30,7 +30,8 @@ struct ChainScalars {
 };
 
 struct WarpScratch {            // one per team
-    float4 x[64];               // posed coordinates; w = XS radius
+    float4 x[65];               // posed coordinates, w = XS radius; [64] the far dummy atom that
+                                // empty pair slots point to (init_scratch)
     float4 g[64];               // dSF/dx
     float hs[PV_MAX_M][32];     // L-BFGS history: s vectors, lane = tangent coordinate
     float hy[PV_MAX_M][32];     //                 y vectors
@@ -85,9 +86,17 @@ struct Site {                      // where a pose is scored
     const PvPocket* P;             // pocket geometry (shared or global memory)
 };
 
-// Pair words of the team width's schedule.
+// Places the far dummy atom of a team's scratch (once per kernel, before its first evaluation):
+// empty pair slots point to it, and its distance to any atom is far beyond the cutoff.
 template <int LANES>
-__device__ __forceinline__ const uint32_t* pair_rounds(const PvLigBlob& L, int& rounds) {
+__device__ __forceinline__ void init_scratch(WarpScratch& S) {
+    if ((threadIdx.x & (LANES - 1)) == 0) S.x[PV_DUMMY_ATOM] = make_float4(1e15f, 1e15f, 1e15f, 0.f);
+    __syncwarp();
+}
+
+// Pair slots of the team width's schedule.
+template <int LANES>
+__device__ __forceinline__ const PvPairSlot* pair_rounds(const PvLigBlob& L, int& rounds) {
     if (LANES == 32) {
         rounds = L.h.n_rounds;
         return L.pairs;
@@ -169,14 +178,16 @@ __device__ __forceinline__ void team_fk(const PvLigBlob& L, WarpScratch& S, cons
     axw = mat_vec(M, axis);   // the hinge axis in the world frame (rotating about it keeps it)
 }
 
-// The lane's pair of one round (source atom xi, partner position xj): its energy and the force
-// on the source, which the target's lane receives with the opposite sign.
-__device__ __forceinline__ float3 pair_force(uint32_t pw, const float4& xi, const float4& xj, float& e_intra) {
+// The lane's pair of one round (source atom xi, partner position xj, the slot's ramp constants):
+// its energy and the force on the source, which the target's lane receives with the opposite
+// sign. An empty slot's partner is the far dummy atom: beyond the cutoff, it adds nothing.
+__device__ __forceinline__ float3 pair_force(const PvPairSlot& ps, const float4& xi, const float4& xj,
+                                             float& e_intra) {
     const float3 d = make_float3(xi.x - xj.x, xi.y - xj.y, xi.z - xj.z);
     const float r2 = dot3(d, d);
-    const bool live = (pw >> 31) && r2 < kCutoff2;
+    const bool live = r2 < kCutoff2;
     float c;
-    const float e = vina_pair_r2(r2, xi.w + xj.w, (pw >> 16) & 1, (pw >> 17) & 1, c);
+    const float e = vina_pair_ramp(r2, xi.w + xj.w, ps.c0, ps.c1, ps.w, c);
     e_intra += live ? e : 0.f;
     c = live ? c : 0.f;
     return c * d;
@@ -186,7 +197,7 @@ __device__ __forceinline__ float3 pair_force(uint32_t pw, const float4& xi, cons
 // component k). parts (optional, lane-uniform): e_inter, e_intra. On return S.g holds dSF/dx of
 // every atom (device order). FK = false: the atoms are already posed in S.x (device order, w = XS
 // radius, written and synced by the caller), x is not used and there is no tangent gradient.
-template <int LANES, bool FK = true>
+template <int LANES, bool FK = true, int LAYOUT = 0>
 __device__ __forceinline__ float team_eval(const PvLigBlob& L, WarpScratch& S, const Site& site,
                                            const Pose& x, float& grad, bool want_grad,
                                            float* parts = nullptr) {
@@ -213,7 +224,7 @@ __device__ __forceinline__ float team_eval(const PvLigBlob& L, WarpScratch& S, c
         if (a < n) {
             const int w = __float_as_int(L.atom[a].w);
             const int slot = (w >> 16) & 255;
-            e_inter += grid_eval(site.maps + (long long)slot * P.nxyz, P, f3(own[h]), acc[h]);
+            e_inter += grid_eval_slot<LAYOUT>(P, slot, f3(own[h]), acc[h]);
         }
     }
     Tm::sync();
@@ -222,35 +233,35 @@ __device__ __forceinline__ float team_eval(const PvLigBlob& L, WarpScratch& S, c
     // registers and rounds need no barrier; positions and pair words are read-only here, so the
     // next round's word and partner position are loaded ahead.
     int rounds;
-    const uint32_t* pr = pair_rounds<LANES>(L, rounds);
+    const PvPairSlot* pr = pair_rounds<LANES>(L, rounds);
     if (rounds > 0) {
-        uint32_t pw = pr[tl];
-        float4 xj = S.x[pw & 63];
+        PvPairSlot ps = pr[tl];
+        float4 xj = S.x[ps.meta & 127];
         if (n <= LANES) {                     // every atom of a pair is its lane's first
             for (int r = 0; r < rounds; ++r) {
-                const uint32_t pw_n = r + 1 < rounds ? pr[(r + 1) * LANES + tl] : 0u;
-                const float4 xj_n = S.x[pw_n & 63];
-                const float3 f = pair_force(pw, own[0], xj, e_intra);
-                const float3 fi = Tm::shfl3(f, (pw >> 8) & (LANES - 1));
+                const PvPairSlot ps_n = pr[min(r + 1, rounds - 1) * LANES + tl];
+                const float4 xj_n = S.x[ps_n.meta & 127];
+                const float3 f = pair_force(ps, own[0], xj, e_intra);
+                const float3 fi = Tm::shfl3(f, (ps.meta >> 8) & (LANES - 1));
                 acc[0] = acc[0] + f;
-                if ((pw >> 13) & 1) acc[0] = acc[0] - fi;
-                pw = pw_n;
+                if ((ps.meta >> 13) & 1) acc[0] = acc[0] - fi;
+                ps = ps_n;
                 xj = xj_n;
             }
         } else {
             for (int r = 0; r < rounds; ++r) {
-                const uint32_t pw_n = r + 1 < rounds ? pr[(r + 1) * LANES + tl] : 0u;
-                const float4 xj_n = S.x[pw_n & 63];
-                const bool hs = (pw >> 6) & 1, hr = (pw >> 14) & 1;
-                const float3 f = pair_force(pw, hs ? own[1] : own[0], xj, e_intra);
-                const float3 fi = Tm::shfl3(f, (pw >> 8) & (LANES - 1));
+                const PvPairSlot ps_n = pr[min(r + 1, rounds - 1) * LANES + tl];
+                const float4 xj_n = S.x[ps_n.meta & 127];
+                const bool hs = (ps.meta >> 7) & 1, hr = (ps.meta >> 14) & 1;
+                const float3 f = pair_force(ps, hs ? own[1] : own[0], xj, e_intra);
+                const float3 fi = Tm::shfl3(f, (ps.meta >> 8) & (LANES - 1));
                 if (hs) acc[1] = acc[1] + f;
                 else acc[0] = acc[0] + f;
-                if ((pw >> 13) & 1) {
+                if ((ps.meta >> 13) & 1) {
                     if (hr) acc[1] = acc[1] - fi;
                     else acc[0] = acc[0] - fi;
                 }
-                pw = pw_n;
+                ps = ps_n;
                 xj = xj_n;
             }
         }

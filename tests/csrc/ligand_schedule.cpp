@@ -5,7 +5,8 @@
 
 #include "pv_ligand.h"
 
-// Copies the schedule of the given team width (32 or 16 lanes): words[r * lanes + l], and the input
+// Copies the schedule of the given team width (32 or 16 lanes): the meta word of each slot,
+// words[r * lanes + l], and the input
 // index of every device atom. info = n_rounds, n_rounds16, team16, n_pairs, n_atoms. Returns the
 // number of rounds copied, or a negative code.
 extern "C" int lig_schedule(int n_atoms, const float* xyz, const uint8_t* el, const uint8_t* don,
@@ -24,8 +25,8 @@ extern "C" int lig_schedule(int n_atoms, const float* xyz, const uint8_t* el, co
     if (lanes != 32 && lanes != 16) return -2;
     const int rounds = lanes == 32 ? L->h.n_rounds : L->h.n_rounds16;
     if (rounds * lanes > max_words) return -3;
-    const uint32_t* w0 = L->pairs + (lanes == 32 ? 0 : L->h.n_rounds * 32);
-    for (int i = 0; i < rounds * lanes; ++i) words[i] = w0[i];
+    const PvPairSlot* w0 = L->pairs + (lanes == 32 ? 0 : L->h.n_rounds * 32);
+    for (int i = 0; i < rounds * lanes; ++i) words[i] = (uint32_t)w0[i].meta;
     for (int a = 0; a < L->h.n_atoms; ++a) atom_src[a] = L->atom_src[a];
     return rounds;
 }

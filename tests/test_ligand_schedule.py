@@ -56,7 +56,7 @@ def _decode(lib, lig, lanes):
         for l in range(lanes):
             w = int(words[r * lanes + l])
             if w >> 31:
-                s_dev, t_dev = l + lanes * ((w >> 6) & 1), w & 63
+                s_dev, t_dev = l + lanes * ((w >> 7) & 1), w & 127
                 assert s_dev < n and t_dev < n
                 sent.append((r, l, int(src[s_dev]), int(src[t_dev]), (w >> 16) & 1, (w >> 17) & 1))
             if (w >> 13) & 1:
