@@ -305,10 +305,12 @@ typedef struct {
  * map_layout -1.
  * Autotuning (warps_per_cta 0, search_variant -1, or map_layout -1 on a set holding both layouts):
  * the first batched dock of a ligand-size bucket on a context times each candidate launch shape on
- * 32 MC steps of its own work items, the fastest of three runs (results are unaffected: the dock
- * itself restarts every chain); a candidate displaces the first one tried only when it is faster
- * by more than 2 %, so that shapes within the trials' noise do not alternate between runs. The
- * chosen shape is then timed on the cell-packed maps too, with the same margin. */
+ * 32 MC steps of its own work items (after 16 untimed steps from the random starts), the fastest of
+ * three runs, per score evaluation the trial ran
+ * (results are unaffected: the dock itself restarts every chain); a candidate displaces the first
+ * one tried only when it is faster by more than 2 %, so that shapes within the trials' noise do not
+ * alternate between runs. The chosen shape is then timed on the cell-packed maps too, with the same
+ * margin. */
 void pv_dock_params_default(pv_dock_params* p);
 
 /* Docks every ligand into every listed pocket (Supplementary Algorithms 2 and 3). Pair

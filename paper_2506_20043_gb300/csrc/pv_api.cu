@@ -1000,20 +1000,21 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     M.rank_stride = R->rank_stride;
     M.ranking = R->d_ranking;
     // autotuning: time each candidate launch shape on kTuneSteps MC steps of its own first work
-    // items (long enough that chains which share a CTA even out, as over a real step block), the
-    // faster of three runs; then, if the set holds cell-packed maps too, the chosen shape on them.
+    // items (long enough that chains which share a CTA even out, as over a real step block), after
+    // kWarmSteps untimed steps from the random starts, per score evaluation, the best of three runs;
+    // then, if the set holds cell-packed maps too, the chosen shape on them.
     // A candidate replaces the incumbent (the first candidate, a fixed preference order) only when
     // it is faster by more than kTuneMargin, so that shapes within the trials' noise do not flip
     // between runs.
     if (need_tune) {
-        constexpr int kTuneSteps = 32;
+        constexpr int kWarmSteps = 16, kTuneSteps = 32;
         constexpr float kTuneMargin = 0.02f;
-        static const int cand[][2] = {{0, 2}, {0, 1}, {0, 4}, {0, 8}, {1, 4}, {2, 4}, {3, 4},
-                                      {4, 2}, {4, 1}, {4, 4}, {5, 4}, {6, 4}, {7, 4}};
+        static const int cand[][2] = {{0, 2}, {0, 1}, {0, 4}, {0, 8}, {1, 2}, {1, 4}, {2, 2}, {2, 4}, {3, 4},
+                                      {4, 2}, {4, 1}, {4, 4}, {5, 2}, {5, 4}, {6, 4}, {7, 4}};
         cudaEvent_t t0, t1;
         cudaEventCreate(&t0);
         cudaEventCreate(&t1);
-        // per-chain time of one shape and layout; < 0 when the shape does not fit
+        // time per score evaluation of one shape and layout; < 0 when the shape does not fit
         auto trial = [&](int v, int wc, int lay, float& per_chain) -> cudaError_t {
             per_chain = -1.f;
             const int lanes_c = search_variant_lanes(v);
@@ -1036,32 +1037,41 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
             a.n_items = 0;                       // an empty launch first: loads the variant's code
             a.queue = ctr + 1;
             a.step0 = 0;
-            a.step1 = std::min(p.steps, kTuneSteps);
+            a.step1 = kWarmSteps;
             a.items_per_block = n_trial;         // one step block
-            a.block_steps = kTuneSteps;
+            a.block_steps = kWarmSteps + kTuneSteps;
             a.layout = lay;
+            const int grid_c = std::max(1, std::min(n_trial, ctx->sms * occ_c));
             cudaError_t x = cudaMemcpyAsync((char*)R->d_work + o_items, trial_items.data(), sizeof(PvItem) * n_trial,
                                             cudaMemcpyHostToDevice, ctx->stream);
             if (x == cudaSuccess) x = cudaMemsetAsync(ctr, 0, sizeof(int) * 2, ctx->stream);
             if (x == cudaSuccess) x = launch_search_round(a, v, 1, wc, ctx->stream);
+            // untimed: the chains' first steps from their random starts, so that the timed steps run
+            // from the states most of a real launch's step blocks start from
             a.n_items = n_trial;
-            float ms = 1e30f;
+            if (x == cudaSuccess) x = cudaMemsetAsync(ctr, 0, sizeof(int) * 2, ctx->stream);
+            if (x == cudaSuccess) x = launch_mark_t0(evals + 1, ctx->stream);
+            if (x == cudaSuccess) x = launch_search_round(a, v, grid_c, wc, ctx->stream);
+            a.step0 = kWarmSteps;
+            a.step1 = kWarmSteps + kTuneSteps;
+            float best = 1e30f;
             for (int rep = 0; rep < 3 && x == cudaSuccess; ++rep) {   // the fastest of three runs
                 x = cudaMemsetAsync(ctr, 0, sizeof(int) * 2, ctx->stream);
+                if (x == cudaSuccess) x = cudaMemsetAsync(evals, 0, sizeof(unsigned long long), ctx->stream);
                 if (x == cudaSuccess) x = launch_mark_t0(evals + 1, ctx->stream);
                 if (x == cudaSuccess) x = cudaEventRecord(t0, ctx->stream);
-                if (x == cudaSuccess)
-                    x = launch_search_round(a, v, std::max(1, std::min(n_trial, ctx->sms * occ_c)), wc, ctx->stream);
+                if (x == cudaSuccess) x = launch_search_round(a, v, grid_c, wc, ctx->stream);
                 if (x == cudaSuccess) x = cudaEventRecord(t1, ctx->stream);
                 if (x == cudaSuccess) x = cudaEventSynchronize(t1);
                 float t = 0.f;
+                unsigned long long n_ev = 0;
                 if (x == cudaSuccess) x = cudaEventElapsedTime(&t, t0, t1);
-                if (x == cudaSuccess) ms = std::min(ms, t);
+                if (x == cudaSuccess) x = cudaMemcpy(&n_ev, evals, sizeof(n_ev), cudaMemcpyDeviceToHost);
+                // per score evaluation: shapes of different CTA sizes run different sets of chains
+                // (of different pockets) in their trial waves, and chains differ in cost
+                if (x == cudaSuccess && n_ev > 0) best = std::min(best, t / (float)n_ev);
             }
-            // per unit of work: the trials cover different numbers of chains
-            if (x == cudaSuccess)
-                per_chain = ms / (float)std::min<long long>((long long)n_trial * wc * (32 / lanes_c),
-                                                           (long long)n_pairs * p.chains);
+            if (x == cudaSuccess && best < 1e30f) per_chain = best;
             return x;
         };
         float best_ms = -1.f;

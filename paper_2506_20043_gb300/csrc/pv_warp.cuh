@@ -315,8 +315,9 @@ __device__ __forceinline__ float team_eval(const PvLigBlob& L, WarpScratch& S, c
         const int nt = 6 + L.h.n_rot;
         const int src = (tl >= 6 && tl < nt) ? L.tor_frag[tl - 6] * k : tl;
         float gp = Tm::shfl(gpsi, src);
-        float c3[6] = {F.x, F.y, F.z, tau.x, tau.y, tau.z};
-        grad = tl < 6 ? c3[tl] : (tl < nt ? gp : 0.f);
+        // lane k takes component k (a select chain: an array indexed by the lane would live in local memory)
+        const float rt = tl == 0 ? F.x : (tl == 1 ? F.y : (tl == 2 ? F.z : (tl == 3 ? tau.x : (tl == 4 ? tau.y : tau.z))));
+        grad = tl < 6 ? rt : (tl < nt ? gp : 0.f);
     }
     Tm::sync();
     return ei + ej;
@@ -424,8 +425,9 @@ __device__ __forceinline__ float mutate(const PvLigBlob& L, Pose& x, uint32_t ch
 template <int LANES>
 __device__ __forceinline__ void store_pose(float* dst, const Pose& x, int n_rot) {
     const int tl = Team<LANES>::lane();
-    float v[7] = {x.T.x, x.T.y, x.T.z, x.q.x, x.q.y, x.q.z, x.q.w};
-    if (tl < 7) dst[tl] = v[tl];
+    const float v = tl == 0 ? x.T.x : (tl == 1 ? x.T.y : (tl == 2 ? x.T.z : (tl == 3 ? x.q.x : (tl == 4 ? x.q.y :
+                    (tl == 5 ? x.q.z : x.q.w)))));
+    if (tl < 7) dst[tl] = v;
     if (tl >= 6 && tl < 6 + n_rot) dst[tl + 1] = x.psi;
 }
 template <int LANES>

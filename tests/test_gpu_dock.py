@@ -109,7 +109,7 @@ def test_tiny_workload_best_score_parity(tiny):
     r = ctx.dock(gs, [pl], [0], chains=64, steps=1000, seed=0)
     _, es = r.chain_records()
     assert abs(es[0].min() - ref_es.min()) <= 0.2, (es[0].min(), ref_es.min())
-    assert r.poses[0][0]["score"] == pytest.approx(es[0].min(), abs=1e-6)
+    assert r.poses[0][0]["score"] == pytest.approx(es[0].min(), abs=1e-5)
 
 
 def test_bitwise_determinism_across_launch_settings(tiny):

@@ -59,7 +59,8 @@ def test_headline_shape_best_score_and_top_pocket_match_oracle():
         ref = rows[(SEED, li)]
         ok_score.append(abs(best[li].min() - ref.min()) <= 0.2)
         top = flat[r.ranking(li)[0]]
-        assert top["score"] == pytest.approx(best[li].min(), abs=1e-6)
+        # the selection re-evaluates the pose, summing e_inter and e_intra separately: the last bits differ
+        assert top["score"] == pytest.approx(best[li].min(), abs=1e-5)
         ok_pocket.append(int(top["pocket"]) == int(ref.argmin()))
     ok = np.array(ok_score) & np.array(ok_pocket)
     diff = np.abs(best.min(axis=1) - np.array([rows[(SEED, li)].min() for li in range(N_LIGANDS)]))
