@@ -625,7 +625,7 @@ extern "C" pv_status pv_score(pv_context* ctx, const pv_grid_set* set, const pv_
     if (n_poses == 0) return PV_OK;
     if (!dev_pose || !dev_energy) return fail(ctx, PV_ERR_ARG, "pose and energy required");
     DeviceGuard g(ctx->device);
-    PV_CU(ctx, launch_score((const PvLigBlob*)lig->d_blob, (int)lig->rec.blob.size(), set->d_pockets + pocket,
+    PV_CU(ctx, launch_score((const PvLigBlob*)lig->d_blob, lig->rec.staged32, set->d_pockets + pocket,
                             slots_of(set), n_poses, 7 + lig->rec.n_rot, dev_pose, dev_energy, dev_grad, dev_parts,
                             nullptr, nullptr, nullptr, ctx->stream));
     return PV_OK;
@@ -640,7 +640,7 @@ extern "C" pv_status pv_score_backward(pv_context* ctx, const pv_grid_set* set, 
     if (!dev_pose || !dev_grad_energy || (!dev_grad_pose && !dev_grad_xyz))
         return fail(ctx, PV_ERR_ARG, "pose, grad_energy and an output required");
     DeviceGuard g(ctx->device);
-    PV_CU(ctx, launch_score((const PvLigBlob*)lig->d_blob, (int)lig->rec.blob.size(), set->d_pockets + pocket,
+    PV_CU(ctx, launch_score((const PvLigBlob*)lig->d_blob, lig->rec.staged32, set->d_pockets + pocket,
                             slots_of(set), n_poses, 7 + lig->rec.n_rot, dev_pose, nullptr, nullptr, nullptr,
                             dev_grad_energy, dev_grad_pose, dev_grad_xyz, ctx->stream));
     return PV_OK;
@@ -654,7 +654,7 @@ extern "C" pv_status pv_score_xyz(pv_context* ctx, const pv_grid_set* set, const
     if (n_poses == 0) return PV_OK;
     if (!dev_xyz || (!dev_energy && !dev_grad_xyz)) return fail(ctx, PV_ERR_ARG, "coordinates and an output required");
     DeviceGuard g(ctx->device);
-    PV_CU(ctx, launch_score_xyz((const PvLigBlob*)lig->d_blob, (int)lig->rec.blob.size(), set->d_pockets + pocket,
+    PV_CU(ctx, launch_score_xyz((const PvLigBlob*)lig->d_blob, lig->rec.staged32, set->d_pockets + pocket,
                                 slots_of(set), n_poses, dev_xyz, dev_grad_energy, dev_energy, dev_grad_xyz,
                                 ctx->stream));
     return PV_OK;
@@ -667,7 +667,7 @@ extern "C" pv_status pv_pose_coords(pv_context* ctx, const pv_ligand* lig, int32
     if (n_poses < 0 || (n_poses > 0 && (!dev_pose || !dev_xyz))) return fail(ctx, PV_ERR_ARG, "bad arguments");
     if (n_poses == 0) return PV_OK;
     DeviceGuard g(ctx->device);
-    PV_CU(ctx, launch_pose_coords((const PvLigBlob*)lig->d_blob, (int)lig->rec.blob.size(), n_poses,
+    PV_CU(ctx, launch_pose_coords((const PvLigBlob*)lig->d_blob, lig->rec.staged32, n_poses,
                                   7 + lig->rec.n_rot, dev_pose, dev_xyz, ctx->stream));
     return PV_OK;
 }
@@ -784,14 +784,15 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
         return fail(ctx, PV_ERR_ARG, "warps_per_cta exceeds the search variant's CTA size");
     if (!(p.temperature > 0.f)) return fail(ctx, PV_ERR_ARG, "temperature must be > 0");
     if (n_pairs < 1) return fail(ctx, PV_ERR_ARG, "no pairs");
-    int max_rot = 0, max_atoms = 0, max_blob = 0;
+    int max_rot = 0, max_atoms = 0, max_stage32 = 0, max_stage16 = 0;
     for (int i = 0; i < n_ligs; ++i) {
         if (!ligs[i] || ligs[i]->ctx != ctx) return fail(ctx, PV_ERR_STATE, "ligand of another context");
         if ((ligs[i]->rec.type_mask & ~set->type_mask) != 0)
             return fail(ctx, PV_ERR_ARG, "grid set lacks a map for a ligand atom type");
         max_rot = std::max(max_rot, ligs[i]->rec.n_rot);
         max_atoms = std::max(max_atoms, ligs[i]->rec.n_atoms);
-        max_blob = std::max(max_blob, (int)ligs[i]->rec.blob.size());
+        max_stage32 = std::max(max_stage32, ligs[i]->rec.staged32);
+        max_stage16 = std::max(max_stage16, ligs[i]->rec.staged16);
     }
     for (int q = 0; q < n_pairs; ++q) {
         if (pair_lig[q] < 0 || pair_lig[q] >= n_ligs) return fail(ctx, PV_ERR_ARG, "pair ligand out of range");
@@ -847,6 +848,8 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     // 16 atoms (one atom per lane; measured +25-35 % evaluations/s), not above (two atoms per lane
     // and twice the pair rounds per chain).
     const int auto_lanes = (all_team16 && max_atoms <= 16) ? 16 : 32;
+    // shared memory of a staged ligand: the record with the schedule of the variant's team width
+    auto stage_bytes = [&](int v) { return search_variant_lanes(v) == 16 ? max_stage16 : max_stage32; };
     int variant = p.search_variant >= 0 ? p.search_variant : (auto_lanes == 16 ? 4 : 0);
     int W = p.warps_per_cta > 0 ? p.warps_per_cta : 4;
     const bool warp_chains = p.mode != PV_MODE_PLAIN;   // batched, or one warp-per-chain launch per pair
@@ -970,7 +973,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     A.block_steps = block_steps;
     A.progress = (int*)(w + o_prog);
     A.C = C;
-    A.lig_smem_bytes = max_blob;
+    A.lig_smem_bytes = stage_bytes(variant);
     A.t0 = evals + 1;
     A.timeout_ns = p.timeout_s > 0 ? (unsigned long long)(p.timeout_s * 1e9) : 0ull;
     A.wait_ns = p.block_wait_s > 0 ? (unsigned long long)(std::min(p.block_wait_s, 1e9) * 1e9) : 30000000000ull;
@@ -984,7 +987,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     T.slots_hi = A.slots_hi;
     T.chains = R->d_chains;
     T.C = C;
-    T.lig_smem_bytes = max_blob;
+    T.lig_smem_bytes = max_stage32;
     T.poses = R->d_poses;
     T.pots = R->d_pots;
     T.xyz = R->d_xyz;
@@ -1007,7 +1010,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     // it is faster by more than kTuneMargin, so that shapes within the trials' noise do not flip
     // between runs.
     if (need_tune) {
-        constexpr int kWarmSteps = 16, kTuneSteps = 32;
+        constexpr int kWarmSteps = 16, kTuneSteps = 32, kTuneBlock = 8;
         constexpr float kTuneMargin = 0.02f;
         static const int cand[][2] = {{0, 2}, {0, 1}, {0, 4}, {0, 8}, {1, 2}, {1, 4}, {2, 2}, {2, 4}, {3, 4},
                                       {4, 2}, {4, 1}, {4, 4}, {5, 2}, {5, 4}, {6, 4}, {7, 4}};
@@ -1019,7 +1022,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
             per_chain = -1.f;
             const int lanes_c = search_variant_lanes(v);
             int occ_c = 0;
-            if (search_max_ctas_per_sm(v, p.focc > 0, lay, wc, search_smem_bytes(max_blob, wc, lanes_c), &occ_c) !=
+            if (search_max_ctas_per_sm(v, p.focc > 0, lay, wc, search_smem_bytes(stage_bytes(v), wc, lanes_c), &occ_c) !=
                     cudaSuccess ||
                 occ_c < 1) {
                 cudaGetLastError();
@@ -1041,6 +1044,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
             a.items_per_block = n_trial;         // one step block
             a.block_steps = kWarmSteps + kTuneSteps;
             a.layout = lay;
+            a.lig_smem_bytes = stage_bytes(v);
             const int grid_c = std::max(1, std::min(n_trial, ctx->sms * occ_c));
             cudaError_t x = cudaMemcpyAsync((char*)R->d_work + o_items, trial_items.data(), sizeof(PvItem) * n_trial,
                                             cudaMemcpyHostToDevice, ctx->stream);
@@ -1052,11 +1056,17 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
             if (x == cudaSuccess) x = cudaMemsetAsync(ctr, 0, sizeof(int) * 2, ctx->stream);
             if (x == cudaSuccess) x = launch_mark_t0(evals + 1, ctx->stream);
             if (x == cudaSuccess) x = launch_search_round(a, v, grid_c, wc, ctx->stream);
+            // timed: the real launch's structure, chained step blocks of kTuneBlock steps handed out by
+            // the queue, so that no trial ends on a few long items (one 32-step block per item left the
+            // trial's time to the slowest CTA of its last wave, which favoured large CTAs)
             a.step0 = kWarmSteps;
             a.step1 = kWarmSteps + kTuneSteps;
+            a.block_steps = kTuneBlock;
+            a.n_items = n_trial * (kTuneSteps / kTuneBlock);
             float best = 1e30f;
             for (int rep = 0; rep < 3 && x == cudaSuccess; ++rep) {   // the fastest of three runs
                 x = cudaMemsetAsync(ctr, 0, sizeof(int) * 2, ctx->stream);
+                if (x == cudaSuccess) x = cudaMemsetAsync(a.progress, 0, sizeof(int) * (size_t)n_trial, ctx->stream);
                 if (x == cudaSuccess) x = cudaMemsetAsync(evals, 0, sizeof(unsigned long long), ctx->stream);
                 if (x == cudaSuccess) x = launch_mark_t0(evals + 1, ctx->stream);
                 if (x == cudaSuccess) x = cudaEventRecord(t0, ctx->stream);
@@ -1126,7 +1136,8 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     }
     // grid of the persistent rounds: every SM filled to its occupancy
     int occ = 0;
-    const int smem = search_smem_bytes(max_blob, W, search_variant_lanes(variant));
+    A.lig_smem_bytes = stage_bytes(variant);
+    const int smem = search_smem_bytes(A.lig_smem_bytes, W, search_variant_lanes(variant));
     e = search_max_ctas_per_sm(variant, p.focc > 0, layout, W, smem, &occ);
     if (e != cudaSuccess || occ < 1) {
         result_free(R);

@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(THREADS, MIN_CTAS) search_round_kernel(SearchA
                 reinterpret_cast<const int*>(A.pockets + pd.pocket)[threadIdx.x];
         __syncthreads();
         if (reload) {
-            stage_ligand(&L, A.ligs[pd.ligand], A.slots_lo, A.slots_hi);
+            stage_ligand<LANES>(&L, A.ligs[pd.ligand], A.slots_lo, A.slots_hi);
             if (threadIdx.x == 0) s_lig = pd.ligand;
         }
         if (threadIdx.x == 0) {

@@ -8,7 +8,7 @@
 #define PV_MAX_POT 33         // 7 + 26 torsions
 #define PV_MAX_TAN 32         // 6 + 26 torsions: one lane per tangent coordinate
 #define PV_MAX_ROUNDS 128     // intra pair rounds of <= 32 disjoint pairs
-#define PV_MAX_M 8            // L-BFGS memory
+#define PV_MAX_M 5            // L-BFGS memory (pairs kept)
 #define PV_CHAIN_STRIDE 80    // floats per chain record (see PvChain)
 
 // Ligand record, identical in global and shared memory. Atoms are stored in device order:
@@ -22,7 +22,9 @@ struct PvLigHeader {
     int32_t type_mask;    // bit t set if XS type t occurs
     int32_t n_rounds16;   // pair rounds of the half-warp schedule (stored after the warp schedule)
     int32_t team16;       // 1 if the ligand fits a half-warp team (<= 32 atoms, <= 10 torsions)
-    int32_t pad[3];
+    int32_t pairs16_at;   // slot index in `pairs` where the half-warp schedule starts (a copy staged
+                          // for half-warp teams holds that schedule alone, at 0)
+    int32_t pad[2];
 };
 
 // One lane's share of one intra-pair round (16 bytes). meta bits: 0-6 the partner atom of the pair
@@ -52,6 +54,10 @@ struct PvLigBlob {
                                      // slots (half-warp schedule); slot l of a round is lane l's
 };
 #define PV_LIG_FIXED_BYTES ((int)offsetof(PvLigBlob, pairs))
+// bytes of a ligand record staged for a team of `lanes` lanes: the fixed part and that width's
+// pair schedule only
+#define PV_LIG_STAGED_BYTES(n_rounds, n_rounds16, lanes) \
+    (PV_LIG_FIXED_BYTES + ((lanes) == 32 ? (n_rounds) * 32 : (n_rounds16) * 16) * (int)sizeof(PvPairSlot))
 
 // One pocket box of a grid set.
 struct PvPocket {

@@ -311,6 +311,7 @@ bool build_ligand(const LigandInput& in, LigandRecord& out, std::string& err) {
     L->h.type_mask = type_mask;
     L->h.n_rounds16 = n_rounds16;
     L->h.team16 = team16 ? 1 : 0;
+    L->h.pairs16_at = n_rounds * 32;
     double g2 = 0.0;
     for (int i = 0; i < n; ++i)
         for (int k = 0; k < 3; ++k) {
@@ -365,6 +366,8 @@ bool build_ligand(const LigandInput& in, LigandRecord& out, std::string& err) {
     out.n_rot = n_rot;
     out.n_pairs = (int)pairs.size();
     out.n_rounds = n_rounds;
+    out.staged32 = PV_LIG_STAGED_BYTES(n_rounds, n_rounds16, 32);
+    out.staged16 = PV_LIG_STAGED_BYTES(n_rounds, n_rounds16, 16);
     out.origin = origin;
     out.type_mask = type_mask;
     out.team16 = team16;

@@ -23,6 +23,7 @@ struct LigandRecord {
     std::vector<uint8_t> blob;   // PvLigBlob followed by the pair rounds, 16-byte padded
     std::vector<uint8_t> xs;     // XS type per input atom
     int n_atoms = 0, n_rot = 0, n_pairs = 0, n_rounds = 0, origin = 0, type_mask = 0;
+    int staged32 = 0, staged16 = 0;   // bytes of the record staged for a warp / half-warp team
     int subtree_atoms = 0;       // sum over torsions of the atoms each one moves
     bool team16 = false;         // fits a half-warp team
 };

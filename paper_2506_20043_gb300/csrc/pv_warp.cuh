@@ -102,7 +102,7 @@ __device__ __forceinline__ const PvPairSlot* pair_rounds(const PvLigBlob& L, int
         return L.pairs;
     }
     rounds = L.h.n_rounds16;
-    return L.pairs + L.h.n_rounds * 32;
+    return L.pairs + L.h.pairs16_at;
 }
 
 // Forward kinematics (Eq. 1: position, orientation, torsions -> atom coordinates). Writes S.x.
