@@ -32,12 +32,16 @@ struct ChainScalars {
 struct WarpScratch {            // one per team
     float4 x[65];               // posed coordinates, w = XS radius; [64] the far dummy atom that
                                 // empty pair slots point to (init_scratch)
-    float4 g[64];               // dSF/dx
+    union {                     // one lives after the other within an evaluation (synced between):
+        float4 fm[3 * PV_MAX_FRAGS];  // during the kinematics: per fragment, its world rotation rows
+                                      // (xyz) with the anchor (w)
+        float4 g[64];                 // after the pair rounds: dSF/dx of every atom, until the next
+                                      // evaluation's kinematics
+    };
     float hs[PV_MAX_M][32];     // L-BFGS history: s vectors, lane = tangent coordinate
     float hy[PV_MAX_M][32];     //                 y vectors
     float cur[40];              // the chain's current POT (MC state)
     float glo[32];              // line search: gradient at the largest Armijo-satisfying trial
-    float4 fm[3 * PV_MAX_FRAGS];// per fragment: world rotation rows (xyz) with the anchor (w)
     ChainScalars cs;
 };
 
