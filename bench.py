@@ -17,6 +17,7 @@ each rank builds only its pockets' maps, and the ranked poses are gathered and m
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -128,6 +129,21 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def stored_grid_profile():
+    """DRAM bytes (read + write) of one map build of the ten boxes, from the committed ncu summary of
+    grid_kernel, if it was taken on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "grid_kernel_multipocket.md")
+    if not os.path.exists(p):
+        return None
+    import re
+    txt = open(p).read()
+    m_hash = re.search(r"kernel source hash at capture:\s*`?([0-9a-f]{16})", txt, re.I)
+    m_tr = re.search(r"dram bytes per launch:\s*([0-9.eE+]+)", txt)
+    if not m_hash or m_hash.group(1) != kernel_source_hash() or not m_tr:
+        return None
+    return float(m_tr.group(1))
+
+
 def stored_profile():
     """Figures of the committed ncu summary of the search kernel, if it was taken on the current
     kernel sources (else {}): 'traffic' = DRAM bytes (read + write) of one launch of the bench's
@@ -186,6 +202,9 @@ def run_ours(args):
     pair_pocket = [local_pocket[p] for _, p, _ in run]
     params = api.DockParams(chains=CHAINS, steps=STEPS, seed=0, top_k=TOP_K, host_copy=False, focc=args.focc,
                             pair_keys=[k for _, _, k in run])
+    if args.shape:   # a fixed launch shape instead of the autotuner's (for profiler captures)
+        v, wc, lay = (int(x) for x in args.shape.split(","))
+        params = dataclasses.replace(params, search_variant=v, warps_per_cta=wc, map_layout=lay)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def step(mid=None):
@@ -316,7 +335,7 @@ def run_ours(args):
                               "peak": round(peak_tflops, 2), "unit": "TFLOP/s",
                               "frac": round(terms * GRID_FLOPS_PER_TERM / map_s / 1e12 / peak_tflops, 4),
                               "term_evals_per_s": round(terms / map_s, 1), "launch_ms": round(map_s * 1e3, 3),
-                              "traffic": None},
+                              "traffic": (round(stored_grid_profile()) if stored_grid_profile() else None)},
             "gpu_launches": args.steps * (6 + 1 + n_rounds + 2),
             "clocks": clocks,
         }
@@ -888,6 +907,8 @@ def main():
     ap.add_argument("--warps", type=int, default=2, help="warps per CTA of --case small")
     ap.add_argument("--small-steps", type=int, default=20, help="MC steps of --case small (one launch)")
     ap.add_argument("--layout", type=int, default=0, choices=[0, 1], help="map layout of --case small (1: cell-packed)")
+    ap.add_argument("--shape", default="", help="variant,warps,layout: fix the headline's launch shape (profiler "
+                                                "captures, whose trials would be profiled too); default autotuned")
     args = ap.parse_args()
     if args.case == "small":
         out = run_small_case(args)
