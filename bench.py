@@ -584,7 +584,8 @@ def run_batch_workload(args):
     stream = ctx.stream
 
     def step():
-        gs = ctx.build_grids(dev_recs[0], boxes[0], types)
+        # both map layouts (appended receptors are packed too): the autotuner picks the one it reads
+        gs = ctx.build_grids(dev_recs[0], boxes[0], types).pack()
         for r in range(1, len(recs)):
             gs.append(dev_recs[r], boxes[r])
         return gs, ctx.dock_pairs(gs, ligs, pair_lig, pair_pocket, params)
@@ -609,6 +610,7 @@ def run_batch_workload(args):
             evals += ev
             search_s += s_s
             shape = r.launch_shape()
+            layout = r.map_layout()
             map_bytes = gs.bytes
     total_t = float(np.sum(times))
     n_pairs = len(pair_lig)
@@ -632,7 +634,8 @@ def run_batch_workload(args):
                        "map_bytes": int(map_bytes), "chains": w.chains, "mc_steps": w.steps,
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "inputs": "receptors and ligands resident in HBM; grids rebuilt every step",
-                       "search_launch": {"variant": shape[0], "warps_per_cta": shape[1]},
+                       "search_launch": {"variant": shape[0], "warps_per_cta": shape[1],
+                                         "map_layout": "cell-packed" if layout == 1 else "plain"},
                        "host_generation_s": round(t_gen, 1)},
             "evals_per_s": round(evals / total_t, 1), "search_s_per_step": round(search_s / args.steps, 3),
             "roofline": {"kernel": "search_round_kernel", "bound": "alu", "achieved": round(achieved, 3),
