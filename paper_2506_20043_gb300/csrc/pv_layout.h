@@ -28,8 +28,8 @@ struct PvLigHeader {
 };
 
 // One lane's share of one intra-pair round (16 bytes). meta bits: 0-6 the partner atom of the pair
-// the lane sends (device order; 64 = the far dummy atom of an empty slot, whose pair lies beyond
-// the cutoff), 7 the pair's own atom is the lane's second (lane + LANES), 8-12 the lane whose pair
+// the lane sends (device order; 64-71 = one of the far dummy atoms of an empty slot, whose pair lies
+// beyond the cutoff), 7 the pair's own atom is the lane's second (lane + LANES), 8-12 the lane whose pair
 // this lane receives, 13 a pair is received, 14 the received pair's atom is the lane's second, 16
 // hydrophobic, 17 H-bond, 31 a pair is sent. The ramp of the hydrophobic or H-bond term is
 // w * sat(c0 + c1 d) on the surface distance d (c0 = c1 = w = 0 without one).
@@ -37,7 +37,8 @@ struct PvPairSlot {
     int32_t meta;
     float c0, c1, w;
 };
-#define PV_DUMMY_ATOM 64
+#define PV_DUMMY_ATOM 64       // the first of PV_N_DUMMY far dummy atoms (64 + k: bank group k)
+#define PV_N_DUMMY 8
 
 struct PvLigBlob {
     PvLigHeader h;

@@ -124,6 +124,98 @@ static int colour_rounds(const std::vector<std::pair<int, int>>& edges, std::vec
     return D;
 }
 
+// Shared-memory banks of the partner gathers. A quarter-warp (8 lanes) reads its partners' float4
+// positions in one shared-memory wavefront when their atom indices differ modulo 8 (the 16-byte
+// bank groups); partners of equal residue are read one after another. So a round costs, per
+// quarter-warp, the largest number of its partners sharing a residue (empty slots read a dummy atom
+// of a free residue), and a quarter-warp's rounds cost at least its largest count of pairs to one
+// residue. Starting from the colouring above, a tabu search moves single pairs between rounds (the
+// best of the moves of a random sample of the pairs in conflict), allowing a lane two pairs in a
+// round for a while at a penalty, and keeps the best colouring without such a clash; it stops at
+// that lower bound or after a fixed amount of work.
+static void balance_banks(const std::vector<std::pair<int, int>>& edges, std::vector<int>& col, int D, int lanes) {
+    const int m = (int)edges.size(), lm = lanes - 1, nq = lanes / 8;
+    if (m == 0 || D < 2) return;
+    auto src = [&](int e) { return edges[e].first & lm; };
+    auto tgt = [&](int e) { return edges[e].second & lm; };
+    auto cell = [&](int e, int c) { return (c * nq + (src(e) >> 3)) * 8 + (edges[e].second & 7); };
+    std::vector<int> cnt((size_t)D * nq * 8, 0), S((size_t)lanes * D, 0), R((size_t)lanes * D, 0);
+    for (int e = 0; e < m; ++e) {
+        cnt[cell(e, col[e])]++;
+        S[src(e) * D + col[e]]++;
+        R[tgt(e) * D + col[e]]++;
+    }
+    auto cost = [&](int rq) {
+        int c = 1;
+        for (int k = 0; k < 8; ++k) c = std::max(c, cnt[rq * 8 + k]);
+        return c;
+    };
+    std::vector<int> load(nq * 8, 0);
+    for (int e = 0; e < m; ++e) load[(src(e) >> 3) * 8 + (edges[e].second & 7)]++;
+    int bound = 0, soft = 0;
+    for (int q = 0; q < nq; ++q) bound += std::max(D, *std::max_element(&load[q * 8], &load[q * 8] + 8));
+    for (int rq = 0; rq < D * nq; ++rq) soft += cost(rq);
+    int best = soft, clashes = 0;
+    std::vector<int> best_col(col), tabu_until((size_t)m * D, 0);
+    const int kPenalty = 3;                  // a lane's second pair in a round, in wavefronts
+    const long long kWork = 2000000;         // pairs scanned and moves evaluated, at most
+    const int kCand = 24;
+    uint64_t rng = 0x9e3779b97f4a7c15ull;    // xorshift64, fixed seed: the schedule is reproducible
+    auto next = [&]() { rng ^= rng << 13; rng ^= rng >> 7; rng ^= rng << 17; return rng; };
+    long long work = 0;
+    std::vector<int> cand;
+    for (int it = 1; best > bound && work < kWork; ++it) {
+        // the moves of up to kCand pairs, drawn from those in a clash or sharing a bank group
+        cand.clear();
+        for (int e = 0; e < m; ++e)
+            if (S[src(e) * D + col[e]] > 1 || R[tgt(e) * D + col[e]] > 1 || cnt[cell(e, col[e])] > 1) cand.push_back(e);
+        for (int i = 0; i < (int)cand.size() && i < kCand; ++i)
+            std::swap(cand[i], cand[i + (int)(next() % (uint64_t)(cand.size() - i))]);
+        if ((int)cand.size() > kCand) cand.resize(kCand);
+        work += m + (long long)cand.size() * (D - 1);
+        int best_d = 1 << 30, be = -1, bc = -1, ties = 0;
+        for (int e : cand) {
+            const int a = col[e], u = src(e), v = tgt(e), rqa = a * nq + (u >> 3);
+            const int ca0 = cost(rqa);
+            cnt[cell(e, a)]--;
+            const int ca1 = cost(rqa);
+            cnt[cell(e, a)]++;
+            const int leave = (S[u * D + a] > 1 ? -1 : 0) + (R[v * D + a] > 1 ? -1 : 0);
+            for (int b = 0; b < D; ++b) {
+                if (b == a) continue;
+                const int dc = leave + (S[u * D + b] > 0 ? 1 : 0) + (R[v * D + b] > 0 ? 1 : 0);
+                const int rqb = b * nq + (u >> 3);
+                const int cb0 = cost(rqb);
+                cnt[cell(e, b)]++;
+                const int cb1 = cost(rqb);
+                cnt[cell(e, b)]--;
+                const int ds = (ca1 - ca0) + (cb1 - cb0), d = kPenalty * dc + ds;
+                // a tabu move is taken only if it gives a new best clash-free colouring
+                if (tabu_until[(size_t)e * D + b] > it && !(clashes + dc == 0 && soft + ds < best)) continue;
+                if (d < best_d) {
+                    best_d = d; be = e; bc = b; ties = 1;
+                } else if (d == best_d && next() % (uint64_t)(++ties) == 0) {
+                    be = e; bc = b;
+                }
+            }
+        }
+        if (be < 0) break;
+        const int a = col[be], u = src(be), v = tgt(be), rqa = a * nq + (u >> 3), rqb = bc * nq + (u >> 3);
+        soft -= cost(rqa) + cost(rqb);
+        S[u * D + a]--; R[v * D + a]--; cnt[cell(be, a)]--;
+        S[u * D + bc]++; R[v * D + bc]++; cnt[cell(be, bc)]++;
+        col[be] = bc;
+        soft += cost(rqa) + cost(rqb);
+        clashes += -((S[u * D + a] > 0) + (R[v * D + a] > 0)) + ((S[u * D + bc] > 1) + (R[v * D + bc] > 1));
+        tabu_until[(size_t)be * D + a] = it + 7 + (int)(next() % 10);
+        if (clashes == 0 && soft < best) {
+            best = soft;
+            best_col = col;
+        }
+    }
+    col = best_col;
+}
+
 bool build_ligand(const LigandInput& in, LigandRecord& out, std::string& err) {
     const int n = in.n_atoms, nb = in.n_bonds;
     if (n < 1 || n > 64) { err = "ligand atom count must be in [1, 64]"; return false; }
@@ -262,6 +354,7 @@ bool build_ligand(const LigandInput& in, LigandRecord& out, std::string& err) {
         orient_pairs(n, edges, lanes);
         std::vector<int> colour;
         const int nr = colour_rounds(edges, colour, lanes);
+        balance_banks(edges, colour, nr, lanes);
         // an empty slot sends its "pair" to the far dummy atom: beyond the cutoff, no energy, no force
         rounds.assign(nr, std::vector<PvPairSlot>(lanes, PvPairSlot{PV_DUMMY_ATOM, 0.f, 0.f, 0.f}));
         for (size_t e = 0; e < edges.size(); ++e) {
@@ -284,6 +377,18 @@ bool build_ligand(const LigandInput& in, LigandRecord& out, std::string& err) {
             t.meta = (int32_t)((uint32_t)t.meta | ((uint32_t)(src % lanes) << 8) | (1u << 13) |
                                ((uint32_t)(tgt / lanes) << 14));
         }
+        // the empty slots of a quarter-warp read the dummy atom of a residue its partners leave free
+        for (auto& round : rounds)
+            for (int q = 0; q < lanes; q += 8) {
+                uint32_t used = 0;
+                for (int l = q; l < q + 8; ++l)
+                    if ((uint32_t)round[l].meta >> 31) used |= 1u << (round[l].meta & 7);
+                int k = 0;
+                while ((used >> k) & 1) ++k;
+                for (int l = q; l < q + 8; ++l)
+                    if (!((uint32_t)round[l].meta >> 31))
+                        round[l].meta = (int32_t)(((uint32_t)round[l].meta & ~127u) | (uint32_t)(PV_DUMMY_ATOM + (k & 7)));
+            }
         return nr;
     };
     std::vector<std::vector<PvPairSlot>> rounds, rounds16;

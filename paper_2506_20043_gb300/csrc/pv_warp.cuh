@@ -30,8 +30,8 @@ struct ChainScalars {
 };
 
 struct WarpScratch {            // one per team
-    float4 x[65];               // posed coordinates, w = XS radius; [64] the far dummy atom that
-                                // empty pair slots point to (init_scratch)
+    float4 x[64 + PV_N_DUMMY];  // posed coordinates, w = XS radius; [64 + k] the far dummy atoms
+                                // that empty pair slots point to (init_scratch)
     union {                     // one lives after the other within an evaluation (synced between):
         float4 fm[3 * PV_MAX_FRAGS];  // during the kinematics: per fragment, its world rotation rows
                                       // (xyz) with the anchor (w)
@@ -90,11 +90,13 @@ struct Site {                      // where a pose is scored
     const PvPocket* P;             // pocket geometry (shared or global memory)
 };
 
-// Places the far dummy atom of a team's scratch (once per kernel, before its first evaluation):
-// empty pair slots point to it, and its distance to any atom is far beyond the cutoff.
+// Places the far dummy atoms of a team's scratch (once per kernel, before its first evaluation):
+// empty pair slots point to them (each to one in a shared-memory bank group that the other partners
+// of its quarter-warp leave free), and their distance to any atom is far beyond the cutoff.
 template <int LANES>
 __device__ __forceinline__ void init_scratch(WarpScratch& S) {
-    if ((threadIdx.x & (LANES - 1)) == 0) S.x[PV_DUMMY_ATOM] = make_float4(1e15f, 1e15f, 1e15f, 0.f);
+    const int tl = threadIdx.x & (LANES - 1);
+    if (tl < PV_N_DUMMY) S.x[PV_DUMMY_ATOM + tl] = make_float4(1e15f, 1e15f, 1e15f, 0.f);
     __syncwarp();
 }
 
@@ -182,6 +184,46 @@ __device__ __forceinline__ void team_fk(const PvLigBlob& L, WarpScratch& S, cons
     axw = mat_vec(M, axis);   // the hinge axis in the world frame (rotating about it keeps it)
 }
 
+// The lane's pairs of two rounds (slots pa, pb; source atoms xia, xib; partners xa, xb), their
+// arithmetic two pairs per instruction (packed FP32x2 adds, multiplies and FMAs; the reciprocal
+// square roots and exponentials one pair at a time): adds both energies to e_intra and returns the
+// forces on the sources in fa, fb. Per pair the same terms as pair_force.
+__device__ __forceinline__ void pair_force2(const PvPairSlot& pa, const PvPairSlot& pb, const float4& xia,
+                                            const float4& xib, const float4& xa, const float4& xb, float& e_intra,
+                                            float3& fa, float3& fb) {
+    const float2 dx = __fadd2_rn(make_float2(xia.x, xib.x), make_float2(-xa.x, -xb.x));
+    const float2 dy = __fadd2_rn(make_float2(xia.y, xib.y), make_float2(-xa.y, -xb.y));
+    const float2 dz = __fadd2_rn(make_float2(xia.z, xib.z), make_float2(-xa.z, -xb.z));
+    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+    const float2 rinv = make_float2(rsqrtf(fmaxf(r2.x, 1e-12f)), rsqrtf(fmaxf(r2.y, 1e-12f)));
+    const float2 r = __fmul2_rn(r2, rinv);
+    const float2 d = __fadd2_rn(r, make_float2(-(xia.w + xa.w), -(xib.w + xb.w)));   // surface distance
+    const float2 a1 = __fmul2_rn(__fmul2_rn(d, d), make_float2(-4.0f * kLog2e, -4.0f * kLog2e));
+    const float2 b = __fadd2_rn(d, make_float2(-3.0f, -3.0f));
+    const float2 a2 = __fmul2_rn(__fmul2_rn(b, b), make_float2(-0.25f * kLog2e, -0.25f * kLog2e));
+    const float2 g1 = make_float2(exp2_approx(a1.x), exp2_approx(a1.y));   // exp(-(d / 0.5)^2)
+    const float2 g2 = make_float2(exp2_approx(a2.x), exp2_approx(a2.y));   // exp(-((d - 3) / 2)^2)
+    const float2 rep = make_float2(fminf(d.x, 0.f), fminf(d.y, 0.f));
+    const float2 c1 = make_float2(pa.c1, pb.c1), w = make_float2(pa.w, pb.w);
+    const float2 t = __ffma2_rn(c1, d, make_float2(pa.c0, pb.c0));        // the ramp w sat(c0 + c1 d)
+    const float2 v = make_float2(__saturatef(t.x), __saturatef(t.y));
+    const float2 dv = make_float2((t.x > 0.0f && t.x <= 1.0f) ? c1.x : 0.0f, (t.y > 0.0f && t.y <= 1.0f) ? c1.y : 0.0f);
+    float2 e = __fmul2_rn(make_float2(kWGauss1, kWGauss1), g1);
+    e = __ffma2_rn(make_float2(kWGauss2, kWGauss2), g2, e);
+    e = __ffma2_rn(__fmul2_rn(make_float2(kWRepulsion, kWRepulsion), rep), rep, e);
+    e = __ffma2_rn(w, v, e);
+    float2 de = __fmul2_rn(__fmul2_rn(make_float2(-8.0f * kWGauss1, -8.0f * kWGauss1), d), g1);
+    de = __ffma2_rn(__fmul2_rn(make_float2(-0.5f * kWGauss2, -0.5f * kWGauss2), b), g2, de);
+    de = __ffma2_rn(make_float2(2.0f * kWRepulsion, 2.0f * kWRepulsion), rep, de);
+    de = __ffma2_rn(w, dv, de);
+    const bool la = r2.x < kCutoff2, lb = r2.y < kCutoff2;
+    e_intra += (la ? e.x : 0.f) + (lb ? e.y : 0.f);
+    const float2 c = __fmul2_rn(make_float2(la ? de.x : 0.f, lb ? de.y : 0.f), rinv);   // dE/dr / r
+    const float2 fx = __fmul2_rn(c, dx), fy = __fmul2_rn(c, dy), fz = __fmul2_rn(c, dz);
+    fa = make_float3(fx.x, fy.x, fz.x);
+    fb = make_float3(fx.y, fy.y, fz.y);
+}
+
 // The lane's pair of one round (source atom xi, partner position xj, the slot's ramp constants):
 // its energy and the force on the source, which the target's lane receives with the opposite
 // sign. An empty slot's partner is the far dummy atom: beyond the cutoff, it adds nothing.
@@ -232,41 +274,66 @@ __device__ __forceinline__ float team_eval(const PvLigBlob& L, WarpScratch& S, c
         }
     }
     Tm::sync();
-    // Pair rounds. Each lane computes the pair it sends (its atom is the source) and takes the
-    // opposite force of the pair it receives from the sending lane by a shuffle, so forces stay in
-    // registers and rounds need no barrier; positions and pair words are read-only here, so the
-    // next round's word and partner position are loaded ahead.
+    // Pair rounds, two per step with packed arithmetic. Each lane computes the pair it sends (its
+    // atom is the source) and takes the opposite force of the pair it receives from the sending lane
+    // by a shuffle, so forces stay in registers and rounds need no barrier.
     int rounds;
     const PvPairSlot* pr = pair_rounds<LANES>(L, rounds);
-    if (rounds > 0) {
-        PvPairSlot ps = pr[tl];
-        float4 xj = S.x[ps.meta & 127];
-        if (n <= LANES) {                     // every atom of a pair is its lane's first
-            for (int r = 0; r < rounds; ++r) {
-                const PvPairSlot ps_n = pr[min(r + 1, rounds - 1) * LANES + tl];
-                const float4 xj_n = S.x[ps_n.meta & 127];
-                const float3 f = pair_force(ps, own[0], xj, e_intra);
-                const float3 fi = Tm::shfl3(f, (ps.meta >> 8) & (LANES - 1));
-                acc[0] = acc[0] + f;
-                if ((ps.meta >> 13) & 1) acc[0] = acc[0] - fi;
-                ps = ps_n;
-                xj = xj_n;
+    if (n <= LANES) {                         // every atom of a pair is its lane's first
+        int r = 0;
+        for (; r + 1 < rounds; r += 2) {
+            const PvPairSlot pa = pr[r * LANES + tl], pb = pr[(r + 1) * LANES + tl];
+            const float4 xa = S.x[pa.meta & 127], xb = S.x[pb.meta & 127];
+            float3 fa, fb;
+            pair_force2(pa, pb, own[0], own[0], xa, xb, e_intra, fa, fb);
+            const float3 fia = Tm::shfl3(fa, (pa.meta >> 8) & (LANES - 1));
+            const float3 fib = Tm::shfl3(fb, (pb.meta >> 8) & (LANES - 1));
+            acc[0] = acc[0] + fa + fb;
+            if ((pa.meta >> 13) & 1) acc[0] = acc[0] - fia;
+            if ((pb.meta >> 13) & 1) acc[0] = acc[0] - fib;
+        }
+        if (r < rounds) {
+            const PvPairSlot pa = pr[r * LANES + tl];
+            const float3 fa = pair_force(pa, own[0], S.x[pa.meta & 127], e_intra);
+            const float3 fia = Tm::shfl3(fa, (pa.meta >> 8) & (LANES - 1));
+            acc[0] = acc[0] + fa;
+            if ((pa.meta >> 13) & 1) acc[0] = acc[0] - fia;
+        }
+    } else {
+        // two atoms per lane: meta bit 7 says the pair's own atom is the lane's second, bit 14 that
+        // the received pair's atom is
+        int r = 0;
+        for (; r + 1 < rounds; r += 2) {
+            const PvPairSlot pa = pr[r * LANES + tl], pb = pr[(r + 1) * LANES + tl];
+            const float4 xa = S.x[pa.meta & 127], xb = S.x[pb.meta & 127];
+            const bool sa = (pa.meta >> 7) & 1, sb = (pb.meta >> 7) & 1;
+            float3 fa, fb;
+            pair_force2(pa, pb, sa ? own[1] : own[0], sb ? own[1] : own[0], xa, xb, e_intra, fa, fb);
+            const float3 fia = Tm::shfl3(fa, (pa.meta >> 8) & (LANES - 1));
+            const float3 fib = Tm::shfl3(fb, (pb.meta >> 8) & (LANES - 1));
+            if (sa) acc[1] = acc[1] + fa;
+            else acc[0] = acc[0] + fa;
+            if (sb) acc[1] = acc[1] + fb;
+            else acc[0] = acc[0] + fb;
+            if ((pa.meta >> 13) & 1) {
+                if ((pa.meta >> 14) & 1) acc[1] = acc[1] - fia;
+                else acc[0] = acc[0] - fia;
             }
-        } else {
-            for (int r = 0; r < rounds; ++r) {
-                const PvPairSlot ps_n = pr[min(r + 1, rounds - 1) * LANES + tl];
-                const float4 xj_n = S.x[ps_n.meta & 127];
-                const bool hs = (ps.meta >> 7) & 1, hr = (ps.meta >> 14) & 1;
-                const float3 f = pair_force(ps, hs ? own[1] : own[0], xj, e_intra);
-                const float3 fi = Tm::shfl3(f, (ps.meta >> 8) & (LANES - 1));
-                if (hs) acc[1] = acc[1] + f;
-                else acc[0] = acc[0] + f;
-                if ((ps.meta >> 13) & 1) {
-                    if (hr) acc[1] = acc[1] - fi;
-                    else acc[0] = acc[0] - fi;
-                }
-                ps = ps_n;
-                xj = xj_n;
+            if ((pb.meta >> 13) & 1) {
+                if ((pb.meta >> 14) & 1) acc[1] = acc[1] - fib;
+                else acc[0] = acc[0] - fib;
+            }
+        }
+        if (r < rounds) {
+            const PvPairSlot pa = pr[r * LANES + tl];
+            const bool sa = (pa.meta >> 7) & 1;
+            const float3 fa = pair_force(pa, sa ? own[1] : own[0], S.x[pa.meta & 127], e_intra);
+            const float3 fia = Tm::shfl3(fa, (pa.meta >> 8) & (LANES - 1));
+            if (sa) acc[1] = acc[1] + fa;
+            else acc[0] = acc[0] + fa;
+            if ((pa.meta >> 13) & 1) {
+                if ((pa.meta >> 14) & 1) acc[1] = acc[1] - fia;
+                else acc[0] = acc[0] - fia;
             }
         }
     }

@@ -34,10 +34,8 @@ def lib(tmp_path_factory):
     return L
 
 
-def _decode(lib, lig, lanes):
-    """Rows (round, lane, source input atom, target input atom, hyd, hb) of the pairs sent, rows
-    (round, lane, sending lane, receiving input atom) of the pairs received, the header and the
-    round count."""
+def _raw(lib, lig, lanes):
+    """The schedule's meta words (rounds x lanes), the device-to-input atom map, the header."""
     xyz = np.ascontiguousarray(lig.xyz, np.float32)
     el, don, acc = (np.ascontiguousarray(a, np.uint8) for a in (lig.element, lig.donor, lig.acceptor))
     bonds = np.ascontiguousarray(lig.bonds, np.int32).reshape(-1, 2)
@@ -50,6 +48,16 @@ def _decode(lib, lig, lanes):
                           len(bonds), p(bonds, C.c_int32), p(rot, C.c_uint8), lanes, p(words, C.c_uint32),
                           len(words), p(src, C.c_int32), p(info, C.c_int32))
     assert nr >= 0, nr
+    return words[:nr * lanes].reshape(nr, lanes), src, info
+
+
+def _decode(lib, lig, lanes):
+    """Rows (round, lane, source input atom, target input atom, hyd, hb) of the pairs sent, rows
+    (round, lane, sending lane, receiving input atom) of the pairs received, the header and the
+    round count."""
+    words, src, info = _raw(lib, lig, lanes)
+    words = words.reshape(-1)
+    nr = len(words) // lanes
     n = int(info[4])
     sent, recv = [], []
     for r in range(nr):
@@ -119,3 +127,42 @@ def _check_schedules(lib, lig, n_atoms):
             src_load = np.bincount(rows[:, 1], minlength=lanes).max()
             tgt_load = np.bincount(recv[:, 1], minlength=lanes).max()
             assert n_rounds == max(src_load, tgt_load), lanes
+
+
+def _bank_cost(words, lanes):
+    """Shared-memory wavefronts of the partner gathers: per round and quarter-warp, the largest
+    number of distinct partner positions (float4, 16-byte bank groups) sharing a residue mod 8;
+    and the lower bound per quarter-warp: its round count, or its largest load on one residue."""
+    cost, load = 0, np.zeros((lanes // 8, 8), np.int64)
+    for r in range(words.shape[0]):
+        for q in range(0, lanes, 8):
+            part = {int(w) & 127 for w in words[r, q:q + 8]}
+            cost += max(np.bincount([a & 7 for a in part], minlength=8))
+            for w in words[r, q:q + 8]:
+                if int(w) >> 31:
+                    load[q // 8, int(w) & 7] += 1
+    return cost, int(sum(max(words.shape[0], load[q].max()) for q in range(lanes // 8)))
+
+
+@pytest.mark.parametrize("n_atoms,n_rot,seed,rings,at_bound", [
+    (30, 6, 0, None, True), (30, 6, 1, None, True), (30, 6, 2, None, True), (24, 6, 5, None, True),
+    (31, 9, 9, None, True), (30, 6, 2, "single", True), (40, 8, 5, "fused", True), (48, 12, 11, None, False),
+    (64, 20, 13, None, False), (60, 12, 8, "linked", False)])
+def test_schedule_partner_gathers_spread_over_bank_groups(lib, n_atoms, n_rot, seed, rings, at_bound):
+    """Empty slots read a dummy atom (64-71) of a residue that no partner of their quarter-warp has,
+    and the rounds are arranged so that a quarter-warp's partners fall into distinct bank groups:
+    ligands of the bench's size reach the lower bound, larger ones stay within 40 % of it."""
+    lig = S.make_ring_ligand(n_atoms, n_rot, seed, rings) if rings else S.make_ligand(n_atoms, n_rot, seed)
+    _, _, info, _ = _decode(lib, S.ligand_centered(lig), 32)
+    for lanes in [32] + ([16] if info[2] else []):
+        words, _, _ = _raw(lib, S.ligand_centered(lig), lanes)
+        for r in range(words.shape[0]):
+            for q in range(0, lanes, 8):
+                w = [int(x) for x in words[r, q:q + 8]]
+                used = {x & 7 for x in w if x >> 31}
+                for x in w:
+                    if not x >> 31:
+                        assert 64 <= (x & 127) < 72 and (x & 7) not in used
+        cost, bound = _bank_cost(words, lanes)
+        assert bound <= cost
+        assert cost == bound if at_bound else cost <= 1.4 * bound, (lanes, cost, bound)
