@@ -296,13 +296,23 @@ typedef struct {
     int32_t map_layout;        /* maps the search reads: 0 plain, 1 cell-packed (the set must hold
                                   them, pv_grid_set_pack), -1 = the autotuner picks between them
                                   when the set holds both, else plain. Results are the same */
+    const void* resume_state;  /* NULL, or a host copy of a checkpoint (pv_dock_result_save_state)
+                                  of a dock of the same job: the same ligands, pairs, pair keys,
+                                  chains, seed, mode and search constants (checked against a hash
+                                  the checkpoint carries, PV_ERR_ARG otherwise). The dock then
+                                  continues every chain from the checkpoint's MC step s0 and runs
+                                  steps s0 .. steps - 1 (steps must exceed s0), so that its chains,
+                                  kept poses and ranking are those of one dock of `steps` steps
+                                  (bitwise, for the same team width). Read before pv_dock returns;
+                                  caller-owned */
+    int64_t resume_bytes;      /* size of resume_state in bytes */
 } pv_dock_params;
 
 /* Defaults: chains 64, steps 1000, seed 0, top_k 9, rmsd_min 1.0, BATCHED, m 5, max_iter 0,
  * max_trials 10, eps 1e-3, rho 1e-4, sigma 0.1, temperature 1.2, amplitude 2.0,
  * steps_per_round 0, use_graph 1, warps_per_cta 0, search_variant -1, host_copy 1, timeout_s 0,
  * focc 0, focc_min_delta 1e-4, rescore 0, max_pockets 0, block_wait_s 30, pair_keys NULL,
- * map_layout -1.
+ * map_layout -1, resume_state NULL, resume_bytes 0.
  * Autotuning (warps_per_cta 0, search_variant -1, or map_layout -1 on a set holding both layouts):
  * the first batched dock of a ligand-size bucket on a context times each candidate launch shape on
  * 32 MC steps of its own work items (after 16 untimed steps from the random starts), the fastest of
@@ -352,7 +362,8 @@ pv_status pv_dock_result_info(const pv_dock_result* r, int32_t* n_pairs, int32_t
 
 /* Host copies (synchronous). poses [n_pairs][top_k]; n_kept [n_pairs]; pots (nullable)
  * [n_pairs][top_k][pot_stride]; xyz (nullable) [n_pairs][top_k][atom_stride][3], input atom
- * order; unused slots have pair = -1. */
+ * order; unused slots have pair = -1 and zero POTs and coordinates, and the strides' padding past
+ * a ligand's 7 + n_rot POT entries and n_atoms atoms is zero. */
 pv_status pv_dock_result_poses(const pv_dock_result* r, pv_pose* poses, int32_t* n_kept,
                                float* pots, float* xyz);
 
@@ -392,6 +403,16 @@ pv_status pv_dock_result_chains(const pv_dock_result* r, const float** dev_recor
 /* Copies all chain records (n_pairs * chains * record_stride floats) into dst, host or device
  * memory. Synchronous. */
 pv_status pv_dock_result_read_chains(const pv_dock_result* r, float* dst);
+
+/* Checkpoint of a dock: the state of every chain after its last MC step (the chain records, with
+ * the consistency check also the chains' neighbour rings), the step count and a hash of the job,
+ * as one opaque host blob that pv_dock_params.resume_state continues from. The chain state between
+ * MC steps is all a chain carries (each local search starts a new L-BFGS history; random numbers
+ * are drawn by step index), so a resumed dock repeats the unbroken one. state_bytes gives the size;
+ * save_state writes it to host_dst (bytes must be at least that size; PV_ERR_ARG otherwise).
+ * Synchronous. A checkpoint is valid on any context and device of the same library build. */
+pv_status pv_dock_result_state_bytes(const pv_dock_result* r, int64_t* bytes);
+pv_status pv_dock_result_save_state(const pv_dock_result* r, void* host_dst, int64_t bytes);
 
 void pv_dock_result_destroy(pv_dock_result* r);
 

@@ -40,7 +40,8 @@ class pv_dock_params(C.Structure):
                 ("host_copy", C.c_int32),
                 ("timeout_s", C.c_double), ("focc", C.c_int32), ("focc_min_delta", C.c_float),
                 ("rescore", C.c_int32), ("max_pockets", C.c_int32), ("block_wait_s", C.c_double),
-                ("pair_keys", C.POINTER(C.c_int32)), ("map_layout", C.c_int32)]
+                ("pair_keys", C.POINTER(C.c_int32)), ("map_layout", C.c_int32),
+                ("resume_state", C.c_void_p), ("resume_bytes", C.c_int64)]
 
 
 class pv_pose(C.Structure):
@@ -104,6 +105,8 @@ SIGNATURES = {
     "pv_dock_result_device": (i32, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),
     "pv_dock_result_chains": (i32, [vp, C.POINTER(vp), pi32, pi32, pi32, pi32]),
     "pv_dock_result_read_chains": (i32, [vp, vp]),
+    "pv_dock_result_state_bytes": (i32, [vp, C.POINTER(C.c_int64)]),
+    "pv_dock_result_save_state": (i32, [vp, vp, C.c_int64]),
     "pv_dock_result_destroy": (None, [vp]),
     "pv_build_grid_noalloc": (i32, [vp, C.POINTER(pv_receptor), C.POINTER(pv_box), C.POINTER(C.c_uint8), i32, vp]),
     "pv_pocket_params_default": (i32, [C.POINTER(pv_pocket_params)]),

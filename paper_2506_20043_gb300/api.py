@@ -61,6 +61,8 @@ class DockParams:
     block_wait_s: float = 30.0     # bound on a step block's wait for its predecessor
     pair_keys: Optional[Sequence[int]] = None   # per pair: its random stream (default: pair index)
     map_layout: int = -1           # 0 plain, 1 cell-packed, -1 autotuned when the set holds both
+    resume_state: Optional[bytes] = None   # a checkpoint (DockResult.save_state) of the same job:
+                                           # continue its chains from the step it had reached
 
     def to_c(self) -> A.pv_dock_params:
         p = A.pv_dock_params()
@@ -73,6 +75,14 @@ class DockParams:
                 if v is None:
                     continue
                 v = (C.c_int32 * len(v))(*[int(k) for k in v])   # kept alive by the struct
+            elif f.name == "resume_state":
+                if v is None:
+                    continue
+                buf = C.create_string_buffer(bytes(v), len(v))
+                p._resume_buf = buf                                  # kept alive with the struct
+                p.resume_state = C.addressof(buf)
+                p.resume_bytes = len(v)
+                continue
             elif isinstance(v, bool):
                 v = int(v)
             setattr(p, f.name, v)
@@ -586,6 +596,15 @@ class DockResult:
         rec = np.zeros((self.n_pairs, ch.value, stride.value), dtype=np.float32)
         self.ctx._check(self.ctx.lib.pv_dock_result_read_chains(self.h, rec.ctypes.data), "pv_dock_result_read_chains")
         return rec[:, :, bo.value:bo.value + self.pot_stride].copy(), rec[:, :, so.value].copy()
+
+    def save_state(self) -> bytes:
+        """Checkpoint of the dock (every chain's state after its last MC step): pass it as
+        DockParams.resume_state to a dock of the same job with more steps to continue from there."""
+        n = C.c_int64()
+        self.ctx._check(self.ctx.lib.pv_dock_result_state_bytes(self.h, C.byref(n)), "pv_dock_result_state_bytes")
+        buf = C.create_string_buffer(n.value)
+        self.ctx._check(self.ctx.lib.pv_dock_result_save_state(self.h, buf, n.value), "pv_dock_result_save_state")
+        return buf.raw
 
     def __del__(self):
         if getattr(self, "h", None) and self.ctx.h:

@@ -80,6 +80,35 @@ struct pv_dock_result {
     int search_variant = 0, warps_per_cta = 0;   // launch shape used (batched)
     int map_layout = 0;                          // map layout the search read
     int mode = PV_MODE_BATCHED;
+    int steps_done = 0, focc = 0;                // checkpoint: MC steps the chains have run
+    uint64_t job = 0;                            //             hash of what fixes their trajectories
+    float* d_ring = nullptr;                     //             neighbour rings (consistency check)
+};
+
+// Checkpoint blob (pv_dock_result_save_state): this header, the chain records, then the neighbour
+// rings when the consistency check ran.
+struct PvStateHeader {
+    uint32_t magic, version;
+    int32_t n_pairs, chains, steps_done, focc, chain_stride, ring_stride;
+    uint64_t job;
+};
+static const uint32_t kStateMagic = 0x54535650u;   // "PVST"
+static const uint32_t kStateVersion = 1;
+
+static int64_t state_bytes(int n_pairs, int chains, int focc) {
+    const int64_t n = (int64_t)n_pairs * chains;
+    return (int64_t)sizeof(PvStateHeader) + n * PV_CHAIN_STRIDE * 4 + (focc > 0 ? n * PV_RING_STRIDE * 4 : 0);
+}
+
+// FNV-1a over what fixes the chains' trajectories: the search constants, the mode, and per pair its
+// ligand record, pocket and random-stream key.
+struct JobHash {
+    uint64_t h = 1469598103934665603ull;
+    void bytes(const void* p, size_t n) {
+        const unsigned char* c = (const unsigned char*)p;
+        for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    }
+    template <class T> void put(const T& v) { bytes(&v, sizeof(T)); }
 };
 
 // ---------------------------------------------------------------------------- helpers ---
@@ -383,6 +412,7 @@ static pv_status add_receptor(pv_context* ctx, pv_grid_set* set, const pv_recept
 extern "C" pv_status pv_build_grids(pv_context* ctx, const pv_receptor* receptor, const pv_box* boxes,
                                     int32_t n_pockets, const uint8_t* lig_types, int32_t n_types,
                                     pv_grid_set** out) {
+    NvtxRange nvtx("pv_build_grids");
     if (!ctx || ctx->magic != kCtxMagic) return PV_ERR_STATE;
     if (!out) return fail(ctx, PV_ERR_ARG, "out is null");
     *out = nullptr;
@@ -411,6 +441,7 @@ extern "C" pv_status pv_build_grids(pv_context* ctx, const pv_receptor* receptor
 
 extern "C" pv_status pv_grid_set_append(pv_context* ctx, pv_grid_set* set, const pv_receptor* receptor,
                                         const pv_box* boxes, int32_t n_pockets, int32_t* first_pocket) {
+    NvtxRange nvtx("pv_grid_set_append");
     if (!ctx || ctx->magic != kCtxMagic) return PV_ERR_STATE;
     if (!set || set->ctx != ctx) return fail(ctx, PV_ERR_STATE, "grid set of another context");
     DeviceGuard g(ctx->device);
@@ -452,6 +483,7 @@ extern "C" pv_status pv_grid_set_build_seconds(const pv_grid_set* set, double* s
 }
 
 extern "C" pv_status pv_grid_set_pack(pv_context* ctx, pv_grid_set* set) {
+    NvtxRange nvtx("pv_grid_set_pack");
     if (!ctx || ctx->magic != kCtxMagic) return PV_ERR_STATE;
     if (!set || set->ctx != ctx) return fail(ctx, PV_ERR_STATE, "grid set of another context");
     if (set->packed) return PV_OK;
@@ -526,6 +558,7 @@ extern "C" pv_status pv_grid_set_read_map(const pv_grid_set* set, int32_t pocket
 // ----------------------------------------------------------------------------- ligands ---
 
 extern "C" pv_status pv_ligand_create(pv_context* ctx, const pv_ligand_desc* d, pv_ligand** out) {
+    NvtxRange nvtx("pv_ligand_create");
     if (!ctx || ctx->magic != kCtxMagic) return PV_ERR_STATE;
     if (!out || !d) return fail(ctx, PV_ERR_ARG, "null argument");
     *out = nullptr;
@@ -620,6 +653,7 @@ static pv_status check_score_args(pv_context* ctx, const pv_grid_set* set, const
 extern "C" pv_status pv_score(pv_context* ctx, const pv_grid_set* set, const pv_ligand* lig, int32_t pocket,
                               int32_t n_poses, const float* dev_pose, float* dev_energy, float* dev_grad,
                               float* dev_parts) {
+    NvtxRange nvtx("pv_score");
     pv_status st = check_score_args(ctx, set, lig, pocket, n_poses);
     if (st != PV_OK) return st;
     if (n_poses == 0) return PV_OK;
@@ -634,6 +668,7 @@ extern "C" pv_status pv_score(pv_context* ctx, const pv_grid_set* set, const pv_
 extern "C" pv_status pv_score_backward(pv_context* ctx, const pv_grid_set* set, const pv_ligand* lig,
                                        int32_t pocket, int32_t n_poses, const float* dev_pose,
                                        const float* dev_grad_energy, float* dev_grad_pose, float* dev_grad_xyz) {
+    NvtxRange nvtx("pv_score_backward");
     pv_status st = check_score_args(ctx, set, lig, pocket, n_poses);
     if (st != PV_OK) return st;
     if (n_poses == 0) return PV_OK;
@@ -649,6 +684,7 @@ extern "C" pv_status pv_score_backward(pv_context* ctx, const pv_grid_set* set, 
 extern "C" pv_status pv_score_xyz(pv_context* ctx, const pv_grid_set* set, const pv_ligand* lig, int32_t pocket,
                                   int32_t n_poses, const float* dev_xyz, const float* dev_grad_energy,
                                   float* dev_energy, float* dev_grad_xyz) {
+    NvtxRange nvtx("pv_score_xyz");
     pv_status st = check_score_args(ctx, set, lig, pocket, n_poses);
     if (st != PV_OK) return st;
     if (n_poses == 0) return PV_OK;
@@ -745,6 +781,8 @@ extern "C" void pv_dock_params_default(pv_dock_params* p) {
     p->block_wait_s = 30.0;
     p->pair_keys = nullptr;
     p->map_layout = -1;
+    p->resume_state = nullptr;
+    p->resume_bytes = 0;
 }
 
 static void result_free(pv_dock_result* r) {
@@ -761,6 +799,7 @@ extern "C" void pv_dock_result_destroy(pv_dock_result* r) { result_free(r); }
 static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* const* ligs, int n_ligs,
                            const std::vector<int>& pair_lig, const std::vector<int>& pair_pocket,
                            const std::vector<int>& pair_key, const pv_dock_params* prm, pv_dock_result** out) {
+    NvtxRange nvtx("pv_dock");
     const int n_pairs = (int)pair_lig.size();
     const pv_dock_params& p = *prm;
     if (!(std::isfinite(p.block_wait_s))) return fail(ctx, PV_ERR_ARG, "block_wait_s must be finite");
@@ -799,11 +838,62 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
         if (pair_pocket[q] < 0 || pair_pocket[q] >= (int)set->pockets.size())
             return fail(ctx, PV_ERR_ARG, "pocket id out of range");
     }
+    // the job a checkpoint belongs to, and the checkpoint this dock continues from
+    JobHash job;
+    job.put(p.seed);
+    job.put(p.chains);
+    job.put(p.mode == PV_MODE_PLAIN ? 1 : 0);   // thread per chain: its own arithmetic
+    job.put(p.bfgs_m);
+    job.put(p.bfgs_max_iter);
+    job.put(p.bfgs_max_trials);
+    job.put(p.bfgs_eps);
+    job.put(p.rho);
+    job.put(p.sigma);
+    job.put(p.temperature);
+    job.put(p.amplitude);
+    job.put(p.focc);
+    job.put(p.focc_min_delta);
+    {
+        std::vector<uint64_t> lig_hash(n_ligs);
+        for (int i = 0; i < n_ligs; ++i) {
+            JobHash h;
+            h.bytes(ligs[i]->rec.blob.data(), ligs[i]->rec.blob.size());
+            lig_hash[i] = h.h;
+        }
+        for (int q = 0; q < n_pairs; ++q) {
+            job.put(lig_hash[pair_lig[q]]);
+            job.put(pair_pocket[q]);
+            job.put(pair_key[q]);
+        }
+    }
+    PvStateHeader resume{};
+    const bool resuming = p.resume_state != nullptr;
+    if (resuming) {
+        if (p.resume_bytes < (int64_t)sizeof(PvStateHeader))
+            return fail(ctx, PV_ERR_ARG, "resume_state is not a dock checkpoint");
+        std::memcpy(&resume, p.resume_state, sizeof(PvStateHeader));
+        if (resume.magic != kStateMagic || resume.version != kStateVersion)
+            return fail(ctx, PV_ERR_ARG, "resume_state is not a dock checkpoint");
+        if (resume.n_pairs != n_pairs || resume.chains != p.chains || resume.focc != p.focc ||
+            resume.chain_stride != PV_CHAIN_STRIDE || resume.ring_stride != PV_RING_STRIDE || resume.job != job.h)
+            return fail(ctx, PV_ERR_ARG, "resume_state is a checkpoint of another job");
+        if (p.resume_bytes != state_bytes(n_pairs, p.chains, p.focc))
+            return fail(ctx, PV_ERR_ARG, "resume_bytes does not match the checkpoint");
+        if (resume.steps_done < 0 || resume.steps_done >= p.steps)
+            return fail(ctx, PV_ERR_ARG, "steps must exceed the checkpoint's MC steps");
+    } else if (p.resume_bytes != 0) {
+        return fail(ctx, PV_ERR_ARG, "resume_bytes without resume_state");
+    }
+    const int s_first = resuming ? resume.steps_done : 0;   // the first MC step this dock runs
+    const int steps_left = p.steps - s_first;
     DeviceGuard g(ctx->device);
     pv_dock_result* R = new (std::nothrow) pv_dock_result();
     if (!R) return fail(ctx, PV_ERR_OOM, "host allocation failed");
     R->ctx = ctx;
     R->n_pairs = n_pairs;
+    R->steps_done = p.steps;
+    R->focc = p.focc;
+    R->job = job.h;
     R->n_ligs = n_ligs;
     R->top_k = p.top_k;
     R->pot_stride = 7 + max_rot;
@@ -889,8 +979,8 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     for (int i = 0; i < n_ligs; ++i) ligptr[i] = ligs[i]->d_blob;
     // one launch (round) covers all MC steps unless steps_per_round asks for more; a launch's steps
     // are cut into chained step blocks of about 1/16 of them (at least 25)
-    const int S_r = p.steps_per_round > 0 ? p.steps_per_round : std::max(1, p.steps);
-    const int n_rounds = p.steps > 0 ? (p.steps + S_r - 1) / S_r : 1;
+    const int S_r = p.steps_per_round > 0 ? p.steps_per_round : std::max(1, steps_left);
+    const int n_rounds = steps_left > 0 ? (steps_left + S_r - 1) / S_r : 1;
     const int block_steps = std::max(25, (S_r + 15) / 16);
     // one workspace allocation
     Layout Lw;
@@ -969,6 +1059,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     A.slots_hi = pack_slots(set->slot, 1);
     A.chains = R->d_chains;
     A.ring = p.focc > 0 ? (float*)(w + o_ring) : nullptr;
+    R->d_ring = A.ring;
     A.items_per_block = (int)items.size();
     A.block_steps = block_steps;
     A.progress = (int*)(w + o_prog);
@@ -1010,6 +1101,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
     // it is faster by more than kTuneMargin, so that shapes within the trials' noise do not flip
     // between runs.
     if (need_tune) {
+        NvtxRange nvtx_tune("autotune launch shape");
         constexpr int kWarmSteps = 16, kTuneSteps = 32, kTuneBlock = 8;
         constexpr float kTuneMargin = 0.02f;
         // in order of preference: the first of a team width is the incumbent the others must beat by
@@ -1156,6 +1248,20 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
         result_free(R);
         return cuda_fail(ctx, e, "kernel configuration");
     }
+    if (resuming) {   // after the autotuner's trials, which ran on these buffers
+        const size_t n_rec = (size_t)n_pairs * p.chains;
+        const char* src = (const char*)p.resume_state + sizeof(PvStateHeader);
+        e = cudaMemcpyAsync(R->d_chains, src, n_rec * PV_CHAIN_STRIDE * sizeof(float), cudaMemcpyHostToDevice,
+                            ctx->stream);
+        if (e == cudaSuccess && p.focc > 0)
+            e = cudaMemcpyAsync(R->d_ring, src + n_rec * PV_CHAIN_STRIDE * sizeof(float),
+                                n_rec * PV_RING_STRIDE * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);   // the caller's buffer is read now
+        if (e != cudaSuccess) {
+            result_free(R);
+            return cuda_fail(ctx, e, "checkpoint upload");
+        }
+    }
     cudaEvent_t ev0, ev1, evs0, evs1;
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);
@@ -1166,17 +1272,19 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
         cudaError_t x = cudaMemsetAsync(ctr, 0, sizeof(int) * (n_rounds + 2), s);
         if (x == cudaSuccess) x = cudaMemsetAsync(evals, 0, sizeof(unsigned long long), s);
         // chain records zeroed: the POT entries past a ligand's 7 + n_rot read as 0, not stale data
-        if (x == cudaSuccess)
+        // (a resumed dock has uploaded its checkpoint's records instead)
+        if (x == cudaSuccess && !resuming)
             x = cudaMemsetAsync(R->d_chains, 0, sizeof(float) * (size_t)n_pairs * p.chains * PV_CHAIN_STRIDE, s);
         if (x == cudaSuccess) x = launch_mark_t0(evals + 1, s);
         const unsigned ev_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
         if (x == cudaSuccess) x = cudaEventRecordWithFlags(evs0, s, ev_flags);
         if (p.mode == PV_MODE_BATCHED) {
             for (int r = 0; r < n_rounds && x == cudaSuccess; ++r) {
+                NvtxRange nvtx_round("search round");
                 SearchArgs a = A;
                 a.queue = ctr + 2 + r;
-                a.step0 = r * S_r;
-                a.step1 = std::min(p.steps, (r + 1) * S_r);
+                a.step0 = s_first + r * S_r;
+                a.step1 = std::min(p.steps, s_first + (r + 1) * S_r);
                 const int n_blocks = a.step1 > a.step0 ? (a.step1 - a.step0 + block_steps - 1) / block_steps : 1;
                 a.n_items = n_blocks * a.items_per_block;
                 x = cudaMemsetAsync(a.progress, 0, sizeof(int) * (size_t)a.items_per_block, s);
@@ -1194,9 +1302,9 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
                 a.items_per_block = item_count[q];
                 a.n_items = item_count[q];
                 a.queue = ctr + 2;
-                a.step0 = 0;
+                a.step0 = s_first;
                 a.step1 = p.steps;
-                a.block_steps = std::max(1, p.steps);
+                a.block_steps = std::max(1, steps_left);
                 x = cudaMemsetAsync(ctr + 2, 0, sizeof(int), s);
                 if (x == cudaSuccess)
                     x = launch_search_round(a, variant, std::max(1, std::min(item_count[q], ctx->sms * occ)), W, s);
@@ -1209,7 +1317,7 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
         } else {
             for (int q = 0; q < n_pairs && x == cudaSuccess; ++q) {
                 SearchArgs a = A;
-                a.step0 = 0;
+                a.step0 = s_first;
                 a.step1 = p.steps;
                 x = launch_plain_search(a, q, (const PvLigBlob*)ligs[pair_lig[q]]->d_blob, s);
                 TopkArgs t = T;
@@ -1444,6 +1552,32 @@ extern "C" pv_status pv_dock_result_chains(const pv_dock_result* r, const float*
     if (record_stride) *record_stride = PV_CHAIN_STRIDE;
     if (best_pot_offset) *best_pot_offset = PV_CH_BEST;
     if (best_score_offset) *best_score_offset = PV_CH_EBEST;
+    return PV_OK;
+}
+
+extern "C" pv_status pv_dock_result_state_bytes(const pv_dock_result* r, int64_t* bytes) {
+    if (!r || !bytes) return PV_ERR_ARG;
+    *bytes = state_bytes(r->n_pairs, r->chains, r->focc);
+    return PV_OK;
+}
+
+extern "C" pv_status pv_dock_result_save_state(const pv_dock_result* r, void* host_dst, int64_t bytes) {
+    if (!r || !host_dst) return PV_ERR_ARG;
+    if (bytes < state_bytes(r->n_pairs, r->chains, r->focc))
+        return fail(r->ctx, PV_ERR_ARG, "checkpoint buffer smaller than pv_dock_result_state_bytes");
+    PvStateHeader h{kStateMagic, kStateVersion, r->n_pairs, r->chains, r->steps_done, r->focc,
+                    PV_CHAIN_STRIDE, PV_RING_STRIDE, r->job};
+    std::memcpy(host_dst, &h, sizeof(h));
+    const size_t n_rec = (size_t)r->n_pairs * r->chains;
+    char* dst = (char*)host_dst + sizeof(h);
+    DeviceGuard g(r->ctx->device);
+    cudaError_t e = cudaStreamSynchronize(r->ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(dst, r->d_chains, n_rec * PV_CHAIN_STRIDE * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && r->focc > 0)
+        e = cudaMemcpy(dst + n_rec * PV_CHAIN_STRIDE * sizeof(float), r->d_ring, n_rec * PV_RING_STRIDE * sizeof(float),
+                       cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(r->ctx, e, "save checkpoint");
     return PV_OK;
 }
 

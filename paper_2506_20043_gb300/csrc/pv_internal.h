@@ -2,11 +2,21 @@
 #pragma once
 #include <stdint.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include "pv_layout.h"
 
 struct pv_context;
 
 namespace pv {
+
+// A named NVTX range over a host scope: a profiler's timeline shows each library call and, inside a
+// dock, its autotuning, search rounds and selection (ranges cost a few nanoseconds without a tool).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Context access for entry points defined outside pv_api.cu (false on a bad handle).
 bool context_device_stream(pv_context* ctx, int* device, cudaStream_t* stream);

@@ -313,12 +313,15 @@ __global__ void __launch_bounds__(kTopkThreads) topk_kernel(TopkArgs A) {
             r.pad[0] = r.pad[1] = 0;
             A.poses[o] = r;
         }
-        for (int i = lane; i < 7 + n_rot; i += 32) A.pots[o * C.pot_stride + i] = best[i];
+        // POT and coordinates; the strides' padding (a ligand with fewer torsions or atoms than the
+        // dock's largest) is written as zeros, so the outputs hold no stale memory
+        for (int i = lane; i < C.pot_stride; i += 32) A.pots[o * C.pot_stride + i] = i < 7 + n_rot ? best[i] : 0.f;
         for (int a = lane; a < n; a += 32) {
             float4 p = scratch[warp].x[a];
             float* dst = A.xyz + (o * C.atom_stride + L.atom_src[a]) * 3;
             dst[0] = p.x; dst[1] = p.y; dst[2] = p.z;
         }
+        for (int i = n * 3 + lane; i < C.atom_stride * 3; i += 32) A.xyz[o * C.atom_stride * 3 + i] = 0.f;
         __syncwarp();
     }
     for (int slot = kept + threadIdx.x; slot < C.top_k; slot += blockDim.x) {
@@ -326,7 +329,10 @@ __global__ void __launch_bounds__(kTopkThreads) topk_kernel(TopkArgs A) {
         r.score = 0.f; r.e_inter = 0.f; r.e_intra = 0.f; r.affinity = 0.f;
         r.pair = -1; r.ligand = -1; r.pocket = -1; r.chain = -1;
         r.score_grid = 0.f; r.e_inter_grid = 0.f; r.pad[0] = r.pad[1] = 0;
-        A.poses[(size_t)pair * C.top_k + slot] = r;
+        const size_t o = (size_t)pair * C.top_k + slot;
+        A.poses[o] = r;
+        for (int i = 0; i < C.pot_stride; ++i) A.pots[o * C.pot_stride + i] = 0.f;
+        for (int i = 0; i < C.atom_stride * 3; ++i) A.xyz[o * C.atom_stride * 3 + i] = 0.f;
     }
     if (threadIdx.x == 0) {
         A.n_kept[pair] = kept;

@@ -83,6 +83,9 @@ def test_dock_params_layout_and_defaults_agree(tmp_path):
         if f.name == "pair_keys":
             assert not p.pair_keys and q.pair_keys is None
             continue
+        if f.name == "resume_state":
+            assert not p.resume_state and p.resume_bytes == 0 and q.resume_state is None
+            continue
         v = getattr(q, f.name)
         if f.name == "mode":
             v = _capi.PV_MODE_BATCHED
