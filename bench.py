@@ -336,7 +336,9 @@ def run_ours(args):
                               "frac": round(terms * GRID_FLOPS_PER_TERM / map_s / 1e12 / peak_tflops, 4),
                               "term_evals_per_s": round(terms / map_s, 1), "launch_ms": round(map_s * 1e3, 3),
                               "traffic": (round(stored_grid_profile()) if stored_grid_profile() else None)},
-            "gpu_launches": args.steps * (6 + 1 + n_rounds + 2),
+            # per step: typing, 4 binning launches and the map build; one cell-packing launch per
+            # pocket; the start stamp, the search rounds, top-k and merge
+            "gpu_launches": args.steps * (6 + len(my_boxes) + 1 + n_rounds + 2),
             "clocks": clocks,
         }
         if not args.no_plain:
@@ -347,7 +349,8 @@ def run_ours(args):
             out["score_microbench"] = run_score_microbench(ctx, api, torch)
         out["rescoring"] = run_rescore_check(ctx, gs, lig, list(range(len(my_boxes))), params)
         if world == 1:
-            out["e2e"] = run_e2e(ctx, api, torch, rec, boxes, lig_src, types, list(range(len(boxes))), args.steps, 0)
+            out["e2e"] = run_e2e(ctx, api, torch, rec, boxes, lig_src, types, list(range(len(boxes))), args.steps, 0,
+                                 focc=args.focc)
         if world == 1 and not args.no_cpu:
             out["cpu_baseline"] = run_cpu_baseline(rec, boxes, lig_src, budget_s=args.cpu_budget)
     if world > 1:
@@ -441,7 +444,7 @@ def run_score_microbench(ctx, api, torch, reps=20):
             "gather_frac": round(l2 / g_gbs, 4)}
 
 
-def run_e2e(ctx, api, torch, rec, boxes, lig_src, types, pockets, steps, seed):
+def run_e2e(ctx, api, torch, rec, boxes, lig_src, types, pockets, steps, seed, focc=0):
     """The same metric through the public API from pinned host buffers: every step uploads the
     receptor and ligand, builds the grids, docks, and reads the ranked poses back."""
     pin = {k: torch.tensor(np.asarray(getattr(rec, k), dtype=np.float32 if k == "xyz" else np.uint8)).pin_memory()
@@ -455,7 +458,8 @@ def run_e2e(ctx, api, torch, rec, boxes, lig_src, types, pockets, steps, seed):
     for _ in range(steps):
         gs = ctx.build_grids(host_rec, boxes, types).pack()
         lig = ctx.ligand(lig_src)
-        r = ctx.dock(gs, [lig], pockets, chains=CHAINS, steps=STEPS, seed=seed, top_k=TOP_K, host_copy=True)
+        r = ctx.dock(gs, [lig], pockets, chains=CHAINS, steps=STEPS, seed=seed, top_k=TOP_K, host_copy=True,
+                     focc=focc)
         poses, kept, pots, xyz = r.fetch()
         rank = r.ranking(0)
         d2h = (poses.nbytes + kept.nbytes + pots.nbytes + xyz.nbytes + rank.nbytes)
