@@ -1105,8 +1105,9 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
         constexpr int kWarmSteps = 16, kTuneSteps = 32, kTuneBlock = 8;
         constexpr float kTuneMargin = 0.02f;
         // in order of preference: the first of a team width is the incumbent the others must beat by
-        // the margin (whole warps: variant 2 x 4 warps measured fastest on the multi-pocket workload)
-        static const int cand[][2] = {{2, 4}, {1, 4}, {0, 2}, {0, 4}, {0, 8}, {1, 2}, {2, 2}, {3, 4}, {0, 1},
+        // the margin (whole warps: variant 3 x 4 warps measured fastest on the multi-pocket workload,
+        // then variant 2 x 4)
+        static const int cand[][2] = {{3, 4}, {2, 4}, {1, 4}, {0, 2}, {0, 4}, {0, 8}, {1, 2}, {2, 2}, {0, 1},
                                       {4, 2}, {4, 1}, {4, 4}, {5, 2}, {5, 4}, {6, 4}, {7, 4}};
         cudaEvent_t t0, t1;
         cudaEventCreate(&t0);

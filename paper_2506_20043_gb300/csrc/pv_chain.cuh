@@ -231,6 +231,24 @@ struct WarpDockObjective {
     }
 };
 
+// The line search's base point, kept in shared memory across evaluations instead of registers.
+__device__ __forceinline__ void stash_state(WarpScratch& S, const Pose& x) {
+    const int tl = threadIdx.x & 31;
+    if (tl == 0) {
+        S.xb_tq[0] = make_float4(x.T.x, x.T.y, x.T.z, 0.f);
+        S.xb_tq[1] = x.q;
+    }
+    S.xb_psi[tl] = x.psi;
+}
+__device__ __forceinline__ void unstash_state(const WarpScratch& S, Pose& x) {
+    const float4 t = S.xb_tq[0];
+    x.T = make_float3(t.x, t.y, t.z);
+    x.q = S.xb_tq[1];
+    x.psi = S.xb_psi[threadIdx.x & 31];
+}
+__device__ __forceinline__ void stash_state(WarpScratch& S, const float& x) { S.xb_psi[threadIdx.x & 31] = x; }
+__device__ __forceinline__ void unstash_state(const WarpScratch& S, float& x) { x = S.xb_psi[threadIdx.x & 31]; }
+
 // RILC-BFGS (Eq. 6-12) of one whole-warp team from x (updated in place); returns the objective at
 // x and, in g_out, the lane's component of its gradient. One evaluation call site: the start
 // point, then every line-search trial. With a neighbour ring (FOCC, dock objective only), the start
@@ -253,18 +271,20 @@ __device__ __forceinline__ float warp_rilc_bfgs(const Obj& obj, WarpScratch& S, 
     float rh = 0.f, al = 0.f, g = 0.f, d = 0.f;
     bool start = true;
     State xt = x;
+    stash_state(S, x);
     for (;;) {
         float ge;
         const float fe = obj.eval(xt, ge);
         ++evals;
         float f = Q.f, gd = Q.gd, lam = Q.lam, lo = Q.lo, hi = Q.hi, flo = Q.flo;
         int it = Q.it, tr = Q.tr, stored = Q.stored, head = Q.head, have_lo = Q.have_lo;
-        bool next_iter = false, stop = false, retry = false;
+        bool next_iter = false, stop = false, retry = false, at_xt = false;
         if (start) {
             start = false;
+            at_xt = true;
             f = fe; g = ge; it = 0; stored = 0; head = 0;
             bool skip = false;
-            if constexpr (FOCC) skip = ring && !focc_pass<32>(x, fe, g, ring, Q.nb_n, n_rot, C.focc_min_delta);
+            if constexpr (FOCC) skip = ring && !focc_pass<32>(xt, fe, g, ring, Q.nb_n, n_rot, C.focc_min_delta);
             if (skip) stop = true;
             else next_iter = true;
         } else {
@@ -283,13 +303,17 @@ __device__ __forceinline__ float warp_rilc_bfgs(const Obj& obj, WarpScratch& S, 
                 ++tr;
                 if (tr < C.bfgs_max_trials) {
                     lam = hi < 0.f ? 2.f * lam : 0.5f * (lo + hi);
-                    xt = obj.retract(x, lam * d);
+                    State xb;
+                    unstash_state(S, xb);
+                    xt = obj.retract(xb, lam * d);
                     retry = true;
                 } else if (!have_lo) {
                     stop = true;                                // no acceptable step: stop at x
                 } else {
                     lam = lo; ft = flo; gt = S.glo[tl];
-                    xt = obj.retract(x, lam * d);               // the same arithmetic as that trial
+                    State xb;
+                    unstash_state(S, xb);
+                    xt = obj.retract(xb, lam * d);               // the same arithmetic as that trial
                     take = true;
                 }
             }
@@ -303,7 +327,10 @@ __device__ __forceinline__ float warp_rilc_bfgs(const Obj& obj, WarpScratch& S, 
                     head = head + 1 == m ? 0 : head + 1;
                     stored = min(stored + 1, m);
                 }
-                x = xt; g = gt; f = ft;
+                Tm::sync();                                     // every lane has read the old base
+                stash_state(S, xt);
+                at_xt = true;
+                g = gt; f = ft;
                 ++it;
                 if (sqrtf(Tm::sum(g * g)) <= C.eps) stop = true;
                 else next_iter = true;
@@ -319,11 +346,13 @@ __device__ __forceinline__ float warp_rilc_bfgs(const Obj& obj, WarpScratch& S, 
                     stop = true;
                 } else {
                     lam = 1.f; lo = 0.f; hi = -1.f; have_lo = 0; tr = 0;
-                    xt = obj.retract(x, lam * d);
+                    xt = obj.retract(xt, lam * d);
                 }
             }
         }
         if (stop) {
+            if (at_xt) x = xt;
+            else unstash_state(S, x);
             Tm::sync();
             g_out = g;
             return f;

@@ -46,7 +46,7 @@ static const VariantEntry kVariants[kSearchVariants] = {
     {(const void*)search_round_kernel<512, 1, 32, false, 0>, 512, 32},   // widest register budget
     {(const void*)search_round_kernel<128, 5, 32, false, 0>, 128, 32},
     {(const void*)search_round_kernel<128, 6, 32, false, 0>, 128, 32},
-    {(const void*)search_round_kernel<128, 8, 32, false, 0>, 128, 32},   // 64 registers
+    {(const void*)search_round_kernel<128, 7, 32, false, 0>, 128, 32},   // 72 registers
     {(const void*)search_round_kernel<512, 1, 16, false, 0>, 512, 16},   // two chains per warp
     {(const void*)search_round_kernel<128, 5, 16, false, 0>, 128, 16},
     {(const void*)search_round_kernel<128, 6, 16, false, 0>, 128, 16},

@@ -7,7 +7,7 @@ namespace pv {
 const void* search_focc_packed_kernel(int variant) {
     static const void* const kFns[kSearchVariants] = {
         (const void*)search_round_kernel<512, 1, 32, true, 1>, (const void*)search_round_kernel<128, 5, 32, true, 1>,
-        (const void*)search_round_kernel<128, 6, 32, true, 1>, (const void*)search_round_kernel<128, 8, 32, true, 1>,
+        (const void*)search_round_kernel<128, 6, 32, true, 1>, (const void*)search_round_kernel<128, 7, 32, true, 1>,
         (const void*)search_round_kernel<512, 1, 16, true, 1>, (const void*)search_round_kernel<128, 5, 16, true, 1>,
         (const void*)search_round_kernel<128, 6, 16, true, 1>, (const void*)search_round_kernel<128, 8, 16, true, 1>,
     };

@@ -8,7 +8,7 @@ namespace pv {
 const void* search_packed_kernel(int variant) {
     static const void* const kFns[kSearchVariants] = {
         (const void*)search_round_kernel<512, 1, 32, false, 1>, (const void*)search_round_kernel<128, 5, 32, false, 1>,
-        (const void*)search_round_kernel<128, 6, 32, false, 1>, (const void*)search_round_kernel<128, 8, 32, false, 1>,
+        (const void*)search_round_kernel<128, 6, 32, false, 1>, (const void*)search_round_kernel<128, 7, 32, false, 1>,
         (const void*)search_round_kernel<512, 1, 16, false, 1>, (const void*)search_round_kernel<128, 5, 16, false, 1>,
         (const void*)search_round_kernel<128, 6, 16, false, 1>, (const void*)search_round_kernel<128, 8, 16, false, 1>,
     };
