@@ -268,7 +268,17 @@ __device__ __forceinline__ float warp_rilc_bfgs(const Obj& obj, WarpScratch& S, 
     // after the evaluation's team barrier and stores them back before the next evaluation, so no
     // lane reads a slot another lane has already rewritten in the same iteration.
     ChainScalars& Q = S.cs;
-    float rh = 0.f, al = 0.f, g = 0.f, d = 0.f;
+    // The lane's gradient and direction components and its history entry's 1 / (y.s) live in
+    // lane-private shared slots, and the base point of the line search in shared memory too
+    // (stash_state): none of them is held in registers through an evaluation, which leaves the
+    // evaluation the registers of the capped variants without spilling.
+    float al = 0.f;
+    float& rh = S.lr[tl];
+    float& g = S.lg[tl];
+    float& d = S.ld[tl];
+    rh = 0.f;
+    g = 0.f;
+    d = 0.f;
     bool start = true;
     State xt = x;
     stash_state(S, x);

@@ -42,6 +42,9 @@ struct WarpScratch {            // one per team
     float hy[PV_MAX_M][32];     //                 y vectors
     float cur[40];              // the chain's current POT (MC state)
     float glo[32];              // line search: gradient at the largest Armijo-satisfying trial
+    float lg[32];               // line search: the lane's gradient component and search
+    float ld[32];               //              direction component (lane-private)
+    float lr[32];               // L-BFGS: 1 / (y.s) of history entry `lane` (lane-private)
     float4 xb_tq[2];            // line search: its base point (translation, orientation; torsions
     float xb_psi[32];           //              per lane), kept here across evaluations
     ChainScalars cs;
