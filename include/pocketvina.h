@@ -319,8 +319,8 @@ typedef struct {
  * three runs, per score evaluation the trial ran
  * (results are unaffected: the dock itself restarts every chain); a candidate displaces the first
  * one tried only when it is faster by more than 2 %, so that shapes within the trials' noise do not
- * alternate between runs. The chosen shape is then timed on the cell-packed maps too, with the same
- * margin. */
+ * alternate between runs. With map_layout -1 on a set holding both layouts, every candidate is timed
+ * on each layout (the cell-packed maps first), and the fastest (shape, layout) is kept. */
 void pv_dock_params_default(pv_dock_params* p);
 
 /* Docks every ligand into every listed pocket (Supplementary Algorithms 2 and 3). Pair

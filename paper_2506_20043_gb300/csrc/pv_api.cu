@@ -1179,31 +1179,32 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
             if (x == cudaSuccess && best < 1e30f) per_chain = best;
             return x;
         };
+        // Every shape on every layout the dock may read (the cell-packed maps first when the set
+        // holds both): the shapes rank differently on the two layouts (more resident CTAs put more
+        // pressure on L1, which the plain maps' four or more sectors per lookup feel most).
         float best_ms = -1.f;
-        int best_v = variant, best_w = W;
+        int best_v = variant, best_w = W, best_lay = layout;
         cudaError_t x = cudaSuccess;
         const bool tune_shape = p.search_variant < 0 || p.warps_per_cta == 0;
+        const int n_lay = tune_layout ? 2 : 1;
         for (const auto& cw : cand) {
-            if (!tune_shape) break;
             const int v = p.search_variant >= 0 ? p.search_variant : cw[0];
             const int wc = p.warps_per_cta > 0 ? p.warps_per_cta : cw[1];
             if (wc > search_variant_max_warps(v)) continue;
             const int lanes_c = search_variant_lanes(v);
             if (lanes_c == 16 && !all_team16) continue;
             if (p.search_variant < 0 && lanes_c != auto_lanes) continue;
-            float pc = 0.f;
-            x = trial(v, wc, layout, pc);
-            if (x != cudaSuccess) break;
-            if (pc < 0.f) continue;
-            if (best_ms < 0.f || pc < best_ms * (1.f - kTuneMargin)) { best_ms = pc; best_v = v; best_w = wc; }
+            for (int li = 0; li < n_lay && x == cudaSuccess; ++li) {
+                const int lay = tune_layout ? 1 - li : layout;
+                float pc = 0.f;
+                x = trial(v, wc, lay, pc);
+                if (x == cudaSuccess && pc > 0.f && (best_ms < 0.f || pc < best_ms * (1.f - kTuneMargin))) {
+                    best_ms = pc; best_v = v; best_w = wc; best_lay = lay;
+                }
+            }
+            if (x != cudaSuccess || !tune_shape) break;   // a fixed shape: only its layouts
         }
-        if (x == cudaSuccess && tune_layout) {
-            float plain_ms = best_ms, packed_ms = -1.f;
-            if (plain_ms < 0.f) x = trial(best_v, best_w, 0, plain_ms);
-            if (x == cudaSuccess) x = trial(best_v, best_w, 1, packed_ms);
-            if (x == cudaSuccess && packed_ms > 0.f && plain_ms > 0.f && packed_ms < plain_ms * (1.f - kTuneMargin))
-                layout = 1;
-        }
+        layout = best_lay;
         cudaEventDestroy(t0);
         cudaEventDestroy(t1);
         if (x != cudaSuccess) {
