@@ -1106,9 +1106,9 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
         constexpr float kTuneMargin = 0.02f;
         // in order of preference: the first of a team width is the incumbent the others must beat by
         // the margin (whole warps: variant 3 x 4 warps measured fastest on the multi-pocket workload,
-        // then variant 2 x 4)
+        // then variant 2 x 4; half warps: variant 5 x 4 on a 16-atom ligand over the same pockets)
         static const int cand[][2] = {{3, 4}, {2, 4}, {1, 4}, {0, 2}, {0, 4}, {0, 8}, {1, 2}, {2, 2}, {0, 1},
-                                      {4, 2}, {4, 1}, {4, 4}, {5, 2}, {5, 4}, {6, 4}, {7, 4}};
+                                      {5, 4}, {4, 2}, {4, 1}, {4, 4}, {5, 2}, {6, 4}, {7, 4}};
         cudaEvent_t t0, t1;
         cudaEventCreate(&t0);
         cudaEventCreate(&t1);

@@ -9,6 +9,29 @@
 
 namespace pv {
 
+// The line search's base point, kept in the team's scratch across evaluations instead of registers
+// (translation and orientation written by the team's first lane, torsions per lane).
+template <int LANES>
+__device__ __forceinline__ void stash_state(WarpScratch& S, const Pose& x) {
+    const int tl = Team<LANES>::lane();
+    if (tl == 0) {
+        S.xb_tq[0] = make_float4(x.T.x, x.T.y, x.T.z, 0.f);
+        S.xb_tq[1] = x.q;
+    }
+    S.xb_psi[tl] = x.psi;
+}
+template <int LANES>
+__device__ __forceinline__ void unstash_state(const WarpScratch& S, Pose& x) {
+    const float4 t = S.xb_tq[0];
+    x.T = make_float3(t.x, t.y, t.z);
+    x.q = S.xb_tq[1];
+    x.psi = S.xb_psi[Team<LANES>::lane()];
+}
+template <int LANES>
+__device__ __forceinline__ void stash_state(WarpScratch& S, const float& x) { S.xb_psi[Team<LANES>::lane()] = x; }
+template <int LANES>
+__device__ __forceinline__ void unstash_state(const WarpScratch& S, float& x) { x = S.xb_psi[Team<LANES>::lane()]; }
+
 // One chain of Algorithm 2 for MC steps [step0, step1), written as a single loop that evaluates
 // one pose per iteration (so a warp's teams stay converged at the evaluator): the random start
 // (a zero-iteration local search), then per step a mutation (Eq. 2) optimised by RILC-BFGS
@@ -35,10 +58,20 @@ __device__ __forceinline__ void run_chain(const SearchArgs& A, const PvLigBlob& 
     int s = step0, flags = 0;
     uint32_t evals = 0, evals_before = 0;
     float e_cur = 0.f, e_best = 0.f, u = 0.f;
-    // local-search state
-    Pose x, xt;
-    float f = 0.f, g = 0.f, d = 0.f, gd = 0.f, lam = 1.f, lo = 0.f, hi = -1.f, flo = 0.f, glo = 0.f;
-    float rh = 0.f, al = 0.f;
+    // local-search state; the base point of the line search (stash_state), the lane's gradient,
+    // direction, gradient at the largest Armijo-satisfying trial and history entry's 1 / (y.s) live
+    // in the team's scratch, not in registers through the evaluations
+    Pose xt;
+    float f = 0.f, gd = 0.f, lam = 1.f, lo = 0.f, hi = -1.f, flo = 0.f;
+    float al = 0.f;
+    float& g = S.lg[tl];
+    float& d = S.ld[tl];
+    float& rh = S.lr[tl];
+    float& glo = S.glo[tl];
+    g = 0.f;
+    d = 0.f;
+    rh = 0.f;
+    glo = 0.f;
     int it = 0, tr = 0, stored = 0, head = 0, iters = 0;
     bool have_lo = false, bstart = true;
     if (stage == kStart) {
@@ -69,13 +102,15 @@ __device__ __forceinline__ void run_chain(const SearchArgs& A, const PvLigBlob& 
         float ge;
         const float fe = team_eval<LANES, true, LAYOUT>(L, S, site, xt, ge, true);
         ++evals;
-        bool bdone = false, next_iter = false;
+        bool bdone = false, next_iter = false, at_xt = false;
         if (bstart) {                                   // the start point of a local search
             bstart = false;
-            x = xt; f = fe; g = ge;
+            stash_state<LANES>(S, xt);
+            at_xt = true;
+            f = fe; g = ge;
             it = 0; stored = 0; head = 0;
             // a mutated candidate that fails the consistency check (Eq. 4-5) is not optimised
-            if (FOCC && stage == kOptimise && !focc_pass<LANES>(x, f, g, ring, nb_n, n_rot, C.focc_min_delta))
+            if (FOCC && stage == kOptimise && !focc_pass<LANES>(xt, f, g, ring, nb_n, n_rot, C.focc_min_delta))
                 bdone = true;
             else
                 next_iter = true;
@@ -94,12 +129,16 @@ __device__ __forceinline__ void run_chain(const SearchArgs& A, const PvLigBlob& 
                 ++tr;
                 if (tr < C.bfgs_max_trials) {
                     lam = hi < 0.f ? 2.f * lam : 0.5f * (lo + hi);
-                    xt = team_retract<LANES>(x, lam * d, n_tan);
+                    Pose xb;
+                    unstash_state<LANES>(S, xb);
+                    xt = team_retract<LANES>(xb, lam * d, n_tan);
                     continue;
                 }
                 if (have_lo) {
                     lam = lo; ft = flo; gt = glo;
-                    xt = team_retract<LANES>(x, lam * d, n_tan);   // the same arithmetic as that trial
+                    Pose xb;
+                    unstash_state<LANES>(S, xb);
+                    xt = team_retract<LANES>(xb, lam * d, n_tan);  // the same arithmetic as that trial
                     take = true;
                 } else {
                     bdone = true;                               // no acceptable step: stop at x
@@ -116,7 +155,10 @@ __device__ __forceinline__ void run_chain(const SearchArgs& A, const PvLigBlob& 
                     head = head + 1 == m ? 0 : head + 1;
                     stored = min(stored + 1, m);
                 }
-                x = xt; g = gt; f = ft;
+                Tm::sync();                                     // every lane has read the old base
+                stash_state<LANES>(S, xt);
+                at_xt = true;
+                g = gt; f = ft;
                 ++it;
                 if (sqrtf(Tm::sum(g * g)) <= C.eps) bdone = true;
                 else next_iter = true;
@@ -132,12 +174,15 @@ __device__ __forceinline__ void run_chain(const SearchArgs& A, const PvLigBlob& 
                     bdone = true;
                 } else {
                     lam = 1.f; lo = 0.f; hi = -1.f; have_lo = false; tr = 0;
-                    xt = team_retract<LANES>(x, lam * d, n_tan);
+                    xt = team_retract<LANES>(xt, lam * d, n_tan);  // from the new base, xt itself
                 }
             }
         }
         if (!bdone) continue;
         // a local search ended at x with SF f: the MC decision
+        Pose x;
+        if (at_xt) x = xt;
+        else unstash_state<LANES>(S, x);
         if (stage == kStart) {
             e_cur = f;
             e_best = f;
@@ -231,23 +276,6 @@ struct WarpDockObjective {
     }
 };
 
-// The line search's base point, kept in shared memory across evaluations instead of registers.
-__device__ __forceinline__ void stash_state(WarpScratch& S, const Pose& x) {
-    const int tl = threadIdx.x & 31;
-    if (tl == 0) {
-        S.xb_tq[0] = make_float4(x.T.x, x.T.y, x.T.z, 0.f);
-        S.xb_tq[1] = x.q;
-    }
-    S.xb_psi[tl] = x.psi;
-}
-__device__ __forceinline__ void unstash_state(const WarpScratch& S, Pose& x) {
-    const float4 t = S.xb_tq[0];
-    x.T = make_float3(t.x, t.y, t.z);
-    x.q = S.xb_tq[1];
-    x.psi = S.xb_psi[threadIdx.x & 31];
-}
-__device__ __forceinline__ void stash_state(WarpScratch& S, const float& x) { S.xb_psi[threadIdx.x & 31] = x; }
-__device__ __forceinline__ void unstash_state(const WarpScratch& S, float& x) { x = S.xb_psi[threadIdx.x & 31]; }
 
 // RILC-BFGS (Eq. 6-12) of one whole-warp team from x (updated in place); returns the objective at
 // x and, in g_out, the lane's component of its gradient. One evaluation call site: the start
@@ -281,7 +309,7 @@ __device__ __forceinline__ float warp_rilc_bfgs(const Obj& obj, WarpScratch& S, 
     d = 0.f;
     bool start = true;
     State xt = x;
-    stash_state(S, x);
+    stash_state<32>(S, x);
     for (;;) {
         float ge;
         const float fe = obj.eval(xt, ge);
@@ -314,7 +342,7 @@ __device__ __forceinline__ float warp_rilc_bfgs(const Obj& obj, WarpScratch& S, 
                 if (tr < C.bfgs_max_trials) {
                     lam = hi < 0.f ? 2.f * lam : 0.5f * (lo + hi);
                     State xb;
-                    unstash_state(S, xb);
+                    unstash_state<32>(S, xb);
                     xt = obj.retract(xb, lam * d);
                     retry = true;
                 } else if (!have_lo) {
@@ -322,7 +350,7 @@ __device__ __forceinline__ float warp_rilc_bfgs(const Obj& obj, WarpScratch& S, 
                 } else {
                     lam = lo; ft = flo; gt = S.glo[tl];
                     State xb;
-                    unstash_state(S, xb);
+                    unstash_state<32>(S, xb);
                     xt = obj.retract(xb, lam * d);               // the same arithmetic as that trial
                     take = true;
                 }
@@ -338,7 +366,7 @@ __device__ __forceinline__ float warp_rilc_bfgs(const Obj& obj, WarpScratch& S, 
                     stored = min(stored + 1, m);
                 }
                 Tm::sync();                                     // every lane has read the old base
-                stash_state(S, xt);
+                stash_state<32>(S, xt);
                 at_xt = true;
                 g = gt; f = ft;
                 ++it;
@@ -362,7 +390,7 @@ __device__ __forceinline__ float warp_rilc_bfgs(const Obj& obj, WarpScratch& S, 
         }
         if (stop) {
             if (at_xt) x = xt;
-            else unstash_state(S, x);
+            else unstash_state<32>(S, x);
             Tm::sync();
             g_out = g;
             return f;
