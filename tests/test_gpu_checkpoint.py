@@ -35,12 +35,14 @@ def _same(a, b):
         assert np.array_equal(a.ranking(i), b.ranking(i))
 
 
-@pytest.mark.parametrize("mode,focc,resume_mode,spr", [
-    ("batched", 0, "batched", 0), ("batched", 4, "batched", 0), ("batched", 0, "batched", 7),
-    ("batched", 0, "plain_warp", 0), ("plain", 0, "plain", 0)])
-def test_resumed_dock_repeats_the_unbroken_one(site, mode, focc, resume_mode, spr):
+@pytest.mark.parametrize("mode,focc,resume_mode,spr,variant", [
+    ("batched", 0, "batched", 0, 1), ("batched", 4, "batched", 0, 1), ("batched", 0, "batched", 7, 1),
+    ("batched", 0, "plain_warp", 0, 1), ("plain", 0, "plain", 0, 1), ("batched", 0, "batched", 0, 5),
+    ("batched", 4, "batched", 0, 5)])
+def test_resumed_dock_repeats_the_unbroken_one(site, mode, focc, resume_mode, spr, variant):
+    """variant 1: a chain per warp; variant 5: a chain per half warp (the flattened chain loop)."""
     ctx, gs, ligs = site
-    kw = dict(chains=48, seed=11, focc=focc, search_variant=1, warps_per_cta=2, map_layout=0)
+    kw = dict(chains=48, seed=11, focc=focc, search_variant=variant, warps_per_cta=2, map_layout=0)
     if mode == "plain":
         kw = dict(chains=48, seed=11)
     full = ctx.dock(gs, ligs, [0, 1], steps=40, mode=mode, **kw)
