@@ -187,7 +187,9 @@ pv_status pv_ligand_xs_types(const pv_ligand* lig, uint8_t* out);
  * tangent coordinates the optimiser uses: translation, rotation vector applied in the world
  * frame about the origin atom, torsions. dev_parts (nullable): [n_poses][2] = e_inter, e_intra.
  * Atoms outside the grid are interpolated at the clamped point plus 10 kcal/mol/A times the
- * distance outside. One warp per pose. */
+ * distance outside. One warp per pose. pv_score, pv_score_backward and pv_score_xyz read the
+ * cell-packed maps when the set holds them (pv_grid_set_pack), else the plain ones: the same
+ * corner values and arithmetic, so the same results. */
 pv_status pv_score(pv_context* ctx, const pv_grid_set* set, const pv_ligand* lig, int32_t pocket,
                    int32_t n_poses, const float* dev_pose, float* dev_energy, float* dev_grad,
                    float* dev_parts);

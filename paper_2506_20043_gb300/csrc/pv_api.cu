@@ -661,7 +661,7 @@ extern "C" pv_status pv_score(pv_context* ctx, const pv_grid_set* set, const pv_
     DeviceGuard g(ctx->device);
     PV_CU(ctx, launch_score((const PvLigBlob*)lig->d_blob, lig->rec.staged32, set->d_pockets + pocket,
                             slots_of(set), n_poses, 7 + lig->rec.n_rot, dev_pose, dev_energy, dev_grad, dev_parts,
-                            nullptr, nullptr, nullptr, ctx->stream));
+                            nullptr, nullptr, nullptr, set->packed ? 1 : 0, ctx->stream));
     return PV_OK;
 }
 
@@ -677,7 +677,7 @@ extern "C" pv_status pv_score_backward(pv_context* ctx, const pv_grid_set* set, 
     DeviceGuard g(ctx->device);
     PV_CU(ctx, launch_score((const PvLigBlob*)lig->d_blob, lig->rec.staged32, set->d_pockets + pocket,
                             slots_of(set), n_poses, 7 + lig->rec.n_rot, dev_pose, nullptr, nullptr, nullptr,
-                            dev_grad_energy, dev_grad_pose, dev_grad_xyz, ctx->stream));
+                            dev_grad_energy, dev_grad_pose, dev_grad_xyz, set->packed ? 1 : 0, ctx->stream));
     return PV_OK;
 }
 
@@ -692,7 +692,7 @@ extern "C" pv_status pv_score_xyz(pv_context* ctx, const pv_grid_set* set, const
     DeviceGuard g(ctx->device);
     PV_CU(ctx, launch_score_xyz((const PvLigBlob*)lig->d_blob, lig->rec.staged32, set->d_pockets + pocket,
                                 slots_of(set), n_poses, dev_xyz, dev_grad_energy, dev_energy, dev_grad_xyz,
-                                ctx->stream));
+                                set->packed ? 1 : 0, ctx->stream));
     return PV_OK;
 }
 

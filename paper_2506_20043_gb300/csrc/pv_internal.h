@@ -51,17 +51,18 @@ cudaError_t launch_pack_cells(const PvPocket* pockets_dev, const PvPocket* pocke
                               int n_maps, cudaStream_t s);
 
 // ---- scoring (pv_score.cu) ----
-// pocket: device pointer to the pocket record (its maps pointer included)
+// pocket: device pointer to the pocket record (its maps pointers included); layout: the maps read,
+// 0 plain, 1 cell-packed (the pocket must hold them)
 cudaError_t launch_score(const PvLigBlob* lig, int lig_bytes, const PvPocket* pocket,
                          PvSlots slots, int n_poses, int pot_stride,
                          const float* pose, float* energy, float* grad, float* parts,
                          const float* grad_energy, float* grad_pose, float* grad_xyz,
-                         cudaStream_t s);
+                         int layout, cudaStream_t s);
 // SF of posed atom coordinates [n][n_atoms][3] (input order); energy and grad_xyz nullable,
 // grad_xyz scaled by grad_energy (nullable: 1).
 cudaError_t launch_score_xyz(const PvLigBlob* lig, int lig_bytes, const PvPocket* pocket, PvSlots slots,
                              int n_poses, const float* xyz, const float* grad_energy, float* energy,
-                             float* grad_xyz, cudaStream_t s);
+                             float* grad_xyz, int layout, cudaStream_t s);
 cudaError_t launch_pose_coords(const PvLigBlob* lig, int lig_bytes, int n_poses, int pot_stride,
                                const float* pose, float* xyz, cudaStream_t s);
 

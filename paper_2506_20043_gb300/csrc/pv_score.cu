@@ -36,6 +36,7 @@ __device__ __forceinline__ Pose read_pose(const float* p, int n_rot) {
     return x;
 }
 
+template <int LAYOUT>
 __global__ void __launch_bounds__(kScoreWarps * 32) score_kernel(ScoreArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     PvLigBlob& L = *reinterpret_cast<PvLigBlob*>(smem);
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(kScoreWarps * 32) score_kernel(ScoreArgs A) {
         }
         const bool want_grad = A.grad || A.grad_pose || A.grad_xyz;
         float g = 0.f, parts[2];
-        const float e = warp_eval(L, S, site, x, g, want_grad, parts);
+        const float e = warp_eval<LAYOUT>(L, S, site, x, g, want_grad, parts);
         if (A.energy && lane == 0) A.energy[i] = e;
         if (A.parts && lane == 0) { A.parts[2 * i] = parts[0]; A.parts[2 * i + 1] = parts[1]; }
         if (A.grad && lane < nt) A.grad[(size_t)i * nt + lane] = g;
@@ -103,27 +104,29 @@ __global__ void __launch_bounds__(kScoreWarps * 32) score_kernel(ScoreArgs A) {
     }
 }
 
-static cudaError_t launch(const ScoreArgs& a, cudaStream_t s) {
+static cudaError_t launch(const ScoreArgs& a, int layout, cudaStream_t s) {
     const int smem = ((a.lig_bytes + 127) & ~127) + kScoreWarps * (int)sizeof(WarpScratch);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    static int configured[64];
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (smem > configured[dev]) {
-        e = cudaFuncSetAttribute(score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    static int configured[2][64];
+    if (dev < 0 || dev >= 64 || layout < 0 || layout > 1) return cudaErrorInvalidValue;
+    const void* fn = layout == 1 ? (const void*)score_kernel<1> : (const void*)score_kernel<0>;
+    if (smem > configured[layout][dev]) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        configured[dev] = smem;
+        configured[layout][dev] = smem;
     }
     int sms = 0, occ = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, score_kernel, kScoreWarps * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kScoreWarps * 32, smem);
     if (e != cudaSuccess) return e;
     int need = (a.n_poses + kScoreWarps - 1) / kScoreWarps;
     int grid = sms * (occ > 0 ? occ : 1);
     if (need < grid) grid = need;
     if (grid < 1) return cudaSuccess;
-    score_kernel<<<grid, kScoreWarps * 32, smem, s>>>(a);
+    if (layout == 1) score_kernel<1><<<grid, kScoreWarps * 32, smem, s>>>(a);
+    else score_kernel<0><<<grid, kScoreWarps * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -131,7 +134,7 @@ cudaError_t launch_score(const PvLigBlob* lig, int lig_bytes, const PvPocket* po
                          PvSlots slots, int n_poses, int pot_stride,
                          const float* pose, float* energy, float* grad, float* parts,
                          const float* grad_energy, float* grad_pose, float* grad_xyz,
-                         cudaStream_t s) {
+                         int layout, cudaStream_t s) {
     ScoreArgs a{};
     a.lig = lig; a.lig_bytes = lig_bytes; a.pocket = pocket;
     uint64_t lo = 0, hi = 0;
@@ -143,7 +146,7 @@ cudaError_t launch_score(const PvLigBlob* lig, int lig_bytes, const PvPocket* po
     a.n_poses = n_poses; a.pot_stride = pot_stride; a.pose = pose;
     a.energy = energy; a.grad = grad; a.parts = parts;
     a.grad_energy = grad_energy; a.grad_pose = grad_pose; a.grad_xyz = grad_xyz;
-    return launch(a, s);
+    return launch(a, layout, s);
 }
 
 // SF of posed ligands given by their atom coordinates (input order), one warp per ligand: the atoms
@@ -161,6 +164,7 @@ struct ScoreXyzArgs {
     float* grad_xyz;            // nullable
 };
 
+template <int LAYOUT>
 __global__ void __launch_bounds__(kScoreWarps * 32) score_xyz_kernel(ScoreXyzArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     PvLigBlob& L = *reinterpret_cast<PvLigBlob*>(smem);
@@ -185,7 +189,7 @@ __global__ void __launch_bounds__(kScoreWarps * 32) score_xyz_kernel(ScoreXyzArg
         }
         __syncwarp();
         float g = 0.f;
-        const float e = team_eval<32, false>(L, S, site, none, g, false);
+        const float e = team_eval<32, false, LAYOUT>(L, S, site, none, g, false);
         if (A.energy && lane == 0) A.energy[i] = e;
         if (A.grad_xyz) {
             const float s = A.grad_energy ? A.grad_energy[i] : 1.f;
@@ -201,7 +205,7 @@ __global__ void __launch_bounds__(kScoreWarps * 32) score_xyz_kernel(ScoreXyzArg
 
 cudaError_t launch_score_xyz(const PvLigBlob* lig, int lig_bytes, const PvPocket* pocket, PvSlots slots,
                              int n_poses, const float* xyz, const float* grad_energy, float* energy,
-                             float* grad_xyz, cudaStream_t s) {
+                             float* grad_xyz, int layout, cudaStream_t s) {
     ScoreXyzArgs a{};
     a.lig = lig; a.lig_bytes = lig_bytes; a.pocket = pocket;
     uint64_t lo = 0, hi = 0;
@@ -215,21 +219,23 @@ cudaError_t launch_score_xyz(const PvLigBlob* lig, int lig_bytes, const PvPocket
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    static int configured[64];
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (smem > configured[dev]) {
-        e = cudaFuncSetAttribute(score_xyz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    static int configured[2][64];
+    if (dev < 0 || dev >= 64 || layout < 0 || layout > 1) return cudaErrorInvalidValue;
+    const void* fn = layout == 1 ? (const void*)score_xyz_kernel<1> : (const void*)score_xyz_kernel<0>;
+    if (smem > configured[layout][dev]) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        configured[dev] = smem;
+        configured[layout][dev] = smem;
     }
     int sms = 0, occ = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, score_xyz_kernel, kScoreWarps * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kScoreWarps * 32, smem);
     if (e != cudaSuccess) return e;
     const int need = (n_poses + kScoreWarps - 1) / kScoreWarps;
     const int grid = std::min(need, sms * (occ > 0 ? occ : 1));
     if (grid < 1) return cudaSuccess;
-    score_xyz_kernel<<<grid, kScoreWarps * 32, smem, s>>>(a);
+    if (layout == 1) score_xyz_kernel<1><<<grid, kScoreWarps * 32, smem, s>>>(a);
+    else score_xyz_kernel<0><<<grid, kScoreWarps * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -238,7 +244,7 @@ cudaError_t launch_pose_coords(const PvLigBlob* lig, int lig_bytes, int n_poses,
     ScoreArgs a{};
     a.lig = lig; a.lig_bytes = lig_bytes; a.n_poses = n_poses; a.pot_stride = pot_stride;
     a.pose = pose; a.fk_only = 1; a.xyz = xyz;
-    return launch(a, s);
+    return launch(a, 0, s);
 }
 
 }  // namespace pv

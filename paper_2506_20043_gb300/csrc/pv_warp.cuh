@@ -580,11 +580,13 @@ __device__ __forceinline__ void focc_push(float* ring, const Pose& x, float f, f
     Tm::sync();
 }
 
-// Whole-warp names used by the selection and scoring kernels.
+// Whole-warp names used by the selection and scoring kernels (LAYOUT: the maps read, 0 plain, 1
+// cell-packed; the same corners and arithmetic either way).
+template <int LAYOUT = 0>
 static __device__ __forceinline__ float warp_eval(const PvLigBlob& L, WarpScratch& S, const Site& site,
                                                   const Pose& x, float& grad, bool want_grad,
                                                   float* parts = nullptr) {
-    return team_eval<32>(L, S, site, x, grad, want_grad, parts);
+    return team_eval<32, true, LAYOUT>(L, S, site, x, grad, want_grad, parts);
 }
 __device__ __forceinline__ void warp_fk(const PvLigBlob& L, WarpScratch& S, const Pose& x, float3& axw, float3& xa) {
     team_fk<32>(L, S, x, axw, xa);

@@ -72,3 +72,25 @@ def test_gather_probe_on_both_layouts(site):
     for layout in (0, 1):
         ms, pts, gbs = ctx.measure_gather(gs, -1, n_points=1 << 20, reps=3, layout=layout)
         assert ms > 0 and gbs > 0
+
+
+def test_scoring_reads_the_packed_maps_with_the_same_bits(site):
+    """pv_score, pv_score_backward and pv_score_xyz read the cell-packed maps once the set holds
+    them: the same energies, gradients and coordinate gradients, bit for bit, as from the plain
+    maps (which tests/test_gpu_score.py checks against the oracle)."""
+    import torch
+    ctx, rec, boxes, lig, small, types = site
+    gs = ctx.build_grids(rec, boxes[:2], types)
+    poses = torch.tensor(S.random_poses(3000, boxes[1], lig.n_rot, 77), device="cuda")
+    xyz = ctx.pose_coords(lig, poses)
+    ge = torch.linspace(-1.0, 2.0, poses.shape[0], device="cuda")
+    out = []
+    for packed in (False, True):
+        if packed:
+            gs.pack()
+        e, g, parts = ctx.score(gs, lig, 1, poses, grad=True, parts=True)
+        gp, gx = ctx.score_backward(gs, lig, 1, poses, ge, want_pose=True, want_xyz=True)
+        ex, gxx = ctx.score_xyz(gs, lig, 1, xyz, grad=True)
+        out.append([t.cpu().numpy() for t in (e, g, parts, gp, gx, ex, gxx)])
+    for a, b in zip(*out):
+        np.testing.assert_array_equal(a, b)
