@@ -119,13 +119,41 @@ DOCK_SOURCES = ("pv_api.cu", "pv_chain.cuh", "pv_device.cuh", "pv_grid.cu", "pv_
                 "pv_stage.cuh", "pv_terms.h", "pv_thread.cuh", "pv_warp.cuh")
 
 
+def _code_only(text: str, hash_comment: str) -> str:
+    """The source without its comments (C/C++ `//` and `/* */`, or the given line-comment marker
+    for Python) and with runs of whitespace collapsed; string and character literals are kept."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":                                    # a literal: copied through its closing quote
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith(hash_comment, i):
+            while i < n and text[i] != "\n":
+                i += 1
+        elif hash_comment == "//" and text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_source_hash() -> str:
-    """Hash of the dock path's sources and of the build script (its compiler flags shape the code)."""
+    """Hash of the code (comments and layout left out) of the dock path's sources and of the build
+    script (its compiler flags shape the code): a stored profile stays valid while none of them
+    changes."""
     d = os.path.join(ROOT, "paper_2506_20043_gb300", "csrc")
     h = hashlib.sha256()
     for f in sorted(DOCK_SOURCES):
-        h.update(open(os.path.join(d, f), "rb").read())
-    h.update(open(os.path.join(ROOT, "paper_2506_20043_gb300", "build.py"), "rb").read())
+        h.update(_code_only(open(os.path.join(d, f), encoding="utf-8").read(), "//").encode())
+    h.update(_code_only(open(os.path.join(ROOT, "paper_2506_20043_gb300", "build.py"), encoding="utf-8").read(),
+                        "#").encode())
     return h.hexdigest()[:16]
 
 

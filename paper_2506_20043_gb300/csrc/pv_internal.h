@@ -100,7 +100,8 @@ struct SearchArgs {
 int search_smem_bytes(int lig_bytes, int warps, int lanes);
 // Variants of the round kernel: 0-3 run a chain per warp, 4-7 a chain per half warp (ligands of
 // at most 32 atoms and 10 torsions); within each group the launch bounds (max threads per CTA,
-// min CTAs per SM) are (512, 1), (128, 5), (128, 6), (128, 8), i.e. decreasing register budgets.
+// min CTAs per SM) are (512, 1), (128, 5), (128, 6), (128, 7) for a chain per warp and (512, 1),
+// (128, 5), (128, 6), (128, 8) for a chain per half warp, i.e. decreasing register budgets.
 constexpr int kSearchVariants = 8;
 int search_variant_max_warps(int variant);
 int search_variant_lanes(int variant);
