@@ -1105,10 +1105,15 @@ static pv_status dock_impl(pv_context* ctx, const pv_grid_set* set, pv_ligand* c
         constexpr int kWarmSteps = 16, kTuneSteps = 32, kTuneBlock = 8;
         constexpr float kTuneMargin = 0.02f;
         // in order of preference: the first of a team width is the incumbent the others must beat by
-        // the margin (whole warps: variant 3 x 4 warps measured fastest on the multi-pocket workload,
-        // then variant 2 x 4; half warps: variant 5 x 4 on a 16-atom ligand over the same pockets)
-        static const int cand[][2] = {{3, 4}, {2, 4}, {1, 4}, {0, 2}, {0, 4}, {0, 8}, {1, 2}, {2, 2}, {0, 1},
-                                      {5, 4}, {4, 2}, {4, 1}, {4, 4}, {5, 2}, {6, 4}, {7, 4}};
+        // the margin (whole warps: variant 3 x 4 warps measured fastest on the multi-pocket workload
+        // of 30-atom ligands, then variant 2 x 4, and variant 1 x 4 on batches with ligands of more
+        // than 32 atoms, two per lane, whose evaluation needs more registers; half warps: variant
+        // 5 x 4 on a 16-atom ligand over the same pockets)
+        static const int cand_small[][2] = {{3, 4}, {2, 4}, {1, 4}, {0, 2}, {0, 4}, {0, 8}, {1, 2}, {2, 2}, {0, 1},
+                                            {5, 4}, {4, 2}, {4, 1}, {4, 4}, {5, 2}, {6, 4}, {7, 4}};
+        static const int cand_large[][2] = {{1, 4}, {3, 4}, {2, 4}, {0, 2}, {0, 4}, {0, 8}, {1, 2}, {2, 2}, {0, 1},
+                                            {5, 4}, {4, 2}, {4, 1}, {4, 4}, {5, 2}, {6, 4}, {7, 4}};
+        const auto& cand = max_atoms > 32 ? cand_large : cand_small;
         cudaEvent_t t0, t1;
         cudaEventCreate(&t0);
         cudaEventCreate(&t1);
